@@ -1,0 +1,255 @@
+/*
+ * rcfar.h -- C ABI of the GB300 radar chain library (librcfar.so).
+ *
+ * The library computes the data path of Rohman, Andra and Nishimoto,
+ * "Optimized 2D CA-CFAR for Drone-Mounted Radar Signal Processing Using
+ * Integral Image Algorithm":
+ *   Sec. II.A  fast-time DC-shift removal + linear-trend subtraction, slow-time
+ *              mean filter + normalisation, slow-time transform restricted to
+ *              the 0.3-0.8 Hz respiration band, magnitude  -> band map P
+ *   Sec. II.B  summed-area table of P (eq. 3), 2D cell-averaging CFAR whose
+ *              reference sum comes from four-corner lookups (eq. 4) of an
+ *              outer rectangle minus a guard rectangle, threshold T = alpha*A
+ *              (eq. 2) and the H0/H1 decision of eq. 1.
+ *
+ * Conventions shared by every entry point
+ *   - Every function returns rcfar_status and never throws.
+ *   - Pointers named x, map, det, thr, view fields and frame fields are DEVICE
+ *     pointers owned by the caller, unless stated otherwise; the library owns
+ *     only the workspace inside its handle. Arrays are row-major with the
+ *     stated leading dimension (in elements).
+ *   - A raw frame X is [M][ldx] float32: row m = fast-time sample (range bin),
+ *     column n = slow-time sample (trace), N <= ldx. (Sec. II.A, X in R^{MxN}.)
+ *   - Work is enqueued on the given stream (a cudaStream_t; NULL = legacy
+ *     default stream) and returns before it completes. Asynchronous faults that
+ *     kernels detect (a value outside the stated bound, an expired bounded wait)
+ *     are recorded in a device status word and reported by rcfar_get_error.
+ *   - A handle serves one stream at a time: calls on one handle must not run
+ *     concurrently on different streams. Create one handle per stream instead.
+ *   - Interpretation choices where the paper is silent (band edges, window
+ *     semantics, edge policy, eq. 2's exponent sign, CUT == T) are documented
+ *     at the function that applies them.
+ */
+#ifndef RCFAR_H
+#define RCFAR_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum rcfar_status {
+  RCFAR_OK = 0,
+  RCFAR_ERR_INVALID_ARG = 1,      /* null pointer, size <= 0, even mean filter, pfa not in (0,1), ... */
+  RCFAR_ERR_UNSUPPORTED = 2,      /* size beyond the handle's create-time limits */
+  RCFAR_ERR_OUT_OF_WORKSPACE = 3, /* a batch needs more workspace than the handle holds */
+  RCFAR_ERR_CUDA = 4,             /* a CUDA runtime call failed */
+  RCFAR_ERR_TIMEOUT = 5,          /* a bounded device-side wait expired (results invalid) */
+  RCFAR_ERR_BAD_STATE = 6,        /* stale view, wrong handle, destroyed handle */
+  RCFAR_ERR_RANGE = 7             /* a map value exceeded the stated bound or was NaN (results invalid) */
+} rcfar_status;
+
+typedef struct rcfar_ctx* rcfar_handle;
+typedef void* rcfar_stream; /* cudaStream_t */
+
+/* Storage type of a CFAR input map. */
+typedef enum rcfar_map_dtype {
+  RCFAR_MAP_F32 = 0,
+  RCFAR_MAP_F16 = 1 /* IEEE half; value = stored * 2^map_exp2 */
+} rcfar_map_dtype;
+
+/* How the summed-area table is stored (paper eq. 3).
+ *  TILE_F32 : per 32x128 tile, an FP32 table relative to the tile's origin,
+ *             plus exact 64-bit fixed-point carries along each tile row band
+ *             (global table on the row above the band) and each tile column
+ *             (band-local sums left of the tile). 4 bytes per cell.
+ *  I64      : the global table itself in 64-bit fixed point (exact for the
+ *             quantised map; 8 bytes per cell).
+ *  NAIVE_F32: the global table in plain FP32 (for contrast only: large maps
+ *             lose the reference sums to cancellation).
+ * Fixed-point values are round(x * 2^scale_log2) and are added modulo 2^64,
+ * so every region sum that fits in 63 bits is exact even where the table
+ * itself wraps. */
+typedef enum rcfar_sat_mode {
+  RCFAR_SAT_TILE_F32 = 0,
+  RCFAR_SAT_I64 = 1,
+  RCFAR_SAT_NAIVE_F32 = 2
+} rcfar_sat_mode;
+
+typedef struct rcfar_config {
+  int32_t device;        /* CUDA device ordinal */
+  int32_t max_rows;      /* largest M (frame) / map row count */
+  int32_t max_cols;      /* largest map column count (band bins incl. halo) */
+  int32_t max_n;         /* largest slow-time length N */
+  int32_t max_window;    /* largest per-side half-width guard + training */
+  int32_t max_frames;    /* largest number of frames in one rcfar_run_batch */
+  int64_t batch_bytes;   /* device workspace reserved for rcfar_run_batch (0: none) */
+} rcfar_config;
+
+/* Preprocessing parameters (Sec. II.A). */
+typedef struct rcfar_pre_params {
+  double fs_hz;     /* slow-time sampling rate (traces per second) */
+  double f_lo_hz;   /* respiration band, inclusive: 0.3 in the paper */
+  double f_hi_hz;   /* 0.8 in the paper */
+  int32_t mean_len; /* odd mean-filter length along slow time (e.g. 5) */
+  int32_t halo_c;   /* extra bins stored each side of the band (use the CFAR's guard_c + train_c);
+                       rcfar_run_batch: -1 = each frame uses its own window's guard_c + train_c */
+} rcfar_pre_params;
+
+/* Spectral bins of a band map: map column j holds bin k = c0 + j. */
+typedef struct rcfar_band {
+  int32_t k_lo, k_hi; /* respiration band bins (CUT columns are k_lo-c0 .. k_hi-c0) */
+  int32_t c0, c1;     /* first and last stored bin, clipped to [0, N/2] */
+  int32_t cols;       /* c1 - c0 + 1 */
+  float value_bound;  /* every normalised map value is <= this (= N) */
+} rcfar_band;
+
+/* CFAR window (Sec. II.B): per-side counts in each dimension. The guard
+ * rectangle [r-guard_r, r+guard_r] x [c-guard_c, c+guard_c] contains the CUT;
+ * training cells fill the ring out to half-sizes guard+train. */
+typedef struct rcfar_window {
+  int32_t train_r, train_c;
+  int32_t guard_r, guard_c;
+  double pfa; /* false-alarm probability, 0 < pfa < 1 */
+} rcfar_window;
+
+/* Description of a summed-area table produced by rcfar_sat. The arrays live
+ * in the handle's workspace and stay valid until the next rcfar_sat or
+ * rcfar_run_batch on the same handle. */
+typedef struct rcfar_sat_view {
+  int32_t rows, cols;
+  int32_t mode;          /* rcfar_sat_mode */
+  int32_t tile_h, tile_w;
+  int32_t scale_log2;    /* fixed-point scale s (TILE_F32, I64) */
+  void* table;           /* TILE_F32/NAIVE_F32: float [rows][ld]; I64: int64 [rows][ld] */
+  int64_t ld;
+  int64_t* row_carry;    /* TILE_F32: [rows/tile_h][ld_carry]: global table on each band's last row */
+  int64_t* col_carry;    /* TILE_F32: [cols/tile_w][rows]: band-local sums left of each tile column */
+  int64_t ld_carry;
+  uint64_t generation;   /* handle-side stamp; a stale view is rejected */
+} rcfar_sat_view;
+
+/* One frame of a batch: raw frame in, decisions (and optionally the map and
+ * thresholds) out. det is [M][ld_det] with band.cols columns. */
+typedef struct rcfar_frame_desc {
+  const float* x;
+  int32_t M, N;
+  int64_t ldx;
+  rcfar_window window;
+  uint8_t* det;
+  int64_t ld_det;
+  float* thr;      /* optional (NULL): threshold T at CUTs, 0 elsewhere */
+  int64_t ld_thr;
+  float* map;      /* optional (NULL): normalised band map P */
+  int64_t ld_map;
+} rcfar_frame_desc;
+
+/* ---- handle ------------------------------------------------------------ */
+
+/* Allocates the workspace for the limits in cfg on cfg->device. */
+rcfar_status rcfar_create(const rcfar_config* cfg, rcfar_handle* out);
+/* Waits for the handle's device work to finish and frees it. */
+rcfar_status rcfar_destroy(rcfar_handle h);
+
+/* ---- host-only helpers (no GPU needed) -------------------------------- */
+
+/* eq. 2 with the exponent's sign corrected (the printed alpha = N(Pfa^{1/N}-1)
+ * is negative for Pfa < 1): alpha = n_ref * (pfa^(-1/n_ref) - 1), exact for a
+ * cell-averaging CFAR on iid exponential (square-law) noise. */
+rcfar_status rcfar_alpha(int32_t n_ref, double pfa, double* alpha_out);
+/* n_ref = (2(g_r+t_r)+1)(2(g_c+t_c)+1) - (2g_r+1)(2g_c+1) (Sec. II.B "N"). */
+rcfar_status rcfar_n_ref(const rcfar_window* w, int32_t* n_ref_out);
+/* Respiration band of a length-N slow-time transform (Sec. II.A, 0.3-0.8 Hz):
+ * k_lo = ceil(f_lo N / fs), k_hi = floor(f_hi N / fs) (inclusive; values
+ * within 1e-9 of an integer count as that integer), c0 = max(0, k_lo - halo_c),
+ * c1 = min(N/2, k_hi + halo_c). An empty stored range (c1 < c0) is
+ * RCFAR_ERR_INVALID_ARG; an empty band with a non-empty halo is valid and
+ * has no CUT columns. */
+rcfar_status rcfar_band_plan(int32_t N, const rcfar_pre_params* p, rcfar_band* out);
+/* Fixed-point scale chosen for a map with |values| <= bound whose largest
+ * region sum spans at most max_cells cells. */
+rcfar_status rcfar_sat_scale(float bound, int64_t max_cells, int32_t* scale_log2_out);
+const char* rcfar_status_string(rcfar_status s);
+
+/* ---- the per-step path ------------------------------------------------- */
+
+/* Sec. II.A: raw frame x [M][ldx] -> normalised band map [M][ld_map] with
+ * band_out->cols columns. Steps, all on the GPU:
+ *   x'[m,n] = x[m,n] - a_n - b_n (m - (M-1)/2)      (per-trace LS line over m)
+ *   y[m,n]  = mean of x'[m, n-h..n+h] inside [0,N)   (h = (mean_len-1)/2)
+ *   y      /= max |y| over the frame                  (unchanged if 0)
+ *   P[m,j]  = | sum_n y[m,n] exp(-2 pi i (c0+j) n / N) |
+ * band_out (host pointer, may be NULL) receives the bins used. The first call
+ * for a new (N, band) builds its twiddle table (one allocation). */
+rcfar_status rcfar_preprocess(rcfar_handle h, const float* x, int32_t M, int32_t N, int64_t ldx,
+                              const rcfar_pre_params* p, float* map, int64_t ld_map,
+                              rcfar_band* band_out, rcfar_stream stream);
+
+/* eq. 3: summed-area table of map [rows][ld] (dtype; F16 values are
+ * stored * 2^map_exp2) in the given mode. value_bound > 0 is an upper bound
+ * on |value| supplied by the caller (rcfar_preprocess's band.value_bound for
+ * its maps); value_bound <= 0 makes the library measure max |value| first
+ * (one extra read of the map). Values above the bound, and NaNs, raise
+ * RCFAR_ERR_RANGE at rcfar_get_error. view_out (host pointer) describes the
+ * table, which lives in the handle's workspace. */
+rcfar_status rcfar_sat(rcfar_handle h, const void* map, int32_t dtype, int32_t map_exp2, int32_t rows,
+                       int32_t cols, int64_t ld, float value_bound, int32_t mode,
+                       rcfar_sat_view* view_out, rcfar_stream stream);
+
+/* eqs. 1, 2, 4: 2D CA-CFAR on a table from rcfar_sat and its map. For every
+ * interior CUT (outer rectangle inside the map) whose column lies in
+ * [cut_c_lo, cut_c_hi]: S_ref = A(outer) - A(guard), each region sum from four
+ * table lookups A = L1 + L4 - (L2 + L3); T = alpha * S_ref / n_ref;
+ * det = 1 (H1) iff CUT > T (CUT == T decides H0). Every other cell gets
+ * det = 0 and thr = 0. det is uint8 [rows][ld_det]; thr (optional, NULL) is
+ * float [rows][ld_thr]. Zero interior CUTs is valid (all-zero det). */
+rcfar_status rcfar_cfar(rcfar_handle h, const rcfar_sat_view* view, const void* map, int32_t dtype,
+                        int32_t map_exp2, int64_t ld_map, const rcfar_window* w, int32_t cut_c_lo,
+                        int32_t cut_c_hi, uint8_t* det, int64_t ld_det, float* thr, int64_t ld_thr,
+                        rcfar_stream stream);
+
+/* The same decisions with S_ref summed cell by cell over the n_ref training
+ * cells (the sliding-window CA-CFAR that the SAT replaces; Sec. III, Table I
+ * "CA-CFAR"). map is float32 [rows][ld_map]. */
+rcfar_status rcfar_cfar_direct(rcfar_handle h, const float* map, int32_t rows, int32_t cols,
+                               int64_t ld_map, const rcfar_window* w, int32_t cut_c_lo,
+                               int32_t cut_c_hi, uint8_t* det, int64_t ld_det, float* thr,
+                               int64_t ld_thr, rcfar_stream stream);
+
+/* Writes the table's values S(r, c) as float64 [rows][ld_out] (testing and
+ * error studies; S = local + carries * 2^-scale, exact unless the table
+ * wrapped modulo 2^64). */
+rcfar_status rcfar_sat_materialize(rcfar_handle h, const rcfar_sat_view* view, double* out,
+                                   int64_t ld_out, rcfar_stream stream);
+
+/* ---- batched path ------------------------------------------------------ */
+
+/* Whole chain (rcfar_preprocess -> rcfar_sat(TILE_F32) -> rcfar_cfar with the
+ * band's CUT columns) for n frames of uneven size and window in a handful of
+ * launches over all frames. frames is a HOST array of n descriptors; their
+ * pointers are device pointers. Each frame's results are identical whatever
+ * the rest of the batch holds. Fails with RCFAR_ERR_OUT_OF_WORKSPACE if the
+ * batch needs more than cfg.batch_bytes (see rcfar_batch_bytes). */
+rcfar_status rcfar_run_batch(rcfar_handle h, const rcfar_frame_desc* frames, int32_t n,
+                             const rcfar_pre_params* p, rcfar_stream stream);
+/* Workspace bytes one frame of size M x N with parameters p (and window w,
+ * needed when p->halo_c is -1) takes in a batch. */
+rcfar_status rcfar_batch_bytes(int32_t M, int32_t N, const rcfar_pre_params* p, const rcfar_window* w,
+                               int64_t* bytes_out);
+/* Builds the twiddle tables a batch of these sizes needs ahead of time, so
+ * that rcfar_run_batch can be captured in a CUDA graph (no allocation inside). */
+rcfar_status rcfar_prepare(rcfar_handle h, const int32_t* Ns, int32_t n, const rcfar_pre_params* p);
+
+/* ---- errors ------------------------------------------------------------ */
+
+/* Waits for the stream, then returns (and clears) the first asynchronous
+ * error the kernels recorded on this handle: RCFAR_ERR_RANGE,
+ * RCFAR_ERR_TIMEOUT or RCFAR_OK. */
+rcfar_status rcfar_get_error(rcfar_handle h, rcfar_stream stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* RCFAR_H */

@@ -1,0 +1,270 @@
+"""Python binding of librcfar, the GB300 radar-chain library.
+
+Argument marshalling only: every step of the path runs in the library's CUDA
+kernels (see include/rcfar.h for the meaning of every argument). Tensors are
+torch CUDA tensors; their device pointers and the current torch stream are
+passed to the C ABI. If the library has not been built, every call raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Optional, Sequence
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "librcfar.so")
+
+RCFAR_OK = 0
+RCFAR_ERR_INVALID_ARG = 1
+RCFAR_ERR_UNSUPPORTED = 2
+RCFAR_ERR_OUT_OF_WORKSPACE = 3
+RCFAR_ERR_CUDA = 4
+RCFAR_ERR_TIMEOUT = 5
+RCFAR_ERR_BAD_STATE = 6
+RCFAR_ERR_RANGE = 7
+
+RCFAR_MAP_F32 = 0
+RCFAR_MAP_F16 = 1
+RCFAR_SAT_TILE_F32 = 0
+RCFAR_SAT_I64 = 1
+RCFAR_SAT_NAIVE_F32 = 2
+
+SAT_TILE_H = 32
+SAT_TILE_W = 128
+
+# Every symbol include/rcfar.h declares.
+EXPORTS = (
+    "rcfar_create", "rcfar_destroy", "rcfar_alpha", "rcfar_n_ref", "rcfar_band_plan", "rcfar_sat_scale",
+    "rcfar_status_string", "rcfar_preprocess", "rcfar_sat", "rcfar_cfar", "rcfar_cfar_direct",
+    "rcfar_sat_materialize", "rcfar_run_batch", "rcfar_batch_bytes", "rcfar_prepare", "rcfar_get_error",
+)
+
+
+class RcfarError(RuntimeError):
+    def __init__(self, status: int, what: str):
+        self.status = status
+        super().__init__(f"{what}: {status_string(status)} (status {status})")
+
+
+class rcfar_config(ctypes.Structure):
+    _fields_ = [("device", ctypes.c_int32), ("max_rows", ctypes.c_int32), ("max_cols", ctypes.c_int32),
+                ("max_n", ctypes.c_int32), ("max_window", ctypes.c_int32), ("max_frames", ctypes.c_int32),
+                ("batch_bytes", ctypes.c_int64)]
+
+
+class rcfar_pre_params(ctypes.Structure):
+    _fields_ = [("fs_hz", ctypes.c_double), ("f_lo_hz", ctypes.c_double), ("f_hi_hz", ctypes.c_double),
+                ("mean_len", ctypes.c_int32), ("halo_c", ctypes.c_int32)]
+
+
+class rcfar_band(ctypes.Structure):
+    _fields_ = [("k_lo", ctypes.c_int32), ("k_hi", ctypes.c_int32), ("c0", ctypes.c_int32), ("c1", ctypes.c_int32),
+                ("cols", ctypes.c_int32), ("value_bound", ctypes.c_float)]
+
+
+class rcfar_window(ctypes.Structure):
+    _fields_ = [("train_r", ctypes.c_int32), ("train_c", ctypes.c_int32), ("guard_r", ctypes.c_int32),
+                ("guard_c", ctypes.c_int32), ("pfa", ctypes.c_double)]
+
+
+class rcfar_sat_view(ctypes.Structure):
+    _fields_ = [("rows", ctypes.c_int32), ("cols", ctypes.c_int32), ("mode", ctypes.c_int32),
+                ("tile_h", ctypes.c_int32), ("tile_w", ctypes.c_int32), ("scale_log2", ctypes.c_int32),
+                ("table", ctypes.c_void_p), ("ld", ctypes.c_int64), ("row_carry", ctypes.c_void_p),
+                ("col_carry", ctypes.c_void_p), ("ld_carry", ctypes.c_int64), ("generation", ctypes.c_uint64)]
+
+
+class rcfar_frame_desc(ctypes.Structure):
+    _fields_ = [("x", ctypes.c_void_p), ("M", ctypes.c_int32), ("N", ctypes.c_int32), ("ldx", ctypes.c_int64),
+                ("window", rcfar_window), ("det", ctypes.c_void_p), ("ld_det", ctypes.c_int64),
+                ("thr", ctypes.c_void_p), ("ld_thr", ctypes.c_int64), ("map", ctypes.c_void_p),
+                ("ld_map", ctypes.c_int64)]
+
+
+_lib = None
+
+
+def lib() -> ctypes.CDLL:
+    """The loaded librcfar.so (raises if it was not built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"librcfar.so is not built ({LIB_PATH}); run paper_2012_11077_gb300.build.build()")
+        L = ctypes.CDLL(LIB_PATH)
+        P, I32, I64, F32, F64 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_float, ctypes.c_double
+        sig = {
+            "rcfar_create": [ctypes.POINTER(rcfar_config), ctypes.POINTER(P)],
+            "rcfar_destroy": [P],
+            "rcfar_alpha": [I32, F64, ctypes.POINTER(F64)],
+            "rcfar_n_ref": [ctypes.POINTER(rcfar_window), ctypes.POINTER(I32)],
+            "rcfar_band_plan": [I32, ctypes.POINTER(rcfar_pre_params), ctypes.POINTER(rcfar_band)],
+            "rcfar_sat_scale": [F32, I64, ctypes.POINTER(I32)],
+            "rcfar_status_string": [ctypes.c_int],
+            "rcfar_preprocess": [P, P, I32, I32, I64, ctypes.POINTER(rcfar_pre_params), P, I64,
+                                 ctypes.POINTER(rcfar_band), P],
+            "rcfar_sat": [P, P, I32, I32, I32, I32, I64, F32, I32, ctypes.POINTER(rcfar_sat_view), P],
+            "rcfar_cfar": [P, ctypes.POINTER(rcfar_sat_view), P, I32, I32, I64, ctypes.POINTER(rcfar_window), I32,
+                           I32, P, I64, P, I64, P],
+            "rcfar_cfar_direct": [P, P, I32, I32, I64, ctypes.POINTER(rcfar_window), I32, I32, P, I64, P, I64, P],
+            "rcfar_sat_materialize": [P, ctypes.POINTER(rcfar_sat_view), P, I64, P],
+            "rcfar_run_batch": [P, ctypes.POINTER(rcfar_frame_desc), I32, ctypes.POINTER(rcfar_pre_params), P],
+            "rcfar_batch_bytes": [I32, I32, ctypes.POINTER(rcfar_pre_params), ctypes.POINTER(rcfar_window),
+                                  ctypes.POINTER(I64)],
+            "rcfar_prepare": [P, ctypes.POINTER(I32), I32, ctypes.POINTER(rcfar_pre_params)],
+            "rcfar_get_error": [P, P],
+        }
+        for name, args in sig.items():
+            fn = getattr(L, name)
+            fn.argtypes = args
+            fn.restype = ctypes.c_char_p if name == "rcfar_status_string" else ctypes.c_int
+        _lib = L
+    return _lib
+
+
+def status_string(status: int) -> str:
+    return lib().rcfar_status_string(int(status)).decode()
+
+
+def _check(st: int, what: str):
+    if st != RCFAR_OK:
+        raise RcfarError(st, what)
+
+
+def _ptr(t) -> Optional[int]:
+    if t is None:
+        return None
+    return int(t.data_ptr())
+
+
+def _stream(stream) -> Optional[int]:
+    if stream is None:
+        import torch
+        return int(torch.cuda.current_stream().cuda_stream) or None
+    if isinstance(stream, int):
+        return stream or None
+    return int(stream.cuda_stream) or None
+
+
+def _ld(t) -> int:
+    """Leading dimension (elements) of a row-major 2D tensor."""
+    if t.dim() != 2 or t.stride(1) != 1:
+        raise ValueError("expected a row-major 2D tensor")
+    return int(t.stride(0))
+
+
+def make_window(train_r, train_c, guard_r, guard_c, pfa) -> rcfar_window:
+    return rcfar_window(int(train_r), int(train_c), int(guard_r), int(guard_c), float(pfa))
+
+
+def make_pre_params(fs_hz=20.0, f_lo_hz=0.3, f_hi_hz=0.8, mean_len=5, halo_c=0) -> rcfar_pre_params:
+    return rcfar_pre_params(float(fs_hz), float(f_lo_hz), float(f_hi_hz), int(mean_len), int(halo_c))
+
+
+# ---------------------------------------------------------------- host-only
+def rcfar_alpha(n_ref: int, pfa: float) -> float:
+    out = ctypes.c_double()
+    _check(lib().rcfar_alpha(int(n_ref), float(pfa), ctypes.byref(out)), "rcfar_alpha")
+    return out.value
+
+
+def rcfar_n_ref(window: rcfar_window) -> int:
+    out = ctypes.c_int32()
+    _check(lib().rcfar_n_ref(ctypes.byref(window), ctypes.byref(out)), "rcfar_n_ref")
+    return out.value
+
+
+def rcfar_band_plan(N: int, params: rcfar_pre_params) -> rcfar_band:
+    out = rcfar_band()
+    _check(lib().rcfar_band_plan(int(N), ctypes.byref(params), ctypes.byref(out)), "rcfar_band_plan")
+    return out
+
+
+def rcfar_sat_scale(bound: float, max_cells: int) -> int:
+    out = ctypes.c_int32()
+    _check(lib().rcfar_sat_scale(float(bound), int(max_cells), ctypes.byref(out)), "rcfar_sat_scale")
+    return out.value
+
+
+def rcfar_batch_bytes(M: int, N: int, params: rcfar_pre_params, window: Optional[rcfar_window] = None) -> int:
+    out = ctypes.c_int64()
+    _check(lib().rcfar_batch_bytes(int(M), int(N), ctypes.byref(params),
+                                   ctypes.byref(window) if window is not None else None, ctypes.byref(out)),
+           "rcfar_batch_bytes")
+    return out.value
+
+
+# ---------------------------------------------------------------- handle
+def rcfar_create(device: int = 0, max_rows: int = 1024, max_cols: int = 1024, max_n: int = 4096,
+                 max_window: int = 32, max_frames: int = 64, batch_bytes: int = 0) -> int:
+    cfg = rcfar_config(int(device), int(max_rows), int(max_cols), int(max_n), int(max_window), int(max_frames),
+                       int(batch_bytes))
+    h = ctypes.c_void_p()
+    _check(lib().rcfar_create(ctypes.byref(cfg), ctypes.byref(h)), "rcfar_create")
+    return h.value
+
+
+def rcfar_destroy(h: int):
+    _check(lib().rcfar_destroy(h), "rcfar_destroy")
+
+
+def rcfar_get_error(h: int, stream=None) -> int:
+    """Waits for the stream; returns the asynchronous status (does not raise)."""
+    return lib().rcfar_get_error(h, _stream(stream))
+
+
+def rcfar_preprocess(h: int, x, params: rcfar_pre_params, map_out, stream=None) -> rcfar_band:
+    """x: float32 [M][N] CUDA tensor (row-major); map_out: float32 [M][>=cols]."""
+    M, N = int(x.shape[0]), int(x.shape[1])
+    band = rcfar_band()
+    _check(lib().rcfar_preprocess(h, _ptr(x), M, N, _ld(x), ctypes.byref(params), _ptr(map_out), _ld(map_out),
+                                  ctypes.byref(band), _stream(stream)), "rcfar_preprocess")
+    return band
+
+
+def rcfar_sat(h: int, map_t, value_bound: float = 0.0, mode: int = RCFAR_SAT_TILE_F32, map_exp2: int = 0,
+              stream=None) -> rcfar_sat_view:
+    import torch
+    dtype = RCFAR_MAP_F16 if map_t.dtype == torch.float16 else RCFAR_MAP_F32
+    view = rcfar_sat_view()
+    _check(lib().rcfar_sat(h, _ptr(map_t), dtype, int(map_exp2), int(map_t.shape[0]), int(map_t.shape[1]),
+                           _ld(map_t), float(value_bound), int(mode), ctypes.byref(view), _stream(stream)),
+           "rcfar_sat")
+    return view
+
+
+def rcfar_cfar(h: int, view: rcfar_sat_view, map_t, window: rcfar_window, cut_c_lo: int, cut_c_hi: int, det,
+               thr=None, map_exp2: int = 0, stream=None):
+    import torch
+    dtype = RCFAR_MAP_F16 if map_t.dtype == torch.float16 else RCFAR_MAP_F32
+    _check(lib().rcfar_cfar(h, ctypes.byref(view), _ptr(map_t), dtype, int(map_exp2), _ld(map_t),
+                            ctypes.byref(window), int(cut_c_lo), int(cut_c_hi), _ptr(det), _ld(det), _ptr(thr),
+                            _ld(thr) if thr is not None else 0, _stream(stream)), "rcfar_cfar")
+
+
+def rcfar_cfar_direct(h: int, map_t, window: rcfar_window, cut_c_lo: int, cut_c_hi: int, det, thr=None,
+                      stream=None):
+    _check(lib().rcfar_cfar_direct(h, _ptr(map_t), int(map_t.shape[0]), int(map_t.shape[1]), _ld(map_t),
+                                   ctypes.byref(window), int(cut_c_lo), int(cut_c_hi), _ptr(det), _ld(det),
+                                   _ptr(thr), _ld(thr) if thr is not None else 0, _stream(stream)),
+           "rcfar_cfar_direct")
+
+
+def rcfar_sat_materialize(h: int, view: rcfar_sat_view, out, stream=None):
+    _check(lib().rcfar_sat_materialize(h, ctypes.byref(view), _ptr(out), _ld(out), _stream(stream)),
+           "rcfar_sat_materialize")
+
+
+def frame_desc(x, window: rcfar_window, det, thr=None, map_out=None) -> rcfar_frame_desc:
+    return rcfar_frame_desc(_ptr(x), int(x.shape[0]), int(x.shape[1]), _ld(x), window, _ptr(det), _ld(det),
+                            _ptr(thr), _ld(thr) if thr is not None else 0, _ptr(map_out),
+                            _ld(map_out) if map_out is not None else 0)
+
+
+def rcfar_run_batch(h: int, frames: Sequence[rcfar_frame_desc], params: rcfar_pre_params, stream=None):
+    arr = (rcfar_frame_desc * len(frames))(*frames)
+    _check(lib().rcfar_run_batch(h, arr, len(frames), ctypes.byref(params), _stream(stream)), "rcfar_run_batch")
+
+
+def rcfar_prepare(h: int, Ns: Sequence[int], params: rcfar_pre_params):
+    arr = (ctypes.c_int32 * len(Ns))(*[int(n) for n in Ns])
+    _check(lib().rcfar_prepare(h, arr, len(Ns), ctypes.byref(params)), "rcfar_prepare")

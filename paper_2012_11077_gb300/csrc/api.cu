@@ -1,0 +1,841 @@
+// C ABI of librcfar (see include/rcfar.h): handle, workspace, plans,
+// validation and launch orchestration. All numerical work happens in the
+// kernels of pre.cu, sat.cu and cfar.cu.
+#include "rcfar_internal.cuh"
+
+#include <cmath>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <new>
+#include <tuple>
+#include <vector>
+
+using namespace rcfar;
+
+namespace {
+
+constexpr int kStatsRows = 64;  // rows per column-statistics CTA
+
+inline long long ceil_div(long long a, long long b) { return (a + b - 1) / b; }
+inline long long round_up(long long a, long long b) { return ceil_div(a, b) * b; }
+inline size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+struct Twiddle {
+  float* W = nullptr;
+  long long ldw = 0;
+};
+
+// Bump allocator over a device region.
+struct Carver {
+  char* base;
+  size_t cap, off = 0;
+  Carver(void* b, size_t c) : base((char*)b), cap(c) {}
+  template <typename T>
+  T* take(size_t count) {
+    const size_t bytes = align256(count * sizeof(T));
+    if (off + bytes > cap) return nullptr;
+    T* p = reinterpret_cast<T*>(base + off);
+    off += bytes;
+    return p;
+  }
+};
+
+// Per-frame preprocessing geometry (depends on the frame's own shape only,
+// so a frame is computed the same way alone and inside any batch).
+struct PreGeom {
+  int n_strips, n_chunks, rows_per_chunk;
+  int mtiles, ntiles, splitk, kper;
+  int n_norm;
+  long long ldk;
+};
+
+PreGeom pre_geom(int M, int N, int C) {
+  PreGeom g;
+  g.n_strips = (int)ceil_div(N, kStatsStrip);
+  g.rows_per_chunk = kStatsRows;
+  g.n_chunks = (int)ceil_div(M, kStatsRows);
+  g.mtiles = (int)ceil_div(M, kDftBM);
+  g.ntiles = (int)ceil_div(2LL * C, kDftBN);
+  const int tiles = g.mtiles * g.ntiles;
+  int sk = (int)ceil_div(300, tiles);
+  const int max_sk = (int)std::max<long long>(1, N / 256);
+  if (sk > max_sk) sk = max_sk;
+  if (sk < 1) sk = 1;
+  g.kper = (int)round_up(ceil_div(N, sk), kDftBK);
+  g.splitk = (int)ceil_div(N, g.kper);
+  g.ldk = round_up(2LL * C, 4);
+  g.n_norm = (int)std::min<long long>(std::max<long long>(1, ceil_div((long long)M * C, 1024)), 1024);
+  return g;
+}
+
+struct SatGeom {
+  int n_bands, n_chunks;
+  long long ld_table, ld_carry;
+};
+
+SatGeom sat_geom(int rows, int cols) {
+  SatGeom g;
+  g.n_bands = (int)ceil_div(rows, kSatTileH);
+  g.n_chunks = (int)ceil_div(cols, kSatTileW);
+  g.ld_table = round_up(cols, 4);
+  g.ld_carry = (long long)g.n_chunks * kSatTileW;
+  return g;
+}
+
+// bytes of SAT storage (TILE_F32 needs 4 B/cell, I64 8 B/cell)
+size_t sat_bytes(int rows, int cols, int mode) {
+  SatGeom g = sat_geom(rows, cols);
+  size_t b = 0;
+  b += align256((size_t)rows * g.ld_table * (mode == RCFAR_SAT_I64 ? 8 : 4));
+  b += 2 * align256((size_t)g.n_bands * g.ld_carry * 8);     // row_carry + agg
+  b += align256((size_t)g.n_chunks * rows * 8);               // col_carry
+  return b;
+}
+size_t sat_flag_bytes(int rows, int cols) {
+  SatGeom g = sat_geom(rows, cols);
+  return align256((size_t)g.n_bands * g.n_chunks * 4);
+}
+
+struct CfarTile {
+  int bh, bw;
+};
+
+CfarTile pick_cfar_tile(int mode, int wr, int wc, size_t smem_cap) {
+  const CfarTile cand[] = {{32, 64}, {32, 32}, {16, 32}, {16, 16}, {8, 16}};
+  for (const CfarTile& t : cand)
+    if (cfar_smem_bytes(mode, t.bh, t.bw, wr, wc) <= smem_cap) return t;
+  return {0, 0};
+}
+
+}  // namespace
+
+static int n_ref_of(const rcfar_window& w) {
+  const long long wr = w.guard_r + w.train_r, wc = w.guard_c + w.train_c;
+  return (int)((2 * wr + 1) * (2 * wc + 1) - (2LL * w.guard_r + 1) * (2LL * w.guard_c + 1));
+}
+
+struct rcfar_ctx {
+  rcfar_config cfg{};
+  int device = 0;
+  size_t smem_optin = 48 * 1024;
+  void* ws = nullptr;  // one allocation holds everything below
+  size_t ws_bytes = 0;
+  // control words
+  int* status = nullptr;
+  unsigned* sat_ticket = nullptr;
+  unsigned* sat_done = nullptr;
+  unsigned* sat_gen = nullptr;
+  int* sat_scale = nullptr;
+  float* map_bound = nullptr;
+  unsigned* ymax = nullptr;
+  // per-step preprocessing
+  float2* stats = nullptr;
+  float2* partial = nullptr;
+  unsigned* strip_cnt = nullptr;
+  unsigned* tile_cnt = nullptr;
+  float* kpart = nullptr;
+  size_t kpart_floats = 0;
+  // per-step SAT
+  void* sat_table = nullptr;
+  unsigned long long* row_carry = nullptr;
+  unsigned long long* agg = nullptr;
+  unsigned long long* col_carry = nullptr;
+  unsigned* sat_flags = nullptr;
+  uint64_t sat_generation = 0;
+  // batch arena
+  void* batch = nullptr;
+  size_t batch_bytes = 0;
+  // twiddle plans
+  std::mutex mu;
+  std::map<std::tuple<int, int, int>, Twiddle> plans;
+};
+
+namespace {
+
+rcfar_status cuda_fail(cudaError_t e) { return e == cudaSuccess ? RCFAR_OK : RCFAR_ERR_CUDA; }
+
+struct DeviceGuard {
+  int prev = -1;
+  explicit DeviceGuard(int dev) {
+    cudaGetDevice(&prev);
+    if (prev != dev) cudaSetDevice(dev);
+  }
+  ~DeviceGuard() {
+    int cur = -1;
+    cudaGetDevice(&cur);
+    if (prev >= 0 && cur != prev) cudaSetDevice(prev);
+  }
+};
+
+bool valid_window(const rcfar_window* w) {
+  return w && w->train_r >= 0 && w->train_c >= 0 && w->guard_r >= 0 && w->guard_c >= 0 &&
+         w->pfa > 0.0 && w->pfa < 1.0 && n_ref_of(*w) > 0;
+}
+
+}  // namespace
+
+static double alpha_of(int n_ref, double pfa) { return (double)n_ref * (std::pow(pfa, -1.0 / (double)n_ref) - 1.0); }
+
+static bool band_of(int N, const rcfar_pre_params* p, rcfar_band* b) {
+  if (!p || N <= 0 || !(p->fs_hz > 0.0) || !(p->f_lo_hz >= 0.0) || !(p->f_hi_hz >= p->f_lo_hz) || p->halo_c < 0)
+    return false;
+  const double lo = p->f_lo_hz * (double)N / p->fs_hz;
+  const double hi = p->f_hi_hz * (double)N / p->fs_hz;
+  long long k_lo = (long long)std::ceil(lo - 1e-9);
+  long long k_hi = (long long)std::floor(hi + 1e-9);
+  const long long nyq = N / 2;
+  if (k_lo < 0) k_lo = 0;
+  if (k_hi > nyq) k_hi = nyq;
+  long long c0 = k_lo - p->halo_c;
+  long long c1 = k_hi + p->halo_c;
+  if (c0 < 0) c0 = 0;
+  if (c1 > nyq) c1 = nyq;
+  if (c1 < c0) return false;
+  b->k_lo = (int)k_lo;
+  b->k_hi = (int)k_hi;
+  b->c0 = (int)c0;
+  b->c1 = (int)c1;
+  b->cols = (int)(c1 - c0 + 1);
+  b->value_bound = (float)N;
+  return true;
+}
+
+static bool valid_pre(const rcfar_pre_params* p) {
+  return p && p->mean_len >= 1 && (p->mean_len & 1) && (p->mean_len - 1) / 2 <= kMaxMeanHalf;
+}
+
+// twiddle plan for (N, c0, C); builds it on first use
+static rcfar_status get_plan(rcfar_ctx* h, int N, int c0, int C, cudaStream_t s, Twiddle* out) {
+  std::lock_guard<std::mutex> lk(h->mu);
+  auto key = std::make_tuple(N, c0, C);
+  auto it = h->plans.find(key);
+  if (it != h->plans.end()) {
+    *out = it->second;
+    return RCFAR_OK;
+  }
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(s, &cs) == cudaSuccess && cs != cudaStreamCaptureStatusNone)
+    return RCFAR_ERR_BAD_STATE;  // plans must exist before capture (rcfar_prepare)
+  Twiddle t;
+  t.ldw = round_up(2LL * C, 4);
+  if (cudaMalloc(&t.W, (size_t)N * t.ldw * sizeof(float)) != cudaSuccess) return RCFAR_ERR_CUDA;
+  cudaError_t e = launch_twiddles(t.W, t.ldw, N, c0, C, s);
+  if (e != cudaSuccess) {
+    cudaFree(t.W);
+    return RCFAR_ERR_CUDA;
+  }
+  h->plans[key] = t;
+  *out = t;
+  return RCFAR_OK;
+}
+
+static PreFrameDev make_pre_frame(const float* x, int M, int N, long long ldx, const rcfar_band& b, int h,
+                                  const Twiddle& tw, const PreGeom& g) {
+  PreFrameDev F;
+  std::memset(&F, 0, sizeof(F));
+  F.x = x;
+  F.ldx = ldx;
+  F.M = M;
+  F.N = N;
+  F.c0 = b.c0;
+  F.C = b.cols;
+  F.h = h;
+  F.mbar = (float)((M - 1) * 0.5);
+  F.inv_M = (float)(1.0 / (double)M);
+  const double D = (double)M * ((double)M * M - 1.0) / 12.0;
+  F.inv_D = D > 0 ? (float)(1.0 / D) : 0.0f;
+  F.W = tw.W;
+  F.ldw = tw.ldw;
+  F.rows_per_chunk = g.rows_per_chunk;
+  F.n_chunks = g.n_chunks;
+  F.n_strips = g.n_strips;
+  F.mtiles = g.mtiles;
+  F.ntiles = g.ntiles;
+  F.splitk = g.splitk;
+  F.kper = g.kper;
+  F.ldk = g.ldk;
+  F.n_norm = g.n_norm;
+  return F;
+}
+
+// workspace of one frame in a batch: data, and control words zeroed per batch
+static size_t frame_data_bytes(int M, int N, int C) {
+  const PreGeom g = pre_geom(M, N, C);
+  size_t t = 0;
+  t += align256((size_t)N * sizeof(float2));                       // stats
+  t += align256((size_t)g.n_chunks * N * sizeof(float2));          // partial
+  t += g.splitk > 1 ? align256((size_t)g.splitk * M * g.ldk * 4) : 0;
+  t += align256((size_t)M * round_up(C, 4) * 4);                   // map
+  t += sat_bytes(M, C, RCFAR_SAT_TILE_F32);
+  return t;
+}
+static size_t frame_ctl_bytes(int M, int N, int C) {
+  const PreGeom g = pre_geom(M, N, C);
+  return align256((size_t)g.n_strips * 4) + align256((size_t)g.mtiles * g.ntiles * 4) + 256 + sat_flag_bytes(M, C);
+}
+
+// -------------------------------------------------------------------------
+extern "C" {
+
+const char* rcfar_status_string(rcfar_status s) {
+  switch (s) {
+    case RCFAR_OK: return "ok";
+    case RCFAR_ERR_INVALID_ARG: return "invalid argument";
+    case RCFAR_ERR_UNSUPPORTED: return "size beyond the handle's limits";
+    case RCFAR_ERR_OUT_OF_WORKSPACE: return "batch needs more workspace than the handle holds";
+    case RCFAR_ERR_CUDA: return "CUDA runtime error";
+    case RCFAR_ERR_TIMEOUT: return "bounded device wait expired";
+    case RCFAR_ERR_BAD_STATE: return "bad state (stale view, capture without plan, ...)";
+    case RCFAR_ERR_RANGE: return "map value above its stated bound, or NaN";
+  }
+  return "unknown status";
+}
+
+rcfar_status rcfar_alpha(int32_t n_ref, double pfa, double* alpha_out) {
+  if (!alpha_out || n_ref <= 0 || !(pfa > 0.0 && pfa < 1.0)) return RCFAR_ERR_INVALID_ARG;
+  *alpha_out = alpha_of(n_ref, pfa);
+  return RCFAR_OK;
+}
+
+rcfar_status rcfar_n_ref(const rcfar_window* w, int32_t* n_ref_out) {
+  if (!w || !n_ref_out || w->train_r < 0 || w->train_c < 0 || w->guard_r < 0 || w->guard_c < 0)
+    return RCFAR_ERR_INVALID_ARG;
+  *n_ref_out = n_ref_of(*w);
+  return RCFAR_OK;
+}
+
+rcfar_status rcfar_band_plan(int32_t N, const rcfar_pre_params* p, rcfar_band* out) {
+  if (!out || !band_of(N, p, out)) return RCFAR_ERR_INVALID_ARG;
+  return RCFAR_OK;
+}
+
+rcfar_status rcfar_sat_scale(float bound, int64_t max_cells, int32_t* scale_log2_out) {
+  if (!scale_log2_out || max_cells <= 0 || !(bound >= 0.0f)) return RCFAR_ERR_INVALID_ARG;
+  *scale_log2_out = sat_scale_for(bound, max_cells);
+  return RCFAR_OK;
+}
+
+rcfar_status rcfar_create(const rcfar_config* cfg, rcfar_handle* out) {
+  if (!cfg || !out) return RCFAR_ERR_INVALID_ARG;
+  if (cfg->max_rows <= 0 || cfg->max_cols <= 0 || cfg->max_n <= 0 || cfg->max_window < 0 ||
+      cfg->max_frames < 0 || cfg->batch_bytes < 0)
+    return RCFAR_ERR_INVALID_ARG;
+  *out = nullptr;
+  rcfar_ctx* h = new (std::nothrow) rcfar_ctx();
+  if (!h) return RCFAR_ERR_CUDA;
+  h->cfg = *cfg;
+  h->device = cfg->device;
+  if (cudaSetDevice(cfg->device) != cudaSuccess) {
+    delete h;
+    return RCFAR_ERR_CUDA;
+  }
+  int optin = 0;
+  cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, cfg->device);
+  if (optin > 0) h->smem_optin = (size_t)optin;
+
+  const int R = cfg->max_rows, Cm = std::max(cfg->max_cols, 1), Nm = cfg->max_n;
+  // per-step preprocessing: largest frame is max_rows x max_n with up to N/2+1 bins
+  const int max_tiles = (int)(ceil_div(R, kDftBM) * ceil_div(2LL * Cm, kDftBN));
+  // split-K scratch: splitk <= 300 / tiles + 1, rows <= 128 * mtiles, ldk <= 64 * ntiles
+  const size_t kpart = (size_t)(300 + max_tiles) * kDftBM * kDftBN;
+  const int max_strips = (int)ceil_div(Nm, kStatsStrip);
+  const int max_chunks = (int)ceil_div(R, kStatsRows);
+
+  size_t total = 0;
+  total += 256;                                   // control words
+  total += align256((size_t)Nm * sizeof(float2));  // stats
+  total += align256((size_t)max_chunks * Nm * sizeof(float2));
+  total += align256((size_t)max_strips * 4);
+  total += align256((size_t)max_tiles * 4);
+  total += align256(kpart * 4);
+  total += sat_bytes(R, Cm, RCFAR_SAT_I64);
+  total += sat_flag_bytes(R, Cm);
+  if (cudaMalloc(&h->ws, total) != cudaSuccess) {
+    delete h;
+    return RCFAR_ERR_CUDA;
+  }
+  h->ws_bytes = total;
+  cudaMemset(h->ws, 0, total);
+  Carver cv(h->ws, total);
+  unsigned* ctl = cv.take<unsigned>(64);
+  h->status = reinterpret_cast<int*>(ctl + 0);
+  h->sat_ticket = ctl + 1;
+  h->sat_done = ctl + 2;
+  h->sat_gen = ctl + 3;
+  h->sat_scale = reinterpret_cast<int*>(ctl + 4);
+  h->map_bound = reinterpret_cast<float*>(ctl + 5);
+  h->ymax = ctl + 6;
+  h->stats = cv.take<float2>(Nm);
+  h->partial = cv.take<float2>((size_t)max_chunks * Nm);
+  h->strip_cnt = cv.take<unsigned>(max_strips);
+  h->tile_cnt = cv.take<unsigned>(max_tiles);
+  h->kpart = cv.take<float>(kpart);
+  h->kpart_floats = kpart;
+  {
+    SatGeom g = sat_geom(R, Cm);
+    h->sat_table = cv.take<char>((size_t)R * g.ld_table * 8);
+    h->row_carry = cv.take<unsigned long long>((size_t)g.n_bands * g.ld_carry);
+    h->agg = cv.take<unsigned long long>((size_t)g.n_bands * g.ld_carry);
+    h->col_carry = cv.take<unsigned long long>((size_t)g.n_chunks * R);
+    h->sat_flags = cv.take<unsigned>((size_t)g.n_bands * g.n_chunks);
+  }
+  const unsigned one = 1u;
+  cudaMemcpy(h->sat_gen, &one, sizeof(one), cudaMemcpyHostToDevice);
+  if (cfg->batch_bytes > 0) {
+    if (cudaMalloc(&h->batch, (size_t)cfg->batch_bytes) != cudaSuccess) {
+      cudaFree(h->ws);
+      delete h;
+      return RCFAR_ERR_CUDA;
+    }
+    h->batch_bytes = (size_t)cfg->batch_bytes;
+  }
+  if (cudaDeviceSynchronize() != cudaSuccess) {
+    cudaFree(h->ws);
+    if (h->batch) cudaFree(h->batch);
+    delete h;
+    return RCFAR_ERR_CUDA;
+  }
+  *out = h;
+  return RCFAR_OK;
+}
+
+rcfar_status rcfar_destroy(rcfar_handle h) {
+  if (!h) return RCFAR_ERR_INVALID_ARG;
+  DeviceGuard g(h->device);
+  cudaError_t e = cudaDeviceSynchronize();
+  for (auto& kv : h->plans) cudaFree(kv.second.W);
+  if (h->ws) cudaFree(h->ws);
+  if (h->batch) cudaFree(h->batch);
+  delete h;
+  return cuda_fail(e);
+}
+
+rcfar_status rcfar_get_error(rcfar_handle h, rcfar_stream stream) {
+  if (!h) return RCFAR_ERR_INVALID_ARG;
+  DeviceGuard g(h->device);
+  cudaStream_t s = (cudaStream_t)stream;
+  if (cudaStreamSynchronize(s) != cudaSuccess) return RCFAR_ERR_CUDA;
+  int st = 0;
+  if (cudaMemcpy(&st, h->status, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) return RCFAR_ERR_CUDA;
+  if (st) {
+    // clear the status and any counters a broken launch may have left behind
+    cudaMemset(h->status, 0, sizeof(int));
+    cudaMemset(h->sat_ticket, 0, 2 * sizeof(unsigned));
+    cudaMemset(h->strip_cnt, 0, 4);
+    cudaDeviceSynchronize();
+  }
+  if (st & kStatusTimeout) return RCFAR_ERR_TIMEOUT;
+  if (st & kStatusRange) return RCFAR_ERR_RANGE;
+  return RCFAR_OK;
+}
+
+rcfar_status rcfar_preprocess(rcfar_handle h, const float* x, int32_t M, int32_t N, int64_t ldx,
+                              const rcfar_pre_params* p, float* map, int64_t ld_map, rcfar_band* band_out,
+                              rcfar_stream stream) {
+  if (!h || !x || !map || M <= 0 || N <= 0 || ldx < N || !valid_pre(p)) return RCFAR_ERR_INVALID_ARG;
+  if (p->mean_len > N) return RCFAR_ERR_INVALID_ARG;
+  rcfar_band b;
+  if (!band_of(N, p, &b)) return RCFAR_ERR_INVALID_ARG;
+  if (ld_map < b.cols) return RCFAR_ERR_INVALID_ARG;
+  if (M > h->cfg.max_rows || N > h->cfg.max_n || b.cols > h->cfg.max_cols) return RCFAR_ERR_UNSUPPORTED;
+  DeviceGuard dg(h->device);
+  cudaStream_t s = (cudaStream_t)stream;
+  const PreGeom g = pre_geom(M, N, b.cols);
+  if (g.splitk > 1 && (size_t)g.splitk * M * g.ldk > h->kpart_floats) return RCFAR_ERR_UNSUPPORTED;
+  Twiddle tw;
+  rcfar_status st = get_plan(h, N, b.c0, b.cols, s, &tw);
+  if (st != RCFAR_OK) return st;
+
+  static thread_local PreBatch pb;
+  pb.n = 1;
+  PreFrameDev& F = pb.f[0];
+  F = make_pre_frame(x, M, N, ldx, b, (p->mean_len - 1) / 2, tw, g);
+  F.stats = h->stats;
+  F.partial = h->partial;
+  F.strip_cnt = h->strip_cnt;
+  F.ymax = h->ymax;
+  F.map = map;
+  F.ld_map = ld_map;
+  F.kpart = h->kpart;
+  F.tile_cnt = h->tile_cnt;
+  F.item_stats = 0;
+  F.item_dft = 0;
+  F.item_norm = 0;
+  cudaError_t e = launch_colstats(pb, g.n_strips * g.n_chunks, s);
+  if (e == cudaSuccess) e = launch_band_dft(pb, g.mtiles * g.ntiles * g.splitk, s);
+  if (e == cudaSuccess) e = launch_normalise(pb, g.n_norm, s);
+  if (e != cudaSuccess) return RCFAR_ERR_CUDA;
+  if (band_out) *band_out = b;
+  return RCFAR_OK;
+}
+
+rcfar_status rcfar_sat(rcfar_handle h, const void* map, int32_t dtype, int32_t map_exp2, int32_t rows, int32_t cols,
+                       int64_t ld, float value_bound, int32_t mode, rcfar_sat_view* view_out, rcfar_stream stream) {
+  if (!h || !map || !view_out || rows <= 0 || cols <= 0 || ld < cols) return RCFAR_ERR_INVALID_ARG;
+  if (dtype != RCFAR_MAP_F32 && dtype != RCFAR_MAP_F16) return RCFAR_ERR_INVALID_ARG;
+  if (mode < RCFAR_SAT_TILE_F32 || mode > RCFAR_SAT_NAIVE_F32) return RCFAR_ERR_INVALID_ARG;
+  if (value_bound != value_bound) return RCFAR_ERR_INVALID_ARG;
+  if (map_exp2 < -100 || map_exp2 > 100) return RCFAR_ERR_INVALID_ARG;
+  if (rows > h->cfg.max_rows || cols > h->cfg.max_cols) return RCFAR_ERR_UNSUPPORTED;
+  DeviceGuard dg(h->device);
+  cudaStream_t s = (cudaStream_t)stream;
+  const SatGeom g = sat_geom(rows, cols);
+  const float in_scale = dtype == RCFAR_MAP_F16 ? std::ldexp(1.0f, map_exp2) : 1.0f;
+  const long long wmax = h->cfg.max_window;
+  const long long max_cells = std::max<long long>((long long)kSatTileH * kSatTileW, (2 * wmax + 1) * (2 * wmax + 1));
+
+  static thread_local SatBatch sb;
+  sb.n = 1;
+  sb.total = g.n_bands;
+  sb.ticket = h->sat_ticket;
+  sb.done = h->sat_done;
+  sb.gen = h->sat_gen;
+  sb.status = h->status;
+  SatMapDev& m = sb.m[0];
+  std::memset(&m, 0, sizeof(m));
+  m.map = map;
+  m.ld = ld;
+  m.rows = rows;
+  m.cols = cols;
+  m.in_scale = in_scale;
+  m.max_cells = max_cells;
+  if (mode == RCFAR_SAT_NAIVE_F32) {
+    m.scale_log2 = 0;  // plain FP32: no fixed point; the check only rejects Inf/NaN without a bound
+    m.bound = value_bound > 0.0f ? value_bound : 3.4028235e38f;
+  } else if (value_bound > 0.0f) {
+    m.bound = value_bound;
+    m.scale_log2 = sat_scale_for(value_bound, max_cells);
+  } else {
+    cudaError_t e = launch_map_max(map, dtype, in_scale, rows, cols, ld, h->map_bound, s);
+    if (e != cudaSuccess) return RCFAR_ERR_CUDA;
+    m.scale_log2 = kScaleFromDevice;
+    m.bound_dev = h->map_bound;
+  }
+  m.table = h->sat_table;
+  m.ld_table = g.ld_table;
+  m.row_carry = h->row_carry;
+  m.agg = h->agg;
+  m.col_carry = h->col_carry;
+  m.ld_carry = g.ld_carry;
+  m.flags = h->sat_flags;
+  m.scale_out = h->sat_scale;
+  m.n_bands = g.n_bands;
+  m.n_chunks = g.n_chunks;
+  m.item0 = 0;
+  cudaError_t e = launch_sat(sb, mode, dtype, s);
+  if (e != cudaSuccess) return RCFAR_ERR_CUDA;
+
+  rcfar_sat_view v;
+  std::memset(&v, 0, sizeof(v));
+  v.rows = rows;
+  v.cols = cols;
+  v.mode = mode;
+  v.tile_h = kSatTileH;
+  v.tile_w = kSatTileW;
+  v.scale_log2 = (m.scale_log2 == kScaleFromDevice) ? INT32_MIN : m.scale_log2;
+  v.table = h->sat_table;
+  v.ld = g.ld_table;
+  v.row_carry = reinterpret_cast<int64_t*>(h->row_carry);
+  v.col_carry = reinterpret_cast<int64_t*>(h->col_carry);
+  v.ld_carry = g.ld_carry;
+  v.generation = ++h->sat_generation;
+  *view_out = v;
+  return RCFAR_OK;
+}
+
+static rcfar_status check_view(rcfar_handle h, const rcfar_sat_view* v) {
+  if (!v) return RCFAR_ERR_INVALID_ARG;
+  if (v->generation != h->sat_generation || v->table != h->sat_table) return RCFAR_ERR_BAD_STATE;
+  return RCFAR_OK;
+}
+
+static void fill_cfar_window(CfarMapDev& P, const rcfar_window* w, int rows, int cols, int cut_c_lo, int cut_c_hi) {
+  P.wr = w->guard_r + w->train_r;
+  P.wc = w->guard_c + w->train_c;
+  P.gr = w->guard_r;
+  P.gc = w->guard_c;
+  const int nr = n_ref_of(*w);
+  P.kthr = (float)(alpha_of(nr, w->pfa) / (double)nr);
+  P.row_lo = P.wr;
+  P.row_hi = rows - 1 - P.wr;
+  P.cut_lo = std::max(P.wc, cut_c_lo);
+  P.cut_hi = std::min(cols - 1 - P.wc, cut_c_hi);
+}
+
+rcfar_status rcfar_cfar(rcfar_handle h, const rcfar_sat_view* view, const void* map, int32_t dtype, int32_t map_exp2,
+                        int64_t ld_map, const rcfar_window* w, int32_t cut_c_lo, int32_t cut_c_hi, uint8_t* det,
+                        int64_t ld_det, float* thr, int64_t ld_thr, rcfar_stream stream) {
+  if (!h || !view || !map || !det || !valid_window(w)) return RCFAR_ERR_INVALID_ARG;
+  if (dtype != RCFAR_MAP_F32 && dtype != RCFAR_MAP_F16) return RCFAR_ERR_INVALID_ARG;
+  if (ld_map < view->cols || ld_det < view->cols || (thr && ld_thr < view->cols)) return RCFAR_ERR_INVALID_ARG;
+  rcfar_status st = check_view(h, view);
+  if (st != RCFAR_OK) return st;
+  if (w->guard_r + w->train_r > h->cfg.max_window || w->guard_c + w->train_c > h->cfg.max_window)
+    return RCFAR_ERR_UNSUPPORTED;
+  DeviceGuard dg(h->device);
+  cudaStream_t s = (cudaStream_t)stream;
+  static thread_local CfarBatch cb;
+  cb.n = 1;
+  CfarMapDev& P = cb.m[0];
+  std::memset(&P, 0, sizeof(P));
+  P.table = view->table;
+  P.ld_table = view->ld;
+  P.row_carry = reinterpret_cast<const unsigned long long*>(view->row_carry);
+  P.col_carry = reinterpret_cast<const unsigned long long*>(view->col_carry);
+  P.ld_carry = view->ld_carry;
+  P.scale_dev = h->sat_scale;
+  P.map = map;
+  P.ld_map = ld_map;
+  P.in_scale = dtype == RCFAR_MAP_F16 ? std::ldexp(1.0f, map_exp2) : 1.0f;
+  P.rows = view->rows;
+  P.cols = view->cols;
+  fill_cfar_window(P, w, view->rows, view->cols, cut_c_lo, cut_c_hi);
+  P.det = det;
+  P.ld_det = ld_det;
+  P.thr = thr;
+  P.ld_thr = ld_thr;
+  const CfarTile t = pick_cfar_tile(view->mode, P.wr, P.wc, std::min<size_t>(h->smem_optin, 200 * 1024));
+  if (t.bh == 0) return RCFAR_ERR_UNSUPPORTED;
+  P.bh = t.bh;
+  P.bw = t.bw;
+  P.tiles_x = (int)ceil_div(view->cols, t.bw);
+  const int blocks = P.tiles_x * (int)ceil_div(view->rows, t.bh);
+  P.item0 = 0;
+  cudaError_t e = launch_cfar(cb, view->mode, dtype, blocks,
+                              cfar_smem_bytes(view->mode, t.bh, t.bw, P.wr, P.wc), s);
+  return cuda_fail(e);
+}
+
+rcfar_status rcfar_cfar_direct(rcfar_handle h, const float* map, int32_t rows, int32_t cols, int64_t ld_map,
+                               const rcfar_window* w, int32_t cut_c_lo, int32_t cut_c_hi, uint8_t* det,
+                               int64_t ld_det, float* thr, int64_t ld_thr, rcfar_stream stream) {
+  if (!h || !map || !det || rows <= 0 || cols <= 0 || ld_map < cols || ld_det < cols || !valid_window(w))
+    return RCFAR_ERR_INVALID_ARG;
+  if (thr && ld_thr < cols) return RCFAR_ERR_INVALID_ARG;
+  if (w->guard_r + w->train_r > h->cfg.max_window || w->guard_c + w->train_c > h->cfg.max_window)
+    return RCFAR_ERR_UNSUPPORTED;
+  DeviceGuard dg(h->device);
+  cudaStream_t s = (cudaStream_t)stream;
+  CfarMapDev P;
+  std::memset(&P, 0, sizeof(P));
+  P.map = map;
+  P.ld_map = ld_map;
+  P.in_scale = 1.0f;
+  P.rows = rows;
+  P.cols = cols;
+  fill_cfar_window(P, w, rows, cols, cut_c_lo, cut_c_hi);
+  P.det = det;
+  P.ld_det = ld_det;
+  P.thr = thr;
+  P.ld_thr = ld_thr;
+  int bh = 32, bw = 64;
+  while (cfar_direct_smem_bytes(bh, bw, P.wr, P.wc) > std::min<size_t>(h->smem_optin, 200 * 1024) && bw > 8) {
+    if (bw > bh) bw /= 2; else bh /= 2;
+  }
+  if (cfar_direct_smem_bytes(bh, bw, P.wr, P.wc) > std::min<size_t>(h->smem_optin, 200 * 1024))
+    return RCFAR_ERR_UNSUPPORTED;
+  P.bh = bh;
+  P.bw = bw;
+  P.tiles_x = (int)ceil_div(cols, bw);
+  const int blocks = P.tiles_x * (int)ceil_div(rows, bh);
+  return cuda_fail(launch_cfar_direct(P, blocks, cfar_direct_smem_bytes(bh, bw, P.wr, P.wc), s));
+}
+
+rcfar_status rcfar_sat_materialize(rcfar_handle h, const rcfar_sat_view* view, double* out, int64_t ld_out,
+                                   rcfar_stream stream) {
+  if (!h || !view || !out || ld_out < view->cols) return RCFAR_ERR_INVALID_ARG;
+  rcfar_status st = check_view(h, view);
+  if (st != RCFAR_OK) return st;
+  DeviceGuard dg(h->device);
+  SatMapDev m;
+  std::memset(&m, 0, sizeof(m));
+  m.rows = view->rows;
+  m.cols = view->cols;
+  m.table = view->table;
+  m.ld_table = view->ld;
+  m.row_carry = reinterpret_cast<unsigned long long*>(view->row_carry);
+  m.col_carry = reinterpret_cast<unsigned long long*>(view->col_carry);
+  m.ld_carry = view->ld_carry;
+  m.scale_out = h->sat_scale;
+  return cuda_fail(launch_sat_materialize(m, view->mode, out, ld_out, (cudaStream_t)stream));
+}
+
+// ---- batched chain -----------------------------------------------------------
+
+rcfar_status rcfar_batch_bytes(int32_t M, int32_t N, const rcfar_pre_params* p, const rcfar_window* w,
+                               int64_t* bytes_out) {
+  if (!bytes_out || M <= 0 || N <= 0 || !valid_pre(p)) return RCFAR_ERR_INVALID_ARG;
+  rcfar_pre_params pf = *p;
+  if (pf.halo_c < 0) {
+    if (!w || !valid_window(w)) return RCFAR_ERR_INVALID_ARG;
+    pf.halo_c = w->guard_c + w->train_c;
+  }
+  rcfar_band b;
+  if (!band_of(N, &pf, &b)) return RCFAR_ERR_INVALID_ARG;
+  *bytes_out = (int64_t)(frame_data_bytes(M, N, b.cols) + frame_ctl_bytes(M, N, b.cols));
+  return RCFAR_OK;
+}
+
+rcfar_status rcfar_prepare(rcfar_handle h, const int32_t* Ns, int32_t n, const rcfar_pre_params* p) {
+  if (!h || (!Ns && n > 0) || n < 0 || !valid_pre(p)) return RCFAR_ERR_INVALID_ARG;
+  DeviceGuard dg(h->device);
+  for (int i = 0; i < n; ++i) {
+    rcfar_band b;
+    if (!band_of(Ns[i], p, &b)) return RCFAR_ERR_INVALID_ARG;
+    Twiddle tw;
+    rcfar_status st = get_plan(h, Ns[i], b.c0, b.cols, 0, &tw);
+    if (st != RCFAR_OK) return st;
+  }
+  return cuda_fail(cudaDeviceSynchronize());
+}
+
+rcfar_status rcfar_run_batch(rcfar_handle h, const rcfar_frame_desc* frames, int32_t n, const rcfar_pre_params* p,
+                             rcfar_stream stream) {
+  if (!h || (!frames && n > 0) || n < 0 || !valid_pre(p)) return RCFAR_ERR_INVALID_ARG;
+  if (n == 0) return RCFAR_OK;
+  if (n > h->cfg.max_frames) return RCFAR_ERR_UNSUPPORTED;
+  DeviceGuard dg(h->device);
+  cudaStream_t s = (cudaStream_t)stream;
+  // validate and size
+  std::vector<rcfar_band> bands(n);
+  size_t need_data = 0, need_ctl = 0;
+  for (int i = 0; i < n; ++i) {
+    const rcfar_frame_desc& f = frames[i];
+    if (!f.x || !f.det || f.M <= 0 || f.N <= 0 || f.ldx < f.N || !valid_window(&f.window) || p->mean_len > f.N)
+      return RCFAR_ERR_INVALID_ARG;
+    rcfar_pre_params pf = *p;
+    if (pf.halo_c < 0) pf.halo_c = f.window.guard_c + f.window.train_c;
+    if (!band_of(f.N, &pf, &bands[i])) return RCFAR_ERR_INVALID_ARG;
+    const int C = bands[i].cols;
+    if (f.ld_det < C || (f.thr && f.ld_thr < C) || (f.map && f.ld_map < C)) return RCFAR_ERR_INVALID_ARG;
+    if (f.M > h->cfg.max_rows || f.N > h->cfg.max_n ||
+        f.window.guard_r + f.window.train_r > h->cfg.max_window ||
+        f.window.guard_c + f.window.train_c > h->cfg.max_window)
+      return RCFAR_ERR_UNSUPPORTED;
+    need_ctl += frame_ctl_bytes(f.M, f.N, C);
+    need_data += frame_data_bytes(f.M, f.N, C);
+  }
+  if (need_ctl + need_data > h->batch_bytes) return RCFAR_ERR_OUT_OF_WORKSPACE;
+  // plans
+  std::vector<Twiddle> tws(n);
+  for (int i = 0; i < n; ++i) {
+    rcfar_status st = get_plan(h, frames[i].N, bands[i].c0, bands[i].cols, s, &tws[i]);
+    if (st != RCFAR_OK) return st;
+  }
+  Carver ctl(h->batch, need_ctl);
+  Carver data((char*)h->batch + need_ctl, h->batch_bytes - need_ctl);
+  if (cudaMemsetAsync(h->batch, 0, need_ctl, s) != cudaSuccess) return RCFAR_ERR_CUDA;
+
+  static thread_local PreBatch pb;
+  static thread_local SatBatch sb;
+  static thread_local CfarBatch cb;
+  for (int base = 0; base < n; base += kMaxBatch) {
+    const int cnt = std::min(kMaxBatch, n - base);
+    pb.n = cnt;
+    sb.n = cnt;
+    cb.n = cnt;
+    sb.ticket = h->sat_ticket;
+    sb.done = h->sat_done;
+    sb.gen = h->sat_gen;
+    sb.status = h->status;
+    int it_stats = 0, it_dft = 0, it_norm = 0, it_sat = 0, it_cfar = 0;
+    int cfar_mode_smem = 0;
+    for (int k = 0; k < cnt; ++k) {
+      const int i = base + k;
+      const rcfar_frame_desc& f = frames[i];
+      const rcfar_band& b = bands[i];
+      const int C = b.cols;
+      const PreGeom g = pre_geom(f.M, f.N, C);
+      PreFrameDev& F = pb.f[k];
+      F = make_pre_frame(f.x, f.M, f.N, f.ldx, b, (p->mean_len - 1) / 2, tws[i], g);
+      F.stats = data.take<float2>(f.N);
+      F.partial = data.take<float2>((size_t)g.n_chunks * f.N);
+      F.kpart = g.splitk > 1 ? data.take<float>((size_t)g.splitk * f.M * g.ldk) : nullptr;
+      float* map = f.map;
+      long long ld_map = f.ld_map;
+      if (!map) {
+        ld_map = round_up(C, 4);
+        map = data.take<float>((size_t)f.M * ld_map);
+      }
+      F.map = map;
+      F.ld_map = ld_map;
+      F.strip_cnt = ctl.take<unsigned>(g.n_strips);
+      F.tile_cnt = ctl.take<unsigned>((size_t)g.mtiles * g.ntiles);
+      unsigned* words = ctl.take<unsigned>(64);
+      F.ymax = words;
+      F.item_stats = it_stats;
+      F.item_dft = it_dft;
+      F.item_norm = it_norm;
+      it_stats += g.n_strips * g.n_chunks;
+      it_dft += g.mtiles * g.ntiles * g.splitk;
+      it_norm += g.n_norm;
+
+      const SatGeom sg = sat_geom(f.M, C);
+      SatMapDev& m = sb.m[k];
+      std::memset(&m, 0, sizeof(m));
+      m.map = map;
+      m.ld = ld_map;
+      m.rows = f.M;
+      m.cols = C;
+      m.in_scale = 1.0f;
+      const long long wr = f.window.guard_r + f.window.train_r, wc = f.window.guard_c + f.window.train_c;
+      m.max_cells = std::max<long long>((long long)kSatTileH * kSatTileW, (2 * wr + 1) * (2 * wc + 1));
+      m.bound = b.value_bound;
+      m.scale_log2 = sat_scale_for(b.value_bound, m.max_cells);
+      m.table = data.take<float>((size_t)f.M * sg.ld_table);
+      m.ld_table = sg.ld_table;
+      m.row_carry = data.take<unsigned long long>((size_t)sg.n_bands * sg.ld_carry);
+      m.agg = data.take<unsigned long long>((size_t)sg.n_bands * sg.ld_carry);
+      m.col_carry = data.take<unsigned long long>((size_t)sg.n_chunks * f.M);
+      m.ld_carry = sg.ld_carry;
+      m.flags = ctl.take<unsigned>((size_t)sg.n_bands * sg.n_chunks);
+      m.scale_out = reinterpret_cast<int*>(words + 1);
+      m.n_bands = sg.n_bands;
+      m.n_chunks = sg.n_chunks;
+      m.item0 = it_sat;
+      it_sat += sg.n_bands;
+      if (!F.stats || !F.partial || (g.splitk > 1 && !F.kpart) || !map || !m.table || !m.row_carry || !m.agg ||
+          !m.col_carry || !m.flags || !F.strip_cnt || !F.tile_cnt || !words)
+        return RCFAR_ERR_OUT_OF_WORKSPACE;
+
+      CfarMapDev& P = cb.m[k];
+      std::memset(&P, 0, sizeof(P));
+      P.table = m.table;
+      P.ld_table = m.ld_table;
+      P.row_carry = m.row_carry;
+      P.col_carry = m.col_carry;
+      P.ld_carry = m.ld_carry;
+      P.scale_dev = m.scale_out;
+      P.map = map;
+      P.ld_map = ld_map;
+      P.in_scale = 1.0f;
+      P.rows = f.M;
+      P.cols = C;
+      fill_cfar_window(P, &f.window, f.M, C, b.k_lo - b.c0, b.k_hi - b.c0);
+      P.det = f.det;
+      P.ld_det = f.ld_det;
+      P.thr = f.thr;
+      P.ld_thr = f.ld_thr;
+      // tile from this frame's own window (batch composition does not matter)
+      const CfarTile t = pick_cfar_tile(RCFAR_SAT_TILE_F32, P.wr, P.wc, std::min<size_t>(h->smem_optin, 200 * 1024));
+      if (t.bh == 0) return RCFAR_ERR_UNSUPPORTED;
+      P.bh = t.bh;
+      P.bw = t.bw;
+      P.tiles_x = (int)ceil_div(C, t.bw);
+      P.item0 = it_cfar;
+      it_cfar += P.tiles_x * (int)ceil_div(f.M, t.bh);
+      cfar_mode_smem = std::max<int>(cfar_mode_smem, (int)cfar_smem_bytes(RCFAR_SAT_TILE_F32, t.bh, t.bw, P.wr, P.wc));
+    }
+    sb.total = it_sat;
+    cudaError_t e = launch_colstats(pb, it_stats, s);
+    if (e == cudaSuccess) e = launch_band_dft(pb, it_dft, s);
+    if (e == cudaSuccess) e = launch_normalise(pb, it_norm, s);
+    if (e == cudaSuccess) e = launch_sat(sb, RCFAR_SAT_TILE_F32, RCFAR_MAP_F32, s);
+    if (e == cudaSuccess) e = launch_cfar(cb, RCFAR_SAT_TILE_F32, RCFAR_MAP_F32, it_cfar, (size_t)cfar_mode_smem, s);
+    if (e != cudaSuccess) return RCFAR_ERR_CUDA;
+  }
+  return RCFAR_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,103 @@
+"""The C ABI library on a machine without a GPU: it builds, loads, exports every
+symbol the header declares, and its host-only helpers agree with the oracle."""
+import math
+import os
+import re
+
+import numpy as np
+import pytest
+
+import oracle
+from oracle import cfar as ocfar
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def rc():
+    from paper_2012_11077_gb300 import build as b
+    b.build()
+    import paper_2012_11077_gb300 as pkg
+    pkg.lib()
+    return pkg
+
+
+def declared_symbols():
+    txt = open(os.path.join(ROOT, "include", "rcfar.h")).read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    return sorted(set(re.findall(r"\b(rcfar_[a-z_0-9]+)\s*\(", txt)))
+
+
+def test_exports_every_declared_symbol(rc):
+    names = declared_symbols()
+    assert len(names) >= 16
+    L = rc.lib()
+    for n in names:
+        assert hasattr(L, n), n
+    assert sorted(rc.EXPORTS) == names
+
+
+def test_alpha_and_n_ref_match_oracle(rc):
+    for tr, gd, pfa in [(8, 2, 1e-4), (16, 4, 1e-6), (4, 1, 1e-3), (1, 1, 1e-3), (12, 8, 1e-5)]:
+        w = rc.make_window(tr, tr, gd, gd, pfa)
+        nr = rc.rcfar_n_ref(w)
+        assert nr == ocfar.n_ref(tr, tr, gd, gd)
+        assert abs(rc.rcfar_alpha(nr, pfa) - ocfar.alpha(nr, pfa)) <= 1e-12 * ocfar.alpha(nr, pfa)
+    w = rc.make_window(3, 5, 1, 2, 1e-3)
+    assert rc.rcfar_n_ref(w) == ocfar.n_ref(3, 5, 1, 2)
+
+
+def test_band_plan_matches_oracle(rc):
+    for halo in (0, 5, 20):
+        p = rc.make_pre_params(20.0, 0.3, 0.8, 5, halo)
+        for N in list(range(5, 300)) + list(range(256, 4097, 7)) + [4000, 4096, 600]:
+            o = oracle.band_plan(N, 20.0, 0.3, 0.8, halo)
+            if o.cols < 1:  # nothing to store: rejected
+                with pytest.raises(rc.RcfarError):
+                    rc.rcfar_band_plan(N, p)
+                continue
+            b = rc.rcfar_band_plan(N, p)
+            assert (b.k_lo, b.k_hi, b.c0, b.c1) == (o.k_lo, o.k_hi, o.c0, o.c1), N
+            assert b.cols == o.cols and b.value_bound == N
+
+
+def test_sat_scale_bounds_region_sums(rc):
+    for bound, cells in [(1.0, 4096), (4096.0, 4096), (1e8, 1089), (3.0, 16641), (1e-20, 10)]:
+        s = rc.rcfar_sat_scale(bound, cells)
+        assert bound * cells * 2.0 ** s <= 2.0 ** 62
+        assert bound * cells * 2.0 ** (s + 2) > 2.0 ** 62 or s == 100  # tight within 4x
+
+
+def test_invalid_arguments_rejected_without_gpu(rc):
+    with pytest.raises(rc.RcfarError) as e:
+        rc.rcfar_alpha(0, 0.1)
+    assert e.value.status == rc.RCFAR_ERR_INVALID_ARG
+    with pytest.raises(rc.RcfarError):
+        rc.rcfar_alpha(16, 1.0)
+    with pytest.raises(rc.RcfarError):
+        rc.rcfar_band_plan(0, rc.make_pre_params())
+    with pytest.raises(rc.RcfarError) as e:
+        rc.rcfar_create(max_rows=0)
+    assert e.value.status == rc.RCFAR_ERR_INVALID_ARG
+    with pytest.raises(rc.RcfarError):
+        rc.rcfar_batch_bytes(10, 10, rc.make_pre_params(mean_len=4))
+    assert rc.status_string(rc.RCFAR_ERR_RANGE).startswith("map value")
+
+
+def test_batch_bytes_grows_with_frame(rc):
+    p = rc.make_pre_params(20.0, 0.3, 0.8, 5, 20)
+    a = rc.rcfar_batch_bytes(256, 512, p)
+    b = rc.rcfar_batch_bytes(1024, 4096, p)
+    assert 0 < a < b
+    # at least the band map, its table and the statistics
+    band = oracle.band_plan(4096, 20.0, halo=20)
+    assert b >= 1024 * band.cols * 8 + 4096 * 8
+
+
+def test_product_path_does_not_import_oracle():
+    pkg = os.path.join(ROOT, "paper_2012_11077_gb300")
+    for dirpath, _, files in os.walk(pkg):
+        for f in files:
+            if f.endswith((".py", ".cu", ".cuh", ".h")):
+                txt = open(os.path.join(dirpath, f)).read()
+                assert "import oracle" not in txt and "from oracle" not in txt, f

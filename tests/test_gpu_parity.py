@@ -1,0 +1,337 @@
+"""GPU parity: every kernel of the chain against the FP64 oracle, through the C ABI.
+
+Tolerances (from the stated targets):
+  * decisions: bit-exact, except CUTs with |CUT - T| / T < 1e-5 under the oracle,
+    which are counted and reported (near ties);
+  * float outputs (band map, thresholds): |gpu - oracle| <= 1e-4 * max(|oracle|,
+    1e-6 * max |oracle|) per element;
+  * table entries of integer-valued maps: exact.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from oracle import cfar as ocfar
+import synth
+from tests._golden import worked_example
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+REL = 1e-4
+MARGIN = 1e-5
+
+
+@pytest.fixture(scope="module")
+def rc():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2012_11077_gb300 import build as b
+    b.build()
+    import paper_2012_11077_gb300 as pkg
+    pkg.lib()
+    return pkg
+
+
+@pytest.fixture(scope="module")
+def h(rc):
+    hd = rc.rcfar_create(device=0, max_rows=8192, max_cols=8192, max_n=4096, max_window=40, max_frames=64,
+                         batch_bytes=1 << 30)
+    yield hd
+    rc.rcfar_destroy(hd)
+
+
+def dev_t(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def rel_err(g, o):
+    o = np.asarray(o, dtype=np.float64)
+    g = np.asarray(g, dtype=np.float64)
+    floor = 1e-6 * np.max(np.abs(o)) if o.size else 0.0
+    return np.abs(g - o) / np.maximum(np.abs(o), max(floor, 1e-300))
+
+
+def run_cfar(rc, h, P, win, mode, cut=None, dtype=torch.float32, exp2=0, bound=None):
+    rows, cols = P.shape
+    Pt = dev_t(P).to(dtype)
+    view = rc.rcfar_sat(h, Pt, value_bound=float(bound if bound is not None else 0.0), mode=mode, map_exp2=exp2)
+    det = torch.full((rows, cols), 7, dtype=torch.uint8, device="cuda")
+    thr = torch.full((rows, cols), -1.0, dtype=torch.float32, device="cuda")
+    lo, hi = cut if cut is not None else (0, cols - 1)
+    w = rc.make_window(*win)
+    rc.rcfar_cfar(h, view, Pt, w, lo, hi, det, thr, map_exp2=exp2)
+    st = rc.rcfar_get_error(h)
+    assert st == rc.RCFAR_OK, rc.status_string(st)
+    return det.cpu().numpy(), thr.cpu().numpy(), view
+
+
+# ------------------------------------------------------------------ eq. 3 table
+SAT_SHAPES = [(1, 1), (5, 7), (31, 127), (32, 128), (33, 129), (100, 300), (257, 383), (64, 1000)]
+
+
+@pytest.mark.parametrize("shape", SAT_SHAPES)
+@pytest.mark.parametrize("mode", [0, 1, 2])
+def test_sat_integer_map_exact(rc, h, shape, mode):
+    P = synth.integer_map(*shape, hi=16, seed=shape[0] * 1000 + shape[1])
+    Pt = dev_t(P)
+    view = rc.rcfar_sat(h, Pt, value_bound=16.0, mode=mode)
+    out = torch.empty(shape, dtype=torch.float64, device="cuda")
+    rc.rcfar_sat_materialize(h, view, out)
+    assert rc.rcfar_get_error(h) == rc.RCFAR_OK
+    np.testing.assert_array_equal(out.cpu().numpy(), ocfar.sat(P))
+
+
+@pytest.mark.parametrize("mode", [0, 1])
+def test_sat_float_map_error_bound(rc, h, mode):
+    P = synth.square_law_map(300, 700, n_targets=20, dyn_range_db=40.0, seed=3)
+    Pt = dev_t(P)
+    view = rc.rcfar_sat(h, Pt, value_bound=float(P.max()), mode=mode)
+    out = torch.empty(P.shape, dtype=torch.float64, device="cuda")
+    rc.rcfar_sat_materialize(h, view, out)
+    S = ocfar.sat(P.astype(np.float64))
+    err = np.abs(out.cpu().numpy() - S)
+    if mode == 1:
+        # exact sums of values quantised to 2^-s: at most cells * 2^-(s+1)
+        cells = np.arange(1, 301)[:, None] * np.arange(1, 701)[None, :]
+        assert np.all(err <= cells * 2.0 ** (-view.scale_log2 - 1) + 1e-9)
+    else:
+        # FP32 inside a 32 x 128 tile: bounded by the tile's own sum
+        tile_sum = P.reshape(-1).max() * 32 * 128
+        assert err.max() <= 64 * np.finfo(np.float32).eps * tile_sum
+
+
+def test_sat_auto_bound_matches_given_bound(rc, h):
+    P = synth.square_law_map(130, 260, n_targets=5, seed=4)
+    Pt = dev_t(P)
+    v1 = rc.rcfar_sat(h, Pt, value_bound=0.0, mode=1)
+    o1 = torch.empty(P.shape, dtype=torch.float64, device="cuda")
+    rc.rcfar_sat_materialize(h, v1, o1)
+    v2 = rc.rcfar_sat(h, Pt, value_bound=float(P.max()), mode=1)
+    o2 = torch.empty(P.shape, dtype=torch.float64, device="cuda")
+    rc.rcfar_sat_materialize(h, v2, o2)
+    assert rc.rcfar_get_error(h) == rc.RCFAR_OK
+    np.testing.assert_array_equal(o1.cpu().numpy(), o2.cpu().numpy())
+
+
+def test_range_error_reported(rc, h):
+    P = synth.square_law_map(64, 64, n_targets=0, seed=5)
+    P[10, 10] = np.nan
+    rc.rcfar_sat(h, dev_t(P), value_bound=100.0, mode=0)
+    assert rc.rcfar_get_error(h) == rc.RCFAR_ERR_RANGE
+    P[10, 10] = 1000.0  # above the stated bound
+    rc.rcfar_sat(h, dev_t(P), value_bound=100.0, mode=0)
+    assert rc.rcfar_get_error(h) == rc.RCFAR_ERR_RANGE
+    rc.rcfar_sat(h, dev_t(np.minimum(P, 50.0)), value_bound=100.0, mode=0)
+    assert rc.rcfar_get_error(h) == rc.RCFAR_OK
+
+
+def test_stale_view_rejected(rc, h):
+    P = dev_t(synth.integer_map(40, 40, seed=1))
+    v1 = rc.rcfar_sat(h, P, value_bound=16.0)
+    rc.rcfar_sat(h, P, value_bound=16.0)
+    det = torch.empty((40, 40), dtype=torch.uint8, device="cuda")
+    with pytest.raises(rc.RcfarError) as e:
+        rc.rcfar_cfar(h, v1, P, rc.make_window(2, 2, 1, 1, 1e-3), 0, 39, det)
+    assert e.value.status == rc.RCFAR_ERR_BAD_STATE
+
+
+# ------------------------------------------------------------------ CFAR, eqs. 1, 2, 4
+CFAR_CASES = [
+    ((64, 64), (8, 8, 2, 2, 1e-4), None),
+    ((300, 200), (4, 4, 1, 1, 1e-3), None),
+    ((129, 260), (16, 16, 4, 4, 1e-6), (30, 200)),
+    ((77, 301), (3, 5, 1, 2, 1e-2), None),
+    ((40, 33), (12, 12, 8, 8, 1e-3), None),   # larger window than map: zero CUTs
+    ((500, 150), (1, 1, 0, 0, 1e-1), (3, 140)),
+]
+
+
+def cfar_map(shape, seed):
+    P = synth.square_law_map(*shape, n_targets=max(1, shape[0] * shape[1] // 2000), dyn_range_db=30.0, seed=seed)
+    return P
+
+
+@pytest.mark.parametrize("shape,win,cut", CFAR_CASES)
+@pytest.mark.parametrize("mode", [0, 1, 2])
+def test_cfar_sat_parity(rc, h, shape, win, cut, mode):
+    P = cfar_map(shape, seed=shape[0] + shape[1])
+    det, thr, _ = run_cfar(rc, h, P, win, mode, cut=cut, bound=float(P.max()))
+    ref = ocfar.cfar_direct(P.astype(np.float64), *win, cut_cols=cut)
+    cmp = ocfar.compare_decisions(det, ref.det, P, ref.thr, ref.cut, margin=MARGIN)
+    assert cmp.mismatches == 0, cmp
+    assert np.all(det[~ref.cut] == 0) and np.all(thr[~ref.cut] == 0)
+    if ref.cut.any():
+        e = rel_err(thr[ref.cut], ref.thr[ref.cut])
+        assert e.max() <= (1e-4 if mode == 2 else 1e-6), e.max()
+
+
+@pytest.mark.parametrize("shape,win,cut", CFAR_CASES)
+def test_cfar_direct_parity(rc, h, shape, win, cut):
+    P = cfar_map(shape, seed=shape[0] * 3 + shape[1])
+    rows, cols = shape
+    det = torch.full((rows, cols), 7, dtype=torch.uint8, device="cuda")
+    thr = torch.full((rows, cols), -1.0, dtype=torch.float32, device="cuda")
+    lo, hi = cut if cut is not None else (0, cols - 1)
+    rc.rcfar_cfar_direct(h, dev_t(P), rc.make_window(*win), lo, hi, det, thr)
+    assert rc.rcfar_get_error(h) == rc.RCFAR_OK
+    ref = ocfar.cfar_direct(P.astype(np.float64), *win, cut_cols=cut)
+    cmp = ocfar.compare_decisions(det.cpu().numpy(), ref.det, P, ref.thr, ref.cut, margin=MARGIN)
+    assert cmp.mismatches == 0, cmp
+    if ref.cut.any():
+        assert rel_err(thr.cpu().numpy()[ref.cut], ref.thr[ref.cut]).max() <= 1e-5
+
+
+def test_cfar_fp16_storage(rc, h):
+    # FP16 map storage with a power-of-two scale: the decisions equal the oracle's
+    # on the same (FP16-rounded) values.
+    P = synth.square_law_map(200, 300, n_targets=30, dyn_range_db=60.0, seed=21)
+    exp2 = int(math.ceil(math.log2(P.max() / 60000.0)))
+    P16 = (P / 2.0 ** exp2).astype(np.float16)
+    Pq = P16.astype(np.float64) * 2.0 ** exp2
+    win = (8, 8, 2, 2, 1e-4)
+    Pt = dev_t(P16)
+    view = rc.rcfar_sat(h, Pt, value_bound=float(Pq.max()), mode=0, map_exp2=exp2)
+    det = torch.empty((200, 300), dtype=torch.uint8, device="cuda")
+    thr = torch.empty((200, 300), dtype=torch.float32, device="cuda")
+    rc.rcfar_cfar(h, view, Pt, rc.make_window(*win), 0, 299, det, thr, map_exp2=exp2)
+    assert rc.rcfar_get_error(h) == rc.RCFAR_OK
+    ref = ocfar.cfar_direct(Pq, *win)
+    cmp = ocfar.compare_decisions(det.cpu().numpy(), ref.det, Pq, ref.thr, ref.cut, margin=MARGIN)
+    assert cmp.mismatches == 0, cmp
+
+
+def test_worked_example(rc, h):
+    P, win, sref, det_ref = worked_example()
+    for mode in (0, 1, 2):
+        det, thr, _ = run_cfar(rc, h, P.astype(np.float32), win, mode, bound=128.0)
+        np.testing.assert_array_equal(det, det_ref)
+        a = ocfar.alpha(16, win[4])
+        np.testing.assert_allclose(thr[2:5, 2:5], a * sref / 16.0, rtol=1e-6)
+
+
+def test_planted_target_and_scale_invariance(rc, h):
+    rng = np.random.default_rng(5)
+    P = rng.exponential(size=(96, 160)).astype(np.float32)
+    P[50, 70] += 300.0
+    det, _, _ = run_cfar(rc, h, P, (8, 8, 2, 2, 1e-6), 0, bound=float(P.max()))
+    assert det[50, 70] == 1 and det.sum() == 1
+    for k in (-10, 12):
+        d2, _, _ = run_cfar(rc, h, P * np.float32(2.0 ** k), (8, 8, 2, 2, 1e-6), 0,
+                            bound=float(P.max()) * 2.0 ** k)
+        np.testing.assert_array_equal(d2, det)
+
+
+# ------------------------------------------------------------------ Sec. II.A preprocessing
+PRE_CASES = [("small", synth.small_frame_case(0)), ("large", synth.large_frame_case(0)),
+             ("ragged", synth.ChainCase(synth.FrameSpec(M=129, N=601, n_targets=3, seed=7),
+                                        synth.Window(4, 4, 1, 1, 1e-3))),
+             ("tiny", synth.ChainCase(synth.FrameSpec(M=3, N=64, n_targets=1, seed=8), synth.Window(1, 1, 0, 0, 1e-2)))]
+
+
+@pytest.mark.parametrize("name,case", PRE_CASES)
+def test_preprocess_and_chain_parity(rc, h, name, case):
+    X = synth.radar_frame(case.spec)
+    w = case.window
+    P_o, band_o, res_o = oracle.run_chain(X, synth.FS_HZ, case.mean_len, w.train_r, w.train_c, w.guard_r, w.guard_c,
+                                          w.pfa)
+    params = rc.make_pre_params(synth.FS_HZ, mean_len=case.mean_len, halo_c=case.halo_c)
+    band = rc.rcfar_band_plan(case.spec.N, params)
+    assert (band.c0, band.c1, band.k_lo, band.k_hi) == (band_o.c0, band_o.c1, band_o.k_lo, band_o.k_hi)
+    P = torch.empty((case.spec.M, band.cols + 3), dtype=torch.float32, device="cuda")[:, :band.cols]
+    rc.rcfar_preprocess(h, dev_t(X), params, P)
+    Pg = P.cpu().numpy()
+    e = rel_err(Pg, P_o)
+    assert e.max() <= REL, e.max()
+    view = rc.rcfar_sat(h, P, value_bound=band.value_bound)
+    det = torch.empty((case.spec.M, band.cols), dtype=torch.uint8, device="cuda")
+    thr = torch.empty((case.spec.M, band.cols), dtype=torch.float32, device="cuda")
+    rc.rcfar_cfar(h, view, P, rc.make_window(w.train_r, w.train_c, w.guard_r, w.guard_c, w.pfa),
+                  band.k_lo - band.c0, band.k_hi - band.c0, det, thr)
+    assert rc.rcfar_get_error(h) == rc.RCFAR_OK
+    cmp = ocfar.compare_decisions(det.cpu().numpy(), res_o.det, P_o, res_o.thr, res_o.cut, margin=MARGIN)
+    assert cmp.mismatches == 0, cmp
+    if res_o.cut.any():
+        assert rel_err(thr.cpu().numpy()[res_o.cut], res_o.thr[res_o.cut]).max() <= REL
+
+
+def test_preprocess_strided_input(rc, h):
+    case = synth.ChainCase(synth.FrameSpec(M=200, N=300, n_targets=2, seed=9), synth.Window(4, 4, 1, 1, 1e-3))
+    X = synth.radar_frame(case.spec)
+    buf = torch.zeros((200, 301), dtype=torch.float32, device="cuda")  # odd leading dimension
+    buf[:, :300] = dev_t(X)
+    params = rc.make_pre_params(synth.FS_HZ, halo_c=5)
+    band = rc.rcfar_band_plan(300, params)
+    P = torch.empty((200, band.cols), dtype=torch.float32, device="cuda")
+    rc.rcfar_preprocess(h, buf[:, :300], params, P)
+    P_o, _ = oracle.preprocess_frame(X, synth.FS_HZ, 5, halo=5)
+    assert rel_err(P.cpu().numpy(), P_o).max() <= REL
+
+
+# ------------------------------------------------------------------ batched chain
+def test_run_batch_parity_and_mix_invariance(rc, h):
+    cases = synth.mixed_batch_cases(10, seed=3, m_range=(64, 300), n_range=(256, 1200))
+    # one halo for the whole batch: the largest column half-width
+    halo = max(c.halo_c for c in cases)
+    params = rc.make_pre_params(synth.FS_HZ, mean_len=5, halo_c=halo)
+    frames, outs, refs = [], [], []
+    for c in cases:
+        X = synth.radar_frame(c.spec)
+        band = rc.rcfar_band_plan(c.spec.N, params)
+        x = dev_t(X)
+        det = torch.full((c.spec.M, band.cols), 9, dtype=torch.uint8, device="cuda")
+        thr = torch.empty((c.spec.M, band.cols), dtype=torch.float32, device="cuda")
+        mp = torch.empty((c.spec.M, band.cols), dtype=torch.float32, device="cuda")
+        w = c.window
+        win = rc.make_window(w.train_r, w.train_c, w.guard_r, w.guard_c, w.pfa)
+        frames.append(rc.frame_desc(x, win, det, thr, mp))
+        outs.append((x, det, thr, mp, win, band))
+        P_o, band_o = oracle.preprocess_frame(X, synth.FS_HZ, 5, halo=halo)
+        res_o = oracle.cfar_chain(P_o, band_o, w.train_r, w.train_c, w.guard_r, w.guard_c, w.pfa)
+        refs.append((P_o, res_o))
+    rc.rcfar_run_batch(h, frames, params)
+    assert rc.rcfar_get_error(h) == rc.RCFAR_OK
+    total_ties = 0
+    for (x, det, thr, mp, win, band), (P_o, res_o) in zip(outs, refs):
+        assert rel_err(mp.cpu().numpy(), P_o).max() <= REL
+        cmp = ocfar.compare_decisions(det.cpu().numpy(), res_o.det, P_o, res_o.thr, res_o.cut, margin=MARGIN)
+        assert cmp.mismatches == 0, cmp
+        total_ties += cmp.near_ties
+    # each frame alone gives bit-identical outputs
+    for i in (0, 3, 9):
+        x, det, thr, mp, win, band = outs[i]
+        det1 = torch.empty_like(det)
+        thr1 = torch.empty_like(thr)
+        mp1 = torch.empty_like(mp)
+        rc.rcfar_run_batch(h, [rc.frame_desc(x, win, det1, thr1, mp1)], params)
+        assert torch.equal(det1, det) and torch.equal(thr1, thr) and torch.equal(mp1, mp)
+    # and reversed order in the batch changes nothing
+    dets2 = []
+    frames2 = []
+    for (x, det, thr, mp, win, band) in reversed(outs):
+        d2 = torch.empty_like(det)
+        dets2.append((d2, det))
+        frames2.append(rc.frame_desc(x, win, d2))
+    rc.rcfar_run_batch(h, frames2, params)
+    for d2, det in dets2:
+        assert torch.equal(d2, det)
+
+
+def test_run_batch_workspace_limit(rc):
+    small = rc.rcfar_create(device=0, max_rows=1024, max_cols=512, max_n=4096, max_window=20, max_frames=8,
+                            batch_bytes=1 << 20)
+    try:
+        c = synth.large_frame_case(0)
+        params = rc.make_pre_params(synth.FS_HZ, halo_c=c.halo_c)
+        band = rc.rcfar_band_plan(c.spec.N, params)
+        x = torch.zeros((c.spec.M, c.spec.N), dtype=torch.float32, device="cuda")
+        det = torch.empty((c.spec.M, band.cols), dtype=torch.uint8, device="cuda")
+        win = rc.make_window(16, 16, 4, 4, 1e-6)
+        with pytest.raises(rc.RcfarError) as e:
+            rc.rcfar_run_batch(small, [rc.frame_desc(x, win, det)], params)
+        assert e.value.status == rc.RCFAR_ERR_OUT_OF_WORKSPACE
+    finally:
+        rc.rcfar_destroy(small)
