@@ -197,7 +197,9 @@ rcfar_status rcfar_sat(rcfar_handle h, const void* map, int32_t dtype, int32_t m
                        int32_t cols, int64_t ld, float value_bound, int32_t mode,
                        rcfar_sat_view* view_out, rcfar_stream stream);
 
-/* eqs. 1, 2, 4: 2D CA-CFAR on a table from rcfar_sat and its map. For every
+/* eqs. 1, 2, 4: 2D CA-CFAR on a table from rcfar_sat and its map. For an
+ * I64 table the map may be NULL: the CUT value then comes from the table
+ * itself as the sum over the 1x1 region (exact fixed point). For every
  * interior CUT (outer rectangle inside the map) whose column lies in
  * [cut_c_lo, cut_c_hi]: S_ref = A(outer) - A(guard), each region sum from four
  * table lookups A = L1 + L4 - (L2 + L3); T = alpha * S_ref / n_ref;
@@ -225,7 +227,7 @@ rcfar_status rcfar_sat_materialize(rcfar_handle h, const rcfar_sat_view* view, d
 
 /* ---- batched path ------------------------------------------------------ */
 
-/* Whole chain (rcfar_preprocess -> rcfar_sat(TILE_F32) -> rcfar_cfar with the
+/* Whole chain (rcfar_preprocess -> rcfar_sat(I64) -> rcfar_cfar with the
  * band's CUT columns) for n frames of uneven size and window in a handful of
  * launches over all frames. frames is a HOST array of n descriptors; their
  * pointers are device pointers. Each frame's results are identical whatever
@@ -240,6 +242,21 @@ rcfar_status rcfar_batch_bytes(int32_t M, int32_t N, const rcfar_pre_params* p, 
 /* Builds the twiddle tables a batch of these sizes needs ahead of time, so
  * that rcfar_run_batch can be captured in a CUDA graph (no allocation inside). */
 rcfar_status rcfar_prepare(rcfar_handle h, const int32_t* Ns, int32_t n, const rcfar_pre_params* p);
+
+/* ---- tracing ----------------------------------------------------------- */
+
+/* Per-kernel device time of the handle's launches (CUDA events around each
+ * launch, on the launching stream). Not usable inside CUDA-graph capture. */
+typedef struct rcfar_trace_entry {
+  char name[32];     /* kernel family: colstats, band_dft, normalise, sat, cfar, cfar_direct, ... */
+  int64_t launches;
+  double total_ms;
+} rcfar_trace_entry;
+/* Starts (on != 0) or stops recording; starting clears earlier records. */
+rcfar_status rcfar_trace_enable(rcfar_handle h, int32_t on);
+/* Waits for the recorded launches and returns one entry per kernel family
+ * (out: host array of max_entries; *n_out receives the number written). */
+rcfar_status rcfar_trace_read(rcfar_handle h, rcfar_trace_entry* out, int32_t max_entries, int32_t* n_out);
 
 /* ---- errors ------------------------------------------------------------ */
 

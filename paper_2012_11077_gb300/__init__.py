@@ -37,6 +37,7 @@ EXPORTS = (
     "rcfar_create", "rcfar_destroy", "rcfar_alpha", "rcfar_n_ref", "rcfar_band_plan", "rcfar_sat_scale",
     "rcfar_status_string", "rcfar_preprocess", "rcfar_sat", "rcfar_cfar", "rcfar_cfar_direct",
     "rcfar_sat_materialize", "rcfar_run_batch", "rcfar_batch_bytes", "rcfar_prepare", "rcfar_get_error",
+    "rcfar_trace_enable", "rcfar_trace_read",
 )
 
 
@@ -72,6 +73,10 @@ class rcfar_sat_view(ctypes.Structure):
                 ("tile_h", ctypes.c_int32), ("tile_w", ctypes.c_int32), ("scale_log2", ctypes.c_int32),
                 ("table", ctypes.c_void_p), ("ld", ctypes.c_int64), ("row_carry", ctypes.c_void_p),
                 ("col_carry", ctypes.c_void_p), ("ld_carry", ctypes.c_int64), ("generation", ctypes.c_uint64)]
+
+
+class rcfar_trace_entry(ctypes.Structure):
+    _fields_ = [("name", ctypes.c_char * 32), ("launches", ctypes.c_int64), ("total_ms", ctypes.c_double)]
 
 
 class rcfar_frame_desc(ctypes.Structure):
@@ -112,6 +117,8 @@ def lib() -> ctypes.CDLL:
                                   ctypes.POINTER(I64)],
             "rcfar_prepare": [P, ctypes.POINTER(I32), I32, ctypes.POINTER(rcfar_pre_params)],
             "rcfar_get_error": [P, P],
+            "rcfar_trace_enable": [P, I32],
+            "rcfar_trace_read": [P, ctypes.POINTER(rcfar_trace_entry), I32, ctypes.POINTER(I32)],
         }
         for name, args in sig.items():
             fn = getattr(L, name)
@@ -221,7 +228,7 @@ def rcfar_preprocess(h: int, x, params: rcfar_pre_params, map_out, stream=None) 
     return band
 
 
-def rcfar_sat(h: int, map_t, value_bound: float = 0.0, mode: int = RCFAR_SAT_TILE_F32, map_exp2: int = 0,
+def rcfar_sat(h: int, map_t, value_bound: float = 0.0, mode: int = RCFAR_SAT_I64, map_exp2: int = 0,
               stream=None) -> rcfar_sat_view:
     import torch
     dtype = RCFAR_MAP_F16 if map_t.dtype == torch.float16 else RCFAR_MAP_F32
@@ -235,8 +242,9 @@ def rcfar_sat(h: int, map_t, value_bound: float = 0.0, mode: int = RCFAR_SAT_TIL
 def rcfar_cfar(h: int, view: rcfar_sat_view, map_t, window: rcfar_window, cut_c_lo: int, cut_c_hi: int, det,
                thr=None, map_exp2: int = 0, stream=None):
     import torch
-    dtype = RCFAR_MAP_F16 if map_t.dtype == torch.float16 else RCFAR_MAP_F32
-    _check(lib().rcfar_cfar(h, ctypes.byref(view), _ptr(map_t), dtype, int(map_exp2), _ld(map_t),
+    dtype = RCFAR_MAP_F16 if map_t is not None and map_t.dtype == torch.float16 else RCFAR_MAP_F32
+    _check(lib().rcfar_cfar(h, ctypes.byref(view), _ptr(map_t), dtype, int(map_exp2),
+                            _ld(map_t) if map_t is not None else 0,
                             ctypes.byref(window), int(cut_c_lo), int(cut_c_hi), _ptr(det), _ld(det), _ptr(thr),
                             _ld(thr) if thr is not None else 0, _stream(stream)), "rcfar_cfar")
 
@@ -268,3 +276,15 @@ def rcfar_run_batch(h: int, frames: Sequence[rcfar_frame_desc], params: rcfar_pr
 def rcfar_prepare(h: int, Ns: Sequence[int], params: rcfar_pre_params):
     arr = (ctypes.c_int32 * len(Ns))(*[int(n) for n in Ns])
     _check(lib().rcfar_prepare(h, arr, len(Ns), ctypes.byref(params)), "rcfar_prepare")
+
+
+def rcfar_trace_enable(h: int, on: bool = True):
+    _check(lib().rcfar_trace_enable(h, 1 if on else 0), "rcfar_trace_enable")
+
+
+def rcfar_trace_read(h: int) -> dict:
+    """{kernel family: (launches, total_ms)} of the launches recorded since tracing started."""
+    arr = (rcfar_trace_entry * 32)()
+    n = ctypes.c_int32()
+    _check(lib().rcfar_trace_read(h, arr, 32, ctypes.byref(n)), "rcfar_trace_read")
+    return {arr[i].name.decode(): (int(arr[i].launches), float(arr[i].total_ms)) for i in range(n.value)}

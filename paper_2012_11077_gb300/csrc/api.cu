@@ -16,6 +16,9 @@ using namespace rcfar;
 namespace {
 
 constexpr int kStatsRows = 64;  // rows per column-statistics CTA
+// The batched chain stores the exact 64-bit table: its decisions are exact
+// for every window (the FP32 tile-local table loses small windows' sums).
+constexpr int kBatchSatMode = RCFAR_SAT_I64;
 
 inline long long ceil_div(long long a, long long b) { return (a + b - 1) / b; }
 inline long long round_up(long long a, long long b) { return ceil_div(a, b) * b; }
@@ -88,23 +91,53 @@ size_t sat_bytes(int rows, int cols, int mode) {
   SatGeom g = sat_geom(rows, cols);
   size_t b = 0;
   b += align256((size_t)rows * g.ld_table * (mode == RCFAR_SAT_I64 ? 8 : 4));
-  b += 2 * align256((size_t)g.n_bands * g.ld_carry * 8);     // row_carry + agg
+  b += 2 * align256((size_t)g.n_bands * g.ld_carry * 8);     // row_carry + v_agg
+  b += 2 * align256((size_t)g.n_bands * g.n_chunks * kSatTileH * 8);  // h_agg + h_inc
   b += align256((size_t)g.n_chunks * rows * 8);               // col_carry
   return b;
 }
 size_t sat_flag_bytes(int rows, int cols) {
   SatGeom g = sat_geom(rows, cols);
-  return align256((size_t)g.n_bands * g.n_chunks * 4);
+  return 2 * align256((size_t)g.n_bands * g.n_chunks * 4);   // h_flags + v_flags
+}
+
+// Carve the look-back arrays of one table from a data and a control region.
+struct SatArrays {
+  unsigned long long *row_carry, *v_agg, *h_agg, *h_inc, *col_carry;
+  unsigned *h_flags, *v_flags;
+};
+template <typename CarveData, typename CarveCtl>
+bool carve_sat(CarveData& data, CarveCtl& ctl, int rows, int cols, SatArrays* a) {
+  SatGeom g = sat_geom(rows, cols);
+  a->row_carry = data.template take<unsigned long long>((size_t)g.n_bands * g.ld_carry);
+  a->v_agg = data.template take<unsigned long long>((size_t)g.n_bands * g.ld_carry);
+  a->h_agg = data.template take<unsigned long long>((size_t)g.n_bands * g.n_chunks * kSatTileH);
+  a->h_inc = data.template take<unsigned long long>((size_t)g.n_bands * g.n_chunks * kSatTileH);
+  a->col_carry = data.template take<unsigned long long>((size_t)g.n_chunks * rows);
+  a->h_flags = ctl.template take<unsigned>((size_t)g.n_bands * g.n_chunks);
+  a->v_flags = ctl.template take<unsigned>((size_t)g.n_bands * g.n_chunks);
+  return a->row_carry && a->v_agg && a->h_agg && a->h_inc && a->col_carry && a->h_flags && a->v_flags;
+}
+void set_sat_arrays(SatMapDev& m, const SatArrays& a) {
+  m.row_carry = a.row_carry;
+  m.v_agg = a.v_agg;
+  m.h_agg = a.h_agg;
+  m.h_inc = a.h_inc;
+  m.col_carry = a.col_carry;
+  m.h_flags = a.h_flags;
+  m.v_flags = a.v_flags;
 }
 
 struct CfarTile {
   int bh, bw;
 };
 
+// Output tile of the SAT CFAR: the widest candidate whose halo fits in
+// shared memory, with halo rows at most 256 columns wide.
 CfarTile pick_cfar_tile(int mode, int wr, int wc, size_t smem_cap) {
   const CfarTile cand[] = {{32, 64}, {32, 32}, {16, 32}, {16, 16}, {8, 16}};
   for (const CfarTile& t : cand)
-    if (cfar_smem_bytes(mode, t.bh, t.bw, wr, wc) <= smem_cap) return t;
+    if (cfar_smem_bytes(mode, t.bh, t.bw, wr, wc) <= smem_cap && t.bw + 2 * wc + 1 <= 256) return t;
   return {0, 0};
 }
 
@@ -132,16 +165,15 @@ struct rcfar_ctx {
   // per-step preprocessing
   float2* stats = nullptr;
   float2* partial = nullptr;
+  float* rowpart = nullptr;
+  float2* strip_ab = nullptr;
   unsigned* strip_cnt = nullptr;
   unsigned* tile_cnt = nullptr;
   float* kpart = nullptr;
   size_t kpart_floats = 0;
   // per-step SAT
   void* sat_table = nullptr;
-  unsigned long long* row_carry = nullptr;
-  unsigned long long* agg = nullptr;
-  unsigned long long* col_carry = nullptr;
-  unsigned* sat_flags = nullptr;
+  SatArrays sat{};
   uint64_t sat_generation = 0;
   // batch arena
   void* batch = nullptr;
@@ -149,7 +181,38 @@ struct rcfar_ctx {
   // twiddle plans
   std::mutex mu;
   std::map<std::tuple<int, int, int>, Twiddle> plans;
+  // tracing
+  bool trace_on = false;
+  struct TraceRec {
+    const char* name;
+    cudaEvent_t a, b;
+  };
+  std::vector<TraceRec> trace_pool;
+  size_t trace_used = 0;
 };
+
+namespace {
+// Brackets one kernel launch with events while tracing is on.
+struct TraceScope {
+  rcfar_ctx* h;
+  rcfar_ctx::TraceRec* rec = nullptr;
+  cudaStream_t s;
+  TraceScope(rcfar_ctx* hh, const char* name, cudaStream_t st) : h(hh), s(st) {
+    if (!h->trace_on) return;
+    if (h->trace_used == h->trace_pool.size()) {
+      rcfar_ctx::TraceRec r{name, nullptr, nullptr};
+      if (cudaEventCreate(&r.a) != cudaSuccess || cudaEventCreate(&r.b) != cudaSuccess) return;
+      h->trace_pool.push_back(r);
+    }
+    rec = &h->trace_pool[h->trace_used++];
+    rec->name = name;
+    cudaEventRecord(rec->a, s);
+  }
+  ~TraceScope() {
+    if (rec) cudaEventRecord(rec->b, s);
+  }
+};
+}  // namespace
 
 namespace {
 
@@ -265,9 +328,11 @@ static size_t frame_data_bytes(int M, int N, int C) {
   size_t t = 0;
   t += align256((size_t)N * sizeof(float2));                       // stats
   t += align256((size_t)g.n_chunks * N * sizeof(float2));          // partial
+  t += align256((size_t)g.n_strips * M * sizeof(float));           // rowpart
+  t += align256((size_t)g.n_strips * sizeof(float2));              // strip_ab
   t += g.splitk > 1 ? align256((size_t)g.splitk * M * g.ldk * 4) : 0;
   t += align256((size_t)M * round_up(C, 4) * 4);                   // map
-  t += sat_bytes(M, C, RCFAR_SAT_TILE_F32);
+  t += sat_bytes(M, C, kBatchSatMode);
   return t;
 }
 static size_t frame_ctl_bytes(int M, int N, int C) {
@@ -346,6 +411,8 @@ rcfar_status rcfar_create(const rcfar_config* cfg, rcfar_handle* out) {
   total += 256;                                   // control words
   total += align256((size_t)Nm * sizeof(float2));  // stats
   total += align256((size_t)max_chunks * Nm * sizeof(float2));
+  total += align256((size_t)max_strips * R * sizeof(float));
+  total += align256((size_t)max_strips * sizeof(float2));
   total += align256((size_t)max_strips * 4);
   total += align256((size_t)max_tiles * 4);
   total += align256(kpart * 4);
@@ -368,6 +435,8 @@ rcfar_status rcfar_create(const rcfar_config* cfg, rcfar_handle* out) {
   h->ymax = ctl + 6;
   h->stats = cv.take<float2>(Nm);
   h->partial = cv.take<float2>((size_t)max_chunks * Nm);
+  h->rowpart = cv.take<float>((size_t)max_strips * R);
+  h->strip_ab = cv.take<float2>(max_strips);
   h->strip_cnt = cv.take<unsigned>(max_strips);
   h->tile_cnt = cv.take<unsigned>(max_tiles);
   h->kpart = cv.take<float>(kpart);
@@ -375,10 +444,7 @@ rcfar_status rcfar_create(const rcfar_config* cfg, rcfar_handle* out) {
   {
     SatGeom g = sat_geom(R, Cm);
     h->sat_table = cv.take<char>((size_t)R * g.ld_table * 8);
-    h->row_carry = cv.take<unsigned long long>((size_t)g.n_bands * g.ld_carry);
-    h->agg = cv.take<unsigned long long>((size_t)g.n_bands * g.ld_carry);
-    h->col_carry = cv.take<unsigned long long>((size_t)g.n_chunks * R);
-    h->sat_flags = cv.take<unsigned>((size_t)g.n_bands * g.n_chunks);
+    carve_sat(cv, cv, R, Cm, &h->sat);
   }
   const unsigned one = 1u;
   cudaMemcpy(h->sat_gen, &one, sizeof(one), cudaMemcpyHostToDevice);
@@ -405,10 +471,48 @@ rcfar_status rcfar_destroy(rcfar_handle h) {
   DeviceGuard g(h->device);
   cudaError_t e = cudaDeviceSynchronize();
   for (auto& kv : h->plans) cudaFree(kv.second.W);
+  for (auto& r : h->trace_pool) {
+    cudaEventDestroy(r.a);
+    cudaEventDestroy(r.b);
+  }
   if (h->ws) cudaFree(h->ws);
   if (h->batch) cudaFree(h->batch);
   delete h;
   return cuda_fail(e);
+}
+
+rcfar_status rcfar_trace_enable(rcfar_handle h, int32_t on) {
+  if (!h) return RCFAR_ERR_INVALID_ARG;
+  if (on) h->trace_used = 0;
+  h->trace_on = on != 0;
+  return RCFAR_OK;
+}
+
+rcfar_status rcfar_trace_read(rcfar_handle h, rcfar_trace_entry* out, int32_t max_entries, int32_t* n_out) {
+  if (!h || !n_out || (max_entries > 0 && !out) || max_entries < 0) return RCFAR_ERR_INVALID_ARG;
+  DeviceGuard dg(h->device);
+  std::vector<rcfar_trace_entry> acc;
+  for (size_t i = 0; i < h->trace_used; ++i) {
+    const rcfar_ctx::TraceRec& r = h->trace_pool[i];
+    if (cudaEventSynchronize(r.b) != cudaSuccess) return RCFAR_ERR_CUDA;
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, r.a, r.b) != cudaSuccess) return RCFAR_ERR_CUDA;
+    size_t j = 0;
+    for (; j < acc.size(); ++j)
+      if (std::strncmp(acc[j].name, r.name, sizeof(acc[j].name)) == 0) break;
+    if (j == acc.size()) {
+      rcfar_trace_entry e;
+      std::memset(&e, 0, sizeof(e));
+      std::strncpy(e.name, r.name, sizeof(e.name) - 1);
+      acc.push_back(e);
+    }
+    acc[j].launches += 1;
+    acc[j].total_ms += ms;
+  }
+  const int n = (int)std::min<size_t>(acc.size(), (size_t)max_entries);
+  for (int i = 0; i < n; ++i) out[i] = acc[i];
+  *n_out = n;
+  return RCFAR_OK;
 }
 
 rcfar_status rcfar_get_error(rcfar_handle h, rcfar_stream stream) {
@@ -453,6 +557,8 @@ rcfar_status rcfar_preprocess(rcfar_handle h, const float* x, int32_t M, int32_t
   F = make_pre_frame(x, M, N, ldx, b, (p->mean_len - 1) / 2, tw, g);
   F.stats = h->stats;
   F.partial = h->partial;
+  F.rowpart = h->rowpart;
+  F.strip_ab = h->strip_ab;
   F.strip_cnt = h->strip_cnt;
   F.ymax = h->ymax;
   F.map = map;
@@ -462,9 +568,19 @@ rcfar_status rcfar_preprocess(rcfar_handle h, const float* x, int32_t M, int32_t
   F.item_stats = 0;
   F.item_dft = 0;
   F.item_norm = 0;
-  cudaError_t e = launch_colstats(pb, g.n_strips * g.n_chunks, s);
-  if (e == cudaSuccess) e = launch_band_dft(pb, g.mtiles * g.ntiles * g.splitk, s);
-  if (e == cudaSuccess) e = launch_normalise(pb, g.n_norm, s);
+  cudaError_t e;
+  {
+    TraceScope t(h, "colstats", s);
+    e = launch_colstats(pb, g.n_strips * g.n_chunks, s);
+  }
+  if (e == cudaSuccess) {
+    TraceScope t(h, "band_dft", s);
+    e = launch_band_dft(pb, g.mtiles * g.ntiles * g.splitk, s);
+  }
+  if (e == cudaSuccess) {
+    TraceScope t(h, "normalise", s);
+    e = launch_normalise(pb, g.n_norm, s);
+  }
   if (e != cudaSuccess) return RCFAR_ERR_CUDA;
   if (band_out) *band_out = b;
   return RCFAR_OK;
@@ -487,7 +603,7 @@ rcfar_status rcfar_sat(rcfar_handle h, const void* map, int32_t dtype, int32_t m
 
   static thread_local SatBatch sb;
   sb.n = 1;
-  sb.total = g.n_bands;
+  sb.total = g.n_bands * g.n_chunks;
   sb.ticket = h->sat_ticket;
   sb.done = h->sat_done;
   sb.gen = h->sat_gen;
@@ -507,6 +623,7 @@ rcfar_status rcfar_sat(rcfar_handle h, const void* map, int32_t dtype, int32_t m
     m.bound = value_bound;
     m.scale_log2 = sat_scale_for(value_bound, max_cells);
   } else {
+    TraceScope t(h, "map_max", s);
     cudaError_t e = launch_map_max(map, dtype, in_scale, rows, cols, ld, h->map_bound, s);
     if (e != cudaSuccess) return RCFAR_ERR_CUDA;
     m.scale_log2 = kScaleFromDevice;
@@ -514,16 +631,17 @@ rcfar_status rcfar_sat(rcfar_handle h, const void* map, int32_t dtype, int32_t m
   }
   m.table = h->sat_table;
   m.ld_table = g.ld_table;
-  m.row_carry = h->row_carry;
-  m.agg = h->agg;
-  m.col_carry = h->col_carry;
+  set_sat_arrays(m, h->sat);
   m.ld_carry = g.ld_carry;
-  m.flags = h->sat_flags;
   m.scale_out = h->sat_scale;
   m.n_bands = g.n_bands;
   m.n_chunks = g.n_chunks;
   m.item0 = 0;
-  cudaError_t e = launch_sat(sb, mode, dtype, s);
+  cudaError_t e;
+  {
+    TraceScope t(h, "sat", s);
+    e = launch_sat(sb, mode, dtype, s);
+  }
   if (e != cudaSuccess) return RCFAR_ERR_CUDA;
 
   rcfar_sat_view v;
@@ -536,8 +654,8 @@ rcfar_status rcfar_sat(rcfar_handle h, const void* map, int32_t dtype, int32_t m
   v.scale_log2 = (m.scale_log2 == kScaleFromDevice) ? INT32_MIN : m.scale_log2;
   v.table = h->sat_table;
   v.ld = g.ld_table;
-  v.row_carry = reinterpret_cast<int64_t*>(h->row_carry);
-  v.col_carry = reinterpret_cast<int64_t*>(h->col_carry);
+  v.row_carry = reinterpret_cast<int64_t*>(h->sat.row_carry);
+  v.col_carry = reinterpret_cast<int64_t*>(h->sat.col_carry);
   v.ld_carry = g.ld_carry;
   v.generation = ++h->sat_generation;
   *view_out = v;
@@ -566,9 +684,11 @@ static void fill_cfar_window(CfarMapDev& P, const rcfar_window* w, int rows, int
 rcfar_status rcfar_cfar(rcfar_handle h, const rcfar_sat_view* view, const void* map, int32_t dtype, int32_t map_exp2,
                         int64_t ld_map, const rcfar_window* w, int32_t cut_c_lo, int32_t cut_c_hi, uint8_t* det,
                         int64_t ld_det, float* thr, int64_t ld_thr, rcfar_stream stream) {
-  if (!h || !view || !map || !det || !valid_window(w)) return RCFAR_ERR_INVALID_ARG;
+  if (!h || !view || !det || !valid_window(w)) return RCFAR_ERR_INVALID_ARG;
+  if (!map && view->mode != RCFAR_SAT_I64) return RCFAR_ERR_INVALID_ARG;
   if (dtype != RCFAR_MAP_F32 && dtype != RCFAR_MAP_F16) return RCFAR_ERR_INVALID_ARG;
-  if (ld_map < view->cols || ld_det < view->cols || (thr && ld_thr < view->cols)) return RCFAR_ERR_INVALID_ARG;
+  if ((map && ld_map < view->cols) || ld_det < view->cols || (thr && ld_thr < view->cols))
+    return RCFAR_ERR_INVALID_ARG;
   rcfar_status st = check_view(h, view);
   if (st != RCFAR_OK) return st;
   if (w->guard_r + w->train_r > h->cfg.max_window || w->guard_c + w->train_c > h->cfg.max_window)
@@ -602,6 +722,7 @@ rcfar_status rcfar_cfar(rcfar_handle h, const rcfar_sat_view* view, const void* 
   P.tiles_x = (int)ceil_div(view->cols, t.bw);
   const int blocks = P.tiles_x * (int)ceil_div(view->rows, t.bh);
   P.item0 = 0;
+  TraceScope tr(h, "cfar", s);
   cudaError_t e = launch_cfar(cb, view->mode, dtype, blocks,
                               cfar_smem_bytes(view->mode, t.bh, t.bw, P.wr, P.wc), s);
   return cuda_fail(e);
@@ -639,6 +760,7 @@ rcfar_status rcfar_cfar_direct(rcfar_handle h, const float* map, int32_t rows, i
   P.bw = bw;
   P.tiles_x = (int)ceil_div(cols, bw);
   const int blocks = P.tiles_x * (int)ceil_div(rows, bh);
+  TraceScope tr(h, "cfar_direct", s);
   return cuda_fail(launch_cfar_direct(P, blocks, cfar_direct_smem_bytes(bh, bw, P.wr, P.wc), s));
 }
 
@@ -751,6 +873,8 @@ rcfar_status rcfar_run_batch(rcfar_handle h, const rcfar_frame_desc* frames, int
       F = make_pre_frame(f.x, f.M, f.N, f.ldx, b, (p->mean_len - 1) / 2, tws[i], g);
       F.stats = data.take<float2>(f.N);
       F.partial = data.take<float2>((size_t)g.n_chunks * f.N);
+      F.rowpart = data.take<float>((size_t)g.n_strips * f.M);
+      F.strip_ab = data.take<float2>(g.n_strips);
       F.kpart = g.splitk > 1 ? data.take<float>((size_t)g.splitk * f.M * g.ldk) : nullptr;
       float* map = f.map;
       long long ld_map = f.ld_map;
@@ -783,20 +907,19 @@ rcfar_status rcfar_run_batch(rcfar_handle h, const rcfar_frame_desc* frames, int
       m.max_cells = std::max<long long>((long long)kSatTileH * kSatTileW, (2 * wr + 1) * (2 * wc + 1));
       m.bound = b.value_bound;
       m.scale_log2 = sat_scale_for(b.value_bound, m.max_cells);
-      m.table = data.take<float>((size_t)f.M * sg.ld_table);
+      m.table = data.take<long long>((size_t)f.M * sg.ld_table);
       m.ld_table = sg.ld_table;
-      m.row_carry = data.take<unsigned long long>((size_t)sg.n_bands * sg.ld_carry);
-      m.agg = data.take<unsigned long long>((size_t)sg.n_bands * sg.ld_carry);
-      m.col_carry = data.take<unsigned long long>((size_t)sg.n_chunks * f.M);
+      SatArrays sa;
+      const bool sat_ok = carve_sat(data, ctl, f.M, C, &sa);
+      set_sat_arrays(m, sa);
       m.ld_carry = sg.ld_carry;
-      m.flags = ctl.take<unsigned>((size_t)sg.n_bands * sg.n_chunks);
       m.scale_out = reinterpret_cast<int*>(words + 1);
       m.n_bands = sg.n_bands;
       m.n_chunks = sg.n_chunks;
       m.item0 = it_sat;
-      it_sat += sg.n_bands;
-      if (!F.stats || !F.partial || (g.splitk > 1 && !F.kpart) || !map || !m.table || !m.row_carry || !m.agg ||
-          !m.col_carry || !m.flags || !F.strip_cnt || !F.tile_cnt || !words)
+      it_sat += sg.n_bands * sg.n_chunks;
+      if (!F.stats || !F.partial || !F.rowpart || !F.strip_ab || (g.splitk > 1 && !F.kpart) || !map || !m.table ||
+          !sat_ok || !F.strip_cnt || !F.tile_cnt || !words)
         return RCFAR_ERR_OUT_OF_WORKSPACE;
 
       CfarMapDev& P = cb.m[k];
@@ -818,21 +941,37 @@ rcfar_status rcfar_run_batch(rcfar_handle h, const rcfar_frame_desc* frames, int
       P.thr = f.thr;
       P.ld_thr = f.ld_thr;
       // tile from this frame's own window (batch composition does not matter)
-      const CfarTile t = pick_cfar_tile(RCFAR_SAT_TILE_F32, P.wr, P.wc, std::min<size_t>(h->smem_optin, 200 * 1024));
+      const CfarTile t = pick_cfar_tile(kBatchSatMode, P.wr, P.wc, std::min<size_t>(h->smem_optin, 200 * 1024));
       if (t.bh == 0) return RCFAR_ERR_UNSUPPORTED;
       P.bh = t.bh;
       P.bw = t.bw;
       P.tiles_x = (int)ceil_div(C, t.bw);
       P.item0 = it_cfar;
       it_cfar += P.tiles_x * (int)ceil_div(f.M, t.bh);
-      cfar_mode_smem = std::max<int>(cfar_mode_smem, (int)cfar_smem_bytes(RCFAR_SAT_TILE_F32, t.bh, t.bw, P.wr, P.wc));
+      cfar_mode_smem = std::max<int>(cfar_mode_smem, (int)cfar_smem_bytes(kBatchSatMode, t.bh, t.bw, P.wr, P.wc));
     }
     sb.total = it_sat;
-    cudaError_t e = launch_colstats(pb, it_stats, s);
-    if (e == cudaSuccess) e = launch_band_dft(pb, it_dft, s);
-    if (e == cudaSuccess) e = launch_normalise(pb, it_norm, s);
-    if (e == cudaSuccess) e = launch_sat(sb, RCFAR_SAT_TILE_F32, RCFAR_MAP_F32, s);
-    if (e == cudaSuccess) e = launch_cfar(cb, RCFAR_SAT_TILE_F32, RCFAR_MAP_F32, it_cfar, (size_t)cfar_mode_smem, s);
+    cudaError_t e;
+    {
+      TraceScope t(h, "colstats", s);
+      e = launch_colstats(pb, it_stats, s);
+    }
+    if (e == cudaSuccess) {
+      TraceScope t(h, "band_dft", s);
+      e = launch_band_dft(pb, it_dft, s);
+    }
+    if (e == cudaSuccess) {
+      TraceScope t(h, "normalise", s);
+      e = launch_normalise(pb, it_norm, s);
+    }
+    if (e == cudaSuccess) {
+      TraceScope t(h, "sat", s);
+      e = launch_sat(sb, kBatchSatMode, RCFAR_MAP_F32, s);
+    }
+    if (e == cudaSuccess) {
+      TraceScope t(h, "cfar", s);
+      e = launch_cfar(cb, kBatchSatMode, RCFAR_MAP_F32, it_cfar, (size_t)cfar_mode_smem, s);
+    }
     if (e != cudaSuccess) return RCFAR_ERR_CUDA;
   }
   return RCFAR_OK;

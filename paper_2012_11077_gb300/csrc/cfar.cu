@@ -21,6 +21,8 @@ namespace {
 
 typedef unsigned long long u64;
 
+constexpr int kHaloGroups = 8;  // halo rows up to 256 columns wide
+
 __device__ __forceinline__ float ld_map_val(const float* p, float) { return __ldg(p); }
 __device__ __forceinline__ float ld_map_val(const __half* p, float scale) { return __half2float(__ldg(p)) * scale; }
 
@@ -44,15 +46,20 @@ __global__ void __launch_bounds__(256) k_cfar(const __grid_constant__ CfarBatch 
   if constexpr (MODE != RCFAR_SAT_NAIVE_F32) s = __ldcg(P.scale_dev);
   const float scalef = ldexpf(1.0f, s);
 
-  // table over rows r0-wr-1 .. r0+bh+wr-1 and cols c0-wc-1 .. c0+bw+wc-1
+  // table over rows r0-wr-1 .. r0+bh+wr-1 and cols c0-wc-1 .. c0+bw+wc-1;
+  // each lane issues all of its loads of a halo row before storing any
+  // (HC <= 32 * kHaloGroups), so a warp keeps several requests in flight
   for (int hr = warp; hr < HR; hr += 8) {
     const int r = r0 - wr - 1 + hr;
     const bool row_ok = r >= 0 && r < P.rows;
     const int band = r >> 5;  // kSatTileH == 32
-    for (int hc = lane; hc < HC; hc += 32) {
+    SV vals[kHaloGroups];
+#pragma unroll
+    for (int u = 0; u < kHaloGroups; ++u) {
+      const int hc = lane + 32 * u;
       const int c = c0 - wc - 1 + hc;
       SV val = SV(0);
-      if (row_ok && c >= 0 && c < P.cols) {
+      if (hc < HC && row_ok && c >= 0 && c < P.cols) {
         if constexpr (MODE == RCFAR_SAT_TILE_F32) {
           const float l = __ldg(reinterpret_cast<const float*>(P.table) + (long long)r * P.ld_table + c);
           u64 q = (u64)__float2ll_rn(l * scalef);
@@ -65,7 +72,12 @@ __global__ void __launch_bounds__(256) k_cfar(const __grid_constant__ CfarBatch 
           val = __ldg(reinterpret_cast<const float*>(P.table) + (long long)r * P.ld_table + c);
         }
       }
-      S[hr * HC + hc] = val;
+      vals[u] = val;
+    }
+#pragma unroll
+    for (int u = 0; u < kHaloGroups; ++u) {
+      const int hc = lane + 32 * u;
+      if (hc < HC) S[hr * HC + hc] = vals[u];
     }
   }
   __syncthreads();
@@ -87,10 +99,25 @@ __global__ void __launch_bounds__(256) k_cfar(const __grid_constant__ CfarBatch 
       const SV outer = (S[ra * HC + ca] + S[rb * HC + cb]) - (S[ra * HC + cb] + S[rb * HC + ca]);
       const SV guard = (S[rc * HC + cg] + S[rd * HC + cd]) - (S[rc * HC + cd] + S[rd * HC + cg]);
       const SV ref = outer - guard;
-      if constexpr (MODE == RCFAR_SAT_NAIVE_F32) t = ref * kk;
-      else t = (float)(long long)ref * kk;
-      const float cut = ld_map_val(map + (long long)r * P.ld_map + c, P.in_scale);
-      d = cut > t ? 1 : 0;
+      if constexpr (MODE == RCFAR_SAT_I64) {
+        // T = (alpha / n_ref) * S_ref in fixed-point units; the CUT value comes
+        // from the map when one is given (one coalesced load instead of four
+        // table lookups), else from the exact table (eq. 4 on the 1x1 region)
+        const float ts = (float)(long long)ref * P.kthr;
+        t = ts * ldexpf(1.0f, -s);
+        if (map != nullptr) {
+          d = ld_map_val(map + (long long)r * P.ld_map + c, P.in_scale) > t ? 1 : 0;
+        } else {
+          const int r1 = rr + wr + 1, c1 = cc + wc + 1;
+          const u64 qc = (S[r1 * HC + c1] + S[(r1 - 1) * HC + c1 - 1]) - (S[(r1 - 1) * HC + c1] + S[r1 * HC + c1 - 1]);
+          d = (float)(long long)qc > ts ? 1 : 0;
+        }
+      } else {
+        if constexpr (MODE == RCFAR_SAT_NAIVE_F32) t = ref * kk;
+        else t = (float)(long long)ref * kk;
+        const float cut = ld_map_val(map + (long long)r * P.ld_map + c, P.in_scale);
+        d = cut > t ? 1 : 0;
+      }
     }
     P.det[(long long)r * P.ld_det + c] = d;
     if (P.thr) P.thr[(long long)r * P.ld_thr + c] = t;

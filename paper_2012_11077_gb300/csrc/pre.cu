@@ -2,10 +2,15 @@
 //
 //   k_colstats : per trace n, the least-squares line over fast time m
 //                (a_n = mean, b_n = slope about mbar) -- "DC-shift removal and
-//                linear trend subtraction".
+//                linear trend subtraction"; also the pieces of each row's
+//                slow-time mean of y (see k_band_dft).
 //   k_band_dft : fused detrend + slow-time mean filter + max|y| + band DFT
 //                (a GEMM of y [M x N] with the twiddle matrix [N x 2C]) +
 //                magnitude. CUDA-core FP32 with split-K for small frames.
+//                Each row's mean c_m over n is subtracted before the product
+//                and N c_m added back to bin 0 only: a constant contributes
+//                to no other bin, and removing it keeps the FP32 rounding of
+//                the large per-range DC offsets out of the small bins.
 //   k_normalise: divide the map by max|y| ("then normalized"); the DFT is
 //                linear, so scaling its magnitude equals transforming y/max|y|.
 //   k_twiddles : twiddle matrix W[n][2j] = cos(2 pi t/N), W[n][2j+1] = -sin,
@@ -45,6 +50,19 @@ __device__ __forceinline__ void load4_masked(const float* row, int col, int n, b
   }
 }
 
+// Weight of sample j in sum_n y[n] for the truncated centred mean filter:
+// w_j = sum over outputs n whose window holds j of 1 / |window(n)| (1 inside).
+__device__ __forceinline__ float mean_weight(int j, int N, int h) {
+  if (j >= N) return 0.f;
+  if (j >= 2 * h && j <= N - 1 - 2 * h) return 1.f;
+  float w = 0.f;
+  for (int n = max(0, j - h); n <= min(N - 1, j + h); ++n) {
+    const int cnt = min(n + h, N - 1) - max(n - h, 0) + 1;
+    w += 1.f / (float)cnt;
+  }
+  return w;
+}
+
 // grid: for every frame, n_strips x n_chunks CTAs of 256 threads.
 // Thread (g = warp, lane) sums rows g, g+8, ... of its chunk for 4 columns.
 __global__ void __launch_bounds__(256) k_colstats(const __grid_constant__ PreBatch b) {
@@ -59,16 +77,24 @@ __global__ void __launch_bounds__(256) k_colstats(const __grid_constant__ PreBat
   const int r1 = min(F.M, r0 + F.rows_per_chunk);
   const bool vec = ((F.ldx & 3) == 0) && ((reinterpret_cast<uintptr_t>(F.x) & 15) == 0);
 
+  float wj[4];
+#pragma unroll
+  for (int k = 0; k < 4; ++k) wj[k] = mean_weight(col0 + k, F.N, F.h);
   float sx[4] = {0.f, 0.f, 0.f, 0.f}, smx[4] = {0.f, 0.f, 0.f, 0.f};
   for (int m = r0 + g; m < r1; m += 8) {
     float v[4];
     load4_masked(F.x + (long long)m * F.ldx, col0, F.N, vec, v);
     const float dm = (float)m - F.mbar;
+    float rs = 0.f;
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
       sx[k] += v[k];
       smx[k] = fmaf(dm, v[k], smx[k]);
+      rs = fmaf(wj[k], v[k], rs);
     }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) rs += __shfl_xor_sync(0xffffffffu, rs, o);
+    if (lane == 0) F.rowpart[(long long)strip * F.M + m] = rs;
   }
   __shared__ float2 red[8][kStatsStrip];
   __shared__ bool is_last;
@@ -94,8 +120,10 @@ __global__ void __launch_bounds__(256) k_colstats(const __grid_constant__ PreBat
   __syncthreads();
   if (is_last) {
     __threadfence();
+    __shared__ float2 ab[kStatsStrip];
     if (threadIdx.x < kStatsStrip) {
       const int c = strip * kStatsStrip + threadIdx.x;
+      float2 st = make_float2(0.f, 0.f);
       if (c < F.N) {
         float2 t = make_float2(0.f, 0.f);
         for (int ch = 0; ch < F.n_chunks; ++ch) {  // fixed order: deterministic
@@ -103,10 +131,22 @@ __global__ void __launch_bounds__(256) k_colstats(const __grid_constant__ PreBat
           t.x += p.x;
           t.y += p.y;
         }
-        F.stats[c] = make_float2(t.x * F.inv_M, t.y * F.inv_D);
+        st = make_float2(t.x * F.inv_M, t.y * F.inv_D);
+        F.stats[c] = st;
       }
+      const float w = mean_weight(c, F.N, F.h);
+      ab[threadIdx.x] = make_float2(w * st.x, w * st.y);
     }
-    if (threadIdx.x == 0) F.strip_cnt[strip] = 0u;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      float2 t = make_float2(0.f, 0.f);
+      for (int i = 0; i < kStatsStrip; ++i) {
+        t.x += ab[i].x;
+        t.y += ab[i].y;
+      }
+      F.strip_ab[strip] = t;
+      F.strip_cnt[strip] = 0u;
+    }
   }
   if (local == 0 && threadIdx.x == 0) *F.ymax = 0u;
 }
@@ -138,14 +178,36 @@ __global__ void __launch_bounds__(256) k_band_dft(const __grid_constant__ PreBat
   float (*Xs)[kDftBK + 2 * kMaxMeanHalf + 1] =
       reinterpret_cast<float (*)[kDftBK + 2 * kMaxMeanHalf + 1]>(dft_smem + kDftBK * kDftBM + kDftBK * kDftBN);
   __shared__ float red_max[8];
+  __shared__ float cm[kDftBM];
 
   const int tid = threadIdx.x;
+  // row means of y: (sum_j w_j x[m,j] - sum_j w_j a_j - (m - mbar) sum_j w_j b_j) / N
+  if (tid < kDftBM) {
+    const int m = m0 + tid;
+    float c = 0.f;
+    if (m < F.M) {
+      float rsum = 0.f, A = 0.f, Bv = 0.f;
+      for (int sI = 0; sI < F.n_strips; ++sI) {  // fixed order: deterministic
+        rsum += __ldg(&F.rowpart[(long long)sI * F.M + m]);
+        const float2 ab = __ldg(&F.strip_ab[sI]);
+        A += ab.x;
+        Bv += ab.y;
+      }
+      c = (rsum - A - ((float)m - F.mbar) * Bv) / (float)F.N;
+    }
+    cm[tid] = c;
+  }
+  __syncthreads();
   const int tm = tid >> 4, tn = tid & 15;
-  float acc[8][4];
+  // two-level accumulation: each K step of 32 samples sums into `part`,
+  // which is then added into `acc` with a compensation term (Kahan), so the
+  // rounding error does not grow with the large oscillating partial sums of
+  // strongly modulated rows
+  float acc[8][4], comp[8][4];
 #pragma unroll
   for (int i = 0; i < 8; ++i)
 #pragma unroll
-    for (int j = 0; j < 4; ++j) acc[i][j] = 0.f;
+    for (int j = 0; j < 4; ++j) acc[i][j] = comp[i][j] = 0.f;
   float ymax = 0.f;
 
   for (int n0 = kbeg; n0 < kend; n0 += kDftBK) {
@@ -185,11 +247,17 @@ __global__ void __launch_bounds__(256) k_band_dft(const __grid_constant__ PreBat
           const int lo = max(n - h, 0), hi = min(n + h, F.N - 1);
           y = s / (float)(hi - lo + 1);
           ymax = fmaxf(ymax, fabsf(y));
+          y -= cm[r];
         }
         As[k][r] = y;
       }
     }
     __syncthreads();
+    float part[8][4];
+#pragma unroll
+    for (int i = 0; i < 8; ++i)
+#pragma unroll
+      for (int j = 0; j < 4; ++j) part[i][j] = 0.f;
 #pragma unroll 8
     for (int k = 0; k < kDftBK; ++k) {
       const float4 a0 = *reinterpret_cast<const float4*>(&As[k][tm * 8]);
@@ -200,8 +268,17 @@ __global__ void __launch_bounds__(256) k_band_dft(const __grid_constant__ PreBat
 #pragma unroll
       for (int i = 0; i < 8; ++i)
 #pragma unroll
-        for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(a[i], bv[j], acc[i][j]);
+        for (int j = 0; j < 4; ++j) part[i][j] = fmaf(a[i], bv[j], part[i][j]);
     }
+#pragma unroll
+    for (int i = 0; i < 8; ++i)
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const float y = part[i][j] - comp[i][j];
+        const float t = acc[i][j] + y;
+        comp[i][j] = __fsub_rn(__fsub_rn(t, acc[i][j]), y);
+        acc[i][j] = t;
+      }
   }
   (void)XW;
 
@@ -227,7 +304,9 @@ __global__ void __launch_bounds__(256) k_band_dft(const __grid_constant__ PreBat
       for (int p = 0; p < 2; ++p) {
         const int col = j0 + tn * 4 + 2 * p;
         if (col < twoC) {
-          const float re = acc[i][2 * p], im = acc[i][2 * p + 1];
+          float re = acc[i][2 * p];
+          const float im = acc[i][2 * p + 1];
+          if (col == 0 && F.c0 == 0) re = fmaf((float)F.N, cm[tm * 8 + i], re);  // bin 0 gets the mean back
           F.map[(long long)m * F.ld_map + (col >> 1)] = sqrtf(fmaf(re, re, im * im));
         }
       }
@@ -267,6 +346,7 @@ __global__ void __launch_bounds__(256) k_band_dft(const __grid_constant__ PreBat
       re += v.x;
       im += v.y;
     }
+    if (col == 0 && F.c0 == 0) re = fmaf((float)F.N, cm[r], re);  // bin 0 gets the mean back
     F.map[(long long)m * F.ld_map + (col >> 1)] = sqrtf(fmaf(re, re, im * im));
   }
   if (tid == 0) F.tile_cnt[rem] = 0u;

@@ -46,6 +46,8 @@ struct PreFrameDev {
   long long ldw;
   float2* stats;        // [N] (a_n, b_n) of the fast-time line fit
   float2* partial;      // [n_chunks][N] partial sums (sum x, sum (m-mbar) x)
+  float* rowpart;       // [n_strips][M] partial row sums sum_j w_j x[m, j]
+  float2* strip_ab;     // [n_strips] (sum_j w_j a_j, sum_j w_j b_j) over the strip
   unsigned* strip_cnt;  // [n_strips] arrival counters (self-resetting)
   unsigned* ymax;       // float bits of max |y| over the frame
   float* map;           // [M][ld_map] band map (unnormalised until k_normalise)
@@ -75,20 +77,25 @@ struct SatMapDev {
   long long max_cells;   // largest region (cells) the scale must cover
   void* table;           // float (TILE_F32, NAIVE) or int64 (I64) [rows][ld_table]
   long long ld_table;
-  unsigned long long* row_carry;  // [n_bands][ld_carry] inclusive band values
-  unsigned long long* agg;        // [n_bands][ld_carry] band aggregates
-  unsigned long long* col_carry;  // [n_chunks][rows]
+  // vertical carries: per (band, column) -- band aggregate and inclusive value
+  unsigned long long* v_agg;      // [n_bands][ld_carry]
+  unsigned long long* row_carry;  // [n_bands][ld_carry] = S(last row of band, c)
   long long ld_carry;
-  unsigned* flags;       // [n_bands][n_chunks]
+  // horizontal carries: per (tile, band row) -- row totals, aggregate and inclusive
+  unsigned long long* h_agg;      // [n_bands * n_chunks][32]
+  unsigned long long* h_inc;      // [n_bands * n_chunks][32]
+  unsigned long long* col_carry;  // [n_chunks][rows] band-local sums left of the tile
+  unsigned* h_flags;     // [n_bands * n_chunks]
+  unsigned* v_flags;     // [n_bands * n_chunks]
   int* scale_out;        // device slot receiving the scale used
   int n_bands, n_chunks;
-  int item0;
+  int item0;             // first tile ticket of this map
 };
 
 struct SatBatch {
   int n;
-  int total;         // CTAs in the launch (bands over all maps)
-  unsigned* ticket;  // dynamic band ticket (self-resetting)
+  int total;         // CTAs in the launch (tiles over all maps)
+  unsigned* ticket;  // dynamic tile ticket (self-resetting)
   unsigned* done;    // CTAs finished (self-resetting)
   unsigned* gen;     // launch generation tag of the look-back flags
   int* status;

@@ -1,18 +1,21 @@
 // Summed-area table of a CFAR input map (paper eq. 3), one pass over the map.
 //
-// Decomposition: the map is cut into bands of kSatTileH rows, one CTA per
-// band (taken in ticket order), and each band into chunks of kSatTileW
-// columns processed left to right. For cell (r, c) in band b, chunk j:
-//   S(r, c) = L(r, c) + RC_b(c) + CC_j(r)
+// The map is cut into tiles of kSatTileH x kSatTileW cells (band b = tile
+// row, chunk j = tile column), one CTA per tile, taken in row-major ticket
+// order. For cell (r, c) of tile (b, j):
+//   S(r, c) = L(r, c) + CC_j(r) + RC_b(c)
 //   L      : table of the tile relative to its own origin (tile-local)
-//   RC_b(c): S(first row of b - 1, c)       -- the global table on the row
-//            above the band; an exclusive scan over bands, resolved with a
-//            decoupled look-back on per-(band, chunk) flags
-//   CC_j(r): sum over band rows <= r and columns left of chunk j -- kept
-//            inside the CTA as running row totals.
+//   CC_j(r): sum over band rows <= r and columns left of the tile
+//   RC_b(c): S(first row of band b - 1, c), the table on the row above
+// Both carries are exclusive scans across tiles, resolved with decoupled
+// look-backs: horizontally over the row totals of the tiles to the left
+// (vectors of kSatTileH values), then vertically over the column aggregates
+// of the tiles above (vectors of kSatTileW values). Each tile publishes its
+// aggregate before it looks back, and waits only on tiles with smaller
+// tickets, so the chains stay short and every wait ends.
 // Carries are 64-bit fixed point q = round(x * 2^s) added modulo 2^64
 // (exact; every region sum below 2^63 comes out exact even if S wraps).
-//   TILE_F32 : stores L in FP32 plus RC (as the band-inclusive values) and CC.
+//   TILE_F32 : stores L in FP32, RC (as each band's inclusive values) and CC.
 //   I64      : stores S itself in fixed point (L exact as well).
 //   NAIVE_F32: FP32 everywhere, stores S in FP32.
 // Within a tile, row prefixes use warp shuffles (32 lanes x 4 columns) and
@@ -110,6 +113,21 @@ __device__ __forceinline__ void st_flag(unsigned* p, unsigned v) {
   asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
 
+// Poll a look-back flag until it carries this launch's generation and a
+// published state; gives up after kSpinLimit polls, records the timeout and
+// returns 0xffffffff.
+__device__ __forceinline__ unsigned wait_flag(const unsigned* fp, unsigned gen, int* status) {
+  for (unsigned it = 0;; ++it) {
+    const unsigned f = ld_flag(fp);
+    if ((f >> 2) == gen && (f & 3u) != 0u) return f;
+    if (it >= kSpinLimit) {
+      atomicOr(status, kStatusTimeout);
+      return 0xffffffffu;
+    }
+    __nanosleep(32);
+  }
+}
+
 template <typename Acc>
 __device__ __forceinline__ Acc ld_carry(const u64* p) {
   const u64 v = __ldcg(p);
@@ -132,7 +150,8 @@ __global__ void __launch_bounds__(256) k_sat(const __grid_constant__ SatBatch B)
   __shared__ unsigned s_item, s_gen;
   __shared__ Loc s_wt[8][kSatTileW];
   __shared__ Acc s_wc[8][kSatTileW];
-  __shared__ Acc s_wq[8];
+  __shared__ Acc s_rq[kSatTileH];
+  __shared__ Acc s_cc[kSatTileH];
   __shared__ Acc s_rc[kSatTileW];
 
   const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
@@ -145,8 +164,10 @@ __global__ void __launch_bounds__(256) k_sat(const __grid_constant__ SatBatch B)
   const unsigned gen = s_gen & 0x3fffffffu;
   const int mi = find_item(B.m, B.n, item, &SatMapDev::item0);
   const SatMapDev& Mp = B.m[mi];
-  const int band = item - Mp.item0;
-  const int r0 = band * kSatTileH;
+  const int tile = item - Mp.item0;
+  const int b = tile / Mp.n_chunks, j = tile - b * Mp.n_chunks;
+  const int r0 = b * kSatTileH;
+  const int cbase = j * kSatTileW + lane * 4;
   const InT* map = reinterpret_cast<const InT*>(Mp.map);
   const bool vec = ((Mp.ld & 3) == 0) &&
                    ((reinterpret_cast<uintptr_t>(map) & (std::is_same<InT, float>::value ? 15 : 7)) == 0);
@@ -157,110 +178,134 @@ __global__ void __launch_bounds__(256) k_sat(const __grid_constant__ SatBatch B)
     bound = __ldcg(Mp.bound_dev);
     s = sat_scale_for(bound, Mp.max_cells);
   }
-  if (item == Mp.item0 && tid == 0 && Mp.scale_out) *Mp.scale_out = s;
+  if (tile == 0 && tid == 0 && Mp.scale_out) *Mp.scale_out = s;
   const float scalef = ldexpf(1.0f, s);
 
-  bool bad = false;
-  Acc runq[4];
+  // ---- load and quantise the tile (warp w: rows 4w..4w+3, lane: 4 columns)
+  float v[4][4];
 #pragma unroll
-  for (int i = 0; i < 4; ++i) runq[i] = Acc(0);
+  for (int i = 0; i < 4; ++i) {
+    const int r = r0 + w * 4 + i;
+    if (r < Mp.rows) {
+      load_row4<InT>(map + (long long)r * Mp.ld, cbase, Mp.cols, vec, Mp.in_scale, v[i]);
+    } else {
+#pragma unroll
+      for (int k = 0; k < 4; ++k) v[i][k] = 0.f;
+    }
+  }
+  bool bad = false;
+  Acc q[4][4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      bad |= !(fabsf(v[i][k]) <= bound);  // NaN fails too
+      if constexpr (std::is_same<Acc, float>::value) q[i][k] = v[i][k];
+      else q[i][k] = (u64)__float2ll_rn(v[i][k] * scalef);
+    }
 
-  float vn[4][4];
-  auto load_chunk = [&](int j, float (&v)[4][4]) {
-    const int c = j * kSatTileW + lane * 4;
+  // ---- tile-local table
+  Loc L[4][4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      if constexpr (std::is_same<Loc, float>::value) L[i][k] = v[i][k];
+      else L[i][k] = q[i][k];
+    }
+  tile_prefix<Loc>(L, s_wt, w, lane);
+
+  if constexpr (MODE == RCFAR_SAT_TILE_F32) {
+    float* out = reinterpret_cast<float*>(Mp.table);
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
       const int r = r0 + w * 4 + i;
-      if (r < Mp.rows) {
-        load_row4<InT>(map + (long long)r * Mp.ld, c, Mp.cols, vec, Mp.in_scale, v[i]);
+      if (r >= Mp.rows) continue;
+      float* o = out + (long long)r * Mp.ld_table + cbase;
+      if (cbase + 3 < Mp.cols) {
+        *reinterpret_cast<float4*>(o) = make_float4(L[i][0], L[i][1], L[i][2], L[i][3]);
       } else {
 #pragma unroll
-        for (int k = 0; k < 4; ++k) v[i][k] = 0.f;
+        for (int k = 0; k < 4; ++k)
+          if (cbase + k < Mp.cols) o[k] = L[i][k];
       }
     }
-  };
-  load_chunk(0, vn);
+  }
 
-  for (int j = 0; j < Mp.n_chunks; ++j) {
-    float v[4][4];
+  // ---- row totals (exact) and column sums (exact) of the tile
 #pragma unroll
-    for (int i = 0; i < 4; ++i)
+  for (int i = 0; i < 4; ++i) {
+    const Acc t = warp_sum<Acc>(q[i][0] + q[i][1] + q[i][2] + q[i][3]);
+    if (lane == i) s_rq[w * 4 + i] = t;
+  }
+  if constexpr (MODE == RCFAR_SAT_I64) {
+    // the exact tile table's last row is the column prefix itself
+    if (w == 7) {
 #pragma unroll
-      for (int k = 0; k < 4; ++k) v[i][k] = vn[i][k];
-    if (j + 1 < Mp.n_chunks) load_chunk(j + 1, vn);
-    const int cbase = j * kSatTileW + lane * 4;
-
-    // quantise (and check the bound; NaN fails the comparison)
-    Acc q[4][4];
-#pragma unroll
-    for (int i = 0; i < 4; ++i)
-#pragma unroll
-      for (int k = 0; k < 4; ++k) {
-        bad |= !(fabsf(v[i][k]) <= bound);
-        if constexpr (std::is_same<Acc, float>::value) q[i][k] = v[i][k];
-        else q[i][k] = (u64)__float2ll_rn(v[i][k] * scalef);
-      }
-
-    // tile-local table
-    Loc L[4][4];
-#pragma unroll
-    for (int i = 0; i < 4; ++i)
-#pragma unroll
-      for (int k = 0; k < 4; ++k) {
-        if constexpr (std::is_same<Loc, float>::value) L[i][k] = v[i][k];
-        else L[i][k] = q[i][k];
-      }
-    tile_prefix<Loc>(L, s_wt, w, lane);
-
-    if constexpr (MODE == RCFAR_SAT_TILE_F32) {
-      float* out = reinterpret_cast<float*>(Mp.table);
-#pragma unroll
-      for (int i = 0; i < 4; ++i) {
-        const int r = r0 + w * 4 + i;
-        if (r >= Mp.rows) continue;
-        float* o = out + (long long)r * Mp.ld_table + cbase;
-        if (cbase + 3 < Mp.cols) {
-          *reinterpret_cast<float4*>(o) = make_float4(L[i][0], L[i][1], L[i][2], L[i][3]);
-        } else {
-#pragma unroll
-          for (int k = 0; k < 4; ++k)
-            if (cbase + k < Mp.cols) o[k] = L[i][k];
-        }
-      }
+      for (int k = 0; k < 4; ++k) s_wc[0][lane * 4 + k] = L[3][k];
     }
-
-    // row totals of this chunk, and the band-local carry CC_j(r)
-    Acc rq[4], pre[4];
-#pragma unroll
-    for (int i = 0; i < 4; ++i) rq[i] = warp_sum<Acc>(q[i][0] + q[i][1] + q[i][2] + q[i][3]);
-    pre[0] = runq[0];
-#pragma unroll
-    for (int i = 1; i < 4; ++i) pre[i] = pre[i - 1] + runq[i];
-    // column sums of q over this thread's rows
+  } else {
 #pragma unroll
     for (int k = 0; k < 4; ++k) s_wc[w][lane * 4 + k] = q[0][k] + q[1][k] + q[2][k] + q[3][k];
-    if (lane == 0) s_wq[w] = pre[3];
-    __syncthreads();
-    Acc base_w = Acc(0), band_run = Acc(0);
-#pragma unroll
-    for (int ww = 0; ww < 8; ++ww) {
-      if (ww < w) base_w += s_wq[ww];
-      band_run += s_wq[ww];
-    }
-    if constexpr (MODE == RCFAR_SAT_TILE_F32) {
-      if (lane < 4) {
-        const int r = r0 + w * 4 + lane;
-        Acc cc = pre[0];
-#pragma unroll
-        for (int i = 1; i < 4; ++i)
-          if (lane == i) cc = pre[i];
-        if (r < Mp.rows) st_carry<Acc>(Mp.col_carry + (long long)j * Mp.rows + r, base_w + cc);
-      }
-    }
+  }
+  __syncthreads();
 
-    // band aggregate A(c) = S_band(last row, c) and the look-back (warp 0)
-    if (w == 0) {
-      Acc a[4];
+  const int ntile = b * Mp.n_chunks + j;
+  if (w == 0) {
+    // ---- horizontal look-back: lane = band row
+    const Acc my = s_rq[lane];
+    Acc hc = Acc(0);
+    if (j == 0) {
+      st_carry<Acc>(Mp.h_inc + (long long)ntile * kSatTileH + lane, my);
+      __threadfence();
+      __syncwarp();
+      if (lane == 0) st_flag(Mp.h_flags + ntile, (gen << 2) | 2u);
+    } else {
+      st_carry<Acc>(Mp.h_agg + (long long)ntile * kSatTileH + lane, my);
+      __threadfence();
+      __syncwarp();
+      if (lane == 0) st_flag(Mp.h_flags + ntile, (gen << 2) | 1u);
+      // warp-parallel window: lane l polls the tile l places to the left; the
+      // nearest inclusive value ends the walk, aggregates before it are summed
+      for (int jj = j - 1; jj >= 0; jj -= 32) {
+        const int p = jj - lane;
+        unsigned f = 2u;
+        if (p >= 0) f = wait_flag(Mp.h_flags + b * Mp.n_chunks + p, gen, B.status);
+        if (__any_sync(0xffffffffu, f == 0xffffffffu)) break;  // timed out: status recorded
+        const unsigned incm = __ballot_sync(0xffffffffu, p >= 0 && (f & 3u) == 2u);
+        const int take = incm ? __ffs(incm) : min(32, jj + 1);
+        __threadfence();
+        for (int l = 0; l < take; ++l) {
+          const long long pt = (long long)b * Mp.n_chunks + (jj - l);
+          const u64* src = ((incm >> l) & 1u) ? Mp.h_inc : Mp.h_agg;
+          hc += ld_carry<Acc>(src + pt * kSatTileH + lane);
+        }
+        if (incm) break;
+      }
+      st_carry<Acc>(Mp.h_inc + (long long)ntile * kSatTileH + lane, hc + my);
+      __threadfence();
+      __syncwarp();
+      if (lane == 0) st_flag(Mp.h_flags + ntile, (gen << 2) | 2u);
+    }
+    // CC_j(r) = sum over band rows <= r of the horizontal carries
+    Acc cc = hc;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const Acc y = __shfl_up_sync(0xffffffffu, cc, o);
+      if (lane >= o) cc += y;
+    }
+    s_cc[lane] = cc;
+    if constexpr (MODE == RCFAR_SAT_TILE_F32) {
+      if (r0 + lane < Mp.rows) st_carry<Acc>(Mp.col_carry + (long long)j * Mp.rows + r0 + lane, cc);
+    }
+    const Acc base = __shfl_sync(0xffffffffu, cc, 31);
+
+    // ---- column aggregate A(c) = S_band(last row, c); vertical look-back
+    Acc a[4];
+    if constexpr (MODE == RCFAR_SAT_I64) {
+#pragma unroll
+      for (int k = 0; k < 4; ++k) a[k] = s_wc[0][lane * 4 + k] + base;
+    } else {
 #pragma unroll
       for (int k = 0; k < 4; ++k) {
         Acc t = s_wc[0][lane * 4 + k];
@@ -272,91 +317,78 @@ __global__ void __launch_bounds__(256) k_sat(const __grid_constant__ SatBatch B)
       for (int k = 1; k < 4; ++k) a[k] += a[k - 1];
       const Acc e = warp_excl_scan(a[3], lane);
 #pragma unroll
-      for (int k = 0; k < 4; ++k) a[k] += e + band_run;
-
-      const long long crow = (long long)j * kSatTileW + lane * 4;
-      unsigned* flag = Mp.flags + (long long)band * Mp.n_chunks + j;
-      Acc rc[4] = {Acc(0), Acc(0), Acc(0), Acc(0)};
-      if (band == 0) {
+      for (int k = 0; k < 4; ++k) a[k] += e + base;
+    }
+    const long long crow = (long long)j * kSatTileW + lane * 4;
+    Acc rc[4] = {Acc(0), Acc(0), Acc(0), Acc(0)};
+    if (b == 0) {
 #pragma unroll
-        for (int k = 0; k < 4; ++k) st_carry<Acc>(Mp.row_carry + crow + k, a[k]);
-        __threadfence();
-        __syncwarp();
-        if (lane == 0) st_flag(flag, (gen << 2) | 2u);
-      } else {
-        u64* aggp = Mp.agg + (long long)band * Mp.ld_carry + crow;
+      for (int k = 0; k < 4; ++k) st_carry<Acc>(Mp.row_carry + crow + k, a[k]);
+      __threadfence();
+      __syncwarp();
+      if (lane == 0) st_flag(Mp.v_flags + ntile, (gen << 2) | 2u);
+    } else {
+      u64* aggp = Mp.v_agg + (long long)b * Mp.ld_carry + crow;
 #pragma unroll
-        for (int k = 0; k < 4; ++k) st_carry<Acc>(aggp + k, a[k]);
+      for (int k = 0; k < 4; ++k) st_carry<Acc>(aggp + k, a[k]);
+      __threadfence();
+      __syncwarp();
+      if (lane == 0) st_flag(Mp.v_flags + ntile, (gen << 2) | 1u);
+      for (int bb = b - 1; bb >= 0; bb -= 32) {
+        const int p = bb - lane;
+        unsigned f = 2u;
+        if (p >= 0) f = wait_flag(Mp.v_flags + p * Mp.n_chunks + j, gen, B.status);
+        if (__any_sync(0xffffffffu, f == 0xffffffffu)) break;  // timed out: status recorded
+        const unsigned incm = __ballot_sync(0xffffffffu, p >= 0 && (f & 3u) == 2u);
+        const int take = incm ? __ffs(incm) : min(32, bb + 1);
         __threadfence();
-        __syncwarp();
-        if (lane == 0) st_flag(flag, (gen << 2) | 1u);
-        // look back over earlier bands of the same map
-        int bb = band - 1;
-        while (bb >= 0) {
-          unsigned f = 0;
-          if (lane == 0) {
-            const unsigned* fp = Mp.flags + (long long)bb * Mp.n_chunks + j;
-            unsigned it = 0;
-            for (;;) {
-              f = ld_flag(fp);
-              if ((f >> 2) == gen && (f & 3u) != 0u) break;
-              if (++it >= kSpinLimit) {
-                atomicOr(B.status, kStatusTimeout);
-                f = 0xffffffffu;
-                break;
-              }
-              __nanosleep(64);
-            }
-          }
-          f = __shfl_sync(0xffffffffu, f, 0);
-          if (f == 0xffffffffu) break;  // timed out: results invalid, status set
-          __threadfence();
-          const u64* src = ((f & 3u) == 2u ? Mp.row_carry : Mp.agg) + (long long)bb * Mp.ld_carry + crow;
+        for (int l = 0; l < take; ++l) {
+          const u64* src = (((incm >> l) & 1u) ? Mp.row_carry : Mp.v_agg) + (long long)(bb - l) * Mp.ld_carry + crow;
 #pragma unroll
           for (int k = 0; k < 4; ++k) rc[k] += ld_carry<Acc>(src + k);
-          if ((f & 3u) == 2u) break;
-          --bb;
         }
-        u64* incp = Mp.row_carry + (long long)band * Mp.ld_carry + crow;
-#pragma unroll
-        for (int k = 0; k < 4; ++k) st_carry<Acc>(incp + k, rc[k] + a[k]);
-        __threadfence();
-        __syncwarp();
-        if (lane == 0) st_flag(flag, (gen << 2) | 2u);
+        if (incm) break;
       }
-      if constexpr (MODE != RCFAR_SAT_TILE_F32) {
+      u64* incp = Mp.row_carry + (long long)b * Mp.ld_carry + crow;
 #pragma unroll
-        for (int k = 0; k < 4; ++k) s_rc[lane * 4 + k] = rc[k];
-      }
+      for (int k = 0; k < 4; ++k) st_carry<Acc>(incp + k, rc[k] + a[k]);
+      __threadfence();
+      __syncwarp();
+      if (lane == 0) st_flag(Mp.v_flags + ntile, (gen << 2) | 2u);
     }
+#pragma unroll
+    for (int k = 0; k < 4; ++k) s_rc[lane * 4 + k] = rc[k];
+  }
 
-    if constexpr (MODE != RCFAR_SAT_TILE_F32) {
-      __syncthreads();
-      Acc rcv[4];
+  if constexpr (MODE != RCFAR_SAT_TILE_F32) {
+    __syncthreads();
+    Acc rcv[4];
 #pragma unroll
-      for (int k = 0; k < 4; ++k) rcv[k] = s_rc[lane * 4 + k];
+    for (int k = 0; k < 4; ++k) rcv[k] = s_rc[lane * 4 + k];
 #pragma unroll
-      for (int i = 0; i < 4; ++i) {
-        const int r = r0 + w * 4 + i;
-        if (r >= Mp.rows) continue;
-        const Acc cc = base_w + pre[i];
-        if constexpr (MODE == RCFAR_SAT_I64) {
-          long long* o = reinterpret_cast<long long*>(Mp.table) + (long long)r * Mp.ld_table + cbase;
+    for (int i = 0; i < 4; ++i) {
+      const int r = r0 + w * 4 + i;
+      if (r >= Mp.rows) continue;
+      const Acc cc = s_cc[w * 4 + i];
+      if constexpr (MODE == RCFAR_SAT_I64) {
+        long long* o = reinterpret_cast<long long*>(Mp.table) + (long long)r * Mp.ld_table + cbase;
+        if (cbase + 3 < Mp.cols) {
+          const longlong2 v0 = make_longlong2((long long)(L[i][0] + rcv[0] + cc), (long long)(L[i][1] + rcv[1] + cc));
+          const longlong2 v1 = make_longlong2((long long)(L[i][2] + rcv[2] + cc), (long long)(L[i][3] + rcv[3] + cc));
+          reinterpret_cast<longlong2*>(o)[0] = v0;
+          reinterpret_cast<longlong2*>(o)[1] = v1;
+        } else {
 #pragma unroll
           for (int k = 0; k < 4; ++k)
             if (cbase + k < Mp.cols) o[k] = (long long)(L[i][k] + rcv[k] + cc);
-        } else {
-          float* o = reinterpret_cast<float*>(Mp.table) + (long long)r * Mp.ld_table + cbase;
-#pragma unroll
-          for (int k = 0; k < 4; ++k)
-            if (cbase + k < Mp.cols) o[k] = L[i][k] + rcv[k] + cc;
         }
+      } else {
+        float* o = reinterpret_cast<float*>(Mp.table) + (long long)r * Mp.ld_table + cbase;
+#pragma unroll
+        for (int k = 0; k < 4; ++k)
+          if (cbase + k < Mp.cols) o[k] = L[i][k] + rcv[k] + cc;
       }
     }
-
-#pragma unroll
-    for (int i = 0; i < 4; ++i) runq[i] += rq[i];
-    __syncthreads();
   }
 
   if (bad) atomicOr(B.status, kStatusRange);
