@@ -59,22 +59,27 @@ typedef enum rcfar_map_dtype {
   RCFAR_MAP_F16 = 1 /* IEEE half; value = stored * 2^map_exp2 */
 } rcfar_map_dtype;
 
-/* How the summed-area table is stored (paper eq. 3).
- *  TILE_F32 : per 32x128 tile, an FP32 table relative to the tile's origin,
- *             plus exact 64-bit fixed-point carries along each tile row band
- *             (global table on the row above the band) and each tile column
- *             (band-local sums left of the tile). 4 bytes per cell.
- *  I64      : the global table itself in 64-bit fixed point (exact for the
- *             quantised map; 8 bytes per cell).
- *  NAIVE_F32: the global table in plain FP32 (for contrast only: large maps
- *             lose the reference sums to cancellation).
+/* How the summed-area table is stored (paper eq. 3). The map is cut into
+ * tiles of 32 rows x 128 columns; band b = tile row, chunk j = tile column.
+ * For cell (r, c) of tile (b, j):
+ *   S(r, c) = L(r, c) + CC_j(r) + RC_{b-1}(c)
+ *   L     : the table of the tile relative to its own origin
+ *   CC_j  : col_carry[j][r] = sum of the band's rows <= r left of the tile
+ *   RC_b  : row_carry[b][c] = S(last row of band b, c)   (RC_{-1} = 0)
+ *  TILE_I64 : L in 64-bit fixed point plus the carries. Exact; 8 B/cell.
+ *  TILE_F32 : L in FP32 plus exact 64-bit carries. 4 B/cell; L's rounding
+ *             grows with the tile's sum (precision study).
+ *  I64      : S itself in 64-bit fixed point (carries folded in). Exact.
+ *  NAIVE_F32: S itself in plain FP32 (for contrast only: large maps lose the
+ *             reference sums to cancellation).
  * Fixed-point values are round(x * 2^scale_log2) and are added modulo 2^64,
  * so every region sum that fits in 63 bits is exact even where the table
  * itself wraps. */
 typedef enum rcfar_sat_mode {
   RCFAR_SAT_TILE_F32 = 0,
   RCFAR_SAT_I64 = 1,
-  RCFAR_SAT_NAIVE_F32 = 2
+  RCFAR_SAT_NAIVE_F32 = 2,
+  RCFAR_SAT_TILE_I64 = 3
 } rcfar_sat_mode;
 
 typedef struct rcfar_config {
@@ -85,6 +90,8 @@ typedef struct rcfar_config {
   int32_t max_window;    /* largest per-side half-width guard + training */
   int32_t max_frames;    /* largest number of frames in one rcfar_run_batch */
   int64_t batch_bytes;   /* device workspace reserved for rcfar_run_batch (0: none) */
+  int32_t cfar_tile_rows; /* SAT-CFAR output tile (0, 0: chosen from the window); */
+  int32_t cfar_tile_cols; /* rows in {8,16,32,64}, cols in {16,32,64,128} */
 } rcfar_config;
 
 /* Preprocessing parameters (Sec. II.A). */
@@ -122,10 +129,10 @@ typedef struct rcfar_sat_view {
   int32_t mode;          /* rcfar_sat_mode */
   int32_t tile_h, tile_w;
   int32_t scale_log2;    /* fixed-point scale s (TILE_F32, I64) */
-  void* table;           /* TILE_F32/NAIVE_F32: float [rows][ld]; I64: int64 [rows][ld] */
+  void* table;           /* TILE_F32/NAIVE_F32: float [rows][ld]; TILE_I64/I64: int64 [rows][ld] */
   int64_t ld;
-  int64_t* row_carry;    /* TILE_F32: [rows/tile_h][ld_carry]: global table on each band's last row */
-  int64_t* col_carry;    /* TILE_F32: [cols/tile_w][rows]: band-local sums left of each tile column */
+  int64_t* row_carry;    /* [ceil(rows/tile_h)][ld_carry]: S on each band's last row */
+  int64_t* col_carry;    /* [ceil(cols/tile_w)][rows]: band-local sums left of each tile */
   int64_t ld_carry;
   uint64_t generation;   /* handle-side stamp; a stale view is rejected */
 } rcfar_sat_view;
@@ -198,8 +205,8 @@ rcfar_status rcfar_sat(rcfar_handle h, const void* map, int32_t dtype, int32_t m
                        rcfar_sat_view* view_out, rcfar_stream stream);
 
 /* eqs. 1, 2, 4: 2D CA-CFAR on a table from rcfar_sat and its map. For an
- * I64 table the map may be NULL: the CUT value then comes from the table
- * itself as the sum over the 1x1 region (exact fixed point). For every
+ * exact table (TILE_I64, I64) the map may be NULL: the CUT value then comes
+ * from the table itself as the sum over the 1x1 region. For every
  * interior CUT (outer rectangle inside the map) whose column lies in
  * [cut_c_lo, cut_c_hi]: S_ref = A(outer) - A(guard), each region sum from four
  * table lookups A = L1 + L4 - (L2 + L3); T = alpha * S_ref / n_ref;
@@ -227,7 +234,7 @@ rcfar_status rcfar_sat_materialize(rcfar_handle h, const rcfar_sat_view* view, d
 
 /* ---- batched path ------------------------------------------------------ */
 
-/* Whole chain (rcfar_preprocess -> rcfar_sat(I64) -> rcfar_cfar with the
+/* Whole chain (rcfar_preprocess -> rcfar_sat(TILE_I64) -> rcfar_cfar with the
  * band's CUT columns) for n frames of uneven size and window in a handful of
  * launches over all frames. frames is a HOST array of n descriptors; their
  * pointers are device pointers. Each frame's results are identical whatever

@@ -28,6 +28,7 @@ RCFAR_MAP_F16 = 1
 RCFAR_SAT_TILE_F32 = 0
 RCFAR_SAT_I64 = 1
 RCFAR_SAT_NAIVE_F32 = 2
+RCFAR_SAT_TILE_I64 = 3
 
 SAT_TILE_H = 32
 SAT_TILE_W = 128
@@ -50,7 +51,8 @@ class RcfarError(RuntimeError):
 class rcfar_config(ctypes.Structure):
     _fields_ = [("device", ctypes.c_int32), ("max_rows", ctypes.c_int32), ("max_cols", ctypes.c_int32),
                 ("max_n", ctypes.c_int32), ("max_window", ctypes.c_int32), ("max_frames", ctypes.c_int32),
-                ("batch_bytes", ctypes.c_int64)]
+                ("batch_bytes", ctypes.c_int64), ("cfar_tile_rows", ctypes.c_int32),
+                ("cfar_tile_cols", ctypes.c_int32)]
 
 
 class rcfar_pre_params(ctypes.Structure):
@@ -202,9 +204,9 @@ def rcfar_batch_bytes(M: int, N: int, params: rcfar_pre_params, window: Optional
 
 # ---------------------------------------------------------------- handle
 def rcfar_create(device: int = 0, max_rows: int = 1024, max_cols: int = 1024, max_n: int = 4096,
-                 max_window: int = 32, max_frames: int = 64, batch_bytes: int = 0) -> int:
+                 max_window: int = 32, max_frames: int = 64, batch_bytes: int = 0, cfar_tile=(0, 0)) -> int:
     cfg = rcfar_config(int(device), int(max_rows), int(max_cols), int(max_n), int(max_window), int(max_frames),
-                       int(batch_bytes))
+                       int(batch_bytes), int(cfar_tile[0]), int(cfar_tile[1]))
     h = ctypes.c_void_p()
     _check(lib().rcfar_create(ctypes.byref(cfg), ctypes.byref(h)), "rcfar_create")
     return h.value
@@ -228,7 +230,7 @@ def rcfar_preprocess(h: int, x, params: rcfar_pre_params, map_out, stream=None) 
     return band
 
 
-def rcfar_sat(h: int, map_t, value_bound: float = 0.0, mode: int = RCFAR_SAT_I64, map_exp2: int = 0,
+def rcfar_sat(h: int, map_t, value_bound: float = 0.0, mode: int = RCFAR_SAT_TILE_I64, map_exp2: int = 0,
               stream=None) -> rcfar_sat_view:
     import torch
     dtype = RCFAR_MAP_F16 if map_t.dtype == torch.float16 else RCFAR_MAP_F32

@@ -16,16 +16,17 @@ using namespace rcfar;
 namespace {
 
 constexpr int kStatsRows = 64;  // rows per column-statistics CTA
-// The batched chain stores the exact 64-bit table: its decisions are exact
-// for every window (the FP32 tile-local table loses small windows' sums).
-constexpr int kBatchSatMode = RCFAR_SAT_I64;
+// The batched chain stores the exact 64-bit tile-local table: its decisions
+// are exact for every window (the FP32 tile-local table loses small windows'
+// sums), and it needs no pass to fold the carries in.
+constexpr int kBatchSatMode = RCFAR_SAT_TILE_I64;
 
 inline long long ceil_div(long long a, long long b) { return (a + b - 1) / b; }
 inline long long round_up(long long a, long long b) { return ceil_div(a, b) * b; }
 inline size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 struct Twiddle {
-  float* W = nullptr;
+  float2* W2 = nullptr;
   long long ldw = 0;
 };
 
@@ -50,6 +51,7 @@ struct PreGeom {
   int n_strips, n_chunks, rows_per_chunk;
   int mtiles, ntiles, splitk, kper;
   int n_norm;
+  int npad, ycols, n_y;
   long long ldk;
 };
 
@@ -58,6 +60,9 @@ PreGeom pre_geom(int M, int N, int C) {
   g.n_strips = (int)ceil_div(N, kStatsStrip);
   g.rows_per_chunk = kStatsRows;
   g.n_chunks = (int)ceil_div(M, kStatsRows);
+  g.npad = (int)round_up(N, kDftBK);
+  g.ycols = (int)ceil_div(g.npad, kYCols);
+  g.n_y = (int)ceil_div(M, kYRows) * g.ycols;
   g.mtiles = (int)ceil_div(M, kDftBM);
   g.ntiles = (int)ceil_div(2LL * C, kDftBN);
   const int tiles = g.mtiles * g.ntiles;
@@ -65,8 +70,8 @@ PreGeom pre_geom(int M, int N, int C) {
   const int max_sk = (int)std::max<long long>(1, N / 256);
   if (sk > max_sk) sk = max_sk;
   if (sk < 1) sk = 1;
-  g.kper = (int)round_up(ceil_div(N, sk), kDftBK);
-  g.splitk = (int)ceil_div(N, g.kper);
+  g.kper = (int)round_up(ceil_div(g.npad, sk), kDftBK);
+  g.splitk = (int)ceil_div(g.npad, g.kper);
   g.ldk = round_up(2LL * C, 4);
   g.n_norm = (int)std::min<long long>(std::max<long long>(1, ceil_div((long long)M * C, 1024)), 1024);
   return g;
@@ -86,59 +91,70 @@ SatGeom sat_geom(int rows, int cols) {
   return g;
 }
 
-// bytes of SAT storage (TILE_F32 needs 4 B/cell, I64 8 B/cell)
+inline bool exact_table(int mode) { return mode == RCFAR_SAT_I64 || mode == RCFAR_SAT_TILE_I64; }
+
+// bytes of SAT storage: the table (4 or 8 B per cell) and the carry arrays
 size_t sat_bytes(int rows, int cols, int mode) {
   SatGeom g = sat_geom(rows, cols);
   size_t b = 0;
-  b += align256((size_t)rows * g.ld_table * (mode == RCFAR_SAT_I64 ? 8 : 4));
-  b += 2 * align256((size_t)g.n_bands * g.ld_carry * 8);     // row_carry + v_agg
-  b += 2 * align256((size_t)g.n_bands * g.n_chunks * kSatTileH * 8);  // h_agg + h_inc
-  b += align256((size_t)g.n_chunks * rows * 8);               // col_carry
+  b += align256((size_t)rows * g.ld_table * (exact_table(mode) ? 8 : 4));
+  b += 2 * align256((size_t)g.n_bands * g.ld_carry * 8);                 // col_tot + row_carry
+  b += align256((size_t)g.n_bands * g.n_chunks * kSatTileH * 8);          // row_tot
+  b += align256((size_t)g.n_chunks * rows * 8);                           // col_carry
   return b;
 }
-size_t sat_flag_bytes(int rows, int cols) {
-  SatGeom g = sat_geom(rows, cols);
-  return 2 * align256((size_t)g.n_bands * g.n_chunks * 4);   // h_flags + v_flags
-}
 
-// Carve the look-back arrays of one table from a data and a control region.
+// The carry arrays of one table, carved from a region.
 struct SatArrays {
-  unsigned long long *row_carry, *v_agg, *h_agg, *h_inc, *col_carry;
-  unsigned *h_flags, *v_flags;
+  unsigned long long *col_tot, *row_tot, *row_carry, *col_carry;
 };
-template <typename CarveData, typename CarveCtl>
-bool carve_sat(CarveData& data, CarveCtl& ctl, int rows, int cols, SatArrays* a) {
+template <typename Carve>
+bool carve_sat(Carve& data, int rows, int cols, SatArrays* a) {
   SatGeom g = sat_geom(rows, cols);
+  a->col_tot = data.template take<unsigned long long>((size_t)g.n_bands * g.ld_carry);
   a->row_carry = data.template take<unsigned long long>((size_t)g.n_bands * g.ld_carry);
-  a->v_agg = data.template take<unsigned long long>((size_t)g.n_bands * g.ld_carry);
-  a->h_agg = data.template take<unsigned long long>((size_t)g.n_bands * g.n_chunks * kSatTileH);
-  a->h_inc = data.template take<unsigned long long>((size_t)g.n_bands * g.n_chunks * kSatTileH);
+  a->row_tot = data.template take<unsigned long long>((size_t)g.n_bands * g.n_chunks * kSatTileH);
   a->col_carry = data.template take<unsigned long long>((size_t)g.n_chunks * rows);
-  a->h_flags = ctl.template take<unsigned>((size_t)g.n_bands * g.n_chunks);
-  a->v_flags = ctl.template take<unsigned>((size_t)g.n_bands * g.n_chunks);
-  return a->row_carry && a->v_agg && a->h_agg && a->h_inc && a->col_carry && a->h_flags && a->v_flags;
+  return a->col_tot && a->row_carry && a->row_tot && a->col_carry;
 }
 void set_sat_arrays(SatMapDev& m, const SatArrays& a) {
+  m.col_tot = a.col_tot;
+  m.row_tot = a.row_tot;
   m.row_carry = a.row_carry;
-  m.v_agg = a.v_agg;
-  m.h_agg = a.h_agg;
-  m.h_inc = a.h_inc;
   m.col_carry = a.col_carry;
-  m.h_flags = a.h_flags;
-  m.v_flags = a.v_flags;
 }
 
 struct CfarTile {
   int bh, bw;
 };
 
-// Output tile of the SAT CFAR: the widest candidate whose halo fits in
-// shared memory, with halo rows at most 256 columns wide.
-CfarTile pick_cfar_tile(int mode, int wr, int wc, size_t smem_cap) {
-  const CfarTile cand[] = {{32, 64}, {32, 32}, {16, 32}, {16, 16}, {8, 16}};
+bool cfar_tile_fits(int mode, CfarTile t, int wr, int wc, size_t smem_cap) {
+  return t.bh > 0 && t.bh <= 16 && t.bw > 0 && 256 % t.bw == 0 && t.bh * t.bw <= 1024 &&
+         cfar_smem_bytes(mode, t.bh, t.bw, wr, wc) <= smem_cap && t.bw + 2 * wc + 1 <= 256;
+}
+
+// SAT-CFAR geometry: a strip of bw columns, bh CUT rows per step. The
+// configured one if it fits, else the first candidate whose ring of table
+// rows fits in shared memory (halo rows at most 256 wide). The choice
+// depends only on the window, never on the rest of a batch.
+CfarTile pick_cfar_tile(int mode, int wr, int wc, size_t smem_cap, CfarTile pref) {
+  if (cfar_tile_fits(mode, pref, wr, wc, smem_cap)) return pref;
+  const CfarTile cand[] = {{16, 64}, {16, 32}, {8, 64}, {8, 32}, {8, 16}, {4, 16}};
   for (const CfarTile& t : cand)
-    if (cfar_smem_bytes(mode, t.bh, t.bw, wr, wc) <= smem_cap && t.bw + 2 * wc + 1 <= 256) return t;
+    if (cfar_tile_fits(mode, t, wr, wc, smem_cap)) return t;
   return {0, 0};
+}
+
+constexpr int kCfarRun = 256;  // rows per SAT-CFAR CTA
+
+// Fills the strip geometry of a CFAR descriptor; returns its CTA count.
+int set_cfar_geometry(CfarMapDev& P, CfarTile t, int rows, int cols) {
+  P.bh = t.bh;
+  P.bw = t.bw;
+  P.run = (int)round_up(std::min<long long>(kCfarRun, round_up(rows, t.bh)), t.bh);
+  P.ring_rows = cfar_ring_rows(t.bh, P.wr);
+  P.tiles_x = (int)ceil_div(cols, t.bw);
+  return P.tiles_x * (int)ceil_div(rows, P.run);
 }
 
 }  // namespace
@@ -156,9 +172,6 @@ struct rcfar_ctx {
   size_t ws_bytes = 0;
   // control words
   int* status = nullptr;
-  unsigned* sat_ticket = nullptr;
-  unsigned* sat_done = nullptr;
-  unsigned* sat_gen = nullptr;
   int* sat_scale = nullptr;
   float* map_bound = nullptr;
   unsigned* ymax = nullptr;
@@ -171,6 +184,8 @@ struct rcfar_ctx {
   unsigned* tile_cnt = nullptr;
   float* kpart = nullptr;
   size_t kpart_floats = 0;
+  float2* ysplit = nullptr;
+  float* rowmean = nullptr;
   // per-step SAT
   void* sat_table = nullptr;
   SatArrays sat{};
@@ -281,11 +296,13 @@ static rcfar_status get_plan(rcfar_ctx* h, int N, int c0, int C, cudaStream_t s,
   if (cudaStreamIsCapturing(s, &cs) == cudaSuccess && cs != cudaStreamCaptureStatusNone)
     return RCFAR_ERR_BAD_STATE;  // plans must exist before capture (rcfar_prepare)
   Twiddle t;
-  t.ldw = round_up(2LL * C, 4);
-  if (cudaMalloc(&t.W, (size_t)N * t.ldw * sizeof(float)) != cudaSuccess) return RCFAR_ERR_CUDA;
-  cudaError_t e = launch_twiddles(t.W, t.ldw, N, c0, C, s);
+  t.ldw = round_up(2LL * C, kDftBN);
+  const size_t bytes = (size_t)round_up(N, kDftBK) * t.ldw * sizeof(float2);
+  if (cudaMalloc(&t.W2, bytes) != cudaSuccess) return RCFAR_ERR_CUDA;
+  cudaError_t e = cudaMemsetAsync(t.W2, 0, bytes, s);  // padding rows and columns stay zero
+  if (e == cudaSuccess) e = launch_twiddles(t.W2, t.ldw, N, c0, C, s);
   if (e != cudaSuccess) {
-    cudaFree(t.W);
+    cudaFree(t.W2);
     return RCFAR_ERR_CUDA;
   }
   h->plans[key] = t;
@@ -308,8 +325,10 @@ static PreFrameDev make_pre_frame(const float* x, int M, int N, long long ldx, c
   F.inv_M = (float)(1.0 / (double)M);
   const double D = (double)M * ((double)M * M - 1.0) / 12.0;
   F.inv_D = D > 0 ? (float)(1.0 / D) : 0.0f;
-  F.W = tw.W;
+  F.W2 = tw.W2;
   F.ldw = tw.ldw;
+  F.npad = g.npad;
+  F.ycols = g.ycols;
   F.rows_per_chunk = g.rows_per_chunk;
   F.n_chunks = g.n_chunks;
   F.n_strips = g.n_strips;
@@ -331,13 +350,15 @@ static size_t frame_data_bytes(int M, int N, int C) {
   t += align256((size_t)g.n_strips * M * sizeof(float));           // rowpart
   t += align256((size_t)g.n_strips * sizeof(float2));              // strip_ab
   t += g.splitk > 1 ? align256((size_t)g.splitk * M * g.ldk * 4) : 0;
+  t += align256((size_t)M * g.npad * sizeof(float2));              // ysplit
+  t += align256((size_t)M * sizeof(float));                        // rowmean
   t += align256((size_t)M * round_up(C, 4) * 4);                   // map
   t += sat_bytes(M, C, kBatchSatMode);
   return t;
 }
 static size_t frame_ctl_bytes(int M, int N, int C) {
   const PreGeom g = pre_geom(M, N, C);
-  return align256((size_t)g.n_strips * 4) + align256((size_t)g.mtiles * g.ntiles * 4) + 256 + sat_flag_bytes(M, C);
+  return align256((size_t)g.n_strips * 4) + align256((size_t)g.mtiles * g.ntiles * 4) + 256;
 }
 
 // -------------------------------------------------------------------------
@@ -416,8 +437,9 @@ rcfar_status rcfar_create(const rcfar_config* cfg, rcfar_handle* out) {
   total += align256((size_t)max_strips * 4);
   total += align256((size_t)max_tiles * 4);
   total += align256(kpart * 4);
+  total += align256((size_t)R * round_up(Nm, kDftBK) * sizeof(float2));  // ysplit
+  total += align256((size_t)R * sizeof(float));                          // rowmean
   total += sat_bytes(R, Cm, RCFAR_SAT_I64);
-  total += sat_flag_bytes(R, Cm);
   if (cudaMalloc(&h->ws, total) != cudaSuccess) {
     delete h;
     return RCFAR_ERR_CUDA;
@@ -427,9 +449,6 @@ rcfar_status rcfar_create(const rcfar_config* cfg, rcfar_handle* out) {
   Carver cv(h->ws, total);
   unsigned* ctl = cv.take<unsigned>(64);
   h->status = reinterpret_cast<int*>(ctl + 0);
-  h->sat_ticket = ctl + 1;
-  h->sat_done = ctl + 2;
-  h->sat_gen = ctl + 3;
   h->sat_scale = reinterpret_cast<int*>(ctl + 4);
   h->map_bound = reinterpret_cast<float*>(ctl + 5);
   h->ymax = ctl + 6;
@@ -441,13 +460,13 @@ rcfar_status rcfar_create(const rcfar_config* cfg, rcfar_handle* out) {
   h->tile_cnt = cv.take<unsigned>(max_tiles);
   h->kpart = cv.take<float>(kpart);
   h->kpart_floats = kpart;
+  h->ysplit = cv.take<float2>((size_t)R * round_up(Nm, kDftBK));
+  h->rowmean = cv.take<float>(R);
   {
     SatGeom g = sat_geom(R, Cm);
     h->sat_table = cv.take<char>((size_t)R * g.ld_table * 8);
-    carve_sat(cv, cv, R, Cm, &h->sat);
+    carve_sat(cv, R, Cm, &h->sat);
   }
-  const unsigned one = 1u;
-  cudaMemcpy(h->sat_gen, &one, sizeof(one), cudaMemcpyHostToDevice);
   if (cfg->batch_bytes > 0) {
     if (cudaMalloc(&h->batch, (size_t)cfg->batch_bytes) != cudaSuccess) {
       cudaFree(h->ws);
@@ -470,7 +489,7 @@ rcfar_status rcfar_destroy(rcfar_handle h) {
   if (!h) return RCFAR_ERR_INVALID_ARG;
   DeviceGuard g(h->device);
   cudaError_t e = cudaDeviceSynchronize();
-  for (auto& kv : h->plans) cudaFree(kv.second.W);
+  for (auto& kv : h->plans) cudaFree(kv.second.W2);
   for (auto& r : h->trace_pool) {
     cudaEventDestroy(r.a);
     cudaEventDestroy(r.b);
@@ -525,8 +544,6 @@ rcfar_status rcfar_get_error(rcfar_handle h, rcfar_stream stream) {
   if (st) {
     // clear the status and any counters a broken launch may have left behind
     cudaMemset(h->status, 0, sizeof(int));
-    cudaMemset(h->sat_ticket, 0, 2 * sizeof(unsigned));
-    cudaMemset(h->strip_cnt, 0, 4);
     cudaDeviceSynchronize();
   }
   if (st & kStatusTimeout) return RCFAR_ERR_TIMEOUT;
@@ -565,13 +582,20 @@ rcfar_status rcfar_preprocess(rcfar_handle h, const float* x, int32_t M, int32_t
   F.ld_map = ld_map;
   F.kpart = h->kpart;
   F.tile_cnt = h->tile_cnt;
+  F.ysplit = h->ysplit;
+  F.rowmean = h->rowmean;
   F.item_stats = 0;
   F.item_dft = 0;
   F.item_norm = 0;
+  F.item_y = 0;
   cudaError_t e;
   {
     TraceScope t(h, "colstats", s);
     e = launch_colstats(pb, g.n_strips * g.n_chunks, s);
+  }
+  if (e == cudaSuccess) {
+    TraceScope t(h, "ysplit", s);
+    e = launch_ysplit(pb, g.n_y, s);
   }
   if (e == cudaSuccess) {
     TraceScope t(h, "band_dft", s);
@@ -590,7 +614,7 @@ rcfar_status rcfar_sat(rcfar_handle h, const void* map, int32_t dtype, int32_t m
                        int64_t ld, float value_bound, int32_t mode, rcfar_sat_view* view_out, rcfar_stream stream) {
   if (!h || !map || !view_out || rows <= 0 || cols <= 0 || ld < cols) return RCFAR_ERR_INVALID_ARG;
   if (dtype != RCFAR_MAP_F32 && dtype != RCFAR_MAP_F16) return RCFAR_ERR_INVALID_ARG;
-  if (mode < RCFAR_SAT_TILE_F32 || mode > RCFAR_SAT_NAIVE_F32) return RCFAR_ERR_INVALID_ARG;
+  if (mode < RCFAR_SAT_TILE_F32 || mode > RCFAR_SAT_TILE_I64) return RCFAR_ERR_INVALID_ARG;
   if (value_bound != value_bound) return RCFAR_ERR_INVALID_ARG;
   if (map_exp2 < -100 || map_exp2 > 100) return RCFAR_ERR_INVALID_ARG;
   if (rows > h->cfg.max_rows || cols > h->cfg.max_cols) return RCFAR_ERR_UNSUPPORTED;
@@ -603,10 +627,6 @@ rcfar_status rcfar_sat(rcfar_handle h, const void* map, int32_t dtype, int32_t m
 
   static thread_local SatBatch sb;
   sb.n = 1;
-  sb.total = g.n_bands * g.n_chunks;
-  sb.ticket = h->sat_ticket;
-  sb.done = h->sat_done;
-  sb.gen = h->sat_gen;
   sb.status = h->status;
   SatMapDev& m = sb.m[0];
   std::memset(&m, 0, sizeof(m));
@@ -636,11 +656,11 @@ rcfar_status rcfar_sat(rcfar_handle h, const void* map, int32_t dtype, int32_t m
   m.scale_out = h->sat_scale;
   m.n_bands = g.n_bands;
   m.n_chunks = g.n_chunks;
-  m.item0 = 0;
+  m.item_tile = m.item_band = m.item_vscan = 0;
   cudaError_t e;
   {
     TraceScope t(h, "sat", s);
-    e = launch_sat(sb, mode, dtype, s);
+    e = launch_sat(sb, mode, dtype, g.n_bands * g.n_chunks, g.n_bands, (int)ceil_div(cols, 32), s);
   }
   if (e != cudaSuccess) return RCFAR_ERR_CUDA;
 
@@ -685,7 +705,7 @@ rcfar_status rcfar_cfar(rcfar_handle h, const rcfar_sat_view* view, const void* 
                         int64_t ld_map, const rcfar_window* w, int32_t cut_c_lo, int32_t cut_c_hi, uint8_t* det,
                         int64_t ld_det, float* thr, int64_t ld_thr, rcfar_stream stream) {
   if (!h || !view || !det || !valid_window(w)) return RCFAR_ERR_INVALID_ARG;
-  if (!map && view->mode != RCFAR_SAT_I64) return RCFAR_ERR_INVALID_ARG;
+  if (!map && !exact_table(view->mode)) return RCFAR_ERR_INVALID_ARG;
   if (dtype != RCFAR_MAP_F32 && dtype != RCFAR_MAP_F16) return RCFAR_ERR_INVALID_ARG;
   if ((map && ld_map < view->cols) || ld_det < view->cols || (thr && ld_thr < view->cols))
     return RCFAR_ERR_INVALID_ARG;
@@ -715,16 +735,15 @@ rcfar_status rcfar_cfar(rcfar_handle h, const rcfar_sat_view* view, const void* 
   P.ld_det = ld_det;
   P.thr = thr;
   P.ld_thr = ld_thr;
-  const CfarTile t = pick_cfar_tile(view->mode, P.wr, P.wc, std::min<size_t>(h->smem_optin, 200 * 1024));
+  P.mode = view->mode;
+  const CfarTile t = pick_cfar_tile(view->mode, P.wr, P.wc, std::min<size_t>(h->smem_optin, 200 * 1024),
+                                    {h->cfg.cfar_tile_rows, h->cfg.cfar_tile_cols});
   if (t.bh == 0) return RCFAR_ERR_UNSUPPORTED;
-  P.bh = t.bh;
-  P.bw = t.bw;
-  P.tiles_x = (int)ceil_div(view->cols, t.bw);
-  const int blocks = P.tiles_x * (int)ceil_div(view->rows, t.bh);
+  const int blocks = set_cfar_geometry(P, t, view->rows, view->cols);
   P.item0 = 0;
   TraceScope tr(h, "cfar", s);
-  cudaError_t e = launch_cfar(cb, view->mode, dtype, blocks,
-                              cfar_smem_bytes(view->mode, t.bh, t.bw, P.wr, P.wc), s);
+  cudaError_t e = launch_cfar(cb, view->mode, dtype, blocks, cfar_smem_bytes(view->mode, t.bh, t.bw, P.wr, P.wc),
+                              t.bw + 2 * P.wc + 1, s);
   return cuda_fail(e);
 }
 
@@ -857,12 +876,10 @@ rcfar_status rcfar_run_batch(rcfar_handle h, const rcfar_frame_desc* frames, int
     pb.n = cnt;
     sb.n = cnt;
     cb.n = cnt;
-    sb.ticket = h->sat_ticket;
-    sb.done = h->sat_done;
-    sb.gen = h->sat_gen;
     sb.status = h->status;
-    int it_stats = 0, it_dft = 0, it_norm = 0, it_sat = 0, it_cfar = 0;
-    int cfar_mode_smem = 0;
+    int it_stats = 0, it_dft = 0, it_norm = 0, it_cfar = 0, it_y = 0;
+    int it_tile = 0, it_band = 0, it_vscan = 0;
+    int cfar_mode_smem = 0, cfar_max_hc = 0;
     for (int k = 0; k < cnt; ++k) {
       const int i = base + k;
       const rcfar_frame_desc& f = frames[i];
@@ -876,6 +893,8 @@ rcfar_status rcfar_run_batch(rcfar_handle h, const rcfar_frame_desc* frames, int
       F.rowpart = data.take<float>((size_t)g.n_strips * f.M);
       F.strip_ab = data.take<float2>(g.n_strips);
       F.kpart = g.splitk > 1 ? data.take<float>((size_t)g.splitk * f.M * g.ldk) : nullptr;
+      F.ysplit = data.take<float2>((size_t)f.M * g.npad);
+      F.rowmean = data.take<float>(f.M);
       float* map = f.map;
       long long ld_map = f.ld_map;
       if (!map) {
@@ -891,6 +910,8 @@ rcfar_status rcfar_run_batch(rcfar_handle h, const rcfar_frame_desc* frames, int
       F.item_stats = it_stats;
       F.item_dft = it_dft;
       F.item_norm = it_norm;
+      F.item_y = it_y;
+      it_y += g.n_y;
       it_stats += g.n_strips * g.n_chunks;
       it_dft += g.mtiles * g.ntiles * g.splitk;
       it_norm += g.n_norm;
@@ -910,15 +931,19 @@ rcfar_status rcfar_run_batch(rcfar_handle h, const rcfar_frame_desc* frames, int
       m.table = data.take<long long>((size_t)f.M * sg.ld_table);
       m.ld_table = sg.ld_table;
       SatArrays sa;
-      const bool sat_ok = carve_sat(data, ctl, f.M, C, &sa);
+      const bool sat_ok = carve_sat(data, f.M, C, &sa);
       set_sat_arrays(m, sa);
       m.ld_carry = sg.ld_carry;
       m.scale_out = reinterpret_cast<int*>(words + 1);
       m.n_bands = sg.n_bands;
       m.n_chunks = sg.n_chunks;
-      m.item0 = it_sat;
-      it_sat += sg.n_bands * sg.n_chunks;
-      if (!F.stats || !F.partial || !F.rowpart || !F.strip_ab || (g.splitk > 1 && !F.kpart) || !map || !m.table ||
+      m.item_tile = it_tile;
+      m.item_band = it_band;
+      m.item_vscan = it_vscan;
+      it_tile += sg.n_bands * sg.n_chunks;
+      it_band += sg.n_bands;
+      it_vscan += (int)ceil_div(C, 32);
+      if (!F.stats || !F.partial || !F.rowpart || !F.strip_ab || !F.ysplit || !F.rowmean || (g.splitk > 1 && !F.kpart) || !map || !m.table ||
           !sat_ok || !F.strip_cnt || !F.tile_cnt || !words)
         return RCFAR_ERR_OUT_OF_WORKSPACE;
 
@@ -940,21 +965,24 @@ rcfar_status rcfar_run_batch(rcfar_handle h, const rcfar_frame_desc* frames, int
       P.ld_det = f.ld_det;
       P.thr = f.thr;
       P.ld_thr = f.ld_thr;
+      P.mode = kBatchSatMode;
       // tile from this frame's own window (batch composition does not matter)
-      const CfarTile t = pick_cfar_tile(kBatchSatMode, P.wr, P.wc, std::min<size_t>(h->smem_optin, 200 * 1024));
+      const CfarTile t = pick_cfar_tile(kBatchSatMode, P.wr, P.wc, std::min<size_t>(h->smem_optin, 200 * 1024),
+                                        {h->cfg.cfar_tile_rows, h->cfg.cfar_tile_cols});
       if (t.bh == 0) return RCFAR_ERR_UNSUPPORTED;
-      P.bh = t.bh;
-      P.bw = t.bw;
-      P.tiles_x = (int)ceil_div(C, t.bw);
       P.item0 = it_cfar;
-      it_cfar += P.tiles_x * (int)ceil_div(f.M, t.bh);
+      it_cfar += set_cfar_geometry(P, t, f.M, C);
       cfar_mode_smem = std::max<int>(cfar_mode_smem, (int)cfar_smem_bytes(kBatchSatMode, t.bh, t.bw, P.wr, P.wc));
+      cfar_max_hc = std::max(cfar_max_hc, t.bw + 2 * P.wc + 1);
     }
-    sb.total = it_sat;
     cudaError_t e;
     {
       TraceScope t(h, "colstats", s);
       e = launch_colstats(pb, it_stats, s);
+    }
+    if (e == cudaSuccess) {
+      TraceScope t(h, "ysplit", s);
+      e = launch_ysplit(pb, it_y, s);
     }
     if (e == cudaSuccess) {
       TraceScope t(h, "band_dft", s);
@@ -966,11 +994,11 @@ rcfar_status rcfar_run_batch(rcfar_handle h, const rcfar_frame_desc* frames, int
     }
     if (e == cudaSuccess) {
       TraceScope t(h, "sat", s);
-      e = launch_sat(sb, kBatchSatMode, RCFAR_MAP_F32, s);
+      e = launch_sat(sb, kBatchSatMode, RCFAR_MAP_F32, it_tile, it_band, it_vscan, s);
     }
     if (e == cudaSuccess) {
       TraceScope t(h, "cfar", s);
-      e = launch_cfar(cb, kBatchSatMode, RCFAR_MAP_F32, it_cfar, (size_t)cfar_mode_smem, s);
+      e = launch_cfar(cb, kBatchSatMode, RCFAR_MAP_F32, it_cfar, (size_t)cfar_mode_smem, cfar_max_hc, s);
     }
     if (e != cudaSuccess) return RCFAR_ERR_CUDA;
   }

@@ -30,10 +30,13 @@ constexpr int kSatTileW = 128;  // columns per chunk (32 lanes x 4)
 // ---- preprocessing ----------------------------------------------------------
 constexpr int kStatsStrip = 128;  // columns per column-statistics CTA
 
-// CUDA-core band DFT tile: 128 rows x 64 real outputs (32 bins) x 32 samples.
+// Band DFT GEMM tile: 128 rows x 64 real outputs (32 bins) x 32 samples.
 constexpr int kDftBM = 128;
 constexpr int kDftBN = 64;
 constexpr int kDftBK = 32;
+// y pass: 8 rows (one per warp) x 256 samples per CTA.
+constexpr int kYRows = 8;
+constexpr int kYCols = 256;
 
 struct PreFrameDev {
   const float* x;
@@ -42,8 +45,12 @@ struct PreFrameDev {
   int c0, C;  // stored bins c0 .. c0 + C - 1
   int h;      // mean filter half length
   float mbar, inv_M, inv_D;
-  const float* W;  // twiddles [N][ldw]: column 2j = cos, 2j+1 = -sin of bin c0+j
+  const float2* W2;  // twiddles [npad][ldw]: column 2j = cos, 2j+1 = -sin of bin c0+j,
+                     // each split into a TF32 head and tail {hi, lo}; zero padded
   long long ldw;
+  float2* ysplit;    // [M][npad] y minus its row mean, split {hi, lo}; zero for n >= N
+  float* rowmean;    // [M] the row means c_m removed from y
+  int npad;          // N rounded up to kDftBK
   float2* stats;        // [N] (a_n, b_n) of the fast-time line fit
   float2* partial;      // [n_chunks][N] partial sums (sum x, sum (m-mbar) x)
   float* rowpart;       // [n_strips][M] partial row sums sum_j w_j x[m, j]
@@ -57,8 +64,9 @@ struct PreFrameDev {
   unsigned* tile_cnt;   // [mtiles * ntiles] arrival counters (self-resetting)
   int rows_per_chunk, n_chunks, n_strips;
   int mtiles, ntiles, splitk, kper;
-  int item_stats, item_dft, item_norm;  // first CTA of this frame in each launch
-  int n_norm;                            // CTAs of this frame in k_normalise
+  int item_stats, item_dft, item_norm, item_y;  // first CTA of this frame in each launch
+  int n_norm;                                    // CTAs of this frame in k_normalise
+  int ycols;                                     // column blocks of the y pass
 };
 
 struct PreBatch {
@@ -75,29 +83,20 @@ struct SatMapDev {
   const float* bound_dev;
   float bound;           // |value| bound checked per cell
   long long max_cells;   // largest region (cells) the scale must cover
-  void* table;           // float (TILE_F32, NAIVE) or int64 (I64) [rows][ld_table]
+  void* table;           // float (TILE_F32, NAIVE) or int64 (TILE_I64, I64) [rows][ld_table]
   long long ld_table;
-  // vertical carries: per (band, column) -- band aggregate and inclusive value
-  unsigned long long* v_agg;      // [n_bands][ld_carry]
-  unsigned long long* row_carry;  // [n_bands][ld_carry] = S(last row of band, c)
+  unsigned long long* col_tot;    // [n_bands][ld_carry]: tile column totals, then each band's row prefix
+  unsigned long long* row_tot;    // [n_bands * n_chunks][kSatTileH]: tile row totals
+  unsigned long long* row_carry;  // [n_bands][ld_carry]: S(last row of the band, c)
+  unsigned long long* col_carry;  // [n_chunks][rows]: band-local sum left of the tile, rows <= r
   long long ld_carry;
-  // horizontal carries: per (tile, band row) -- row totals, aggregate and inclusive
-  unsigned long long* h_agg;      // [n_bands * n_chunks][32]
-  unsigned long long* h_inc;      // [n_bands * n_chunks][32]
-  unsigned long long* col_carry;  // [n_chunks][rows] band-local sums left of the tile
-  unsigned* h_flags;     // [n_bands * n_chunks]
-  unsigned* v_flags;     // [n_bands * n_chunks]
   int* scale_out;        // device slot receiving the scale used
   int n_bands, n_chunks;
-  int item0;             // first tile ticket of this map
+  int item_tile, item_band, item_vscan;  // first CTA of this map in each launch
 };
 
 struct SatBatch {
   int n;
-  int total;         // CTAs in the launch (tiles over all maps)
-  unsigned* ticket;  // dynamic tile ticket (self-resetting)
-  unsigned* done;    // CTAs finished (self-resetting)
-  unsigned* gen;     // launch generation tag of the look-back flags
   int* status;
   SatMapDev m[kMaxBatch];
 };
@@ -125,9 +124,12 @@ struct CfarMapDev {
   long long ld_det;
   float* thr;
   long long ld_thr;
-  int tiles_x;         // CTAs per tile row
+  int tiles_x;         // CTAs per row of strips
   int item0;
-  int bh, bw;          // output tile
+  int bh, bw;          // CUT rows per step, strip width
+  int run;             // rows per CTA (a multiple of bh)
+  int ring_rows;       // table rows held in shared memory (power of two)
+  int mode;            // rcfar_sat_mode of the table
 };
 
 struct CfarBatch {
@@ -169,18 +171,22 @@ cudaError_t ensure_smem(const void* fn, size_t bytes);
 
 // ---- launchers (implemented in the .cu files) -------------------------------
 cudaError_t launch_colstats(const PreBatch& b, int blocks, cudaStream_t s);
+cudaError_t launch_ysplit(const PreBatch& b, int blocks, cudaStream_t s);
 cudaError_t launch_band_dft(const PreBatch& b, int blocks, cudaStream_t s);
 cudaError_t launch_normalise(const PreBatch& b, int blocks, cudaStream_t s);
-cudaError_t launch_twiddles(float* W, long long ldw, int N, int c0, int C, cudaStream_t s);
+cudaError_t launch_twiddles(float2* W2, long long ldw, int N, int c0, int C, cudaStream_t s);
 
 cudaError_t launch_map_max(const void* map, int dtype, float in_scale, int rows, int cols, long long ld,
                            float* out_bits, cudaStream_t s);
-cudaError_t launch_sat(const SatBatch& b, int mode, int dtype, cudaStream_t s);
+// Summed-area table of every map of the batch: tile pass, carry scans, and
+// (global I64 / NAIVE_F32 only) the pass that folds the carries in.
+cudaError_t launch_sat(const SatBatch& b, int mode, int dtype, int tiles, int bands, int vscans, cudaStream_t s);
 cudaError_t launch_sat_materialize(const SatMapDev& m, int mode, double* out, long long ld_out,
                                    cudaStream_t s);
 
-cudaError_t launch_cfar(const CfarBatch& b, int mode, int dtype, int blocks, size_t smem, cudaStream_t s);
+cudaError_t launch_cfar(const CfarBatch& b, int mode, int dtype, int blocks, size_t smem, int max_hc, cudaStream_t s);
 size_t cfar_smem_bytes(int mode, int bh, int bw, int wr, int wc);
+int cfar_ring_rows(int bh, int wr);
 cudaError_t launch_cfar_direct(const CfarMapDev& m, int blocks, size_t smem, cudaStream_t s);
 size_t cfar_direct_smem_bytes(int bh, int bw, int wr, int wc);
 

@@ -1,25 +1,21 @@
-// Summed-area table of a CFAR input map (paper eq. 3), one pass over the map.
+// Summed-area table of a CFAR input map (paper eq. 3).
 //
 // The map is cut into tiles of kSatTileH x kSatTileW cells (band b = tile
-// row, chunk j = tile column), one CTA per tile, taken in row-major ticket
-// order. For cell (r, c) of tile (b, j):
-//   S(r, c) = L(r, c) + CC_j(r) + RC_b(c)
+// row, chunk j = tile column). For cell (r, c) of tile (b, j):
+//   S(r, c) = L(r, c) + CC_j(r) + RC_{b-1}(c)
 //   L      : table of the tile relative to its own origin (tile-local)
-//   CC_j(r): sum over band rows <= r and columns left of the tile
-//   RC_b(c): S(first row of band b - 1, c), the table on the row above
-// Both carries are exclusive scans across tiles, resolved with decoupled
-// look-backs: horizontally over the row totals of the tiles to the left
-// (vectors of kSatTileH values), then vertically over the column aggregates
-// of the tiles above (vectors of kSatTileW values). Each tile publishes its
-// aggregate before it looks back, and waits only on tiles with smaller
-// tickets, so the chains stay short and every wait ends.
+//   CC_j(r): sum over the band's rows <= r and the columns left of the tile
+//   RC_b(c): S(last row of band b, c)
+// Three wait-free passes (reduce, then scan, then nothing else to wait for):
+//   k_sat_tile  : one CTA per tile; writes L and the tile's exact row and
+//                 column totals (warp-shuffle row scans, shared-memory column
+//                 scans across the 8 warps);
+//   k_sat_hscan : one CTA per band; the band's row prefix of the column
+//                 totals across the whole width, and CC for every tile;
+//   k_sat_vscan : each column's prefix over bands -> RC.
+//   k_sat_finalize (I64 and NAIVE_F32 only) folds the carries into L.
 // Carries are 64-bit fixed point q = round(x * 2^s) added modulo 2^64
 // (exact; every region sum below 2^63 comes out exact even if S wraps).
-//   TILE_F32 : stores L in FP32, RC (as each band's inclusive values) and CC.
-//   I64      : stores S itself in fixed point (L exact as well).
-//   NAIVE_F32: FP32 everywhere, stores S in FP32.
-// Within a tile, row prefixes use warp shuffles (32 lanes x 4 columns) and
-// column prefixes a shared-memory exchange between the 8 warps.
 #include "rcfar_internal.cuh"
 
 #include <type_traits>
@@ -104,30 +100,6 @@ __device__ __forceinline__ void tile_prefix(T x[4][4], T (*wt)[kSatTileW], int w
     for (int k = 0; k < 4; ++k) x[i][k] += e[k];
 }
 
-__device__ __forceinline__ unsigned ld_flag(const unsigned* p) {
-  unsigned v;
-  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
-  return v;
-}
-__device__ __forceinline__ void st_flag(unsigned* p, unsigned v) {
-  asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
-}
-
-// Poll a look-back flag until it carries this launch's generation and a
-// published state; gives up after kSpinLimit polls, records the timeout and
-// returns 0xffffffff.
-__device__ __forceinline__ unsigned wait_flag(const unsigned* fp, unsigned gen, int* status) {
-  for (unsigned it = 0;; ++it) {
-    const unsigned f = ld_flag(fp);
-    if ((f >> 2) == gen && (f & 3u) != 0u) return f;
-    if (it >= kSpinLimit) {
-      atomicOr(status, kStatusTimeout);
-      return 0xffffffffu;
-    }
-    __nanosleep(32);
-  }
-}
-
 template <typename Acc>
 __device__ __forceinline__ Acc ld_carry(const u64* p) {
   const u64 v = __ldcg(p);
@@ -140,34 +112,31 @@ __device__ __forceinline__ void st_carry(u64* p, Acc v) {
   else __stcg(p, v);
 }
 
-template <int MODE, typename InT>
-__global__ void __launch_bounds__(256) k_sat(const __grid_constant__ SatBatch B) {
+template <int MODE>
+struct SatTypes {
   // Acc: carry arithmetic (exact fixed point, or FP32 for the naive table)
   typedef typename std::conditional<MODE == RCFAR_SAT_NAIVE_F32, float, u64>::type Acc;
   // Loc: tile-local table arithmetic
-  typedef typename std::conditional<MODE == RCFAR_SAT_I64, u64, float>::type Loc;
+  typedef typename std::conditional<MODE == RCFAR_SAT_TILE_I64 || MODE == RCFAR_SAT_I64, u64, float>::type Loc;
+};
 
-  __shared__ unsigned s_item, s_gen;
+// Pass 1: one CTA per tile (warp w: rows 4w..4w+3, lane: columns 4l..4l+3).
+template <int MODE, typename InT>
+__global__ void __launch_bounds__(256) k_sat_tile(const __grid_constant__ SatBatch B) {
+  typedef typename SatTypes<MODE>::Acc Acc;
+  typedef typename SatTypes<MODE>::Loc Loc;
   __shared__ Loc s_wt[8][kSatTileW];
   __shared__ Acc s_wc[8][kSatTileW];
-  __shared__ Acc s_rq[kSatTileH];
-  __shared__ Acc s_cc[kSatTileH];
-  __shared__ Acc s_rc[kSatTileW];
 
   const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
-  if (tid == 0) {
-    s_gen = ld_flag(B.gen);
-    s_item = atomicAdd(B.ticket, 1u);
-  }
-  __syncthreads();
-  const int item = (int)s_item;
-  const unsigned gen = s_gen & 0x3fffffffu;
-  const int mi = find_item(B.m, B.n, item, &SatMapDev::item0);
+  const int mi = find_item(B.m, B.n, (int)blockIdx.x, &SatMapDev::item_tile);
   const SatMapDev& Mp = B.m[mi];
-  const int tile = item - Mp.item0;
-  const int b = tile / Mp.n_chunks, j = tile - b * Mp.n_chunks;
+  const int tile = (int)blockIdx.x - Mp.item_tile;
+  const int nch = Mp.n_chunks;
+  const int b = tile / nch, j = tile - b * nch;
   const int r0 = b * kSatTileH;
   const int cbase = j * kSatTileW + lane * 4;
+  const int rows = Mp.rows, cols = Mp.cols;
   const InT* map = reinterpret_cast<const InT*>(Mp.map);
   const bool vec = ((Mp.ld & 3) == 0) &&
                    ((reinterpret_cast<uintptr_t>(map) & (std::is_same<InT, float>::value ? 15 : 7)) == 0);
@@ -181,13 +150,12 @@ __global__ void __launch_bounds__(256) k_sat(const __grid_constant__ SatBatch B)
   if (tile == 0 && tid == 0 && Mp.scale_out) *Mp.scale_out = s;
   const float scalef = ldexpf(1.0f, s);
 
-  // ---- load and quantise the tile (warp w: rows 4w..4w+3, lane: 4 columns)
   float v[4][4];
 #pragma unroll
   for (int i = 0; i < 4; ++i) {
     const int r = r0 + w * 4 + i;
-    if (r < Mp.rows) {
-      load_row4<InT>(map + (long long)r * Mp.ld, cbase, Mp.cols, vec, Mp.in_scale, v[i]);
+    if (r < rows) {
+      load_row4<InT>(map + (long long)r * Mp.ld, cbase, cols, vec, Mp.in_scale, v[i]);
     } else {
 #pragma unroll
       for (int k = 0; k < 4; ++k) v[i][k] = 0.f;
@@ -204,7 +172,14 @@ __global__ void __launch_bounds__(256) k_sat(const __grid_constant__ SatBatch B)
       else q[i][k] = (u64)__float2ll_rn(v[i][k] * scalef);
     }
 
-  // ---- tile-local table
+  // exact row totals -> row_tot[tile][row]
+  u64* rt = Mp.row_tot + (long long)tile * kSatTileH;
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const Acc t = warp_sum<Acc>(q[i][0] + q[i][1] + q[i][2] + q[i][3]);
+    if (lane == i) st_carry<Acc>(rt + w * 4 + i, t);
+  }
+
   Loc L[4][4];
 #pragma unroll
   for (int i = 0; i < 4; ++i)
@@ -213,195 +188,197 @@ __global__ void __launch_bounds__(256) k_sat(const __grid_constant__ SatBatch B)
       if constexpr (std::is_same<Loc, float>::value) L[i][k] = v[i][k];
       else L[i][k] = q[i][k];
     }
-  tile_prefix<Loc>(L, s_wt, w, lane);
+  constexpr bool kExactL = std::is_same<Loc, u64>::value;
+  // 4-row column sums of q (before the prefix), when L is not exact
+  if constexpr (!kExactL) {
+#pragma unroll
+    for (int k = 0; k < 4; ++k) s_wc[w][lane * 4 + k] = q[0][k] + q[1][k] + q[2][k] + q[3][k];
+  }
+  tile_prefix<Loc>(L, s_wt, w, lane);  // contains a __syncthreads
 
-  if constexpr (MODE == RCFAR_SAT_TILE_F32) {
+  // column totals -> col_tot[b][c]
+  if constexpr (kExactL) {
+    // exact L: its last row (warp 7, row 3) is the tile's column prefix, so
+    // the column totals are its differences along the row
+    if (w == 7) {
+      Acc prev = __shfl_up_sync(0xffffffffu, L[3][3], 1);
+      if (lane == 0) prev = Acc(0);
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        const Acc t = L[3][k] - prev;
+        prev = L[3][k];
+        if (cbase + k < cols) st_carry<Acc>(Mp.col_tot + (long long)b * Mp.ld_carry + cbase + k, t);
+      }
+    }
+  } else {
+    if (w == 0) {
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        Acc sum = s_wc[0][lane * 4 + k];
+#pragma unroll
+        for (int ww = 1; ww < 8; ++ww) sum += s_wc[ww][lane * 4 + k];
+        if (cbase + k < cols) st_carry<Acc>(Mp.col_tot + (long long)b * Mp.ld_carry + cbase + k, sum);
+      }
+    }
+  }
+
+  // the tile-local table
+  if constexpr (std::is_same<Loc, float>::value) {
     float* out = reinterpret_cast<float*>(Mp.table);
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
       const int r = r0 + w * 4 + i;
-      if (r >= Mp.rows) continue;
+      if (r >= rows) continue;
       float* o = out + (long long)r * Mp.ld_table + cbase;
-      if (cbase + 3 < Mp.cols) {
+      if (cbase + 3 < cols) {
         *reinterpret_cast<float4*>(o) = make_float4(L[i][0], L[i][1], L[i][2], L[i][3]);
       } else {
 #pragma unroll
         for (int k = 0; k < 4; ++k)
-          if (cbase + k < Mp.cols) o[k] = L[i][k];
+          if (cbase + k < cols) o[k] = L[i][k];
       }
-    }
-  }
-
-  // ---- row totals (exact) and column sums (exact) of the tile
-#pragma unroll
-  for (int i = 0; i < 4; ++i) {
-    const Acc t = warp_sum<Acc>(q[i][0] + q[i][1] + q[i][2] + q[i][3]);
-    if (lane == i) s_rq[w * 4 + i] = t;
-  }
-  if constexpr (MODE == RCFAR_SAT_I64) {
-    // the exact tile table's last row is the column prefix itself
-    if (w == 7) {
-#pragma unroll
-      for (int k = 0; k < 4; ++k) s_wc[0][lane * 4 + k] = L[3][k];
     }
   } else {
-#pragma unroll
-    for (int k = 0; k < 4; ++k) s_wc[w][lane * 4 + k] = q[0][k] + q[1][k] + q[2][k] + q[3][k];
-  }
-  __syncthreads();
-
-  const int ntile = b * Mp.n_chunks + j;
-  if (w == 0) {
-    // ---- horizontal look-back: lane = band row
-    const Acc my = s_rq[lane];
-    Acc hc = Acc(0);
-    if (j == 0) {
-      st_carry<Acc>(Mp.h_inc + (long long)ntile * kSatTileH + lane, my);
-      __threadfence();
-      __syncwarp();
-      if (lane == 0) st_flag(Mp.h_flags + ntile, (gen << 2) | 2u);
-    } else {
-      st_carry<Acc>(Mp.h_agg + (long long)ntile * kSatTileH + lane, my);
-      __threadfence();
-      __syncwarp();
-      if (lane == 0) st_flag(Mp.h_flags + ntile, (gen << 2) | 1u);
-      // warp-parallel window: lane l polls the tile l places to the left; the
-      // nearest inclusive value ends the walk, aggregates before it are summed
-      for (int jj = j - 1; jj >= 0; jj -= 32) {
-        const int p = jj - lane;
-        unsigned f = 2u;
-        if (p >= 0) f = wait_flag(Mp.h_flags + b * Mp.n_chunks + p, gen, B.status);
-        if (__any_sync(0xffffffffu, f == 0xffffffffu)) break;  // timed out: status recorded
-        const unsigned incm = __ballot_sync(0xffffffffu, p >= 0 && (f & 3u) == 2u);
-        const int take = incm ? __ffs(incm) : min(32, jj + 1);
-        __threadfence();
-        for (int l = 0; l < take; ++l) {
-          const long long pt = (long long)b * Mp.n_chunks + (jj - l);
-          const u64* src = ((incm >> l) & 1u) ? Mp.h_inc : Mp.h_agg;
-          hc += ld_carry<Acc>(src + pt * kSatTileH + lane);
-        }
-        if (incm) break;
-      }
-      st_carry<Acc>(Mp.h_inc + (long long)ntile * kSatTileH + lane, hc + my);
-      __threadfence();
-      __syncwarp();
-      if (lane == 0) st_flag(Mp.h_flags + ntile, (gen << 2) | 2u);
-    }
-    // CC_j(r) = sum over band rows <= r of the horizontal carries
-    Acc cc = hc;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      const Acc y = __shfl_up_sync(0xffffffffu, cc, o);
-      if (lane >= o) cc += y;
-    }
-    s_cc[lane] = cc;
-    if constexpr (MODE == RCFAR_SAT_TILE_F32) {
-      if (r0 + lane < Mp.rows) st_carry<Acc>(Mp.col_carry + (long long)j * Mp.rows + r0 + lane, cc);
-    }
-    const Acc base = __shfl_sync(0xffffffffu, cc, 31);
-
-    // ---- column aggregate A(c) = S_band(last row, c); vertical look-back
-    Acc a[4];
-    if constexpr (MODE == RCFAR_SAT_I64) {
-#pragma unroll
-      for (int k = 0; k < 4; ++k) a[k] = s_wc[0][lane * 4 + k] + base;
-    } else {
-#pragma unroll
-      for (int k = 0; k < 4; ++k) {
-        Acc t = s_wc[0][lane * 4 + k];
-#pragma unroll
-        for (int ww = 1; ww < 8; ++ww) t += s_wc[ww][lane * 4 + k];
-        a[k] = t;
-      }
-#pragma unroll
-      for (int k = 1; k < 4; ++k) a[k] += a[k - 1];
-      const Acc e = warp_excl_scan(a[3], lane);
-#pragma unroll
-      for (int k = 0; k < 4; ++k) a[k] += e + base;
-    }
-    const long long crow = (long long)j * kSatTileW + lane * 4;
-    Acc rc[4] = {Acc(0), Acc(0), Acc(0), Acc(0)};
-    if (b == 0) {
-#pragma unroll
-      for (int k = 0; k < 4; ++k) st_carry<Acc>(Mp.row_carry + crow + k, a[k]);
-      __threadfence();
-      __syncwarp();
-      if (lane == 0) st_flag(Mp.v_flags + ntile, (gen << 2) | 2u);
-    } else {
-      u64* aggp = Mp.v_agg + (long long)b * Mp.ld_carry + crow;
-#pragma unroll
-      for (int k = 0; k < 4; ++k) st_carry<Acc>(aggp + k, a[k]);
-      __threadfence();
-      __syncwarp();
-      if (lane == 0) st_flag(Mp.v_flags + ntile, (gen << 2) | 1u);
-      for (int bb = b - 1; bb >= 0; bb -= 32) {
-        const int p = bb - lane;
-        unsigned f = 2u;
-        if (p >= 0) f = wait_flag(Mp.v_flags + p * Mp.n_chunks + j, gen, B.status);
-        if (__any_sync(0xffffffffu, f == 0xffffffffu)) break;  // timed out: status recorded
-        const unsigned incm = __ballot_sync(0xffffffffu, p >= 0 && (f & 3u) == 2u);
-        const int take = incm ? __ffs(incm) : min(32, bb + 1);
-        __threadfence();
-        for (int l = 0; l < take; ++l) {
-          const u64* src = (((incm >> l) & 1u) ? Mp.row_carry : Mp.v_agg) + (long long)(bb - l) * Mp.ld_carry + crow;
-#pragma unroll
-          for (int k = 0; k < 4; ++k) rc[k] += ld_carry<Acc>(src + k);
-        }
-        if (incm) break;
-      }
-      u64* incp = Mp.row_carry + (long long)b * Mp.ld_carry + crow;
-#pragma unroll
-      for (int k = 0; k < 4; ++k) st_carry<Acc>(incp + k, rc[k] + a[k]);
-      __threadfence();
-      __syncwarp();
-      if (lane == 0) st_flag(Mp.v_flags + ntile, (gen << 2) | 2u);
-    }
-#pragma unroll
-    for (int k = 0; k < 4; ++k) s_rc[lane * 4 + k] = rc[k];
-  }
-
-  if constexpr (MODE != RCFAR_SAT_TILE_F32) {
-    __syncthreads();
-    Acc rcv[4];
-#pragma unroll
-    for (int k = 0; k < 4; ++k) rcv[k] = s_rc[lane * 4 + k];
+    long long* out = reinterpret_cast<long long*>(Mp.table);
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
       const int r = r0 + w * 4 + i;
-      if (r >= Mp.rows) continue;
-      const Acc cc = s_cc[w * 4 + i];
-      if constexpr (MODE == RCFAR_SAT_I64) {
-        long long* o = reinterpret_cast<long long*>(Mp.table) + (long long)r * Mp.ld_table + cbase;
-        if (cbase + 3 < Mp.cols) {
-          const longlong2 v0 = make_longlong2((long long)(L[i][0] + rcv[0] + cc), (long long)(L[i][1] + rcv[1] + cc));
-          const longlong2 v1 = make_longlong2((long long)(L[i][2] + rcv[2] + cc), (long long)(L[i][3] + rcv[3] + cc));
-          reinterpret_cast<longlong2*>(o)[0] = v0;
-          reinterpret_cast<longlong2*>(o)[1] = v1;
-        } else {
-#pragma unroll
-          for (int k = 0; k < 4; ++k)
-            if (cbase + k < Mp.cols) o[k] = (long long)(L[i][k] + rcv[k] + cc);
-        }
+      if (r >= rows) continue;
+      long long* o = out + (long long)r * Mp.ld_table + cbase;
+      if (cbase + 3 < cols) {
+        reinterpret_cast<longlong2*>(o)[0] = make_longlong2((long long)L[i][0], (long long)L[i][1]);
+        reinterpret_cast<longlong2*>(o)[1] = make_longlong2((long long)L[i][2], (long long)L[i][3]);
       } else {
-        float* o = reinterpret_cast<float*>(Mp.table) + (long long)r * Mp.ld_table + cbase;
 #pragma unroll
         for (int k = 0; k < 4; ++k)
-          if (cbase + k < Mp.cols) o[k] = L[i][k] + rcv[k] + cc;
+          if (cbase + k < cols) o[k] = (long long)L[i][k];
       }
     }
   }
-
   if (bad) atomicOr(B.status, kStatusRange);
+}
+
+// Block-wide exclusive scan of one value per thread (256 threads).
+template <typename Acc>
+__device__ __forceinline__ Acc block_excl_scan(Acc x, Acc* s_warp, Acc* total) {
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const Acc e = warp_excl_scan(x, lane);
+  if (lane == 31) s_warp[w] = e + x;
   __syncthreads();
-  if (tid == 0) {
-    __threadfence();
-    const unsigned d = atomicAdd(B.done, 1u);
-    if (d == (unsigned)B.total - 1u) {  // last CTA of the launch: reset for the next one
-      *B.ticket = 0u;
-      *B.done = 0u;
-      __threadfence();
-      atomicAdd(B.gen, 1u);
+  Acc base = Acc(0), tot = Acc(0);
+#pragma unroll
+  for (int ww = 0; ww < 8; ++ww) {
+    const Acc t = s_warp[ww];
+    if (ww < w) base += t;
+    tot += t;
+  }
+  __syncthreads();
+  *total = tot;
+  return base + e;
+}
+
+// Pass 2: one CTA per band. (a) the band's inclusive row prefix of the
+// column totals across the whole width, in place; (b) CC for every tile of
+// the band (warp 0, lane = band row).
+template <typename Acc>
+__global__ void __launch_bounds__(256) k_sat_hscan(const __grid_constant__ SatBatch B) {
+  __shared__ Acc s_warp[8];
+  const int mi = find_item(B.m, B.n, (int)blockIdx.x, &SatMapDev::item_band);
+  const SatMapDev& Mp = B.m[mi];
+  const int b = (int)blockIdx.x - Mp.item_band;
+  const int cols = Mp.cols, rows = Mp.rows;
+  u64* row = Mp.col_tot + (long long)b * Mp.ld_carry;
+  const int per = (cols + 255) / 256;
+  const int c0 = threadIdx.x * per, c1 = min(cols, c0 + per);
+  Acc carry = Acc(0);
+  // in chunks of 256 * per columns: one segment per thread
+  {
+    Acc t = Acc(0);
+    for (int c = c0; c < c1; ++c) t += ld_carry<Acc>(row + c);
+    Acc tot;
+    Acc run = block_excl_scan<Acc>(t, s_warp, &tot) + carry;
+    for (int c = c0; c < c1; ++c) {
+      run += ld_carry<Acc>(row + c);
+      st_carry<Acc>(row + c, run);
     }
+  }
+  if (threadIdx.x < 32) {
+    const int lane = threadIdx.x;
+    const int r0 = b * kSatTileH;
+    const u64* rt = Mp.row_tot + (long long)b * Mp.n_chunks * kSatTileH + lane;
+    Acc hc = Acc(0);
+    for (int j0 = 0; j0 < Mp.n_chunks; j0 += 16) {
+      Acc t[16];  // the next 16 tiles' row totals, loaded together
+#pragma unroll
+      for (int u = 0; u < 16; ++u) t[u] = (j0 + u < Mp.n_chunks) ? ld_carry<Acc>(rt + (long long)(j0 + u) * kSatTileH) : Acc(0);
+#pragma unroll
+      for (int u = 0; u < 16; ++u) {
+        const int j = j0 + u;
+        if (j >= Mp.n_chunks) break;
+        Acc cc = hc;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+          const Acc y = __shfl_up_sync(0xffffffffu, cc, o);
+          if (lane >= o) cc += y;
+        }
+        if (r0 + lane < rows) st_carry<Acc>(Mp.col_carry + (long long)j * rows + r0 + lane, cc);
+        hc += t[u];
+      }
+    }
+  }
+}
+
+// Pass 3: RC_b(c) = sum over bands <= b of the bands' row prefixes.
+// CTA = 32 columns (lane) x 8 groups of bands (warp).
+template <typename Acc>
+__global__ void __launch_bounds__(256) k_sat_vscan(const __grid_constant__ SatBatch B) {
+  __shared__ Acc s_tot[8][32];
+  const int mi = find_item(B.m, B.n, (int)blockIdx.x, &SatMapDev::item_vscan);
+  const SatMapDev& Mp = B.m[mi];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int c = ((int)blockIdx.x - Mp.item_vscan) * 32 + lane;
+  const bool ok = c < Mp.cols;
+  const int G = (Mp.n_bands + 7) / 8;
+  const int b0 = w * G, b1 = min(Mp.n_bands, b0 + G);
+  Acc t = Acc(0);
+  if (ok)
+    for (int b = b0; b < b1; ++b) t += ld_carry<Acc>(Mp.col_tot + (long long)b * Mp.ld_carry + c);
+  s_tot[w][lane] = t;
+  __syncthreads();
+  Acc run = Acc(0);
+  for (int ww = 0; ww < w; ++ww) run += s_tot[ww][lane];
+  if (ok)
+    for (int b = b0; b < b1; ++b) {
+      run += ld_carry<Acc>(Mp.col_tot + (long long)b * Mp.ld_carry + c);
+      st_carry<Acc>(Mp.row_carry + (long long)b * Mp.ld_carry + c, run);
+    }
+}
+
+// I64 and NAIVE_F32: fold the carries into the tile-local table in place.
+template <int MODE>
+__global__ void __launch_bounds__(256) k_sat_finalize(const __grid_constant__ SatBatch B) {
+  typedef typename SatTypes<MODE>::Acc Acc;
+  typedef typename SatTypes<MODE>::Loc Loc;
+  const int mi = find_item(B.m, B.n, (int)blockIdx.x, &SatMapDev::item_tile);
+  const SatMapDev& Mp = B.m[mi];
+  const int tile = (int)blockIdx.x - Mp.item_tile;
+  const int b = tile / Mp.n_chunks, j = tile - b * Mp.n_chunks;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int cbase = j * kSatTileW + lane * 4;
+  Acc rc[4];
+#pragma unroll
+  for (int k = 0; k < 4; ++k)
+    rc[k] = (b > 0 && cbase + k < Mp.cols) ? ld_carry<Acc>(Mp.row_carry + (long long)(b - 1) * Mp.ld_carry + cbase + k)
+                                           : Acc(0);
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const int r = b * kSatTileH + w * 4 + i;
+    if (r >= Mp.rows) continue;
+    const Acc cc = ld_carry<Acc>(Mp.col_carry + (long long)j * Mp.rows + r);
+    Loc* o = reinterpret_cast<Loc*>(Mp.table) + (long long)r * Mp.ld_table + cbase;
+#pragma unroll
+    for (int k = 0; k < 4; ++k)
+      if (cbase + k < Mp.cols) o[k] = o[k] + rc[k] + cc;
   }
 }
 
@@ -432,12 +409,17 @@ __global__ void k_sat_materialize(const __grid_constant__ SatMapDev Mp, double* 
        i += (long long)gridDim.x * blockDim.x) {
     const int r = (int)(i / Mp.cols), c = (int)(i % Mp.cols);
     double v;
-    if constexpr (MODE == RCFAR_SAT_TILE_F32) {
-      const float l = reinterpret_cast<const float*>(Mp.table)[(long long)r * Mp.ld_table + c];
+    if constexpr (MODE == RCFAR_SAT_TILE_F32 || MODE == RCFAR_SAT_TILE_I64) {
       const int band = r / kSatTileH, chunk = c / kSatTileW;
       u64 carry = Mp.col_carry[(long long)chunk * Mp.rows + r];
       if (band > 0) carry += Mp.row_carry[(long long)(band - 1) * Mp.ld_carry + c];
-      v = (double)l + (double)(long long)carry * inv;
+      if constexpr (MODE == RCFAR_SAT_TILE_F32) {
+        const float l = reinterpret_cast<const float*>(Mp.table)[(long long)r * Mp.ld_table + c];
+        v = (double)l + (double)(long long)carry * inv;
+      } else {
+        const u64 l = (u64)reinterpret_cast<const long long*>(Mp.table)[(long long)r * Mp.ld_table + c];
+        v = (double)(long long)(l + carry) * inv;
+      }
     } else if constexpr (MODE == RCFAR_SAT_I64) {
       v = (double)reinterpret_cast<const long long*>(Mp.table)[(long long)r * Mp.ld_table + c] * inv;
     } else {
@@ -465,24 +447,33 @@ cudaError_t launch_map_max(const void* map, int dtype, float in_scale, int rows,
   return cudaGetLastError();
 }
 
-cudaError_t launch_sat(const SatBatch& b, int mode, int dtype, cudaStream_t s) {
-  if (b.total <= 0) return cudaSuccess;
+template <int MODE, typename InT>
+static cudaError_t launch_sat_t(const SatBatch& b, int tiles, int bands, int vscans, cudaStream_t s) {
+  typedef typename SatTypes<MODE>::Acc Acc;
+  k_sat_tile<MODE, InT><<<tiles, 256, 0, s>>>(b);
+  k_sat_hscan<Acc><<<bands, 256, 0, s>>>(b);
+  k_sat_vscan<Acc><<<vscans, 256, 0, s>>>(b);
+  if constexpr (MODE == RCFAR_SAT_I64 || MODE == RCFAR_SAT_NAIVE_F32) k_sat_finalize<MODE><<<tiles, 256, 0, s>>>(b);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_sat(const SatBatch& b, int mode, int dtype, int tiles, int bands, int vscans, cudaStream_t s) {
+  if (tiles <= 0) return cudaSuccess;
   const bool h = dtype == RCFAR_MAP_F16;
   switch (mode) {
     case RCFAR_SAT_TILE_F32:
-      if (h) k_sat<RCFAR_SAT_TILE_F32, __half><<<b.total, 256, 0, s>>>(b);
-      else k_sat<RCFAR_SAT_TILE_F32, float><<<b.total, 256, 0, s>>>(b);
-      break;
+      return h ? launch_sat_t<RCFAR_SAT_TILE_F32, __half>(b, tiles, bands, vscans, s)
+               : launch_sat_t<RCFAR_SAT_TILE_F32, float>(b, tiles, bands, vscans, s);
     case RCFAR_SAT_I64:
-      if (h) k_sat<RCFAR_SAT_I64, __half><<<b.total, 256, 0, s>>>(b);
-      else k_sat<RCFAR_SAT_I64, float><<<b.total, 256, 0, s>>>(b);
-      break;
+      return h ? launch_sat_t<RCFAR_SAT_I64, __half>(b, tiles, bands, vscans, s)
+               : launch_sat_t<RCFAR_SAT_I64, float>(b, tiles, bands, vscans, s);
+    case RCFAR_SAT_TILE_I64:
+      return h ? launch_sat_t<RCFAR_SAT_TILE_I64, __half>(b, tiles, bands, vscans, s)
+               : launch_sat_t<RCFAR_SAT_TILE_I64, float>(b, tiles, bands, vscans, s);
     default:
-      if (h) k_sat<RCFAR_SAT_NAIVE_F32, __half><<<b.total, 256, 0, s>>>(b);
-      else k_sat<RCFAR_SAT_NAIVE_F32, float><<<b.total, 256, 0, s>>>(b);
-      break;
+      return h ? launch_sat_t<RCFAR_SAT_NAIVE_F32, __half>(b, tiles, bands, vscans, s)
+               : launch_sat_t<RCFAR_SAT_NAIVE_F32, float>(b, tiles, bands, vscans, s);
   }
-  return cudaGetLastError();
 }
 
 cudaError_t launch_sat_materialize(const SatMapDev& m, int mode, double* out, long long ld_out, cudaStream_t s) {
@@ -493,6 +484,7 @@ cudaError_t launch_sat_materialize(const SatMapDev& m, int mode, double* out, lo
   switch (mode) {
     case RCFAR_SAT_TILE_F32: k_sat_materialize<RCFAR_SAT_TILE_F32><<<blocks, 256, 0, s>>>(m, out, ld_out); break;
     case RCFAR_SAT_I64: k_sat_materialize<RCFAR_SAT_I64><<<blocks, 256, 0, s>>>(m, out, ld_out); break;
+    case RCFAR_SAT_TILE_I64: k_sat_materialize<RCFAR_SAT_TILE_I64><<<blocks, 256, 0, s>>>(m, out, ld_out); break;
     default: k_sat_materialize<RCFAR_SAT_NAIVE_F32><<<blocks, 256, 0, s>>>(m, out, ld_out); break;
   }
   return cudaGetLastError();

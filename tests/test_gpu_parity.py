@@ -113,7 +113,7 @@ SAT_SHAPES = [(1, 1), (5, 7), (31, 127), (32, 128), (33, 129), (100, 300), (257,
 
 
 @pytest.mark.parametrize("shape", SAT_SHAPES)
-@pytest.mark.parametrize("mode", [0, 1, 2])
+@pytest.mark.parametrize("mode", [0, 1, 2, 3])
 def test_sat_integer_map_exact(rc, h, shape, mode):
     P = synth.integer_map(*shape, hi=16, seed=shape[0] * 1000 + shape[1])
     Pt = dev_t(P)
@@ -126,7 +126,7 @@ def test_sat_integer_map_exact(rc, h, shape, mode):
     np.testing.assert_array_equal(out.cpu().numpy(), ocfar.sat(P))
 
 
-@pytest.mark.parametrize("mode", [0, 1])
+@pytest.mark.parametrize("mode", [0, 1, 3])
 def test_sat_float_map_error_bound(rc, h, mode):
     P = synth.square_law_map(300, 700, n_targets=20, dyn_range_db=40.0, seed=3)
     Pt = dev_t(P)
@@ -135,7 +135,7 @@ def test_sat_float_map_error_bound(rc, h, mode):
     rc.rcfar_sat_materialize(h, view, out)
     S = ocfar.sat(P.astype(np.float64))
     err = np.abs(out.cpu().numpy() - S)
-    if mode == 1:
+    if mode in (1, 3):
         # exact sums of values quantised to 2^-s: at most cells * 2^-(s+1)
         cells = np.arange(1, 301)[:, None] * np.arange(1, 701)[None, :]
         assert np.all(err <= cells * 2.0 ** (-view.scale_log2 - 1) + 1e-9)
@@ -147,10 +147,10 @@ def test_sat_float_map_error_bound(rc, h, mode):
 def test_sat_auto_bound_matches_given_bound(rc, h):
     P = synth.square_law_map(130, 260, n_targets=5, seed=4)
     Pt = dev_t(P)
-    v1 = rc.rcfar_sat(h, Pt, value_bound=0.0, mode=1)
+    v1 = rc.rcfar_sat(h, Pt, value_bound=0.0, mode=3)
     o1 = torch.empty(P.shape, dtype=torch.float64, device="cuda")
     rc.rcfar_sat_materialize(h, v1, o1)
-    v2 = rc.rcfar_sat(h, Pt, value_bound=float(P.max()), mode=1)
+    v2 = rc.rcfar_sat(h, Pt, value_bound=float(P.max()), mode=3)
     o2 = torch.empty(P.shape, dtype=torch.float64, device="cuda")
     rc.rcfar_sat_materialize(h, v2, o2)
     assert rc.rcfar_get_error(h) == rc.RCFAR_OK
@@ -160,12 +160,12 @@ def test_sat_auto_bound_matches_given_bound(rc, h):
 def test_range_error_reported(rc, h):
     P = synth.square_law_map(64, 64, n_targets=0, seed=5)
     P[10, 10] = np.nan
-    rc.rcfar_sat(h, dev_t(P), value_bound=100.0, mode=0)
+    rc.rcfar_sat(h, dev_t(P), value_bound=100.0, mode=3)
     assert rc.rcfar_get_error(h) == rc.RCFAR_ERR_RANGE
     P[10, 10] = 1000.0  # above the stated bound
     rc.rcfar_sat(h, dev_t(P), value_bound=100.0, mode=0)
     assert rc.rcfar_get_error(h) == rc.RCFAR_ERR_RANGE
-    rc.rcfar_sat(h, dev_t(np.minimum(P, 50.0)), value_bound=100.0, mode=0)
+    rc.rcfar_sat(h, dev_t(np.minimum(P, 50.0)), value_bound=100.0, mode=3)
     assert rc.rcfar_get_error(h) == rc.RCFAR_OK
 
 
@@ -196,9 +196,9 @@ def cfar_map(shape, seed):
 
 
 @pytest.mark.parametrize("shape,win,cut", CFAR_CASES)
-@pytest.mark.parametrize("mode", [0, 1, 2])
+@pytest.mark.parametrize("mode", [0, 1, 2, 3])
 def test_cfar_sat_parity(rc, h, shape, win, cut, mode):
-    # I64 (mode 1) is exact: decisions bit-exact outside the 1e-5 tie margin.
+    # I64 and TILE_I64 (modes 1, 3) are exact: decisions bit-exact outside the 1e-5 tie margin.
     # TILE_F32 (0) and NAIVE_F32 (2) hold FP32 table entries: their threshold
     # error is bounded by the table's rounding, and decisions may differ only
     # inside that bound.
@@ -220,7 +220,7 @@ def test_cfar_i64_cut_from_table(rc, h, shape, win, cut):
     # I64 table without the map: the CUT value is the table's 1x1 region sum
     P = cfar_map(shape, seed=shape[0] + shape[1])
     rows, cols = shape
-    view = rc.rcfar_sat(h, dev_t(P), value_bound=float(P.max()), mode=rc.RCFAR_SAT_I64)
+    view = rc.rcfar_sat(h, dev_t(P), value_bound=float(P.max()), mode=rc.RCFAR_SAT_TILE_I64)
     det = torch.full((rows, cols), 7, dtype=torch.uint8, device="cuda")
     thr = torch.full((rows, cols), -1.0, dtype=torch.float32, device="cuda")
     lo, hi = cut if cut is not None else (0, cols - 1)
@@ -258,7 +258,7 @@ def test_cfar_fp16_storage(rc, h):
     Pq = P16.astype(np.float64) * 2.0 ** exp2
     win = (8, 8, 2, 2, 1e-4)
     Pt = dev_t(P16)
-    view = rc.rcfar_sat(h, Pt, value_bound=float(Pq.max()), mode=0, map_exp2=exp2)
+    view = rc.rcfar_sat(h, Pt, value_bound=float(Pq.max()), mode=3, map_exp2=exp2)
     det = torch.empty((200, 300), dtype=torch.uint8, device="cuda")
     thr = torch.empty((200, 300), dtype=torch.float32, device="cuda")
     rc.rcfar_cfar(h, view, Pt, rc.make_window(*win), 0, 299, det, thr, map_exp2=exp2)
@@ -270,7 +270,7 @@ def test_cfar_fp16_storage(rc, h):
 
 def test_worked_example(rc, h):
     P, win, sref, det_ref = worked_example()
-    for mode in (0, 1, 2):
+    for mode in (0, 1, 2, 3):
         det, thr, _ = run_cfar(rc, h, P.astype(np.float32), win, mode, bound=128.0)
         np.testing.assert_array_equal(det, det_ref)
         a = ocfar.alpha(16, win[4])
@@ -281,10 +281,10 @@ def test_planted_target_and_scale_invariance(rc, h):
     rng = np.random.default_rng(5)
     P = rng.exponential(size=(96, 160)).astype(np.float32)
     P[50, 70] += 300.0
-    det, _, _ = run_cfar(rc, h, P, (8, 8, 2, 2, 1e-6), 0, bound=float(P.max()))
+    det, _, _ = run_cfar(rc, h, P, (8, 8, 2, 2, 1e-6), 3, bound=float(P.max()))
     assert det[50, 70] == 1 and det.sum() == 1
     for k in (-10, 12):
-        d2, _, _ = run_cfar(rc, h, P * np.float32(2.0 ** k), (8, 8, 2, 2, 1e-6), 0,
+        d2, _, _ = run_cfar(rc, h, P * np.float32(2.0 ** k), (8, 8, 2, 2, 1e-6), 3,
                             bound=float(P.max()) * 2.0 ** k)
         np.testing.assert_array_equal(d2, det)
 
