@@ -250,6 +250,30 @@ rcfar_status rcfar_batch_bytes(int32_t M, int32_t N, const rcfar_pre_params* p, 
  * that rcfar_run_batch can be captured in a CUDA graph (no allocation inside). */
 rcfar_status rcfar_prepare(rcfar_handle h, const int32_t* Ns, int32_t n, const rcfar_pre_params* p);
 
+/* ---- without allocation ------------------------------------------------ */
+
+/* SAT (exact TILE_I64 table) and SAT CA-CFAR of one float32 map, like
+ * rcfar_sat + rcfar_cfar, for callers that cannot allocate device memory:
+ * code that records into a CUDA graph whose capture forbids allocation,
+ * real-time loops whose memory is fixed at start-up (an allocation may
+ * synchronise the device), hosts without a memory manager. The paper has no
+ * counterpart; this is a deployment variant of the same computation.
+ * No handle and no allocation: the scratch (table and carries) is one
+ * 16 MiB array in the library's device memory, held by every GPU that loads
+ * the library until exit. Maps whose table does not fit (about 1.9 million
+ * cells, e.g. 1024 x 1800) return RCFAR_ERR_UNSUPPORTED, as do windows whose
+ * halo does not fit in shared memory. value_bound must be > 0 (an upper
+ * bound on |value|). status (optional device int32) is zeroed and then set to
+ * a non-zero value if a map value exceeds value_bound or is NaN (results
+ * invalid). The first call on a device looks up the array's device address
+ * and must come before any stream capture. All calls share the array: calls
+ * whose work overlaps on the GPU (other streams, other host threads) race
+ * and must be serialised by the caller. */
+rcfar_status rcfar_sat_cfar_static(const float* map, int32_t rows, int32_t cols, int64_t ld_map, float value_bound,
+                                   const rcfar_window* w, int32_t cut_c_lo, int32_t cut_c_hi, uint8_t* det,
+                                   int64_t ld_det, float* thr, int64_t ld_thr, int32_t* status,
+                                   rcfar_stream stream);
+
 /* ---- tracing ----------------------------------------------------------- */
 
 /* Per-kernel device time of the handle's launches (CUDA events around each

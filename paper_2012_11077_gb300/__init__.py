@@ -38,7 +38,7 @@ EXPORTS = (
     "rcfar_create", "rcfar_destroy", "rcfar_alpha", "rcfar_n_ref", "rcfar_band_plan", "rcfar_sat_scale",
     "rcfar_status_string", "rcfar_preprocess", "rcfar_sat", "rcfar_cfar", "rcfar_cfar_direct",
     "rcfar_sat_materialize", "rcfar_run_batch", "rcfar_batch_bytes", "rcfar_prepare", "rcfar_get_error",
-    "rcfar_trace_enable", "rcfar_trace_read",
+    "rcfar_trace_enable", "rcfar_trace_read", "rcfar_sat_cfar_static",
 )
 
 
@@ -121,6 +121,8 @@ def lib() -> ctypes.CDLL:
             "rcfar_get_error": [P, P],
             "rcfar_trace_enable": [P, I32],
             "rcfar_trace_read": [P, ctypes.POINTER(rcfar_trace_entry), I32, ctypes.POINTER(I32)],
+            "rcfar_sat_cfar_static": [P, I32, I32, I64, F32, ctypes.POINTER(rcfar_window), I32, I32, P, I64, P,
+                                      I64, P, P],
         }
         for name, args in sig.items():
             fn = getattr(L, name)
@@ -290,3 +292,12 @@ def rcfar_trace_read(h: int) -> dict:
     n = ctypes.c_int32()
     _check(lib().rcfar_trace_read(h, arr, 32, ctypes.byref(n)), "rcfar_trace_read")
     return {arr[i].name.decode(): (int(arr[i].launches), float(arr[i].total_ms)) for i in range(n.value)}
+
+
+def rcfar_sat_cfar_static(map_t, value_bound: float, window: rcfar_window, cut_c_lo: int, cut_c_hi: int, det,
+                          thr=None, status=None, stream=None):
+    """SAT + CA-CFAR of a float32 map without any device allocation (see rcfar.h)."""
+    _check(lib().rcfar_sat_cfar_static(_ptr(map_t), int(map_t.shape[0]), int(map_t.shape[1]), _ld(map_t),
+                                       float(value_bound), ctypes.byref(window), int(cut_c_lo), int(cut_c_hi),
+                                       _ptr(det), _ld(det), _ptr(thr), _ld(thr) if thr is not None else 0,
+                                       _ptr(status), _stream(stream)), "rcfar_sat_cfar_static")
