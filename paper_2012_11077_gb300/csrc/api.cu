@@ -26,7 +26,7 @@ inline long long round_up(long long a, long long b) { return ceil_div(a, b) * b;
 inline size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 struct Twiddle {
-  float2* W2 = nullptr;
+  float* Wt = nullptr;
   long long ldw = 0;
 };
 
@@ -49,11 +49,25 @@ struct Carver {
 // so a frame is computed the same way alone and inside any batch).
 struct PreGeom {
   int n_strips, n_chunks, rows_per_chunk;
-  int mtiles, ntiles, splitk, kper;
+  int mtiles, ntiles, splitk, kper, bn, nblocks;
   int n_norm;
   int npad, ycols, n_y;
-  long long ldk;
+  long long ldk, ldw;
 };
+
+// band DFT column tiling: ntiles tiles of bn real outputs (bn a multiple of 16, <= 256)
+inline void dft_cols(int C, int* ntiles, int* bn) {
+  const long long twoC = 2LL * C;
+  *ntiles = (int)ceil_div(twoC, kDftMaxBN);
+  *bn = (int)round_up(ceil_div(twoC, *ntiles), 16);
+}
+
+// dynamic shared memory of a k_band_dft launch whose widest tile is bn
+inline int dft_smem_for(int bn) {
+  const int sb = dft_stage_bytes(bn);
+  const int stages = std::min(kDftMaxStages, (kDftSmemCap - 1024) / sb);
+  return 1024 + stages * sb;
+}
 
 PreGeom pre_geom(int M, int N, int C) {
   PreGeom g;
@@ -64,16 +78,19 @@ PreGeom pre_geom(int M, int N, int C) {
   g.ycols = (int)ceil_div(g.npad, kYCols);
   g.n_y = (int)ceil_div(M, kYRows) * g.ycols;
   g.mtiles = (int)ceil_div(M, kDftBM);
-  g.ntiles = (int)ceil_div(2LL * C, kDftBN);
+  dft_cols(C, &g.ntiles, &g.bn);
+  g.ldw = (long long)g.ntiles * g.bn;
   const int tiles = g.mtiles * g.ntiles;
-  int sk = (int)ceil_div(300, tiles);
-  const int max_sk = (int)std::max<long long>(1, N / 256);
-  if (sk > max_sk) sk = max_sk;
-  if (sk < 1) sk = 1;
-  g.kper = (int)round_up(ceil_div(g.npad, sk), kDftBK);
+  // about one CTA per SM for a frame on its own; every split keeps >= 4 K steps
+  // about one CTA per SM for a frame on its own (one wave); splits are whole K blocks
+  const int kblk = kDftBK * kDftKB;
+  g.nblocks = (int)ceil_div(g.npad, kblk);
+  int sk = std::max(1, 152 / tiles);
+  if (sk > g.nblocks) sk = g.nblocks;
+  g.kper = (int)round_up(ceil_div(g.npad, sk), kblk);
   g.splitk = (int)ceil_div(g.npad, g.kper);
-  g.ldk = round_up(2LL * C, 4);
-  g.n_norm = (int)std::min<long long>(std::max<long long>(1, ceil_div((long long)M * C, 1024)), 1024);
+  g.ldk = g.ldw;
+  g.n_norm = M * (int)ceil_div(C, 256);  // k_dft_reduce: one thread per map cell
   return g;
 }
 
@@ -147,13 +164,17 @@ CfarTile pick_cfar_tile(int mode, int wr, int wc, size_t smem_cap, CfarTile pref
 
 constexpr int kCfarRun = 256;  // rows per SAT-CFAR CTA
 
-// Fills the strip geometry of a CFAR descriptor; returns its CTA count.
+// Fills the strip geometry of a CFAR descriptor; returns its CTA count. Runs
+// are at most kCfarRun rows, and shorter for small maps so that a map on its
+// own still spreads over about two CTAs per SM (the halo rows each run
+// re-reads are cheap in L2 at those sizes). Depends only on the map itself.
 int set_cfar_geometry(CfarMapDev& P, CfarTile t, int rows, int cols) {
   P.bh = t.bh;
   P.bw = t.bw;
-  P.run = (int)round_up(std::min<long long>(kCfarRun, round_up(rows, t.bh)), t.bh);
-  P.ring_rows = cfar_ring_rows(t.bh, P.wr);
   P.tiles_x = (int)ceil_div(cols, t.bw);
+  const long long want = ceil_div((long long)rows * P.tiles_x, 2 * 152);
+  P.run = (int)std::min<long long>(kCfarRun, std::max<long long>(t.bh, round_up(want, t.bh)));
+  P.ring_rows = cfar_ring_rows(t.bh, P.wr);
   return P.tiles_x * (int)ceil_div(rows, P.run);
 }
 
@@ -184,7 +205,9 @@ struct rcfar_ctx {
   unsigned* tile_cnt = nullptr;
   float* kpart = nullptr;
   size_t kpart_floats = 0;
-  float2* ysplit = nullptr;
+  void* kpart_own = nullptr;  // separately allocated K-block partials (grown on demand)
+  float* yhi = nullptr;
+  float* ylo = nullptr;
   float* rowmean = nullptr;
   // per-step SAT
   void* sat_table = nullptr;
@@ -296,13 +319,16 @@ static rcfar_status get_plan(rcfar_ctx* h, int N, int c0, int C, cudaStream_t s,
   if (cudaStreamIsCapturing(s, &cs) == cudaSuccess && cs != cudaStreamCaptureStatusNone)
     return RCFAR_ERR_BAD_STATE;  // plans must exist before capture (rcfar_prepare)
   Twiddle t;
-  t.ldw = round_up(2LL * C, kDftBN);
-  const size_t bytes = (size_t)round_up(N, kDftBK) * t.ldw * sizeof(float2);
-  if (cudaMalloc(&t.W2, bytes) != cudaSuccess) return RCFAR_ERR_CUDA;
-  cudaError_t e = cudaMemsetAsync(t.W2, 0, bytes, s);  // padding rows and columns stay zero
-  if (e == cudaSuccess) e = launch_twiddles(t.W2, t.ldw, N, c0, C, s);
+  int ntiles = 0, bn = 0;
+  dft_cols(C, &ntiles, &bn);
+  t.ldw = (long long)ntiles * bn;
+  const int npad = (int)round_up(N, kDftBK);
+  const size_t bytes = 2 * (size_t)t.ldw * npad * sizeof(float);  // head and tail planes
+  if (cudaMalloc(&t.Wt, bytes) != cudaSuccess) return RCFAR_ERR_CUDA;
+  cudaError_t e = cudaMemsetAsync(t.Wt, 0, bytes, s);  // padding rows and columns stay zero
+  if (e == cudaSuccess) e = launch_twiddles(t.Wt, t.ldw, npad, N, c0, C, s);
   if (e != cudaSuccess) {
-    cudaFree(t.W2);
+    cudaFree(t.Wt);
     return RCFAR_ERR_CUDA;
   }
   h->plans[key] = t;
@@ -325,10 +351,11 @@ static PreFrameDev make_pre_frame(const float* x, int M, int N, long long ldx, c
   F.inv_M = (float)(1.0 / (double)M);
   const double D = (double)M * ((double)M * M - 1.0) / 12.0;
   F.inv_D = D > 0 ? (float)(1.0 / D) : 0.0f;
-  F.W2 = tw.W2;
+  F.Wt = tw.Wt;
   F.ldw = tw.ldw;
   F.npad = g.npad;
   F.ycols = g.ycols;
+  F.bn = g.bn;
   F.rows_per_chunk = g.rows_per_chunk;
   F.n_chunks = g.n_chunks;
   F.n_strips = g.n_strips;
@@ -337,6 +364,7 @@ static PreFrameDev make_pre_frame(const float* x, int M, int N, long long ldx, c
   F.splitk = g.splitk;
   F.kper = g.kper;
   F.ldk = g.ldk;
+  F.nblocks = g.nblocks;
   F.n_norm = g.n_norm;
   return F;
 }
@@ -349,8 +377,8 @@ static size_t frame_data_bytes(int M, int N, int C) {
   t += align256((size_t)g.n_chunks * N * sizeof(float2));          // partial
   t += align256((size_t)g.n_strips * M * sizeof(float));           // rowpart
   t += align256((size_t)g.n_strips * sizeof(float2));              // strip_ab
-  t += g.splitk > 1 ? align256((size_t)g.splitk * M * g.ldk * 4) : 0;
-  t += align256((size_t)M * g.npad * sizeof(float2));              // ysplit
+  t += align256((size_t)g.nblocks * M * g.ldk * 4);              // K-block partials
+  t += 2 * align256((size_t)M * g.npad * sizeof(float));           // yhi, ylo
   t += align256((size_t)M * sizeof(float));                        // rowmean
   t += align256((size_t)M * round_up(C, 4) * 4);                   // map
   t += sat_bytes(M, C, kBatchSatMode);
@@ -422,9 +450,8 @@ rcfar_status rcfar_create(const rcfar_config* cfg, rcfar_handle* out) {
 
   const int R = cfg->max_rows, Cm = std::max(cfg->max_cols, 1), Nm = cfg->max_n;
   // per-step preprocessing: largest frame is max_rows x max_n with up to N/2+1 bins
-  const int max_tiles = (int)(ceil_div(R, kDftBM) * ceil_div(2LL * Cm, kDftBN));
-  // split-K scratch: splitk <= 300 / tiles + 1, rows <= 128 * mtiles, ldk <= 64 * ntiles
-  const size_t kpart = (size_t)(300 + max_tiles) * kDftBM * kDftBN;
+  const int max_tiles = (int)(ceil_div(R, kDftBM) * ceil_div(2LL * Cm, kDftMaxBN));
+  const size_t kpart = 0;  // K-block partials are allocated on first use
   const int max_strips = (int)ceil_div(Nm, kStatsStrip);
   const int max_chunks = (int)ceil_div(R, kStatsRows);
 
@@ -437,7 +464,7 @@ rcfar_status rcfar_create(const rcfar_config* cfg, rcfar_handle* out) {
   total += align256((size_t)max_strips * 4);
   total += align256((size_t)max_tiles * 4);
   total += align256(kpart * 4);
-  total += align256((size_t)R * round_up(Nm, kDftBK) * sizeof(float2));  // ysplit
+  total += 2 * align256((size_t)R * round_up(Nm, kDftBK) * sizeof(float));  // yhi, ylo
   total += align256((size_t)R * sizeof(float));                          // rowmean
   total += sat_bytes(R, Cm, RCFAR_SAT_I64);
   if (cudaMalloc(&h->ws, total) != cudaSuccess) {
@@ -460,7 +487,8 @@ rcfar_status rcfar_create(const rcfar_config* cfg, rcfar_handle* out) {
   h->tile_cnt = cv.take<unsigned>(max_tiles);
   h->kpart = cv.take<float>(kpart);
   h->kpart_floats = kpart;
-  h->ysplit = cv.take<float2>((size_t)R * round_up(Nm, kDftBK));
+  h->yhi = cv.take<float>((size_t)R * round_up(Nm, kDftBK));
+  h->ylo = cv.take<float>((size_t)R * round_up(Nm, kDftBK));
   h->rowmean = cv.take<float>(R);
   {
     SatGeom g = sat_geom(R, Cm);
@@ -489,7 +517,8 @@ rcfar_status rcfar_destroy(rcfar_handle h) {
   if (!h) return RCFAR_ERR_INVALID_ARG;
   DeviceGuard g(h->device);
   cudaError_t e = cudaDeviceSynchronize();
-  for (auto& kv : h->plans) cudaFree(kv.second.W2);
+  for (auto& kv : h->plans) cudaFree(kv.second.Wt);
+  if (h->kpart_own) cudaFree(h->kpart_own);
   for (auto& r : h->trace_pool) {
     cudaEventDestroy(r.a);
     cudaEventDestroy(r.b);
@@ -563,13 +592,31 @@ rcfar_status rcfar_preprocess(rcfar_handle h, const float* x, int32_t M, int32_t
   DeviceGuard dg(h->device);
   cudaStream_t s = (cudaStream_t)stream;
   const PreGeom g = pre_geom(M, N, b.cols);
-  if (g.splitk > 1 && (size_t)g.splitk * M * g.ldk > h->kpart_floats) return RCFAR_ERR_UNSUPPORTED;
+  {
+    // K-block partials: grown on demand (outside stream capture)
+    const size_t need = (size_t)g.nblocks * M * g.ldk;
+    if (need > h->kpart_floats) {
+      cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+      if (cudaStreamIsCapturing(s, &cs) == cudaSuccess && cs != cudaStreamCaptureStatusNone) return RCFAR_ERR_BAD_STATE;
+      if (h->kpart_own) {
+        cudaStreamSynchronize(s);
+        cudaFree(h->kpart_own);
+        h->kpart_own = nullptr;
+        h->kpart_floats = 0;
+      }
+      if (cudaMalloc(&h->kpart_own, need * sizeof(float)) != cudaSuccess) return RCFAR_ERR_CUDA;
+      h->kpart = static_cast<float*>(h->kpart_own);
+      h->kpart_floats = need;
+    }
+  }
   Twiddle tw;
   rcfar_status st = get_plan(h, N, b.c0, b.cols, s, &tw);
   if (st != RCFAR_OK) return st;
 
   static thread_local PreBatch pb;
   pb.n = 1;
+  pb.status = h->status;
+  pb.dft_smem = dft_smem_for(g.bn);
   PreFrameDev& F = pb.f[0];
   F = make_pre_frame(x, M, N, ldx, b, (p->mean_len - 1) / 2, tw, g);
   F.stats = h->stats;
@@ -582,7 +629,8 @@ rcfar_status rcfar_preprocess(rcfar_handle h, const float* x, int32_t M, int32_t
   F.ld_map = ld_map;
   F.kpart = h->kpart;
   F.tile_cnt = h->tile_cnt;
-  F.ysplit = h->ysplit;
+  F.yhi = h->yhi;
+  F.ylo = h->ylo;
   F.rowmean = h->rowmean;
   F.item_stats = 0;
   F.item_dft = 0;
@@ -602,8 +650,8 @@ rcfar_status rcfar_preprocess(rcfar_handle h, const float* x, int32_t M, int32_t
     e = launch_band_dft(pb, g.mtiles * g.ntiles * g.splitk, s);
   }
   if (e == cudaSuccess) {
-    TraceScope t(h, "normalise", s);
-    e = launch_normalise(pb, g.n_norm, s);
+    TraceScope t(h, "dft_reduce", s);
+    e = launch_dft_reduce(pb, g.n_norm, s);
   }
   if (e != cudaSuccess) return RCFAR_ERR_CUDA;
   if (band_out) *band_out = b;
@@ -874,9 +922,15 @@ rcfar_status rcfar_run_batch(rcfar_handle h, const rcfar_frame_desc* frames, int
   for (int base = 0; base < n; base += kMaxBatch) {
     const int cnt = std::min(kMaxBatch, n - base);
     pb.n = cnt;
+    pb.status = h->status;
     sb.n = cnt;
     cb.n = cnt;
     sb.status = h->status;
+    {
+      int bn_max = 16;
+      for (int k = 0; k < cnt; ++k) bn_max = std::max(bn_max, pre_geom(frames[base + k].M, frames[base + k].N, bands[base + k].cols).bn);
+      pb.dft_smem = dft_smem_for(bn_max);
+    }
     int it_stats = 0, it_dft = 0, it_norm = 0, it_cfar = 0, it_y = 0;
     int it_tile = 0, it_band = 0, it_vscan = 0;
     int cfar_mode_smem = 0, cfar_max_hc = 0;
@@ -892,8 +946,9 @@ rcfar_status rcfar_run_batch(rcfar_handle h, const rcfar_frame_desc* frames, int
       F.partial = data.take<float2>((size_t)g.n_chunks * f.N);
       F.rowpart = data.take<float>((size_t)g.n_strips * f.M);
       F.strip_ab = data.take<float2>(g.n_strips);
-      F.kpart = g.splitk > 1 ? data.take<float>((size_t)g.splitk * f.M * g.ldk) : nullptr;
-      F.ysplit = data.take<float2>((size_t)f.M * g.npad);
+      F.kpart = data.take<float>((size_t)g.nblocks * f.M * g.ldk);
+      F.yhi = data.take<float>((size_t)f.M * g.npad);
+      F.ylo = data.take<float>((size_t)f.M * g.npad);
       F.rowmean = data.take<float>(f.M);
       float* map = f.map;
       long long ld_map = f.ld_map;
@@ -943,7 +998,7 @@ rcfar_status rcfar_run_batch(rcfar_handle h, const rcfar_frame_desc* frames, int
       it_tile += sg.n_bands * sg.n_chunks;
       it_band += sg.n_bands;
       it_vscan += (int)ceil_div(C, 32);
-      if (!F.stats || !F.partial || !F.rowpart || !F.strip_ab || !F.ysplit || !F.rowmean || (g.splitk > 1 && !F.kpart) || !map || !m.table ||
+      if (!F.stats || !F.partial || !F.rowpart || !F.strip_ab || !F.yhi || !F.ylo || !F.rowmean || !F.kpart || !map || !m.table ||
           !sat_ok || !F.strip_cnt || !F.tile_cnt || !words)
         return RCFAR_ERR_OUT_OF_WORKSPACE;
 
@@ -989,8 +1044,8 @@ rcfar_status rcfar_run_batch(rcfar_handle h, const rcfar_frame_desc* frames, int
       e = launch_band_dft(pb, it_dft, s);
     }
     if (e == cudaSuccess) {
-      TraceScope t(h, "normalise", s);
-      e = launch_normalise(pb, it_norm, s);
+      TraceScope t(h, "dft_reduce", s);
+      e = launch_dft_reduce(pb, it_norm, s);
     }
     if (e == cudaSuccess) {
       TraceScope t(h, "sat", s);

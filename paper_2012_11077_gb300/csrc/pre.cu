@@ -7,14 +7,16 @@
 //   k_ysplit   : detrend + slow-time mean filter + max|y|; writes y minus
 //                its row mean, split into TF32 head and tail.
 //   k_band_dft : band DFT as a GEMM of y [M x N] with the twiddle matrix
-//                [N x 2C] on the tensor cores (split TF32, three products),
-//                then the magnitude; split-K for small frames. Each row's
+//                [N x 2C] on the tcgen05 tensor cores (split TF32, three
+//                products, accumulator in tensor memory), then the magnitude;
+//                split-K for small frames. Each row's
 //                mean c_m was removed from y and N c_m is added back to bin
 //                0 only: a constant contributes to no other bin, and removing
 //                it keeps the FP32 rounding of the large per-range DC offsets
 //                out of the small bins.
-//   k_normalise: divide the map by max|y| ("then normalized"); the DFT is
-//                linear, so scaling its magnitude equals transforming y/max|y|.
+//   k_dft_reduce: sums the K splits' partials (fixed order), magnitude.
+//   Normalisation ("then normalized") divides the magnitude by max|y|: the
+//   DFT is linear, so this equals transforming y / max|y|.
 //   k_twiddles : twiddle matrix W[n][2j] = cos(2 pi t/N), W[n][2j+1] = -sin,
 //                t = (c0 + j) n mod N, computed once per (N, band) in FP64 and
 //                stored split into TF32 head and tail.
@@ -216,7 +218,8 @@ __global__ void __launch_bounds__(256) k_ysplit(const __grid_constant__ PreBatch
       seg[warp][i] = v;
     }
     __syncwarp();
-    float2* yr = F.ysplit + (long long)m * F.npad;
+    float* yh = F.yhi + (long long)m * F.npad;
+    float* yl = F.ylo + (long long)m * F.npad;
 #pragma unroll
     for (int q = 0; q < kYCols / 32; ++q) {
       const int i = lane + 32 * q;
@@ -231,7 +234,8 @@ __global__ void __launch_bounds__(256) k_ysplit(const __grid_constant__ PreBatch
         ymax = fmaxf(ymax, fabsf(y));
         out = split_tf32(y - cmv);
       }
-      yr[n] = out;
+      yh[n] = out.x;
+      yl[n] = out.y;
     }
   }
 #pragma unroll
@@ -245,37 +249,70 @@ __global__ void __launch_bounds__(256) k_ysplit(const __grid_constant__ PreBatch
   }
 }
 
-// D += A * B for one 16x8x8 TF32 tile (FP32 accumulate).
-__device__ __forceinline__ void mma_tf32(float (&d)[4], const unsigned (&a)[4], const unsigned (&b)[2]) {
-  asm volatile(
-      "mma.sync.aligned.m16n8k8.row.col.f32.tf32.tf32.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
-      "{%0,%1,%2,%3};"
-      : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
-      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
-}
+__device__ __forceinline__ unsigned smem_u32(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
 
-__device__ __forceinline__ void cp_async16(void* smem, const void* gmem, bool valid) {
-  const unsigned saddr = (unsigned)__cvta_generic_to_shared(smem);
+__device__ __forceinline__ void cp_async16(unsigned saddr, const void* gmem, bool valid) {
   const int src_bytes = valid ? 16 : 0;  // 0: the 16 bytes are zero-filled, nothing is read
   asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(saddr), "l"(gmem), "r"(src_bytes) : "memory");
 }
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
-template <int N>
-__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
 
-// Shared-memory strides (in float2) of the GEMM tiles, padded so that the
-// fragment loads of a warp fall on distinct banks.
-constexpr int kAS = kDftBK + 4;  // A tile [BM][BK]
-constexpr int kBS = kDftBN + 4;  // B tile [BK][BN]
+// Shared-memory matrix descriptor of a K-major operand tile whose rows are
+// 128 bytes (32 TF32 values) stored with the 128-byte swizzle: 8-row groups
+// 1024 bytes apart (SBO), layout SWIZZLE_128B, descriptor version 1.
+__device__ __forceinline__ unsigned long long umma_desc(unsigned saddr) {
+  return (unsigned long long)((saddr >> 4) & 0x3FFFu) | (1ull << 16) | ((unsigned long long)(1024 >> 4) << 32) |
+         (1ull << 46) | (2ull << 61);
+}
 
-// Band DFT as a GEMM on the tensor cores: ysplit [M x npad] times the
-// twiddle plan [npad x 2C], then the magnitude of each (cos, -sin) column
-// pair. CTA tile kDftBM rows x kDftBN real outputs; K steps of kDftBK samples
-// are staged with cp.async into a two-stage ring. The 8 warps (4 along M x 2
-// along N, 32 x 32 each) issue m16n8k8 TF32 MMAs on the split operands:
-// head*head + head*tail + tail*head (about 22 bits per product). Each K
-// step's partial sum is added to the running sum with Kahan compensation.
-__global__ void __launch_bounds__(256) k_band_dft(const __grid_constant__ PreBatch b) {
+__device__ __forceinline__ void umma_tf32(unsigned tmem_d, unsigned long long a, unsigned long long b, unsigned idesc,
+                                          unsigned accumulate) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem_d),
+      "l"(a), "l"(b), "r"(idesc), "r"(accumulate));
+}
+
+__device__ __forceinline__ void umma_commit(unsigned bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
+}
+
+__device__ __forceinline__ void mbar_init(unsigned bar, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count));
+}
+__device__ __forceinline__ void mbar_arrive(unsigned bar) {
+  asm volatile("{\n .reg .b64 st;\n mbarrier.arrive.shared::cta.b64 st, [%0];\n}\n" ::"r"(bar) : "memory");
+}
+// Wait for the phase of the given parity to complete; gives up after a bounded
+// number of polls (returns false).
+__device__ __forceinline__ bool mbar_wait(unsigned bar, unsigned parity) {
+  for (unsigned it = 0; it < kSpinLimit; ++it) {
+    unsigned done;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(done)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    if (done) return true;
+  }
+  return false;
+}
+
+
+// Band DFT as a GEMM on the 5th-generation tensor cores: (yhi + ylo) [M x npad]
+// times (Whi + Wlo)^T [npad x ldw] in TF32, three products per K step
+// (tail*head + head*tail + head*head, about 22 bits per product). One CTA per
+// (128-row tile, bn-column tile, K split), 12 warps:
+//   warp 0     issues the MMAs (one thread) into tensor memory;
+//   warps 1-7  stage K steps of 32 samples with cp.async into a ring of
+//              stages in the 128-byte-swizzled K-major layout the MMA reads;
+//   warps 8-11 drain the accumulator every kDftKB K steps (a K block of 128
+//              samples) into that block's partial sums in global memory.
+// Two accumulators alternate, so the MMAs of block b+1 run while block b is
+// drained. k_dft_reduce adds the blocks' partials in a fixed order with
+// Kahan compensation. Every wait is bounded: a timeout records
+// kStatusTimeout and the CTA still drains its MMAs, frees its tensor memory
+// and returns.
+__global__ void __launch_bounds__(kDftThreads, 1) k_band_dft(const __grid_constant__ PreBatch b) {
   const int fi = find_item(b.f, b.n, (int)blockIdx.x, &PreFrameDev::item_dft);
   const PreFrameDev& F = b.f[fi];
   const int local = (int)blockIdx.x - F.item_dft;
@@ -284,195 +321,210 @@ __global__ void __launch_bounds__(256) k_band_dft(const __grid_constant__ PreBat
   const int rem = local % per_split;
   const int mt = rem / F.ntiles, nt = rem % F.ntiles;
   const int m0 = mt * kDftBM;
-  const int j0 = nt * kDftBN;  // real output column
-  const int twoC = 2 * F.C;
-  const int kbeg = ks * F.kper;
+  const int bn = F.bn;
+  const int j0 = nt * bn;  // real output column
+  const int kbeg = ks * F.kper;  // a multiple of 32 * kDftKB
   const int kend = min(F.npad, kbeg + F.kper);
+  const int nk = (kend - kbeg) / kDftBK;
+  const int nblk = (nk + kDftKB - 1) / kDftKB;
+  const int blk0 = kbeg / (kDftBK * kDftKB);  // global index of this CTA's first K block
+  const int stage_bytes = dft_stage_bytes(bn);
+  int stages = (b.dft_smem - 1024) / stage_bytes;
+  if (stages > kDftMaxStages) stages = kDftMaxStages;
 
-  extern __shared__ __align__(16) float2 gsm[];
-  float2* As = gsm;                          // [2][BM][kAS]
-  float2* Bs = gsm + 2 * kDftBM * kAS;       // [2][BK][kBS]
+  extern __shared__ __align__(1024) unsigned char dsm[];
+  unsigned char* base = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(dsm) + 1023) & ~uintptr_t(1023));
+  __shared__ __align__(8) unsigned long long bar_full[kDftMaxStages], bar_empty[kDftMaxStages];
+  __shared__ __align__(8) unsigned long long bar_accf[2], bar_acce[2], bar_done;
+  __shared__ unsigned tmem_slot;
+  __shared__ int s_fail;
 
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const int g = lane >> 2, t = lane & 3;
-  const int wm = (warp & 3) * 32, wn = (warp >> 2) * 32;
-
-  // one K step: A 128 x 32 float2 (2048 16-byte chunks), B 32 x 64 float2 (1024 chunks)
-  auto stage = [&](int buf, int k0) {
-    float2* a = As + buf * kDftBM * kAS;
-    float2* bb = Bs + buf * kDftBK * kBS;
-#pragma unroll
-    for (int q = 0; q < 8; ++q) {
-      const int id = tid + 256 * q;
-      const int r = id >> 4, c2 = (id & 15) * 2;  // 16 chunks of 2 float2 per row
-      const int m = m0 + r;
-      const bool ok = m < F.M;
-      const float2* src = F.ysplit + (long long)(ok ? m : 0) * F.npad + k0 + c2;
-      cp_async16(a + r * kAS + c2, src, ok);
-    }
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      const int id = tid + 256 * q;
-      const int k = id >> 5, c2 = (id & 31) * 2;  // 32 chunks of 2 float2 per row
-      const float2* src = F.W2 + (long long)(k0 + k) * F.ldw + j0 + c2;
-      cp_async16(bb + k * kBS + c2, src, true);
-    }
-    cp_async_commit();
-  };
-
-  float acc[2][4][4], comp[2][4][4];
-#pragma unroll
-  for (int i = 0; i < 2; ++i)
-#pragma unroll
-    for (int j = 0; j < 4; ++j)
-#pragma unroll
-      for (int e = 0; e < 4; ++e) acc[i][j][e] = comp[i][j][e] = 0.f;
-
-  stage(0, kbeg);
-  int buf = 0;
-  for (int k0 = kbeg; k0 < kend; k0 += kDftBK, buf ^= 1) {
-    if (k0 + kDftBK < kend) {
-      stage(buf ^ 1, k0 + kDftBK);
-      cp_async_wait<1>();
-    } else {
-      cp_async_wait<0>();
-    }
-    __syncthreads();
-    const float2* a = As + buf * kDftBM * kAS;
-    const float2* bb = Bs + buf * kDftBK * kBS;
-    float part[2][4][4];
-#pragma unroll
-    for (int i = 0; i < 2; ++i)
-#pragma unroll
-      for (int j = 0; j < 4; ++j)
-#pragma unroll
-        for (int e = 0; e < 4; ++e) part[i][j][e] = 0.f;
-#pragma unroll
-    for (int kk = 0; kk < kDftBK; kk += 8) {
-      unsigned ah[2][4], al[2][4], bh[4][2], bl[4][2];
-#pragma unroll
-      for (int i = 0; i < 2; ++i) {
-        const int mr = wm + i * 16 + g;
-        const float2 v0 = a[mr * kAS + kk + t], v1 = a[(mr + 8) * kAS + kk + t];
-        const float2 v2 = a[mr * kAS + kk + t + 4], v3 = a[(mr + 8) * kAS + kk + t + 4];
-        ah[i][0] = __float_as_uint(v0.x); al[i][0] = __float_as_uint(v0.y);
-        ah[i][1] = __float_as_uint(v1.x); al[i][1] = __float_as_uint(v1.y);
-        ah[i][2] = __float_as_uint(v2.x); al[i][2] = __float_as_uint(v2.y);
-        ah[i][3] = __float_as_uint(v3.x); al[i][3] = __float_as_uint(v3.y);
-      }
-#pragma unroll
-      for (int j = 0; j < 4; ++j) {
-        const int nc = wn + j * 8 + g;
-        const float2 u0 = bb[(kk + t) * kBS + nc], u1 = bb[(kk + t + 4) * kBS + nc];
-        bh[j][0] = __float_as_uint(u0.x); bl[j][0] = __float_as_uint(u0.y);
-        bh[j][1] = __float_as_uint(u1.x); bl[j][1] = __float_as_uint(u1.y);
-      }
-#pragma unroll
-      for (int i = 0; i < 2; ++i)
-#pragma unroll
-        for (int j = 0; j < 4; ++j) {
-          mma_tf32(part[i][j], al[i], bh[j]);
-          mma_tf32(part[i][j], ah[i], bl[j]);
-          mma_tf32(part[i][j], ah[i], bh[j]);
-        }
-    }
-#pragma unroll
-    for (int i = 0; i < 2; ++i)
-#pragma unroll
-      for (int j = 0; j < 4; ++j)
-#pragma unroll
-        for (int e = 0; e < 4; ++e) {
-          const float y = part[i][j][e] - comp[i][j][e];
-          const float s2 = acc[i][j][e] + y;
-          comp[i][j][e] = __fsub_rn(__fsub_rn(s2, acc[i][j][e]), y);
-          acc[i][j][e] = s2;
-        }
-    __syncthreads();  // the next stage() overwrites this buffer
+  unsigned tcols = 32;
+  while ((int)tcols < 2 * bn) tcols <<= 1;
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_slot)),
+                 "r"(tcols));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
   }
-
-  // fragment (i, j): rows wm + 16 i + g (+8), real columns wn + 8 j + 2 t (+1)
-  if (F.splitk == 1) {
-#pragma unroll
-    for (int i = 0; i < 2; ++i)
-#pragma unroll
-      for (int j = 0; j < 4; ++j)
-#pragma unroll
-        for (int hlf = 0; hlf < 2; ++hlf) {
-          const int m = m0 + wm + i * 16 + g + 8 * hlf;
-          const int col = j0 + wn + j * 8 + 2 * t;
-          if (m >= F.M || col >= twoC) continue;
-          float re = acc[i][j][2 * hlf];
-          const float im = acc[i][j][2 * hlf + 1];
-          if (col == 0 && F.c0 == 0) re = fmaf((float)F.N, __ldg(&F.rowmean[m]), re);  // bin 0 gets the mean back
-          F.map[(long long)m * F.ld_map + (col >> 1)] = sqrtf(fmaf(re, re, im * im));
-        }
-    return;
-  }
-
-  // split-K: write partials, the last CTA of this output tile reduces them
-  float* part_out = F.kpart + (long long)ks * F.M * F.ldk;
-#pragma unroll
-  for (int i = 0; i < 2; ++i)
-#pragma unroll
-    for (int j = 0; j < 4; ++j)
-#pragma unroll
-      for (int hlf = 0; hlf < 2; ++hlf) {
-        const int m = m0 + wm + i * 16 + g + 8 * hlf;
-        const int col = j0 + wn + j * 8 + 2 * t;
-        if (m >= F.M || col >= twoC) continue;
-        *reinterpret_cast<float2*>(part_out + (long long)m * F.ldk + col) =
-            make_float2(acc[i][j][2 * hlf], acc[i][j][2 * hlf + 1]);
-      }
-  __shared__ bool is_last;
-  __threadfence();
-  __syncthreads();
   if (tid == 0) {
-    const unsigned old = atomicAdd(&F.tile_cnt[rem], 1u);
-    is_last = (old == (unsigned)F.splitk - 1u);
+    for (int i = 0; i < kDftMaxStages; ++i) {
+      mbar_init(smem_u32(&bar_full[i]), 224);
+      mbar_init(smem_u32(&bar_empty[i]), 1);
+    }
+    for (int i = 0; i < 2; ++i) {
+      mbar_init(smem_u32(&bar_accf[i]), 1);    // accumulator i holds a finished block
+      mbar_init(smem_u32(&bar_acce[i]), 128);  // accumulator i was drained
+    }
+    mbar_init(smem_u32(&bar_done), 1);
+    s_fail = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const unsigned tmem = tmem_slot;
+
+  const unsigned idesc = (1u << 4) | (2u << 7) | (2u << 10) | ((unsigned)(bn >> 3) << 17) |
+                         ((unsigned)(kDftBM >> 4) << 24);
+  if (warp == 0) {
+    if (lane == 0) {
+      for (int i = 0; i < nk; ++i) {
+        const int slot = i % stages;
+        const int bi = i / kDftKB, acc = bi & 1;
+        const bool first = (i % kDftKB) == 0;
+        if (first && bi >= 2 && !mbar_wait(smem_u32(&bar_acce[acc]), (unsigned)(((bi - 2) >> 1) & 1))) {
+          s_fail = 1;
+          break;
+        }
+        if (!mbar_wait(smem_u32(&bar_full[slot]), (unsigned)((i / stages) & 1))) {
+          s_fail = 1;
+          break;
+        }
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        unsigned char* st = base + slot * stage_bytes;
+        const unsigned sa_hi = smem_u32(st), sa_lo = sa_hi + kDftBM * 128;
+        const unsigned sb_hi = sa_lo + kDftBM * 128, sb_lo = sb_hi + bn * 128;
+        const unsigned dacc = tmem + (unsigned)(acc * bn);
+#pragma unroll
+        for (int kk = 0; kk < kDftBK / 8; ++kk) {
+          const unsigned off = kk * 32;  // 8 TF32 values along K
+          const unsigned long long ah = umma_desc(sa_hi + off), al = umma_desc(sa_lo + off);
+          const unsigned long long bh = umma_desc(sb_hi + off), bl = umma_desc(sb_lo + off);
+          umma_tf32(dacc, al, bh, idesc, (!first || kk > 0) ? 1u : 0u);
+          umma_tf32(dacc, ah, bl, idesc, 1u);
+          umma_tf32(dacc, ah, bh, idesc, 1u);
+        }
+        umma_commit(smem_u32(&bar_empty[slot]));  // the slot is free once these MMAs finish
+        if ((i % kDftKB) == kDftKB - 1 || i == nk - 1) umma_commit(smem_u32(&bar_accf[acc]));  // block done
+      }
+      umma_commit(smem_u32(&bar_done));  // tracks every MMA issued above
+    }
+  } else if (warp < 8) {
+    // producers: stage i -> ring slot i % stages: A head | A tail | B head | B tail
+    const int ptid = tid - 32;
+    const long long plane = F.ldw * F.npad;
+    for (int i = 0; i < nk; ++i) {
+      const int slot = i % stages;
+      if (i >= stages && !mbar_wait(smem_u32(&bar_empty[slot]), (unsigned)(((i - stages) / stages) & 1))) {
+        s_fail = 1;
+        break;
+      }
+      unsigned char* st = base + slot * stage_bytes;
+      const unsigned sa_hi = smem_u32(st), sa_lo = sa_hi + kDftBM * 128;
+      const unsigned sb_hi = sa_lo + kDftBM * 128, sb_lo = sb_hi + bn * 128;
+      const int k0 = kbeg + i * kDftBK;
+      for (int id = ptid; id < kDftBM * 8; id += 224) {  // A: 128 rows x 8 chunks of 16 bytes
+        const int rr = id >> 3, c = id & 7;
+        const int m = m0 + rr;
+        const bool ok = m < F.M;
+        const long long off = (long long)(ok ? m : 0) * F.npad + k0 + 4 * c;
+        const unsigned sw = rr * 128 + ((c ^ (rr & 7)) << 4);
+        cp_async16(sa_hi + sw, F.yhi + off, ok);
+        cp_async16(sa_lo + sw, F.ylo + off, ok);
+      }
+      const float* wb = F.Wt + (long long)j0 * F.npad + k0;
+      for (int id = ptid; id < bn * 8; id += 224) {  // B: bn rows (output columns) x 8 chunks
+        const int rr = id >> 3, c = id & 7;
+        const float* src = wb + (long long)rr * F.npad + 4 * c;
+        const unsigned sw = rr * 128 + ((c ^ (rr & 7)) << 4);
+        cp_async16(sb_hi + sw, src, true);
+        cp_async16(sb_lo + sw, src + plane, true);
+      }
+      asm volatile("cp.async.commit_group;" ::: "memory");
+      if (i >= 1) {  // two stages of copies in flight: publish the older one
+        asm volatile("cp.async.wait_group 1;" ::: "memory");
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // visible to the tensor cores
+        mbar_arrive(smem_u32(&bar_full[(i - 1) % stages]));
+      }
+    }
+    asm volatile("cp.async.wait_group 0;" ::: "memory");
+    if (!s_fail && nk >= 1) {
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      mbar_arrive(smem_u32(&bar_full[(nk - 1) % stages]));
+    }
+  } else {
+    // drain warps: warp -> TMEM lanes 32 (warp & 3) .. (tile rows)
+    const int q = warp & 3;
+    const int m = m0 + 32 * q + lane;
+    for (int bi = 0; bi < nblk; ++bi) {
+      const int acc = bi & 1;
+      if (!mbar_wait(smem_u32(&bar_accf[acc]), (unsigned)((bi >> 1) & 1))) {
+        s_fail = 1;
+        break;
+      }
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      float* dst = F.kpart + ((long long)(blk0 + bi) * F.M + (m < F.M ? m : 0)) * F.ldk + j0;
+      for (int c = 0; c < bn; c += 8) {
+        unsigned r[8];
+        const unsigned taddr = tmem + ((unsigned)(32 * q) << 16) + (unsigned)(acc * bn + c);
+        asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                     : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+                     : "r"(taddr));
+        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+        if (m < F.M) {
+          float4* d4 = reinterpret_cast<float4*>(dst + c);
+          d4[0] = make_float4(__uint_as_float(r[0]), __uint_as_float(r[1]), __uint_as_float(r[2]), __uint_as_float(r[3]));
+          d4[1] = make_float4(__uint_as_float(r[4]), __uint_as_float(r[5]), __uint_as_float(r[6]), __uint_as_float(r[7]));
+        }
+      }
+      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+      mbar_arrive(smem_u32(&bar_acce[acc]));
+    }
   }
   __syncthreads();
-  if (!is_last) return;
-  __threadfence();
-  for (int idx = tid; idx < kDftBM * (kDftBN / 2); idx += 256) {
-    const int r = idx / (kDftBN / 2), p = idx % (kDftBN / 2);
-    const int m = m0 + r, col = j0 + 2 * p;
-    if (m >= F.M || col >= twoC) continue;
-    float re = 0.f, im = 0.f;
-    for (int sp = 0; sp < F.splitk; ++sp) {  // fixed order: deterministic
-      const float2 v = __ldcg(reinterpret_cast<const float2*>(F.kpart + ((long long)sp * F.M + m) * F.ldk + col));
-      re += v.x;
-      im += v.y;
-    }
-    if (col == 0 && F.c0 == 0) re = fmaf((float)F.N, __ldg(&F.rowmean[m]), re);  // bin 0 gets the mean back
-    F.map[(long long)m * F.ld_map + (col >> 1)] = sqrtf(fmaf(re, re, im * im));
-  }
-  if (tid == 0) F.tile_cnt[rem] = 0u;
+  const bool ok = mbar_wait(smem_u32(&bar_done), 0u) && !s_fail;
+  if (!ok && tid == 0) atomicOr(b.status, kStatusTimeout);
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(tcols));
 }
 
-__global__ void __launch_bounds__(256) k_normalise(const __grid_constant__ PreBatch b) {
+// Sum of the K blocks' partials in a fixed order with Kahan compensation
+// (deterministic, and the same however the K range was split), magnitude,
+// bin 0's mean added back, and the normalisation by max |y| ("then
+// normalized": the DFT is linear, so this equals transforming y / max|y|).
+// Grid: per frame, rows x ceil(C / 256) CTAs; one thread per map cell.
+__global__ void __launch_bounds__(256) k_dft_reduce(const __grid_constant__ PreBatch b) {
   const int fi = find_item(b.f, b.n, (int)blockIdx.x, &PreFrameDev::item_norm);
   const PreFrameDev& F = b.f[fi];
   const int local = (int)blockIdx.x - F.item_norm;
+  const int cblocks = (F.C + 255) / 256;
+  const int m = local / cblocks;
+  const int j = (local - m * cblocks) * 256 + (int)threadIdx.x;
+  if (m >= F.M || j >= F.C) return;
   const float mx = __uint_as_float(__ldcg(F.ymax));
-  if (!(mx > 0.f)) return;
-  const long long total = (long long)F.M * F.C;
-  for (long long i = (long long)local * 256 + threadIdx.x; i < total; i += (long long)F.n_norm * 256) {
-    const int m = (int)(i / F.C), j = (int)(i % F.C);
-    float* p = F.map + (long long)m * F.ld_map + j;
-    *p = *p / mx;
+  const float inv = mx > 0.f ? 1.f / mx : 1.f;
+  const long long plane = (long long)F.M * F.ldk;
+  const float* src = F.kpart + (long long)m * F.ldk + 2 * j;
+  float re = 0.f, im = 0.f, cr = 0.f, ci = 0.f;
+  for (int bi = 0; bi < F.nblocks; ++bi) {
+    const float2 v = __ldcg(reinterpret_cast<const float2*>(src + bi * plane));
+    const float yr = v.x - cr, tr = re + yr;
+    cr = __fsub_rn(__fsub_rn(tr, re), yr);
+    re = tr;
+    const float yi = v.y - ci, ti = im + yi;
+    ci = __fsub_rn(__fsub_rn(ti, im), yi);
+    im = ti;
   }
+  if (j == 0 && F.c0 == 0) re = fmaf((float)F.N, __ldg(&F.rowmean[m]), re);  // bin 0 gets the mean back
+  F.map[(long long)m * F.ld_map + j] = sqrtf(fmaf(re, re, im * im)) * inv;
 }
 
-__global__ void k_twiddles(float2* W2, long long ldw, int N, int c0, int C) {
+__global__ void k_twiddles(float* Wt, long long ldw, int npad, int N, int c0, int C) {
   const long long total = (long long)N * C;
+  const long long plane = ldw * npad;
   for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < total;
        i += (long long)gridDim.x * blockDim.x) {
-    const int n = (int)(i / C), j = (int)(i % C);
+    const int n = (int)(i % N), j = (int)(i / N);
     const long long t = ((long long)(c0 + j) * n) % N;
     double s, c;
     sincospi(2.0 * (double)t / (double)N, &s, &c);
-    W2[(long long)n * ldw + 2 * j] = split_tf32((float)c);
-    W2[(long long)n * ldw + 2 * j + 1] = split_tf32((float)(-s));
+    const float2 cs = split_tf32((float)c), sn = split_tf32((float)(-s));
+    Wt[(long long)(2 * j) * npad + n] = cs.x;
+    Wt[plane + (long long)(2 * j) * npad + n] = cs.y;
+    Wt[(long long)(2 * j + 1) * npad + n] = sn.x;
+    Wt[plane + (long long)(2 * j + 1) * npad + n] = sn.y;
   }
 }
 
@@ -492,25 +544,25 @@ cudaError_t launch_ysplit(const PreBatch& b, int blocks, cudaStream_t s) {
 
 cudaError_t launch_band_dft(const PreBatch& b, int blocks, cudaStream_t s) {
   if (blocks <= 0) return cudaSuccess;
-  const size_t smem = sizeof(float2) * (2 * kDftBM * kAS + 2 * kDftBK * kBS);
+  const size_t smem = (size_t)b.dft_smem;
   cudaError_t e = ensure_smem(reinterpret_cast<const void*>(&k_band_dft), smem);
   if (e != cudaSuccess) return e;
-  k_band_dft<<<blocks, 256, smem, s>>>(b);
+  k_band_dft<<<blocks, kDftThreads, smem, s>>>(b);
   return cudaGetLastError();
 }
 
-cudaError_t launch_normalise(const PreBatch& b, int blocks, cudaStream_t s) {
+cudaError_t launch_dft_reduce(const PreBatch& b, int blocks, cudaStream_t s) {
   if (blocks <= 0) return cudaSuccess;
-  k_normalise<<<blocks, 256, 0, s>>>(b);
+  k_dft_reduce<<<blocks, 256, 0, s>>>(b);
   return cudaGetLastError();
 }
 
-cudaError_t launch_twiddles(float2* W2, long long ldw, int N, int c0, int C, cudaStream_t s) {
+cudaError_t launch_twiddles(float* Wt, long long ldw, int npad, int N, int c0, int C, cudaStream_t s) {
   const long long total = (long long)N * C;
   int blocks = (int)((total + 255) / 256);
   if (blocks > 4096) blocks = 4096;
   if (blocks < 1) blocks = 1;
-  k_twiddles<<<blocks, 256, 0, s>>>(W2, ldw, N, c0, C);
+  k_twiddles<<<blocks, 256, 0, s>>>(Wt, ldw, npad, N, c0, C);
   return cudaGetLastError();
 }
 

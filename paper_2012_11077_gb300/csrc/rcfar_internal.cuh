@@ -30,10 +30,18 @@ constexpr int kSatTileW = 128;  // columns per chunk (32 lanes x 4)
 // ---- preprocessing ----------------------------------------------------------
 constexpr int kStatsStrip = 128;  // columns per column-statistics CTA
 
-// Band DFT GEMM tile: 128 rows x 64 real outputs (32 bins) x 32 samples.
+// Band DFT GEMM on tcgen05: 128 rows (TMEM lanes) x up to 256 real outputs
+// (TMEM columns) per CTA, K steps of 32 samples (one 128-byte swizzle row).
 constexpr int kDftBM = 128;
-constexpr int kDftBN = 64;
+constexpr int kDftMaxBN = 256;
 constexpr int kDftBK = 32;
+constexpr int kDftMaxStages = 4;
+constexpr int kDftSmemCap = 220 * 1024;
+// K block: the tensor-memory accumulator is drained every kDftKB K steps
+// (128 samples) into a partial sum; partials are added with Kahan
+// compensation (the accumulator's own adds lose precision over long runs).
+constexpr int kDftKB = 4;
+constexpr int kDftThreads = 384;  // warp 0 MMA, warps 1-7 producers, warps 8-11 drain
 // y pass: 8 rows (one per warp) x 256 samples per CTA.
 constexpr int kYRows = 8;
 constexpr int kYCols = 256;
@@ -45,32 +53,37 @@ struct PreFrameDev {
   int c0, C;  // stored bins c0 .. c0 + C - 1
   int h;      // mean filter half length
   float mbar, inv_M, inv_D;
-  const float2* W2;  // twiddles [npad][ldw]: column 2j = cos, 2j+1 = -sin of bin c0+j,
-                     // each split into a TF32 head and tail {hi, lo}; zero padded
-  long long ldw;
-  float2* ysplit;    // [M][npad] y minus its row mean, split {hi, lo}; zero for n >= N
+  const float* Wt;   // twiddles, transposed and split: head [ldw][npad] then tail [ldw][npad];
+                     // row 2j = cos, 2j+1 = -sin of bin c0+j (TF32 bit patterns); zero padded
+  long long ldw;     // real output columns incl. padding = ntiles * bn
+  float* yhi;        // [M][npad] y minus its row mean: TF32 head; zero for n >= N
+  float* ylo;        // [M][npad] the TF32 tail
   float* rowmean;    // [M] the row means c_m removed from y
   int npad;          // N rounded up to kDftBK
+  int bn;            // real output columns per CTA (multiple of 16, <= kDftMaxBN)
   float2* stats;        // [N] (a_n, b_n) of the fast-time line fit
   float2* partial;      // [n_chunks][N] partial sums (sum x, sum (m-mbar) x)
   float* rowpart;       // [n_strips][M] partial row sums sum_j w_j x[m, j]
   float2* strip_ab;     // [n_strips] (sum_j w_j a_j, sum_j w_j b_j) over the strip
   unsigned* strip_cnt;  // [n_strips] arrival counters (self-resetting)
   unsigned* ymax;       // float bits of max |y| over the frame
-  float* map;           // [M][ld_map] band map (unnormalised until k_normalise)
+  float* map;           // [M][ld_map] the normalised band map
   long long ld_map;
-  float* kpart;         // split-K partial sums [splitk][M][ldk]
+  float* kpart;         // K-block partial sums [nblocks][M][ldk] (ldk = ldw)
+  int nblocks;          // npad / (32 * kDftKB), rounded up
   long long ldk;
   unsigned* tile_cnt;   // [mtiles * ntiles] arrival counters (self-resetting)
   int rows_per_chunk, n_chunks, n_strips;
   int mtiles, ntiles, splitk, kper;
   int item_stats, item_dft, item_norm, item_y;  // first CTA of this frame in each launch
-  int n_norm;                                    // CTAs of this frame in k_normalise
+  int n_norm;                                    // CTAs of this frame in k_dft_reduce
   int ycols;                                     // column blocks of the y pass
 };
 
 struct PreBatch {
   int n;
+  int dft_smem;  // dynamic shared memory of the k_band_dft launch
+  int* status;   // device status word (bounded waits)
   PreFrameDev f[kMaxBatch];
 };
 
@@ -173,8 +186,10 @@ cudaError_t ensure_smem(const void* fn, size_t bytes);
 cudaError_t launch_colstats(const PreBatch& b, int blocks, cudaStream_t s);
 cudaError_t launch_ysplit(const PreBatch& b, int blocks, cudaStream_t s);
 cudaError_t launch_band_dft(const PreBatch& b, int blocks, cudaStream_t s);
-cudaError_t launch_normalise(const PreBatch& b, int blocks, cudaStream_t s);
-cudaError_t launch_twiddles(float2* W2, long long ldw, int N, int c0, int C, cudaStream_t s);
+cudaError_t launch_dft_reduce(const PreBatch& b, int blocks, cudaStream_t s);
+cudaError_t launch_twiddles(float* Wt, long long ldw, int npad, int N, int c0, int C, cudaStream_t s);
+// bytes of one K step of the band DFT ring: A head and tail (128 rows), B head and tail (bn rows)
+__host__ __device__ inline int dft_stage_bytes(int bn) { return 2 * kDftBM * 128 + 2 * bn * 128; }
 
 cudaError_t launch_map_max(const void* map, int dtype, float in_scale, int rows, int cols, long long ld,
                            float* out_bits, cudaStream_t s);
