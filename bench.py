@@ -43,6 +43,7 @@ def parse_args():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-map", action="store_true", help="skip the 8192^2 SAT+CFAR measurement")
+    ap.add_argument("--no-batch", action="store_true", help="skip the 64-frame mixed batch measurement")
     return ap.parse_args()
 
 
@@ -58,55 +59,104 @@ def load_peaks():
 
 
 class ClockSampler:
-    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+    """SM clock and clock-event (throttle) reasons sampled during the timed region.
 
-    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
-         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
-         "clocks_event_reasons.sw_power_cap")
+    Reads NVML through ctypes every 0.5 ms on a background thread (read-only
+    queries; no setting is changed); falls back to nvidia-smi at 200 ms.
+    """
+
+    REASONS = {0x4: "sw_power_cap", 0x8: "hw_slowdown", 0x20: "sw_thermal_slowdown",
+               0x40: "hw_thermal_slowdown", 0x80: "hw_power_brake_slowdown"}
 
     def __init__(self, device_index: int):
         self.dev = device_index
+        self.samples, self.reasons = [], set()
+        self.max_mhz = None
+        self.thread = None
         self.proc = None
-        self.path = None
+        self.lib = None
+        try:
+            import ctypes
+            lib = ctypes.CDLL("libnvidia-ml.so.1")
+            if lib.nvmlInit_v2() != 0:
+                raise OSError("nvmlInit failed")
+            h = ctypes.c_void_p()
+            if lib.nvmlDeviceGetHandleByIndex_v2(ctypes.c_uint(device_index), ctypes.byref(h)) != 0:
+                raise OSError("no NVML handle")
+            mx = ctypes.c_uint()
+            if lib.nvmlDeviceGetMaxClockInfo(h, ctypes.c_int(1), ctypes.byref(mx)) == 0:
+                self.max_mhz = float(mx.value)
+            self.lib, self.h, self.ct = lib, h, ctypes
+        except Exception:
+            self.lib = None
+
+    def _loop(self):
+        import time as _t
+        ct, lib, h = self.ct, self.lib, self.h
+        clk, rs = ct.c_uint(), ct.c_ulonglong()
+        reason_fn = getattr(lib, "nvmlDeviceGetCurrentClocksEventReasons", None) or \
+            getattr(lib, "nvmlDeviceGetCurrentClocksThrottleReasons")
+        while self.running:
+            if lib.nvmlDeviceGetClockInfo(h, ct.c_int(1), ct.byref(clk)) == 0:
+                self.samples.append(float(clk.value))
+            if reason_fn(h, ct.byref(rs)) == 0:
+                for bit, name in self.REASONS.items():
+                    if rs.value & bit:
+                        self.reasons.add(name)
+            _t.sleep(0.0005)
 
     def start(self):
+        if self.lib is not None:
+            import threading
+            self.running = True
+            self.thread = threading.Thread(target=self._loop, daemon=True)
+            self.thread.start()
+            return
         try:
             fd, self.path = tempfile.mkstemp(suffix=".csv")
             os.close(fd)
             self.f = open(self.path, "w")
-            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.dev), f"--query-gpu={self.Q}",
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.dev), "--query-gpu=clocks.sm,clocks.max.sm,"
+                                          "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+                                          "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap",
                                           "--format=csv,noheader,nounits", "-lms", "200"],
                                          stdout=self.f, stderr=subprocess.DEVNULL)
         except Exception:
             self.proc = None
 
     def stop(self):
+        if self.thread is not None:
+            self.running = False
+            self.thread.join()
+            return {"sm_mhz": statistics.median(self.samples) if self.samples else None,
+                    "sm_max_mhz": self.max_mhz, "reasons": sorted(self.reasons), "samples": len(self.samples),
+                    "source": "nvml"}
         if self.proc is None:
-            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no clock source"], "samples": 0}
         self.proc.terminate()
         try:
             self.proc.wait(timeout=5)
         except Exception:
             self.proc.kill()
         self.f.close()
-        sm, smax, reasons = [], [], set()
+        sm, smax = [], []
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
         with open(self.path) as f:
             for line in f:
                 p = [x.strip() for x in line.split(",")]
-                if len(p) < 9:
+                if len(p) < 6:
                     continue
                 try:
-                    sm.append(float(p[1]))
-                    smax.append(float(p[2]))
+                    sm.append(float(p[0]))
+                    smax.append(float(p[1]))
                 except ValueError:
                     continue
-                for n, v in zip(names, p[5:9]):
+                for n, v in zip(names, p[2:6]):
                     if v.lower() == "active":
-                        reasons.add(n)
+                        self.reasons.add(n)
         os.unlink(self.path)
         return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
-                "reasons": sorted(reasons), "samples": len(sm)}
+                "reasons": sorted(self.reasons), "samples": len(sm), "source": "nvidia-smi"}
 
 
 def dist_setup():
@@ -182,6 +232,87 @@ def reference_arm(args, rank):
                              "sample": f"{args.steps} frames of 1024x4096, numpy FP64 (BLAS threads = all cores)"},
             "e2e": {"value": v, "unit": "frames/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------- batching
+def batch_measure(rc, torch, synth, local, rank, n_frames=64, reps=5):
+    """64 frames of uneven size and window: one rcfar_run_batch (graph-captured)
+    against looping the per-frame path (rcfar_preprocess, rcfar_sat,
+    rcfar_cfar) over the same frames; both produce the same decisions."""
+    cases = synth.mixed_batch_cases(n_frames, seed=100 + rank)
+    params = rc.make_pre_params(synth.FS_HZ, mean_len=5, halo_c=-1)
+    h = rc.rcfar_create(device=local, max_rows=1024, max_cols=1024, max_n=4096, max_window=32,
+                        max_frames=n_frames, batch_bytes=3 << 30)
+    frames, descs, dets, single = [], [], [], []
+    samples = 0
+    for c in cases:
+        x = torch.from_numpy(synth.radar_frame(c.spec)).cuda()
+        w = c.window
+        win = rc.make_window(w.train_r, w.train_c, w.guard_r, w.guard_c, w.pfa)
+        p1 = rc.make_pre_params(synth.FS_HZ, mean_len=5, halo_c=w.train_c + w.guard_c)
+        band = rc.rcfar_band_plan(c.spec.N, p1)
+        det = torch.empty((c.spec.M, band.cols), dtype=torch.uint8, device="cuda")
+        det1 = torch.empty_like(det)
+        P1 = torch.empty((c.spec.M, band.cols), dtype=torch.float32, device="cuda")
+        frames.append(x)
+        dets.append(det)
+        descs.append(rc.frame_desc(x, win, det))
+        single.append((x, p1, band, win, det1, P1))
+        samples += c.spec.M * c.spec.N
+    rc.rcfar_prepare(h, descs, params)
+
+    def per_frame():
+        for x, p1, band, win, det1, P1 in single:
+            rc.rcfar_preprocess(h, x, p1, P1)
+            v = rc.rcfar_sat(h, P1, value_bound=band.value_bound, mode=rc.RCFAR_SAT_TILE_I64)
+            rc.rcfar_cfar(h, v, P1, win, band.k_lo - band.c0, band.k_hi - band.c0, det1)
+
+    def batched():
+        rc.rcfar_run_batch(h, descs, params)
+
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+    def timed(fn, n):
+        for _ in range(2):
+            fn()
+        torch.cuda.synchronize()
+        e0.record()
+        for _ in range(n):
+            fn()
+        e1.record()
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / n
+
+    t_single = timed(per_frame, reps)
+    t_batch_eager = timed(batched, reps)
+    stream = torch.cuda.Stream()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.stream(stream):
+        batched()
+        stream.synchronize()
+        with torch.cuda.graph(g, stream=stream):
+            batched()
+    torch.cuda.synchronize()
+    t_batch = timed(g.replay, reps)
+    rc.rcfar_trace_enable(h, True)
+    batched()
+    tr = rc.rcfar_trace_read(h)
+    rc.rcfar_trace_enable(h, False)
+    per_frame()
+    g.replay()
+    torch.cuda.synchronize()
+    same = all(torch.equal(d, s[4]) for d, s in zip(dets, single))
+    ok = rc.rcfar_get_error(h) == rc.RCFAR_OK
+    rc.rcfar_destroy(h)
+    return {"frames": n_frames, "workload": "64 frames, M ~ U{128..1024}, N ~ U{256..4096}, training {4,8,16}, "
+                                            "guard {1,2,4}, Pfa {1e-3,1e-4,1e-6}, 0-10 targets",
+            "batched_frames_per_s": n_frames / (t_batch * 1e-3),
+            "batched_eager_frames_per_s": n_frames / (t_batch_eager * 1e-3),
+            "per_frame_path_frames_per_s": n_frames / (t_single * 1e-3),
+            "speedup_vs_per_frame": t_single / t_batch,
+            "kernels_us": {k: 1e3 * t / n for k, (n, t) in tr.items()},
+            "samples_per_s": samples / (t_batch * 1e-3),
+            "decisions_identical": bool(same and ok)}
 
 
 # ---------------------------------------------------------------- our arm
@@ -265,11 +396,14 @@ def ours(args, rank, world, local, dist):
     rc.rcfar_trace_enable(h, False)
     step_kernels = {k: {"launches": n, "avg_us": 1e3 * t / n} for k, (n, t) in trace.items()}
     dft_us = step_kernels["band_dft"]["avg_us"]
-    dft_flops = 8.0 * M * N * C  # 2 flops x M rows x N samples x 2C real outputs
-    fp32_peak = 152 * 128 * 2 * peaks["sm_max_mhz"] * 1e6 / 1e12  # TFLOP/s, FP32 FMA pipe at max clock
-    roofline = {"kernel": "band_dft", "bound": "alu", "achieved": dft_flops / (dft_us * 1e-6) / 1e12,
-                "peak": fp32_peak, "unit": "TFLOP/s", "traffic": None,
-                "peak_source": "152 SMs x 128 FP32 lanes x 2 flop x %.0f MHz (max SM clock)" % peaks["sm_max_mhz"]}
+    # algorithmic flops of the band DFT: 2 flops x M rows x N samples x 2C real outputs (one product;
+    # the kernel issues three split-TF32 products, so frac <= 1/3 by construction)
+    dft_flops = 8.0 * M * N * C
+    tf32_peak = peaks["bf16_tflops"] * 0.5  # dense TF32 = half the measured dense BF16 rate (nominal ratio)
+    roofline = {"kernel": "band_dft", "bound": "tensor", "achieved": dft_flops / (dft_us * 1e-6) / 1e12,
+                "peak": tf32_peak, "unit": "TFLOP/s", "traffic": None,
+                "peak_source": "measured bf16 burst %.1f TFLOP/s x 0.5 (TF32/BF16 nominal ratio)" % peaks["bf16_tflops"],
+                "issued_products": 3}
     roofline["frac"] = roofline["achieved"] / roofline["peak"]
 
     # end to end through the public API with host buffers: H2D frame, chain, D2H decisions
@@ -342,6 +476,10 @@ def ours(args, rank, world, local, dist):
                                  "unit": "GB/s", "frac": ach / peaks["hbm_gbs"], "traffic": None}}
         assert rc.rcfar_get_error(h) == rc.RCFAR_OK
 
+    batch = None
+    if not args.no_batch:
+        batch = batch_measure(rc, torch, synth, local, rank)
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         v, n, el = oracle_rate()
@@ -359,7 +497,7 @@ def ours(args, rank, world, local, dist):
                                    "Pfa 1e-6, mean filter 5, fs 20 Hz)",
                        "l2": "inputs larger than L2: ring of 16 distinct frames (268 MB)",
                        "parallelism": f"replicas x{world}"},
-            "roofline": roofline, "kernels": step_kernels, "sat_cfar": sat_cfar, "e2e": e2e,
+            "roofline": roofline, "kernels": step_kernels, "sat_cfar": sat_cfar, "batch": batch, "e2e": e2e,
             "cpu_baseline": cpu, "clocks": clk, "gpu_launches": launches_per_step * args.steps,
             "peaks": peaks["source"]}
     print(json.dumps(line), flush=True)

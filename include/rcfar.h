@@ -246,9 +246,11 @@ rcfar_status rcfar_run_batch(rcfar_handle h, const rcfar_frame_desc* frames, int
  * needed when p->halo_c is -1) takes in a batch. */
 rcfar_status rcfar_batch_bytes(int32_t M, int32_t N, const rcfar_pre_params* p, const rcfar_window* w,
                                int64_t* bytes_out);
-/* Builds the twiddle tables a batch of these sizes needs ahead of time, so
- * that rcfar_run_batch can be captured in a CUDA graph (no allocation inside). */
-rcfar_status rcfar_prepare(rcfar_handle h, const int32_t* Ns, int32_t n, const rcfar_pre_params* p);
+/* Builds the twiddle tables rcfar_run_batch will need for these frames (and
+ * rcfar_preprocess for frames of the same N and band) ahead of time, so that
+ * those calls can be captured in a CUDA graph (no allocation inside). Only
+ * the frames' N and windows are read. */
+rcfar_status rcfar_prepare(rcfar_handle h, const rcfar_frame_desc* frames, int32_t n, const rcfar_pre_params* p);
 
 /* ---- without allocation ------------------------------------------------ */
 

@@ -117,7 +117,7 @@ def lib() -> ctypes.CDLL:
             "rcfar_run_batch": [P, ctypes.POINTER(rcfar_frame_desc), I32, ctypes.POINTER(rcfar_pre_params), P],
             "rcfar_batch_bytes": [I32, I32, ctypes.POINTER(rcfar_pre_params), ctypes.POINTER(rcfar_window),
                                   ctypes.POINTER(I64)],
-            "rcfar_prepare": [P, ctypes.POINTER(I32), I32, ctypes.POINTER(rcfar_pre_params)],
+            "rcfar_prepare": [P, ctypes.POINTER(rcfar_frame_desc), I32, ctypes.POINTER(rcfar_pre_params)],
             "rcfar_get_error": [P, P],
             "rcfar_trace_enable": [P, I32],
             "rcfar_trace_read": [P, ctypes.POINTER(rcfar_trace_entry), I32, ctypes.POINTER(I32)],
@@ -277,9 +277,9 @@ def rcfar_run_batch(h: int, frames: Sequence[rcfar_frame_desc], params: rcfar_pr
     _check(lib().rcfar_run_batch(h, arr, len(frames), ctypes.byref(params), _stream(stream)), "rcfar_run_batch")
 
 
-def rcfar_prepare(h: int, Ns: Sequence[int], params: rcfar_pre_params):
-    arr = (ctypes.c_int32 * len(Ns))(*[int(n) for n in Ns])
-    _check(lib().rcfar_prepare(h, arr, len(Ns), ctypes.byref(params)), "rcfar_prepare")
+def rcfar_prepare(h: int, frames: Sequence[rcfar_frame_desc], params: rcfar_pre_params):
+    arr = (rcfar_frame_desc * len(frames))(*frames)
+    _check(lib().rcfar_prepare(h, arr, len(frames), ctypes.byref(params)), "rcfar_prepare")
 
 
 def rcfar_trace_enable(h: int, on: bool = True):

@@ -15,7 +15,7 @@ using namespace rcfar;
 
 namespace {
 
-constexpr int kStatsRows = 64;  // rows per column-statistics CTA
+constexpr int kStatsRows = kStatsRowsPerChunk;  // rows per column-statistics CTA
 // The batched chain stores the exact 64-bit tile-local table: its decisions
 // are exact for every window (the FP32 tile-local table loses small windows'
 // sums), and it needs no pass to fold the carries in.
@@ -69,7 +69,10 @@ inline int dft_smem_for(int bn) {
   return 1024 + stages * sb;
 }
 
-PreGeom pre_geom(int M, int N, int C) {
+// kblocks_per_cta > 0 fixes how many K blocks one CTA of the band DFT takes
+// (a batch spreads its total work); 0 = one wave for this frame alone. The
+// split never changes results: every K block's partial is reduced in order.
+PreGeom pre_geom(int M, int N, int C, int kblocks_per_cta = 0) {
   PreGeom g;
   g.n_strips = (int)ceil_div(N, kStatsStrip);
   g.rows_per_chunk = kStatsRows;
@@ -85,7 +88,7 @@ PreGeom pre_geom(int M, int N, int C) {
   // about one CTA per SM for a frame on its own (one wave); splits are whole K blocks
   const int kblk = kDftBK * kDftKB;
   g.nblocks = (int)ceil_div(g.npad, kblk);
-  int sk = std::max(1, 152 / tiles);
+  int sk = kblocks_per_cta > 0 ? (int)ceil_div(g.nblocks, kblocks_per_cta) : std::max(1, 152 / tiles);
   if (sk > g.nblocks) sk = g.nblocks;
   g.kper = (int)round_up(ceil_div(g.npad, sk), kblk);
   g.splitk = (int)ceil_div(g.npad, g.kper);
@@ -866,14 +869,16 @@ rcfar_status rcfar_batch_bytes(int32_t M, int32_t N, const rcfar_pre_params* p, 
   return RCFAR_OK;
 }
 
-rcfar_status rcfar_prepare(rcfar_handle h, const int32_t* Ns, int32_t n, const rcfar_pre_params* p) {
-  if (!h || (!Ns && n > 0) || n < 0 || !valid_pre(p)) return RCFAR_ERR_INVALID_ARG;
+rcfar_status rcfar_prepare(rcfar_handle h, const rcfar_frame_desc* frames, int32_t n, const rcfar_pre_params* p) {
+  if (!h || (!frames && n > 0) || n < 0 || !valid_pre(p)) return RCFAR_ERR_INVALID_ARG;
   DeviceGuard dg(h->device);
   for (int i = 0; i < n; ++i) {
+    rcfar_pre_params pf = *p;
+    if (pf.halo_c < 0) pf.halo_c = frames[i].window.guard_c + frames[i].window.train_c;
     rcfar_band b;
-    if (!band_of(Ns[i], p, &b)) return RCFAR_ERR_INVALID_ARG;
+    if (!band_of(frames[i].N, &pf, &b)) return RCFAR_ERR_INVALID_ARG;
     Twiddle tw;
-    rcfar_status st = get_plan(h, Ns[i], b.c0, b.cols, 0, &tw);
+    rcfar_status st = get_plan(h, frames[i].N, b.c0, b.cols, 0, &tw);
     if (st != RCFAR_OK) return st;
   }
   return cuda_fail(cudaDeviceSynchronize());
@@ -926,10 +931,17 @@ rcfar_status rcfar_run_batch(rcfar_handle h, const rcfar_frame_desc* frames, int
     sb.n = cnt;
     cb.n = cnt;
     sb.status = h->status;
+    int kb_per_cta = 1;
     {
       int bn_max = 16;
-      for (int k = 0; k < cnt; ++k) bn_max = std::max(bn_max, pre_geom(frames[base + k].M, frames[base + k].N, bands[base + k].cols).bn);
+      long long units = 0;  // (output tile, K block) pairs of the band DFT over the group
+      for (int k = 0; k < cnt; ++k) {
+        const PreGeom g0 = pre_geom(frames[base + k].M, frames[base + k].N, bands[base + k].cols);
+        bn_max = std::max(bn_max, g0.bn);
+        units += (long long)g0.mtiles * g0.ntiles * g0.nblocks;
+      }
       pb.dft_smem = dft_smem_for(bn_max);
+      kb_per_cta = (int)std::max<long long>(1, units / (2 * 152));  // about two waves
     }
     int it_stats = 0, it_dft = 0, it_norm = 0, it_cfar = 0, it_y = 0;
     int it_tile = 0, it_band = 0, it_vscan = 0;
@@ -939,7 +951,7 @@ rcfar_status rcfar_run_batch(rcfar_handle h, const rcfar_frame_desc* frames, int
       const rcfar_frame_desc& f = frames[i];
       const rcfar_band& b = bands[i];
       const int C = b.cols;
-      const PreGeom g = pre_geom(f.M, f.N, C);
+      const PreGeom g = pre_geom(f.M, f.N, C, kb_per_cta);
       PreFrameDev& F = pb.f[k];
       F = make_pre_frame(f.x, f.M, f.N, f.ldx, b, (p->mean_len - 1) / 2, tws[i], g);
       F.stats = data.take<float2>(f.N);

@@ -21,6 +21,8 @@ namespace {
 
 typedef unsigned long long u64;
 
+constexpr int kMaxCutRows = 4;  // CUT rows per thread and step: bh * bw <= 256 * kMaxCutRows
+
 
 __device__ __forceinline__ float ld_map_val(const float* p, float) { return __ldg(p); }
 __device__ __forceinline__ float ld_map_val(const __half* p, float scale) { return __half2float(__ldg(p)) * scale; }
@@ -127,9 +129,9 @@ __global__ void __launch_bounds__(256) k_cfar(const __grid_constant__ CfarBatch 
     if (g0 < need) fetch_row(g0, nxt[0]);
     if (g1 < need) fetch_row(g1, nxt[1]);
     // this step's CUT values from the map (when reading them from it)
-    float cutv[4];
+    float cutv[kMaxCutRows];
 #pragma unroll
-    for (int i = 0; i < 4; ++i) {
+    for (int i = 0; i < kMaxCutRows; ++i) {
       const int r = R + tid / bw + i * rstep;
       cutv[i] = 0.f;
       if (map != nullptr && i * rstep < bh && col_cut && r < rend && r >= row_lo && r <= row_hi)
@@ -137,7 +139,7 @@ __global__ void __launch_bounds__(256) k_cfar(const __grid_constant__ CfarBatch 
     }
 
 #pragma unroll
-    for (int i = 0; i < 4; ++i) {
+    for (int i = 0; i < kMaxCutRows; ++i) {
       const int rr = tid / bw + i * rstep;
       if (rr >= bh) break;
       const int r = R + rr;

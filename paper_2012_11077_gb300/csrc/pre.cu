@@ -68,8 +68,9 @@ __device__ __forceinline__ float mean_weight(int j, int N, int h) {
   return w;
 }
 
-// grid: for every frame, n_strips x n_chunks CTAs of 256 threads.
-// Thread (g = warp, lane) sums rows g, g+8, ... of its chunk for 4 columns.
+// grid: for every frame, n_strips x n_chunks CTAs of 256 threads; a chunk is
+// 64 rows (kStatsRowsPerChunk). Thread (g = warp, lane) owns rows g, g+8, ...
+// of its chunk for 4 columns; all 8 rows are loaded before any arithmetic.
 __global__ void __launch_bounds__(256) k_colstats(const __grid_constant__ PreBatch b) {
   const int fi = find_item(b.f, b.n, (int)blockIdx.x, &PreFrameDev::item_stats);
   const PreFrameDev& F = b.f[fi];
@@ -78,29 +79,50 @@ __global__ void __launch_bounds__(256) k_colstats(const __grid_constant__ PreBat
   const int chunk = local / F.n_strips;
   const int lane = threadIdx.x & 31, g = threadIdx.x >> 5;
   const int col0 = strip * kStatsStrip + lane * 4;
-  const int r0 = chunk * F.rows_per_chunk;
-  const int r1 = min(F.M, r0 + F.rows_per_chunk);
+  const int r0 = chunk * kStatsRowsPerChunk;
   const bool vec = ((F.ldx & 3) == 0) && ((reinterpret_cast<uintptr_t>(F.x) & 15) == 0);
 
+  float v[8][4];
+#pragma unroll
+  for (int i = 0; i < 8; ++i) {
+    const int m = r0 + g + 8 * i;
+    if (m < F.M) {
+      load4_masked(F.x + (long long)m * F.ldx, col0, F.N, vec, v[i]);
+    } else {
+#pragma unroll
+      for (int k = 0; k < 4; ++k) v[i][k] = 0.f;
+    }
+  }
   float wj[4];
 #pragma unroll
   for (int k = 0; k < 4; ++k) wj[k] = mean_weight(col0 + k, F.N, F.h);
   float sx[4] = {0.f, 0.f, 0.f, 0.f}, smx[4] = {0.f, 0.f, 0.f, 0.f};
-  for (int m = r0 + g; m < r1; m += 8) {
-    float v[4];
-    load4_masked(F.x + (long long)m * F.ldx, col0, F.N, vec, v);
-    const float dm = (float)m - F.mbar;
-    float rs = 0.f;
+  float rs[8];
+#pragma unroll
+  for (int i = 0; i < 8; ++i) {
+    const float dm = (float)(r0 + g + 8 * i) - F.mbar;
+    rs[i] = 0.f;
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
-      sx[k] += v[k];
-      smx[k] = fmaf(dm, v[k], smx[k]);
-      rs = fmaf(wj[k], v[k], rs);
+      sx[k] += v[i][k];
+      smx[k] = fmaf(dm, v[i][k], smx[k]);
+      rs[i] = fmaf(wj[k], v[i][k], rs[i]);
     }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) rs += __shfl_xor_sync(0xffffffffu, rs, o);
-    if (lane == 0) F.rowpart[(long long)strip * F.M + m] = rs;
   }
+  // row sums over the strip (sum_j w_j x[m, j]): reduce the 8 rows across the warp
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+    for (int i = 0; i < 8; ++i) rs[i] += __shfl_xor_sync(0xffffffffu, rs[i], o);
+  if (lane < 8) {
+    float mine = rs[0];
+#pragma unroll
+    for (int i = 1; i < 8; ++i)
+      if (lane == i) mine = rs[i];
+    const int m = r0 + g + 8 * lane;
+    if (m < F.M) F.rowpart[(long long)strip * F.M + m] = mine;
+  }
+
   __shared__ float2 red[8][kStatsStrip];
   __shared__ bool is_last;
 #pragma unroll
@@ -131,10 +153,16 @@ __global__ void __launch_bounds__(256) k_colstats(const __grid_constant__ PreBat
       float2 st = make_float2(0.f, 0.f);
       if (c < F.N) {
         float2 t = make_float2(0.f, 0.f);
-        for (int ch = 0; ch < F.n_chunks; ++ch) {  // fixed order: deterministic
-          const float2 p = __ldcg(&F.partial[(long long)ch * F.N + c]);
-          t.x += p.x;
-          t.y += p.y;
+        for (int ch0 = 0; ch0 < F.n_chunks; ch0 += 8) {  // fixed order: deterministic
+          float2 p[8];
+#pragma unroll
+          for (int u = 0; u < 8; ++u)
+            p[u] = (ch0 + u < F.n_chunks) ? __ldcg(&F.partial[(long long)(ch0 + u) * F.N + c]) : make_float2(0.f, 0.f);
+#pragma unroll
+          for (int u = 0; u < 8; ++u) {
+            t.x += p[u].x;
+            t.y += p[u].y;
+          }
         }
         st = make_float2(t.x * F.inv_M, t.y * F.inv_D);
         F.stats[c] = st;
@@ -206,16 +234,23 @@ __global__ void __launch_bounds__(256) k_ysplit(const __grid_constant__ PreBatch
     const float dm = (float)m - F.mbar;
     const float cmv = (rs - A - dm * Bv) / (float)N;
     if (cbk == 0 && lane == 0) F.rowmean[m] = cmv;
-    // x' over [n0 - h, n0 + 256 + h)
+    // x' over [n0 - h, n0 + 256 + h): all loads issued before any store
     const float* xr = F.x + (long long)m * F.ldx;
-    for (int i = lane; i < kYCols + 2 * h; i += 32) {
+    constexpr int kSeg = (kYCols + 2 * kMaxMeanHalf) / 32;
+    float xv[kSeg];
+    float2 sv[kSeg];
+#pragma unroll
+    for (int u = 0; u < kSeg; ++u) {
+      const int i = lane + 32 * u;
       const int n = n0 - h + i;
-      float v = 0.f;
-      if (n >= 0 && n < N) {
-        const float2 st = __ldg(&F.stats[n]);
-        v = __ldg(xr + n) - st.x - st.y * dm;
-      }
-      seg[warp][i] = v;
+      const bool ok = i < kYCols + 2 * h && n >= 0 && n < N;
+      xv[u] = ok ? __ldg(xr + n) : 0.f;
+      sv[u] = ok ? __ldg(&F.stats[n]) : make_float2(0.f, 0.f);
+    }
+#pragma unroll
+    for (int u = 0; u < kSeg; ++u) {
+      const int i = lane + 32 * u;
+      if (i < kYCols + 2 * h) seg[warp][i] = xv[u] - sv[u].x - sv[u].y * dm;
     }
     __syncwarp();
     float* yh = F.yhi + (long long)m * F.npad;
@@ -498,14 +533,21 @@ __global__ void __launch_bounds__(256) k_dft_reduce(const __grid_constant__ PreB
   const long long plane = (long long)F.M * F.ldk;
   const float* src = F.kpart + (long long)m * F.ldk + 2 * j;
   float re = 0.f, im = 0.f, cr = 0.f, ci = 0.f;
-  for (int bi = 0; bi < F.nblocks; ++bi) {
-    const float2 v = __ldcg(reinterpret_cast<const float2*>(src + bi * plane));
-    const float yr = v.x - cr, tr = re + yr;
-    cr = __fsub_rn(__fsub_rn(tr, re), yr);
-    re = tr;
-    const float yi = v.y - ci, ti = im + yi;
-    ci = __fsub_rn(__fsub_rn(ti, im), yi);
-    im = ti;
+  for (int b0 = 0; b0 < F.nblocks; b0 += 8) {
+    float2 v[8];  // the next 8 blocks' partials, loaded together
+#pragma unroll
+    for (int u = 0; u < 8; ++u)
+      v[u] = (b0 + u < F.nblocks) ? __ldcg(reinterpret_cast<const float2*>(src + (b0 + u) * plane))
+                                  : make_float2(0.f, 0.f);
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const float yr = v[u].x - cr, tr = re + yr;
+      cr = __fsub_rn(__fsub_rn(tr, re), yr);
+      re = tr;
+      const float yi = v[u].y - ci, ti = im + yi;
+      ci = __fsub_rn(__fsub_rn(ti, im), yi);
+      im = ti;
+    }
   }
   if (j == 0 && F.c0 == 0) re = fmaf((float)F.N, __ldg(&F.rowmean[m]), re);  // bin 0 gets the mean back
   F.map[(long long)m * F.ld_map + j] = sqrtf(fmaf(re, re, im * im)) * inv;

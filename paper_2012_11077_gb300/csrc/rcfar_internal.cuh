@@ -28,7 +28,8 @@ constexpr int kSatTileH = 32;   // rows per band (one CTA per band)
 constexpr int kSatTileW = 128;  // columns per chunk (32 lanes x 4)
 
 // ---- preprocessing ----------------------------------------------------------
-constexpr int kStatsStrip = 128;  // columns per column-statistics CTA
+constexpr int kStatsStrip = 128;         // columns per column-statistics CTA
+constexpr int kStatsRowsPerChunk = 64;   // rows per column-statistics CTA (8 warps x 8)
 
 // Band DFT GEMM on tcgen05: 128 rows (TMEM lanes) x up to 256 real outputs
 // (TMEM columns) per CTA, K steps of 32 samples (one 128-byte swizzle row).
