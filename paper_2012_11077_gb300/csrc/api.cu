@@ -787,11 +787,21 @@ rcfar_status rcfar_cfar(rcfar_handle h, const rcfar_sat_view* view, const void* 
   P.thr = thr;
   P.ld_thr = ld_thr;
   P.mode = view->mode;
-  const CfarTile t = pick_cfar_tile(view->mode, P.wr, P.wc, std::min<size_t>(h->smem_optin, 200 * 1024),
-                                    {h->cfg.cfar_tile_rows, h->cfg.cfar_tile_cols});
+  P.item0 = 0;
+  cb.status = h->status;
+  const size_t smem_cap = std::min<size_t>(h->smem_optin, 200 * 1024);
+  // exact global table: stream its rows through the bulk-copy ring
+  int ring_rows = 0, hcp = 0;
+  if (view->mode == RCFAR_SAT_I64 && (view->ld % 2) == 0 && (reinterpret_cast<uintptr_t>(view->table) & 15) == 0 &&
+      cfar_ring_plan(P.wr, P.wc, h->smem_optin, &ring_rows, &hcp)) {
+    const size_t smem = cfar_ring_smem(ring_rows, hcp);
+    const int blocks = cfar_ring_geometry(P, view->rows, view->cols, ring_rows, hcp, cfar_ring_slots(smem));
+    TraceScope tr(h, "cfar", s);
+    return cuda_fail(launch_cfar_ring(cb, map != nullptr, dtype, blocks, smem, s));
+  }
+  const CfarTile t = pick_cfar_tile(view->mode, P.wr, P.wc, smem_cap, {h->cfg.cfar_tile_rows, h->cfg.cfar_tile_cols});
   if (t.bh == 0) return RCFAR_ERR_UNSUPPORTED;
   const int blocks = set_cfar_geometry(P, t, view->rows, view->cols);
-  P.item0 = 0;
   TraceScope tr(h, "cfar", s);
   cudaError_t e = launch_cfar(cb, view->mode, dtype, blocks, cfar_smem_bytes(view->mode, t.bh, t.bw, P.wr, P.wc),
                               t.bw + 2 * P.wc + 1, s);
@@ -930,6 +940,7 @@ rcfar_status rcfar_run_batch(rcfar_handle h, const rcfar_frame_desc* frames, int
     pb.status = h->status;
     sb.n = cnt;
     cb.n = cnt;
+    cb.status = h->status;
     sb.status = h->status;
     int kb_per_cta = 1;
     {

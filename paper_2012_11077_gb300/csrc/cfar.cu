@@ -12,7 +12,10 @@
 // k_cfar_direct : the sliding-window CFAR the SAT replaces: the same
 //                 decisions with S_ref summed over the n_ref training cells.
 #include "rcfar_internal.cuh"
+#include "async_copy.cuh"
+#include "fixed_point.cuh"
 
+#include <algorithm>
 #include <type_traits>
 
 namespace rcfar {
@@ -38,7 +41,7 @@ table_value(const CfarMapDev& P, int r, int c, float scalef) {
   } else {
     u64 q;
     if constexpr (MODE == RCFAR_SAT_TILE_F32)
-      q = (u64)__float2ll_rn(__ldg(reinterpret_cast<const float*>(P.table) + (long long)r * P.ld_table + c) * scalef);
+      q = (u64)q_from_f32_wide(__ldg(reinterpret_cast<const float*>(P.table) + (long long)r * P.ld_table + c), scalef);
     else
       q = (u64)__ldg(reinterpret_cast<const long long*>(P.table) + (long long)r * P.ld_table + c);
     q += __ldg(P.col_carry + (long long)(c >> 7) * P.rows + r);  // kSatTileW == 128
@@ -160,7 +163,7 @@ __global__ void __launch_bounds__(256) k_cfar(const __grid_constant__ CfarBatch 
           // T = (alpha / n_ref) * S_ref in fixed-point units; the CUT value
           // comes from the map when one is given, else from the exact table
           // (eq. 4 on the 1x1 region)
-          const float ts = (float)(long long)ref * kthr;
+          const float ts = f32_from_q((long long)ref) * kthr;
           t = ts * inv_s;
           if (map != nullptr) {
             d = cutv[i] > t ? 1 : 0;
@@ -168,11 +171,11 @@ __global__ void __launch_bounds__(256) k_cfar(const __grid_constant__ CfarBatch 
             const SV* S1 = S + (g & rmask) * HC;        // row r
             const SV* S0 = S + ((g - 1) & rmask) * HC;  // row r - 1
             const u64 qc = (S1[cm] + S0[cm - 1]) - (S0[cm] + S1[cm - 1]);
-            d = (float)(long long)qc > ts ? 1 : 0;
+            d = f32_from_q((long long)qc) > ts ? 1 : 0;
           }
         } else {
           if constexpr (MODE == RCFAR_SAT_NAIVE_F32) t = ref * kk;
-          else t = (float)(long long)ref * kk;
+          else t = f32_from_q((long long)ref) * kk;
           d = cutv[i] > t ? 1 : 0;
         }
       }
@@ -185,6 +188,247 @@ __global__ void __launch_bounds__(256) k_cfar(const __grid_constant__ CfarBatch 
     loaded = need;
     __syncthreads();
   }
+}
+
+
+// S_ref by eq. 4 on the outer rectangle minus eq. 4 on the guard rectangle,
+// regrouped as (four corners added) - (four corners subtracted). Rows: a =
+// r - wr - 1, b = r + wr, c = r - gr - 1, d = r + gr; each pointer is at the
+// CUT's column, so [o] is the column offset o from it.
+__device__ __forceinline__ u64 ref_sum(const u64* ra, const u64* rb, const u64* rc, const u64* rd, int wc, int gc) {
+  const u64 pos = (ra[-wc - 1] + rb[wc]) + (rc[gc] + rd[-gc - 1]);
+  const u64 neg = (ra[wc] + rb[-wc - 1]) + (rc[-gc - 1] + rd[gc]);
+  return pos - neg;
+}
+
+// SAT CFAR streaming an exact global table S (I64 mode: S is eq. 3 itself in
+// 64-bit fixed point, so a lookup is one load). A CTA owns a strip of
+// kRingW columns and a run of rows; warp w handles row w of each stage of
+// kRingSR rows, lane l the columns l, l + 32, l + 64, l + 96 of the strip.
+// The table rows the run reads (row -1 .. last CUT row + wr, strip plus
+// halo) stream through a ring of ring_rows rows in shared memory, kRingSR rows
+// per stage: a stage is kRingSR bulk copies of one table row each, completing
+// on the stage's mbarrier, issued up to NS = ring_rows / kRingSR stages ahead. Warps
+// never wait for one another: each waits only for the stages it reads, and
+// the last warp to finish an output stage (a shared-memory counter per slot)
+// issues the copies that refill the slot. Per CUT: S_ref from 8 lookups in
+// 64-bit integer arithmetic, T = (alpha / n_ref) S_ref, and det = CUT > T
+// with the CUT value from the map (kMapCut) or from the table (eq. 4 on the
+// 1 x 1 region). Rows and strips fully inside the CUT range take a path
+// without per-cell checks.
+template <bool kMapCut, typename InT>
+__global__ void __launch_bounds__(kRingThreads, 1) k_cfar_ring(const __grid_constant__ CfarBatch B) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  u64* bars = reinterpret_cast<u64*>(smem_raw);
+  u64* ring = reinterpret_cast<u64*>(smem_raw + kRingBarBytes);
+  __shared__ int s_fail;
+  __shared__ unsigned s_done[kRingMaxStages];  // warps done with the slot's current stage
+  constexpr int kWarps = kRingThreads / 32;
+
+  const int mi = find_item(B.m, B.n, (int)blockIdx.x, &CfarMapDev::item0);
+  const CfarMapDev& P = B.m[mi];
+  const int local = (int)blockIdx.x - P.item0;
+  const int ty = local / P.tiles_x, tx = local - ty * P.tiles_x;
+  const int rows = P.rows, cols = P.cols;
+  const int R0 = ty * P.run, R1 = min(rows, R0 + P.run);
+  const int c0 = tx * kRingW;
+  const int wr = P.wr, wc = P.wc, gr = P.gr, gc = P.gc;
+  const int hs = (c0 - wc - 1) & ~1;  // table column held in ring column 0 (even)
+  const int HCP = P.hcp;
+  const int RR = P.ring_rows;     // NS stages of kRingSR rows (NS need not be a power of two)
+  const int NS = RR / kRingSR;
+  const int gbase = R0 - wr - 1;  // ring row index g holds table row gbase + g
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const long long* T = reinterpret_cast<const long long*>(P.table);
+  const long long ldt = P.ld_table;
+  // ring slot of row index g: stage g / kRingSR in slot (g / kRingSR) % NS
+  auto slot_row = [&](int g) { return ((g / kRingSR) % NS) * kRingSR + (g % kRingSR); };
+
+  // CUTs of this CTA that take lookups
+  const int rlo = max(R0, P.row_lo), rhi = min(R1 - 1, P.row_hi);
+  const int clo = max(c0, P.cut_lo), chi = min(min(c0 + kRingW, cols) - 1, P.cut_hi);
+  const bool work = rlo <= rhi && clo <= chi;
+  const bool full_strip = clo == c0 && chi == c0 + kRingW - 1;  // every column is a CUT column
+  const int gmax = work ? rhi + wr - gbase : -1;  // last ring row index read
+  const int nq = work ? gmax / kRingSR + 1 : 0;   // table stages
+  const int QL = (2 * wr + kRingSR) / kRingSR;    // output stage t reads table stages t .. t + QL
+  const int nt = (R1 - R0 + kRingSR - 1) / kRingSR;
+  // one table row's copy: columns cs .. ce - 1 (even bounds, inside the row's allocation)
+  const int cs = max(hs, 0);
+  const int ce = (int)min((long long)hs + HCP, ldt);
+  const unsigned row_bytes = (unsigned)(ce - cs) * 8u;
+  const int dcol = cs - hs;
+
+  if (tid == 0) s_fail = 0;
+  if (tid < NS) {
+    mbar_init(smem_u32(&bars[tid]), 1);
+    s_done[tid] = 0;
+  }
+  if (work) {
+    // columns left of the map read as S(., -1) = 0; so does row -1
+    if (hs < 0)
+      for (int i = tid; i < RR * (-hs); i += kRingThreads) ring[(i / (-hs)) * HCP + (i % (-hs))] = 0;
+    if (gbase <= -1) {
+      u64* z = ring + slot_row(-1 - gbase) * HCP;
+      for (int i = tid; i < HCP; i += kRingThreads) z[i] = 0;
+    }
+    fence_proxy_async();
+  }
+  if (tid == 0) mbar_init_fence();
+  __syncthreads();
+
+  auto issue = [&](int q) {  // one whole warp: table stage q into slot q % NS
+    const int g0 = q * kRingSR;
+    const int glo = max(g0, -gbase);  // rows >= 0 only
+    const int ghi = min(g0 + kRingSR, gmax + 1);
+    const int n = max(0, ghi - glo);
+    const unsigned bar = smem_u32(&bars[q % NS]);
+    if (lane == 0) mbar_arrive_expect_tx(bar, (unsigned)n * row_bytes);
+    __syncwarp();
+    if (lane < n) {
+      const int g = glo + lane;
+      bulk_g2s(smem_u32(ring + slot_row(g) * HCP + dcol), T + (long long)(gbase + g) * ldt + cs, row_bytes, bar);
+    }
+  };
+  if (warp == 0)
+    for (int q = 0; q < min(nq, NS); ++q) issue(q);
+
+  const float kthr = P.kthr;
+  int s = 0;
+  if (work) s = __ldcg(P.scale_dev);
+  const float inv_s = ldexpf(1.0f, -s);
+  const InT* map = reinterpret_cast<const InT*>(P.map);
+  const int cw = c0 + lane;     // this lane's columns: cw + 32 k
+  const int x = cw - hs;        // its ring column
+  int waited = -1;
+  // The rows output row r = R0 + kRingSR t + warp reads have ring index
+  // g = kRingSR t + warp + off; each lies in stage t + (warp + off) / kRingSR,
+  // row (warp + off) % kRingSR of it. off for rows r - wr - 1, r + wr,
+  // r - gr - 1, r + gr, r, r - 1:
+  // Relative to the first ring row sb of the slot holding stage t, that row
+  // is at sb + warp + off (stages are consecutive slots; wrapped once).
+  const int coff[6] = {warp, warp + 2 * wr + 1, warp + wr - gr, warp + wr + gr + 1, warp + wr + 1, warp + wr};
+  int sb = 0;  // first ring row of the slot holding stage t
+
+  // CUT values of this warp's row in output stage t (map CUT only)
+  auto load_cut = [&](int t, float (&v)[4]) {
+#pragma unroll
+    for (int k = 0; k < 4; ++k) v[k] = 0.f;
+    if constexpr (kMapCut) {
+      const int r = R0 + t * kRingSR + warp;
+      if (work && t < nt && r >= rlo && r <= rhi) {
+        const InT* mrow = map + (long long)r * P.ld_map + cw;
+        if (full_strip) {
+#pragma unroll
+          for (int k = 0; k < 4; ++k) v[k] = ld_map_val(mrow + 32 * k, P.in_scale);
+        } else {
+#pragma unroll
+          for (int k = 0; k < 4; ++k)
+            if (cw + 32 * k >= clo && cw + 32 * k <= chi) v[k] = ld_map_val(mrow + 32 * k, P.in_scale);
+        }
+      }
+    }
+  };
+  float cut[4];
+  load_cut(0, cut);
+
+  for (int t = 0; t < nt; ++t) {
+    float cut_next[4];
+    load_cut(t + 1, cut_next);
+    if (work) {
+      const int qb = min(t + QL, nq - 1);
+      while (waited < qb) {
+        ++waited;
+        if (!mbar_wait(smem_u32(&bars[waited % NS]), (unsigned)((waited / NS) & 1))) s_fail = 1;
+      }
+    }
+    const int r = R0 + t * kRingSR + warp;
+    if (r < R1) {
+      unsigned char d[4] = {0, 0, 0, 0};
+      float th[4] = {0.f, 0.f, 0.f, 0.f};
+      if (work && r >= rlo && r <= rhi) {
+        // ring row of each lookup row: slot of stage t, plus the row's stage
+        // and row offsets, wrapped once
+        auto rrow = [&](int i) {
+          int v = sb + coff[i];
+          if (v >= RR) v -= RR;
+          return ring + v * HCP + x;
+        };
+        const u64* ra = rrow(0);  // row r - wr - 1 at column cw
+        const u64* rb = rrow(1);  // row r + wr
+        const u64* rc = rrow(2);  // row r - gr - 1
+        const u64* rd = rrow(3);  // row r + gr
+        const u64* r1 = rrow(4);  // row r
+        const u64* r0 = rrow(5);  // row r - 1
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+          const int o = 32 * k;
+          const float ts = f32_from_q((long long)ref_sum(ra + o, rb + o, rc + o, rd + o, wc, gc)) * kthr;
+          th[k] = ts * inv_s;  // T (eq. 2 with A = S_ref / n_ref)
+          if constexpr (kMapCut) {
+            d[k] = cut[k] > th[k];
+          } else {
+            const u64 qc = (r1[o] + r0[o - 1]) - (r0[o] + r1[o - 1]);
+            d[k] = f32_from_q((long long)qc) > ts;
+          }
+        }
+        if (!full_strip) {
+#pragma unroll
+          for (int k = 0; k < 4; ++k)
+            if (cw + 32 * k < clo || cw + 32 * k > chi) {
+              d[k] = 0;
+              th[k] = 0.f;
+            }
+        }
+      }
+      unsigned char* drow = P.det + (long long)r * P.ld_det + cw;
+      float* trow = P.thr ? P.thr + (long long)r * P.ld_thr + cw : nullptr;
+      if (c0 + kRingW <= cols) {
+#pragma unroll
+        for (int k = 0; k < 4; ++k) drow[32 * k] = d[k];
+        if (trow) {
+#pragma unroll
+          for (int k = 0; k < 4; ++k) trow[32 * k] = th[k];
+        }
+      } else {
+#pragma unroll
+        for (int k = 0; k < 4; ++k)
+          if (cw + 32 * k < cols) {
+            drow[32 * k] = d[k];
+            if (trow) trow[32 * k] = th[k];
+          }
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < 4; ++k) cut[k] = cut_next[k];
+    sb += kRingSR;
+    if (sb == RR) sb = 0;
+    // this warp is done with output stage t (its lookups have returned);
+    // the last warp refills slot t % NS with stage t + NS
+    if (work && t + NS < nq) {
+      __syncwarp();
+      unsigned last = 0;
+      if (lane == 0) {
+        __threadfence_block();
+        last = atomicAdd(&s_done[t % NS], 1u) == kWarps - 1;
+        if (last) {
+          s_done[t % NS] = 0;
+          __threadfence_block();
+        }
+      }
+      if (__shfl_sync(0xffffffffu, last, 0)) issue(t + NS);
+    }
+  }
+  // every issued stage has completed before the CTA's shared memory is released
+  if (work) {
+    const int last = min(nq, NS + nt) - 1;
+    while (waited < last) {
+      ++waited;
+      if (!mbar_wait(smem_u32(&bars[waited % NS]), (unsigned)((waited / NS) & 1))) s_fail = 1;
+    }
+  }
+  __syncthreads();
+  if (tid == 0 && s_fail && B.status) atomicOr(B.status, kStatusTimeout);
 }
 
 __global__ void __launch_bounds__(256) k_cfar_direct(const __grid_constant__ CfarMapDev P) {
@@ -276,6 +520,77 @@ cudaError_t launch_cfar(const CfarBatch& b, int mode, int dtype, int blocks, siz
       return h ? launch_cfar_t<RCFAR_SAT_NAIVE_F32, __half>(b, blocks, smem, max_hc, s)
                : launch_cfar_t<RCFAR_SAT_NAIVE_F32, float>(b, blocks, smem, max_hc, s);
   }
+}
+
+
+bool cfar_ring_plan(int wr, int wc, size_t smem_cap, int* ring_rows, int* hcp) {
+  const int h = kRingW + 2 * wc + 2;  // strip + halo, rounded to an even count
+  const int ql = (2 * wr + kRingSR) / kRingSR;
+  // ring: as many stages as fit (at most kRingMaxStages, and at most 8
+  // beyond the ones an output stage reads); at least one stage in flight
+  int ns = (int)((smem_cap - kRingBarBytes) / ((size_t)kRingSR * h * 8));
+  ns = std::min(ns, std::min(kRingMaxStages, ql + 1 + 8));
+  if (ns < ql + 2) return false;
+  *ring_rows = ns * kRingSR;
+  *hcp = h;
+  return true;
+}
+
+size_t cfar_ring_smem(int ring_rows, int hcp) { return (size_t)kRingBarBytes + (size_t)ring_rows * hcp * 8; }
+
+int cfar_ring_slots(size_t smem) {
+  int dev = 0, sms = 0, per = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+    return 152;
+  const void* fn = reinterpret_cast<const void*>(k_cfar_ring<true, float>);
+  if (ensure_smem(fn, smem) != cudaSuccess ||
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_cfar_ring<true, float>, kRingThreads, smem) != cudaSuccess ||
+      per < 1)
+    per = 1;
+  return sms * per;
+}
+
+// Runs per strip chosen to balance the waves of resident CTAs (slots) against
+// the 2 wr + 1 halo rows each run streams in before its first output row.
+int cfar_ring_geometry(CfarMapDev& P, int rows, int cols, int ring_rows, int hcp, int slots) {
+  P.bw = kRingW;
+  P.bh = kRingSR;
+  P.tiles_x = (cols + kRingW - 1) / kRingW;
+  P.ring_rows = ring_rows;
+  P.hcp = hcp;
+  const int max_runs = std::max(1, (rows + kRingSR - 1) / kRingSR);
+  long long best = -1;
+  int best_run = kRingSR;
+  for (int n = 1; n <= max_runs; ++n) {
+    const int run = ((rows + n - 1) / n + kRingSR - 1) / kRingSR * kRingSR;
+    const int runs = (rows + run - 1) / run;
+    const long long ctas = (long long)P.tiles_x * runs;
+    const long long waves = (ctas + slots - 1) / slots;
+    const long long cost = waves * (run + 2 * P.wr + 1 + 8);  // 8: per-CTA set-up, in row units
+    if (best < 0 || cost < best) {
+      best = cost;
+      best_run = run;
+    }
+    if (run == kRingSR) break;
+  }
+  P.run = best_run;
+  return P.tiles_x * ((rows + best_run - 1) / best_run);
+}
+
+template <bool kMapCut, typename InT>
+static cudaError_t launch_ring_t(const CfarBatch& b, int blocks, size_t smem, cudaStream_t s) {
+  auto fn = k_cfar_ring<kMapCut, InT>;
+  cudaError_t e = ensure_smem(reinterpret_cast<const void*>(fn), smem);
+  if (e != cudaSuccess) return e;
+  fn<<<blocks, kRingThreads, smem, s>>>(b);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_cfar_ring(const CfarBatch& b, bool map_cut, int dtype, int blocks, size_t smem, cudaStream_t s) {
+  if (blocks <= 0) return cudaSuccess;
+  if (!map_cut) return launch_ring_t<false, float>(b, blocks, smem, s);
+  return dtype == RCFAR_MAP_F16 ? launch_ring_t<true, __half>(b, blocks, smem, s)
+                                : launch_ring_t<true, float>(b, blocks, smem, s);
 }
 
 cudaError_t launch_cfar_direct(const CfarMapDev& m, int blocks, size_t smem, cudaStream_t s) {

@@ -21,6 +21,7 @@
 //                t = (c0 + j) n mod N, computed once per (N, band) in FP64 and
 //                stored split into TF32 head and tail.
 #include "rcfar_internal.cuh"
+#include "async_copy.cuh"
 
 #include <mutex>
 #include <map>
@@ -284,13 +285,6 @@ __global__ void __launch_bounds__(256) k_ysplit(const __grid_constant__ PreBatch
   }
 }
 
-__device__ __forceinline__ unsigned smem_u32(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
-
-__device__ __forceinline__ void cp_async16(unsigned saddr, const void* gmem, bool valid) {
-  const int src_bytes = valid ? 16 : 0;  // 0: the 16 bytes are zero-filled, nothing is read
-  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(saddr), "l"(gmem), "r"(src_bytes) : "memory");
-}
-
 // Shared-memory matrix descriptor of a K-major operand tile whose rows are
 // 128 bytes (32 TF32 values) stored with the 128-byte swizzle: 8-row groups
 // 1024 bytes apart (SBO), layout SWIZZLE_128B, descriptor version 1.
@@ -310,28 +304,6 @@ __device__ __forceinline__ void umma_tf32(unsigned tmem_d, unsigned long long a,
 __device__ __forceinline__ void umma_commit(unsigned bar) {
   asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
 }
-
-__device__ __forceinline__ void mbar_init(unsigned bar, unsigned count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count));
-}
-__device__ __forceinline__ void mbar_arrive(unsigned bar) {
-  asm volatile("{\n .reg .b64 st;\n mbarrier.arrive.shared::cta.b64 st, [%0];\n}\n" ::"r"(bar) : "memory");
-}
-// Wait for the phase of the given parity to complete; gives up after a bounded
-// number of polls (returns false).
-__device__ __forceinline__ bool mbar_wait(unsigned bar, unsigned parity) {
-  for (unsigned it = 0; it < kSpinLimit; ++it) {
-    unsigned done;
-    asm volatile(
-        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
-        : "=r"(done)
-        : "r"(bar), "r"(parity)
-        : "memory");
-    if (done) return true;
-  }
-  return false;
-}
-
 
 // Band DFT as a GEMM on the 5th-generation tensor cores: (yhi + ylo) [M x npad]
 // times (Whi + Wlo)^T [npad x ldw] in TF32, three products per K step

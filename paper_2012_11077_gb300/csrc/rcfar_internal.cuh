@@ -142,14 +142,26 @@ struct CfarMapDev {
   int item0;
   int bh, bw;          // CUT rows per step, strip width
   int run;             // rows per CTA (a multiple of bh)
-  int ring_rows;       // table rows held in shared memory (power of two)
+  int ring_rows;       // table rows held in shared memory (a power of two; streaming kernel: NS * kRingSR)
   int mode;            // rcfar_sat_mode of the table
+  int hcp;             // streaming kernel: u64 per ring row (strip + halo, even)
 };
 
 struct CfarBatch {
   int n;
+  int* status;  // device status word (bounded waits of the streaming kernel)
   CfarMapDev m[kMaxBatch];
 };
+
+// Streaming SAT-CFAR on an exact global table (I64): strips of kRingW
+// columns, kRingSR rows per stage (one warp per row), table rows brought
+// into a shared-memory ring by the bulk-copy engine.
+constexpr int kRingW = 128;
+constexpr int kRingSR = 32;
+constexpr int kRingThreads = 1024;
+constexpr int kRingBarBytes = 128;  // stage mbarriers at the front of shared memory
+constexpr int kRingMaxStages = 16;
+static_assert(kRingThreads / 32 == kRingSR && kRingW == 128, "one warp per output row and stage, 4 columns per lane");
 
 // Fixed-point scale s such that max_cells * bound * 2^s <= 2^62 (so every
 // region sum the CFAR forms fits in 63 bits); clamped to a float-safe range.
@@ -204,6 +216,15 @@ cudaError_t launch_cfar(const CfarBatch& b, int mode, int dtype, int blocks, siz
 size_t cfar_smem_bytes(int mode, int bh, int bw, int wr, int wc);
 int cfar_ring_rows(int bh, int wr);
 cudaError_t launch_cfar_direct(const CfarMapDev& m, int blocks, size_t smem, cudaStream_t s);
+
+// Streaming CFAR: ring plan for a window (false if it does not fit), its
+// shared memory, the strip/run geometry of one map (returns its CTA count),
+// and the launch. map_cut: CUT values from the map (else from the table).
+bool cfar_ring_plan(int wr, int wc, size_t smem_cap, int* ring_rows, int* hcp);
+size_t cfar_ring_smem(int ring_rows, int hcp);
+int cfar_ring_slots(size_t smem);  // resident CTAs of the streaming kernel on this device
+int cfar_ring_geometry(CfarMapDev& P, int rows, int cols, int ring_rows, int hcp, int slots);
+cudaError_t launch_cfar_ring(const CfarBatch& b, bool map_cut, int dtype, int blocks, size_t smem, cudaStream_t s);
 size_t cfar_direct_smem_bytes(int bh, int bw, int wr, int wc);
 
 }  // namespace rcfar

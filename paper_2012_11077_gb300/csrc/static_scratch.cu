@@ -152,6 +152,7 @@ extern "C" rcfar_status rcfar_sat_cfar_static(const float* map, int32_t rows, in
 
   CfarBatch cb;
   cb.n = 1;
+  cb.status = status_word;
   CfarMapDev& P = cb.m[0];
   std::memset(&P, 0, sizeof(P));
   P.table = table;

@@ -109,12 +109,15 @@ def run_cfar(rc, h, P, win, mode, cut=None, dtype=torch.float32, exp2=0, bound=N
 
 
 # ------------------------------------------------------------------ eq. 3 table
-SAT_SHAPES = [(1, 1), (5, 7), (31, 127), (32, 128), (33, 129), (100, 300), (257, 383), (64, 1000)]
+SAT_SHAPES = [(1, 1), (5, 7), (31, 127), (32, 128), (33, 129), (100, 300), (257, 383), (64, 1000),
+              (2050, 1030)]  # the last spans more tiles than one grid-stride pass
 
 
 @pytest.mark.parametrize("shape", SAT_SHAPES)
 @pytest.mark.parametrize("mode", [0, 1, 2, 3])
 def test_sat_integer_map_exact(rc, h, shape, mode):
+    if mode == 2 and shape[0] * shape[1] > 1_000_000:
+        pytest.skip("a naive FP32 table holds integers only up to 2^24")
     P = synth.integer_map(*shape, hi=16, seed=shape[0] * 1000 + shape[1])
     Pt = dev_t(P)
     # a bound at the map's total keeps the fixed-point table from wrapping, so
@@ -124,6 +127,33 @@ def test_sat_integer_map_exact(rc, h, shape, mode):
     rc.rcfar_sat_materialize(h, view, out)
     assert rc.rcfar_get_error(h) == rc.RCFAR_OK
     np.testing.assert_array_equal(out.cpu().numpy(), ocfar.sat(P))
+
+
+@pytest.mark.parametrize("mode", [1, 3])
+def test_fixed_point_quantisation_exact(rc, h, mode):
+    # The exact tables hold q = round-half-even(v * 2^s) per cell. On a one-row
+    # map the table's successive differences are the q themselves; they must
+    # equal numpy's rint of the exactly scaled value for every kind of input:
+    # exact ties, values that round to zero, subnormals, negatives, and values
+    # across the whole exponent range.
+    rng = np.random.default_rng(5)
+    n = 4096
+    bound = 1.0e6
+    s = rc.rcfar_sat(h, dev_t(np.zeros((1, n), np.float32)), value_bound=bound, mode=mode).scale_log2
+    v = (rng.standard_normal(n) * 10.0 ** rng.uniform(-9, 0, n)).astype(np.float32)
+    k = np.arange(0, n, 7)
+    v[k] = ((2 * rng.integers(-1000, 1000, k.size) + 1) * 2.0 ** (-s - 1)).astype(np.float32)  # ties
+    v[3::11] = np.float32(1e-40)   # subnormal: rounds to zero
+    v[5::13] = np.float32(-2.0 ** (-s - 2))
+    P = v.reshape(1, n)
+    view = rc.rcfar_sat(h, dev_t(P), value_bound=bound, mode=mode)
+    assert view.scale_log2 == s and 20 < s < 40
+    out = torch.empty((1, n), dtype=torch.float64, device="cuda")
+    rc.rcfar_sat_materialize(h, view, out)
+    assert rc.rcfar_get_error(h) == rc.RCFAR_OK
+    S = out.cpu().numpy()[0] * 2.0 ** s          # exact: |S| < 2^53
+    q = np.diff(np.concatenate([[0.0], S]))
+    np.testing.assert_array_equal(q, np.rint(v.astype(np.float64) * 2.0 ** s))
 
 
 @pytest.mark.parametrize("mode", [0, 1, 3])
@@ -187,6 +217,10 @@ CFAR_CASES = [
     ((77, 301), (3, 5, 1, 2, 1e-2), None),
     ((40, 33), (12, 12, 8, 8, 1e-3), None),   # larger window than map: zero CUTs
     ((500, 150), (1, 1, 0, 0, 1e-1), (3, 140)),
+    # several 128-column strips and row runs, ragged edges, odd halo widths
+    ((700, 517), (16, 16, 4, 4, 1e-6), None),
+    ((1030, 390), (6, 9, 2, 3, 1e-4), (40, 350)),
+    ((260, 129), (2, 2, 0, 0, 1e-3), None),
 ]
 
 
@@ -216,11 +250,12 @@ def test_cfar_sat_parity(rc, h, shape, win, cut, mode):
 
 
 @pytest.mark.parametrize("shape,win,cut", CFAR_CASES)
-def test_cfar_i64_cut_from_table(rc, h, shape, win, cut):
-    # I64 table without the map: the CUT value is the table's 1x1 region sum
+@pytest.mark.parametrize("mode", [1, 3])
+def test_cfar_i64_cut_from_table(rc, h, shape, win, cut, mode):
+    # exact tables without the map: the CUT value is the table's 1x1 region sum
     P = cfar_map(shape, seed=shape[0] + shape[1])
     rows, cols = shape
-    view = rc.rcfar_sat(h, dev_t(P), value_bound=float(P.max()), mode=rc.RCFAR_SAT_TILE_I64)
+    view = rc.rcfar_sat(h, dev_t(P), value_bound=float(P.max()), mode=mode)
     det = torch.full((rows, cols), 7, dtype=torch.uint8, device="cuda")
     thr = torch.full((rows, cols), -1.0, dtype=torch.float32, device="cuda")
     lo, hi = cut if cut is not None else (0, cols - 1)
