@@ -32,6 +32,11 @@ if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
 METRIC = "SAT+CA-CFAR Gcells/s and full-chain frames/s at 1 GB300; % HBM roofline; p99 latency"
+# DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) from one ncu --set full capture
+# of each kernel as it stands: k_band_dft on the 1024x4096 frame (bench.py --profile chain); the I64
+# table kernels and k_cfar_ring on a 4096x4096 map (bench.py --profile map), times 4 for the
+# 8192x8192 map (their traffic grows with the cells).
+TRAFFIC = {"band_dft": 43.76e6, "sat_i64_8192": 4 * 222.6e6, "cfar_ring_8192": 4 * 220.5e6}
 RING = 16
 
 
@@ -44,6 +49,11 @@ def parse_args():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-map", action="store_true", help="skip the 8192^2 SAT+CFAR measurement")
     ap.add_argument("--no-batch", action="store_true", help="skip the 64-frame mixed batch measurement")
+    ap.add_argument("--profile", choices=["chain", "map", "batch"],
+                    help="run one small fixed case a few times for a profiler capture and exit (no JSON line): "
+                         "chain = the 1024x4096 frame through the per-frame calls, map = SAT (I64) + CFAR on a "
+                         "--map-size square map, batch = one 64-frame mixed batch")
+    ap.add_argument("--map-size", type=int, default=4096)
     return ap.parse_args()
 
 
@@ -401,7 +411,7 @@ def ours(args, rank, world, local, dist):
     dft_flops = 8.0 * M * N * C
     tf32_peak = peaks["bf16_tflops"] * 0.5  # dense TF32 = half the measured dense BF16 rate (nominal ratio)
     roofline = {"kernel": "band_dft", "bound": "tensor", "achieved": dft_flops / (dft_us * 1e-6) / 1e12,
-                "peak": tf32_peak, "unit": "TFLOP/s", "traffic": None,
+                "peak": tf32_peak, "unit": "TFLOP/s", "traffic": TRAFFIC["band_dft"],
                 "peak_source": "measured bf16 burst %.1f TFLOP/s x 0.5 (TF32/BF16 nominal ratio)" % peaks["bf16_tflops"],
                 "issued_products": 3}
     roofline["frac"] = roofline["achieved"] / roofline["peak"]
@@ -473,7 +483,8 @@ def ours(args, rank, world, local, dist):
                     "kernels_us": {"sat": sat_us, "cfar": cfar_us},
                     "hbm_frac_split": (sat_bytes + cfar_bytes) / (mms * 1e-3) / 1e9 / peaks["hbm_gbs"],
                     "roofline": {"kernel": dom, "bound": "hbm", "achieved": ach, "peak": peaks["hbm_gbs"],
-                                 "unit": "GB/s", "frac": ach / peaks["hbm_gbs"], "traffic": None}}
+                                 "unit": "GB/s", "frac": ach / peaks["hbm_gbs"],
+                                 "traffic": TRAFFIC["cfar_ring_8192" if dom == "cfar" else "sat_i64_8192"]}}
         assert rc.rcfar_get_error(h) == rc.RCFAR_OK
 
     batch = None
@@ -503,8 +514,63 @@ def ours(args, rank, world, local, dist):
     print(json.dumps(line), flush=True)
 
 
+def profile_case(args):
+    """Small fixed workloads for ncu captures: each runs its kernels three times."""
+    import torch
+    import synth
+    import paper_2012_11077_gb300 as rc
+    torch.cuda.set_device(0)
+    if args.profile == "map":
+        n = args.map_size
+        h = rc.rcfar_create(device=0, max_rows=n, max_cols=n, max_n=4096, max_window=40, max_frames=1,
+                            batch_bytes=1 << 24)
+        Pm = torch.from_numpy(synth.square_law_map(n, n, n_targets=200, seed=0)).cuda()
+        det = torch.empty((n, n), dtype=torch.uint8, device="cuda")
+        w = rc.make_window(16, 16, 4, 4, 1e-6)
+        bound = float(Pm.max().item())
+        for _ in range(3):
+            v = rc.rcfar_sat(h, Pm, value_bound=bound, mode=rc.RCFAR_SAT_I64)
+            rc.rcfar_cfar(h, v, Pm, w, 0, n - 1, det)
+    elif args.profile == "chain":
+        h = rc.rcfar_create(device=0, max_rows=1024, max_cols=512, max_n=4096, max_window=40, max_frames=1,
+                            batch_bytes=1 << 24)
+        case = synth.large_frame_case(0)
+        x = torch.from_numpy(synth.radar_frame(case.spec)).cuda()
+        params = rc.make_pre_params(20.0, halo_c=case.halo_c)
+        band = rc.rcfar_band_plan(case.spec.N, params)
+        P = torch.empty((case.spec.M, band.cols), device="cuda")
+        det = torch.empty((case.spec.M, band.cols), dtype=torch.uint8, device="cuda")
+        w = case.window
+        win = rc.make_window(w.train_r, w.train_c, w.guard_r, w.guard_c, w.pfa)
+        for _ in range(3):
+            rc.rcfar_preprocess(h, x, params, P)
+            v = rc.rcfar_sat(h, P, value_bound=band.value_bound, mode=rc.RCFAR_SAT_TILE_I64)
+            rc.rcfar_cfar(h, v, P, win, band.k_lo - band.c0, band.k_hi - band.c0, det)
+    else:
+        h = rc.rcfar_create(device=0, max_rows=1024, max_cols=1024, max_n=4096, max_window=32, max_frames=64,
+                            batch_bytes=3 << 30)
+        params = rc.make_pre_params(synth.FS_HZ, mean_len=5, halo_c=-1)
+        keep, descs = [], []
+        for c in synth.mixed_batch_cases(64, seed=100):
+            x = torch.from_numpy(synth.radar_frame(c.spec)).cuda()
+            w = c.window
+            b = rc.rcfar_band_plan(c.spec.N, rc.make_pre_params(synth.FS_HZ, mean_len=5, halo_c=w.train_c + w.guard_c))
+            d = torch.empty((c.spec.M, b.cols), dtype=torch.uint8, device="cuda")
+            keep += [x, d]
+            descs.append(rc.frame_desc(x, rc.make_window(w.train_r, w.train_c, w.guard_r, w.guard_c, w.pfa), d))
+        for _ in range(3):
+            rc.rcfar_run_batch(h, descs, params)
+    torch.cuda.synchronize()
+    st = rc.rcfar_get_error(h)
+    rc.rcfar_destroy(h)
+    print("profile case", args.profile, "status", st)
+    return 0 if st == rc.RCFAR_OK else 1
+
+
 def main():
     args = parse_args()
+    if args.profile:
+        sys.exit(profile_case(args))
     rank, world, local, dist = dist_setup()
     if args.impl == "reference":
         reference_arm(args, rank)
