@@ -54,6 +54,10 @@ def parse_args():
                          "chain = the 1024x4096 frame through the per-frame calls, map = SAT (I64) + CFAR on a "
                          "--map-size square map, batch = one 64-frame mixed batch")
     ap.add_argument("--map-size", type=int, default=4096)
+    ap.add_argument("--no-serve", action="store_true", help="skip the serving measurement")
+    ap.add_argument("--serve-frames", type=int, default=2000,
+                    help="frames of the paced serving run (200 frames/s offered); 10000 = the full stream")
+    ap.add_argument("--serve-burst", type=int, default=10000, help="frames of the time-compressed serving run")
     return ap.parse_args()
 
 
@@ -326,6 +330,79 @@ def batch_measure(rc, torch, synth, local, rank, n_frames=64, reps=5):
 
 
 # ---------------------------------------------------------------- our arm
+def serving_measure(rc, torch, synth, local, rank, n_paced, n_burst):
+    """Poisson stream from 32 drones (fixed frame size and window per drone,
+    sizes and windows as in the mixed batch) through the library's serving loop
+    (continuous batching, 8 GB device-memory admission budget, 3 batches in
+    flight). Paced: frames submitted at their arrival times (200 frames/s
+    offered): latency = completion - arrival. Time-compressed: every frame
+    submitted at once: sustained frames/s. Inputs come from pinned host memory
+    and decisions go back to it; copies are inside every latency."""
+    params = rc.make_pre_params(synth.FS_HZ, mean_len=5, halo_c=-1)
+    arrivals, drones, variants, cases = synth.serving_stream(n_requests=max(n_paced, n_burst), n_drones=32,
+                                                             rate_hz=200.0, seed=7 + rank, n_variants=4)
+    srv = rc.rcfar_server_create(device=local, budget_bytes=8 << 30, slots=3, max_batch_frames=64, max_rows=1024,
+                                 max_n=4096, max_window=20, params=params)
+    pool, cols = {}, {}
+    for d, vs in enumerate(cases):
+        w = vs[0].window
+        cols[d] = rc.rcfar_band_plan(vs[0].spec.N, rc.make_pre_params(synth.FS_HZ, mean_len=5,
+                                                                      halo_c=w.train_c + w.guard_c)).cols
+        for v, c in enumerate(vs):
+            pool[(d, v)] = torch.from_numpy(synth.radar_frame(c.spec)).pin_memory()
+    wins = [rc.make_window(vs[0].window.train_r, vs[0].window.train_c, vs[0].window.guard_r, vs[0].window.guard_c,
+                           vs[0].window.pfa) for vs in cases]
+    rc.rcfar_server_prepare(srv, [vs[0].spec.N for vs in cases], wins)
+    # decision buffers: one pinned arena, a slice per request
+    n_all = max(n_paced, n_burst)
+    sizes = [pool[(int(drones[i]), int(variants[i]))].shape[0] * cols[int(drones[i])] for i in range(n_all)]
+    arena = torch.empty(sum(sizes), dtype=torch.uint8).pin_memory()
+    offs = [0]
+    for z in sizes:
+        offs.append(offs[-1] + z)
+
+    def det_of(i):
+        d = int(drones[i])
+        return arena[offs[i]:offs[i + 1]].view(pool[(d, 0)].shape[0], cols[d])
+
+    def run(n, paced):
+        done = {}
+        t0 = rc.rcfar_server_now_ns() + 2_000_000
+        for i in range(n):
+            d, v = int(drones[i]), int(variants[i])
+            t_arr = t0 + int(arrivals[i] * 1e9) if paced else 0
+            if paced:
+                while rc.rcfar_server_now_ns() < t_arr:
+                    time.sleep(0.0001)
+            rc.rcfar_server_submit(srv, pool[(d, v)], wins[d], det_of(i), tag=i, arrival_ns=t_arr)
+            if i % 32 == 31:
+                for c in rc.rcfar_server_poll(srv, 1024, 0):
+                    done[c.tag] = c
+        deadline = time.time() + 300
+        while len(done) < n and time.time() < deadline:
+            for c in rc.rcfar_server_poll(srv, 1024, 50):
+                done[c.tag] = c
+        bad = [c for c in done.values() if c.status != rc.RCFAR_OK]
+        if len(done) < n or bad:
+            raise RuntimeError(f"serving: {len(done)} of {n} completed, {len(bad)} failed")
+        lat = sorted((c.done_ns - c.arrival_ns) / 1e6 for c in done.values())
+        first = min(c.arrival_ns for c in done.values())
+        last = max(c.done_ns for c in done.values())
+        return {"frames": n, "p50_ms": lat[len(lat) // 2], "p99_ms": lat[min(len(lat) - 1, int(0.99 * len(lat)))],
+                "max_ms": lat[-1], "frames_per_s": n / ((last - first) / 1e9),
+                "mean_batch": sum(c.batch_frames for c in done.values()) / n}
+
+    run(min(256, n_all), paced=False)  # warm-up: every slot runs batches
+    paced = run(n_paced, paced=True) if n_paced > 0 else None
+    burst = run(n_burst, paced=False) if n_burst > 0 else None
+    st = rc.rcfar_server_get_stats(srv)
+    rc.rcfar_server_destroy(srv)
+    return {"workload": "Poisson stream, 32 drones (fixed size and window each, sizes M ~ U{128..1024}, "
+                        "N ~ U{256..4096}), 200 frames/s offered; pinned host in/out; 8 GB budget, 3 slots",
+            "paced": paced, "time_compressed": burst,
+            "max_inflight_frames": st["max_inflight_frames"], "device_bytes": st["device_bytes"]}
+
+
 def ours(args, rank, world, local, dist):
     import numpy as np
     import torch
@@ -491,6 +568,13 @@ def ours(args, rank, world, local, dist):
     if not args.no_batch:
         batch = batch_measure(rc, torch, synth, local, rank)
 
+    serving = None
+    if not args.no_serve:
+        serving = serving_measure(rc, torch, synth, local, rank, args.serve_frames, args.serve_burst)
+        if batch is not None and serving["time_compressed"]:
+            serving["sustained_vs_per_frame_path"] = (serving["time_compressed"]["frames_per_s"] /
+                                                      batch["per_frame_path_frames_per_s"])
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         v, n, el = oracle_rate()
@@ -508,7 +592,8 @@ def ours(args, rank, world, local, dist):
                                    "Pfa 1e-6, mean filter 5, fs 20 Hz)",
                        "l2": "inputs larger than L2: ring of 16 distinct frames (268 MB)",
                        "parallelism": f"replicas x{world}"},
-            "roofline": roofline, "kernels": step_kernels, "sat_cfar": sat_cfar, "batch": batch, "e2e": e2e,
+            "roofline": roofline, "kernels": step_kernels, "sat_cfar": sat_cfar, "batch": batch,
+            "serving": serving, "e2e": e2e,
             "cpu_baseline": cpu, "clocks": clk, "gpu_launches": launches_per_step * args.steps,
             "peaks": peaks["source"]}
     print(json.dumps(line), flush=True)

@@ -276,6 +276,84 @@ rcfar_status rcfar_sat_cfar_static(const float* map, int32_t rows, int32_t cols,
                                    int64_t ld_det, float* thr, int64_t ld_thr, int32_t* status,
                                    rcfar_stream stream);
 
+/* ---- serving: continuous batching of frames from many sources ---------- */
+
+/* A request loop in the library: frames from many sources (drones) are
+ * submitted from HOST memory at any time; a scheduler thread admits them, in
+ * arrival order, into batches that fit the device-memory budget and runs up
+ * to `slots` batches at once, each on its own stream (copies in, the
+ * rcfar_run_batch chain, decisions out), so the work of requests that arrive
+ * while others are on the GPU overlaps theirs; a completion thread returns the
+ * decisions to the caller's host buffers with timestamps. Each frame's
+ * decisions are identical to those of the frame run alone (rcfar_run_batch
+ * results do not depend on the rest of the batch). The paper processes one
+ * frame at a time (Sec. III); this is the deployment form for many radars.
+ * Twiddle tables are kept on the device per (N, band) once built. The
+ * server's threads call only the library; the server is thread-safe. */
+typedef struct rcfar_server_s* rcfar_server;
+
+typedef struct rcfar_server_config {
+  int32_t device;
+  int64_t budget_bytes;      /* device memory for frames in flight (inputs, decisions, workspaces);
+                                split evenly between the slots */
+  int32_t slots;             /* batches in flight at once, 1..8 */
+  int32_t max_batch_frames;  /* frames per batch, 1..64 */
+  int32_t max_rows;          /* largest M accepted */
+  int32_t max_n;             /* largest N accepted */
+  int32_t max_window;        /* largest guard + training per side accepted */
+  rcfar_pre_params params;   /* fs, band, mean filter; halo_c must be -1 (each frame its own window) */
+} rcfar_server_config;
+
+typedef struct rcfar_request {
+  const float* x;          /* HOST raw frame, M rows of ldx floats (pinned memory: asynchronous copy) */
+  int32_t M, N;
+  int64_t ldx;
+  rcfar_window window;
+  uint8_t* det;            /* HOST output M x C, C = rcfar_band_plan(N, params with halo_c = the
+                              window's guard_c + train_c).cols; written before the completion appears */
+  int64_t ld_det;
+  int64_t tag;             /* caller's identifier, returned with the completion */
+  int64_t arrival_ns;      /* arrival time on rcfar_server_now_ns's clock; 0 = at submission */
+} rcfar_request;
+
+typedef struct rcfar_completion {
+  int64_t tag;
+  int32_t status;          /* rcfar_status of the frame's batch */
+  int32_t batch_frames;    /* frames in the batch it ran in */
+  int32_t slot;
+  int32_t pad;
+  int64_t arrival_ns, admit_ns, done_ns;  /* latency = done_ns - arrival_ns */
+} rcfar_completion;
+
+typedef struct rcfar_server_stats {
+  int64_t submitted, completed, batches;
+  int64_t max_batch_frames_seen;
+  int64_t max_inflight_frames;    /* largest number of frames admitted at once */
+  int64_t device_bytes;           /* device memory held by the server (slots, workspaces, tables) */
+} rcfar_server_stats;
+
+/* Creates the server and its threads; allocates all slot memory up front.
+ * INVALID_ARG for a bad configuration, CUDA if allocation fails. */
+rcfar_status rcfar_server_create(const rcfar_server_config* cfg, rcfar_server* out);
+/* Queues one frame (the request is copied; x and det must stay valid until
+ * its completion is polled). UNSUPPORTED if the frame exceeds the configured
+ * maxima or could never fit one slot's share of the budget; INVALID_ARG for
+ * bad sizes or window; BAD_STATE after destroy has begun. */
+rcfar_status rcfar_server_submit(rcfar_server srv, const rcfar_request* req);
+/* Builds, on every slot, the twiddle tables of frames with these slow-time
+ * lengths N[i] and windows w[i] (host arrays of n), so that the first frames
+ * of each size do not wait for them. Optional. */
+rcfar_status rcfar_server_prepare(rcfar_server srv, const int32_t* N, const rcfar_window* w, int32_t n);
+/* Returns up to max completions (out: host array); waits up to wait_ms
+ * milliseconds for the first one (0: do not wait). */
+rcfar_status rcfar_server_poll(rcfar_server srv, rcfar_completion* out, int32_t max, int32_t* n_out,
+                               int32_t wait_ms);
+rcfar_status rcfar_server_get_stats(rcfar_server srv, rcfar_server_stats* out);
+/* Monotonic clock the server stamps requests with (nanoseconds). */
+int64_t rcfar_server_now_ns(void);
+/* Completes every submitted frame, stops the threads and frees the server. */
+rcfar_status rcfar_server_destroy(rcfar_server srv);
+
 /* ---- tracing ----------------------------------------------------------- */
 
 /* Per-kernel device time of the handle's launches (CUDA events around each

@@ -39,6 +39,8 @@ EXPORTS = (
     "rcfar_status_string", "rcfar_preprocess", "rcfar_sat", "rcfar_cfar", "rcfar_cfar_direct",
     "rcfar_sat_materialize", "rcfar_run_batch", "rcfar_batch_bytes", "rcfar_prepare", "rcfar_get_error",
     "rcfar_trace_enable", "rcfar_trace_read", "rcfar_sat_cfar_static",
+    "rcfar_server_create", "rcfar_server_submit", "rcfar_server_prepare", "rcfar_server_poll", "rcfar_server_get_stats",
+    "rcfar_server_now_ns", "rcfar_server_destroy",
 )
 
 
@@ -91,6 +93,30 @@ class rcfar_frame_desc(ctypes.Structure):
 _lib = None
 
 
+class rcfar_server_config(ctypes.Structure):
+    _fields_ = [("device", ctypes.c_int32), ("budget_bytes", ctypes.c_int64), ("slots", ctypes.c_int32),
+                ("max_batch_frames", ctypes.c_int32), ("max_rows", ctypes.c_int32), ("max_n", ctypes.c_int32),
+                ("max_window", ctypes.c_int32), ("params", rcfar_pre_params)]
+
+
+class rcfar_request(ctypes.Structure):
+    _fields_ = [("x", ctypes.c_void_p), ("M", ctypes.c_int32), ("N", ctypes.c_int32), ("ldx", ctypes.c_int64),
+                ("window", rcfar_window), ("det", ctypes.c_void_p), ("ld_det", ctypes.c_int64),
+                ("tag", ctypes.c_int64), ("arrival_ns", ctypes.c_int64)]
+
+
+class rcfar_completion(ctypes.Structure):
+    _fields_ = [("tag", ctypes.c_int64), ("status", ctypes.c_int32), ("batch_frames", ctypes.c_int32),
+                ("slot", ctypes.c_int32), ("pad", ctypes.c_int32), ("arrival_ns", ctypes.c_int64),
+                ("admit_ns", ctypes.c_int64), ("done_ns", ctypes.c_int64)]
+
+
+class rcfar_server_stats(ctypes.Structure):
+    _fields_ = [("submitted", ctypes.c_int64), ("completed", ctypes.c_int64), ("batches", ctypes.c_int64),
+                ("max_batch_frames_seen", ctypes.c_int64), ("max_inflight_frames", ctypes.c_int64),
+                ("device_bytes", ctypes.c_int64)]
+
+
 def lib() -> ctypes.CDLL:
     """The loaded librcfar.so (raises if it was not built)."""
     global _lib
@@ -123,11 +149,19 @@ def lib() -> ctypes.CDLL:
             "rcfar_trace_read": [P, ctypes.POINTER(rcfar_trace_entry), I32, ctypes.POINTER(I32)],
             "rcfar_sat_cfar_static": [P, I32, I32, I64, F32, ctypes.POINTER(rcfar_window), I32, I32, P, I64, P,
                                       I64, P, P],
+            "rcfar_server_create": [ctypes.POINTER(rcfar_server_config), ctypes.POINTER(P)],
+            "rcfar_server_submit": [P, ctypes.POINTER(rcfar_request)],
+            "rcfar_server_prepare": [P, ctypes.POINTER(I32), ctypes.POINTER(rcfar_window), I32],
+            "rcfar_server_poll": [P, ctypes.POINTER(rcfar_completion), I32, ctypes.POINTER(I32), I32],
+            "rcfar_server_get_stats": [P, ctypes.POINTER(rcfar_server_stats)],
+            "rcfar_server_now_ns": [],
+            "rcfar_server_destroy": [P],
         }
         for name, args in sig.items():
             fn = getattr(L, name)
             fn.argtypes = args
-            fn.restype = ctypes.c_char_p if name == "rcfar_status_string" else ctypes.c_int
+            fn.restype = {"rcfar_status_string": ctypes.c_char_p,
+                          "rcfar_server_now_ns": ctypes.c_int64}.get(name, ctypes.c_int)
         _lib = L
     return _lib
 
@@ -301,3 +335,53 @@ def rcfar_sat_cfar_static(map_t, value_bound: float, window: rcfar_window, cut_c
                                        float(value_bound), ctypes.byref(window), int(cut_c_lo), int(cut_c_hi),
                                        _ptr(det), _ld(det), _ptr(thr), _ld(thr) if thr is not None else 0,
                                        _ptr(status), _stream(stream)), "rcfar_sat_cfar_static")
+
+
+# ---- serving ---------------------------------------------------------------
+
+def rcfar_server_create(device: int = 0, budget_bytes: int = 8 << 30, slots: int = 3, max_batch_frames: int = 64,
+                        max_rows: int = 1024, max_n: int = 4096, max_window: int = 32,
+                        params: Optional[rcfar_pre_params] = None) -> int:
+    cfg = rcfar_server_config(int(device), int(budget_bytes), int(slots), int(max_batch_frames), int(max_rows),
+                              int(max_n), int(max_window), params if params is not None else make_pre_params(halo_c=-1))
+    out = ctypes.c_void_p()
+    _check(lib().rcfar_server_create(ctypes.byref(cfg), ctypes.byref(out)), "rcfar_server_create")
+    return out.value
+
+
+def rcfar_server_submit(srv: int, x, window: rcfar_window, det, tag: int, arrival_ns: int = 0):
+    """x, det: host (CPU) tensors, row-major (pinned memory gives asynchronous copies); they must stay
+    alive until the frame's completion has been polled."""
+    if x.device.type != "cpu" or det.device.type != "cpu":
+        raise ValueError("serving takes host tensors")
+    M, N = int(x.shape[0]), int(x.shape[1])
+    req = rcfar_request(_ptr(x), M, N, _ld(x), window, _ptr(det), _ld(det), int(tag), int(arrival_ns))
+    _check(lib().rcfar_server_submit(srv, ctypes.byref(req)), "rcfar_server_submit")
+
+
+def rcfar_server_prepare(srv: int, sizes: Sequence[int], windows: Sequence[rcfar_window]):
+    n = len(sizes)
+    Ns = (ctypes.c_int32 * n)(*[int(v) for v in sizes])
+    ws = (rcfar_window * n)(*windows)
+    _check(lib().rcfar_server_prepare(srv, Ns, ws, n), "rcfar_server_prepare")
+
+
+def rcfar_server_poll(srv: int, max_n: int = 256, wait_ms: int = 0) -> list:
+    buf = (rcfar_completion * max_n)()
+    n = ctypes.c_int32()
+    _check(lib().rcfar_server_poll(srv, buf, int(max_n), ctypes.byref(n), int(wait_ms)), "rcfar_server_poll")
+    return [buf[i] for i in range(n.value)]
+
+
+def rcfar_server_get_stats(srv: int) -> dict:
+    st = rcfar_server_stats()
+    _check(lib().rcfar_server_get_stats(srv, ctypes.byref(st)), "rcfar_server_get_stats")
+    return {f: getattr(st, f) for f, _ in rcfar_server_stats._fields_}
+
+
+def rcfar_server_now_ns() -> int:
+    return int(lib().rcfar_server_now_ns())
+
+
+def rcfar_server_destroy(srv: int):
+    _check(lib().rcfar_server_destroy(srv), "rcfar_server_destroy")

@@ -189,28 +189,39 @@ def integer_map(rows: int, cols: int, hi: int = 16, seed: int = 0) -> np.ndarray
 
 
 def serving_stream(n_requests: int = 10000, n_drones: int = 32, rate_hz: float = 200.0,
-                   seed: int = 0, m_range=(128, 1024), n_range=(256, 4096)):
+                   seed: int = 0, m_range=(128, 1024), n_range=(256, 4096), n_variants: int = 4):
     """Poisson request stream from simulated drones.
 
-    Returns (arrival_times_s, drone_ids, drone_windows, frame_cases). Each drone
-    has a fixed window drawn from the mixed-batch sets; each request is one frame
-    whose size is drawn as in mixed_batch_cases.
+    Each drone is one radar: a fixed frame size M x N and a fixed window, drawn
+    as in mixed_batch_cases; it has n_variants distinct frames (targets and
+    noise differ). Requests arrive as a Poisson process of rate rate_hz; each
+    comes from a uniformly drawn drone and carries one of its frames.
+    One PCG64 stream (seed) draws, in this order: per drone M, N, training,
+    guard, Pfa; per drone and variant the targets ~ U{0..10} and the frame
+    seed; then the n_requests gaps ~ Exp(rate_hz), drones and variants.
+
+    Returns (arrival_times_s, drone_ids, variants, drone_cases) with
+    drone_cases[d][v] the ChainCase of drone d's frame v.
     """
     rng = np.random.Generator(np.random.PCG64(seed))
-    windows = []
+    shapes = []
     for _ in range(n_drones):
+        M = int(rng.integers(m_range[0], m_range[1] + 1))
+        N = int(rng.integers(n_range[0], n_range[1] + 1))
         tr = int(rng.choice(TRAIN_SET))
         gd = int(rng.choice(GUARD_SET))
         pfa = float(rng.choice(PFA_SET))
-        windows.append(Window(tr, tr, gd, gd, pfa))
+        shapes.append((M, N, Window(tr, tr, gd, gd, pfa)))
+    drone_cases = []
+    for M, N, w in shapes:
+        vs = []
+        for _ in range(n_variants):
+            nt = int(rng.integers(0, 11))
+            fseed = int(rng.integers(0, 2 ** 31 - 1))
+            vs.append(ChainCase(FrameSpec(M=M, N=N, n_targets=nt, seed=fseed), w))
+        drone_cases.append(vs)
     gaps = rng.exponential(1.0 / rate_hz, size=n_requests)
     arrivals = np.cumsum(gaps)
     drones = rng.integers(0, n_drones, size=n_requests)
-    cases = []
-    for i in range(n_requests):
-        M = int(rng.integers(m_range[0], m_range[1] + 1))
-        N = int(rng.integers(n_range[0], n_range[1] + 1))
-        nt = int(rng.integers(0, 11))
-        fseed = int(rng.integers(0, 2 ** 31 - 1))
-        cases.append(ChainCase(FrameSpec(M=M, N=N, n_targets=nt, seed=fseed), windows[int(drones[i])]))
-    return arrivals, drones, windows, cases
+    variants = rng.integers(0, n_variants, size=n_requests)
+    return arrivals, drones, variants, drone_cases
