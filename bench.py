@@ -174,29 +174,18 @@ class ClockSampler:
 
 
 def dist_setup():
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
-    if world > 1:
-        import torch.distributed as dist
-        backend = "nccl"
-        dist.init_process_group(backend=backend)
-        return rank, world, local, dist
-    return rank, world, local, None
+    from paper_2012_11077_gb300 import replicas
+    return replicas.setup()
 
 
 def max_over_ranks(x: float, dist) -> float:
-    if dist is None:
-        return x
-    import torch
-    t = torch.tensor([x], dtype=torch.float64, device="cuda")
-    dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    return float(t.item())
+    from paper_2012_11077_gb300 import replicas
+    return replicas.max_over_ranks(x, dist)
 
 
 def barrier(dist):
-    if dist is not None:
-        dist.barrier()
+    from paper_2012_11077_gb300 import replicas
+    replicas.barrier(dist)
 
 
 # ---------------------------------------------------------------- CPU oracle timing

@@ -371,6 +371,15 @@ rcfar_status rcfar_trace_read(rcfar_handle h, rcfar_trace_entry* out, int32_t ma
 
 /* ---- errors ------------------------------------------------------------ */
 
+/* Self-test of failure detection: runs one kernel that waits on a barrier
+ * nothing completes, giving up after `polls` polls (each suspends at most
+ * about a microsecond), the bounded wait every waiting kernel of the library
+ * uses; the kernel records the timeout and returns, and the device stays
+ * usable. Returns RCFAR_ERR_TIMEOUT when the wait ran out (the expected
+ * result), RCFAR_OK if it completed, RCFAR_ERR_INVALID_ARG unless
+ * 0 < polls <= 2^20, RCFAR_ERR_CUDA on a CUDA error. Synchronous. */
+rcfar_status rcfar_selftest_wait(int32_t device, int32_t polls);
+
 /* Waits for the stream, then returns (and clears) the first asynchronous
  * error the kernels recorded on this handle: RCFAR_ERR_RANGE,
  * RCFAR_ERR_TIMEOUT or RCFAR_OK. */

@@ -40,7 +40,7 @@ EXPORTS = (
     "rcfar_sat_materialize", "rcfar_run_batch", "rcfar_batch_bytes", "rcfar_prepare", "rcfar_get_error",
     "rcfar_trace_enable", "rcfar_trace_read", "rcfar_sat_cfar_static",
     "rcfar_server_create", "rcfar_server_submit", "rcfar_server_prepare", "rcfar_server_poll", "rcfar_server_get_stats",
-    "rcfar_server_now_ns", "rcfar_server_destroy",
+    "rcfar_server_now_ns", "rcfar_server_destroy", "rcfar_selftest_wait",
 )
 
 
@@ -156,6 +156,7 @@ def lib() -> ctypes.CDLL:
             "rcfar_server_get_stats": [P, ctypes.POINTER(rcfar_server_stats)],
             "rcfar_server_now_ns": [],
             "rcfar_server_destroy": [P],
+            "rcfar_selftest_wait": [I32, I32],
         }
         for name, args in sig.items():
             fn = getattr(L, name)
@@ -385,3 +386,8 @@ def rcfar_server_now_ns() -> int:
 
 def rcfar_server_destroy(srv: int):
     _check(lib().rcfar_server_destroy(srv), "rcfar_server_destroy")
+
+
+def rcfar_selftest_wait(device: int = 0, polls: int = 2000) -> int:
+    """Runs the bounded-wait self-test; returns the status (RCFAR_ERR_TIMEOUT expected)."""
+    return int(lib().rcfar_selftest_wait(int(device), int(polls)))

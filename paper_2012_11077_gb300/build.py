@@ -15,7 +15,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "librcfar.so")
-SOURCES = ["api.cu", "pre.cu", "sat.cu", "cfar.cu", "static_scratch.cu", "server.cu"]
+SOURCES = ["api.cu", "pre.cu", "sat.cu", "cfar.cu", "static_scratch.cu", "server.cu", "selftest.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
          "-Xcompiler", "-Wall", "-Wno-deprecated-gpu-targets"]

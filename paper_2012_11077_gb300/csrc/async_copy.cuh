@@ -40,13 +40,13 @@ __device__ __forceinline__ void mbar_arrive_expect_tx(unsigned bar, unsigned tx_
                "r"(tx_bytes)
                : "memory");
 }
-// Wait for the phase of the given parity to complete; gives up after a
-// bounded number of polls and returns false. Each poll may suspend the
-// thread for up to kWaitHintNs until the phase completes, so waiting warps
-// do not take issue slots from working ones (at most about a second in all).
+// Wait for the phase of the given parity to complete; gives up after
+// `limit` polls and returns false. Each poll may suspend the thread for up
+// to kWaitHintNs until the phase completes, so waiting warps do not take
+// issue slots from working ones.
 constexpr unsigned kWaitHintNs = 1000;
-__device__ __forceinline__ bool mbar_wait(unsigned bar, unsigned parity) {
-  for (unsigned it = 0; it < kSpinLimit; ++it) {
+__device__ __forceinline__ bool mbar_wait_bounded(unsigned bar, unsigned parity, unsigned limit) {
+  for (unsigned it = 0; it < limit; ++it) {
     unsigned done;
     asm volatile(
         "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n selp.u32 %0, 1, 0, p;\n}\n"
@@ -56,6 +56,10 @@ __device__ __forceinline__ bool mbar_wait(unsigned bar, unsigned parity) {
     if (done) return true;
   }
   return false;
+}
+// The library's kernels wait at most kSpinLimit polls (about a second).
+__device__ __forceinline__ bool mbar_wait(unsigned bar, unsigned parity) {
+  return mbar_wait_bounded(bar, parity, kSpinLimit);
 }
 
 // Bulk copy global -> shared of `bytes` (a multiple of 16; both addresses

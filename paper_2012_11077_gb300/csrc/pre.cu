@@ -72,7 +72,7 @@ __device__ __forceinline__ float mean_weight(int j, int N, int h) {
 // grid: for every frame, n_strips x n_chunks CTAs of 256 threads; a chunk is
 // 64 rows (kStatsRowsPerChunk). Thread (g = warp, lane) owns rows g, g+8, ...
 // of its chunk for 4 columns; all 8 rows are loaded before any arithmetic.
-__global__ void __launch_bounds__(256) k_colstats(const __grid_constant__ PreBatch b) {
+__global__ void __launch_bounds__(256, 4) k_colstats(const __grid_constant__ PreBatch b) {
   const int fi = find_item(b.f, b.n, (int)blockIdx.x, &PreFrameDev::item_stats);
   const PreFrameDev& F = b.f[fi];
   const int local = (int)blockIdx.x - F.item_stats;
@@ -198,6 +198,15 @@ __device__ __forceinline__ float2 split_tf32(float x) {
   return make_float2(__uint_as_float(hi), __uint_as_float(lo));
 }
 
+// The same split by truncation, in two integer/FP32 instructions: the head
+// keeps the top 11 significant bits (a TF32 value), the tail is the exact
+// remainder; the tensor cores read the top 19 bits of each 32-bit operand,
+// so the tail enters the products truncated to TF32 (22 bits in all).
+__device__ __forceinline__ float2 split_tf32_trunc(float x) {
+  const float hi = __uint_as_float(__float_as_uint(x) & 0xFFFFE000u);
+  return make_float2(hi, x - hi);
+}
+
 // y pass: one warp per frame row, 256 samples per CTA column block.
 //   x'[m,n] = x[m,n] - a_n - b_n (m - mbar)       (detrend)
 //   y[m,n]  = mean of x'[m, n-h..n+h] in [0, N)    (mean filter)
@@ -256,6 +265,7 @@ __global__ void __launch_bounds__(256) k_ysplit(const __grid_constant__ PreBatch
     __syncwarp();
     float* yh = F.yhi + (long long)m * F.npad;
     float* yl = F.ylo + (long long)m * F.npad;
+    const float inv_full = 1.0f / (float)(2 * h + 1);
 #pragma unroll
     for (int q = 0; q < kYCols / 32; ++q) {
       const int i = lane + 32 * q;
@@ -265,10 +275,11 @@ __global__ void __launch_bounds__(256) k_ysplit(const __grid_constant__ PreBatch
       if (n < N) {
         float acc = 0.f;
         for (int d = 0; d <= 2 * h; ++d) acc += seg[warp][i + d];
-        const int lo = max(n - h, 0), hi = min(n + h, N - 1);
-        const float y = acc / (float)(hi - lo + 1);
+        const int cnt = min(n + h, N - 1) - max(n - h, 0) + 1;
+        // a full window multiplies by 1 / (2h + 1); the truncated ones at the ends divide
+        const float y = cnt == 2 * h + 1 ? acc * inv_full : acc / (float)cnt;
         ymax = fmaxf(ymax, fabsf(y));
-        out = split_tf32(y - cmv);
+        out = split_tf32_trunc(y - cmv);
       }
       yh[n] = out.x;
       yl[n] = out.y;
