@@ -287,6 +287,8 @@ def batch_measure(rc, torch, synth, local, rank, n_frames=64, reps=5):
         return e0.elapsed_time(e1) / n
 
     t_single = timed(per_frame, reps)
+    # the library's autotuner picks the batch schedule (results are the same for every schedule)
+    tuning = rc.rcfar_tune_batch(h, descs, params, reps=3)
     t_batch_eager = timed(batched, reps)
     stream = torch.cuda.Stream()
     g = torch.cuda.CUDAGraph()
@@ -314,6 +316,10 @@ def batch_measure(rc, torch, synth, local, rank, n_frames=64, reps=5):
             "per_frame_path_frames_per_s": n_frames / (t_single * 1e-3),
             "speedup_vs_per_frame": t_single / t_batch,
             "kernels_us": {k: 1e3 * t / n for k, (n, t) in tr.items()},
+            "tuning": {"dft_kblocks_per_cta": tuning.dft_kblocks_per_cta,
+                       "sat_mode": "I64 (streaming CFAR)" if tuning.sat_mode == rc.RCFAR_SAT_I64 else "TILE_I64",
+                       "cfar_tile": [tuning.cfar_tile_rows, tuning.cfar_tile_cols],
+                       "candidates": tuning.candidates, "best_ms": tuning.best_ms},
             "samples_per_s": samples / (t_batch * 1e-3),
             "decisions_identical": bool(same and ok)}
 

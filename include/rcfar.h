@@ -252,6 +252,36 @@ rcfar_status rcfar_batch_bytes(int32_t M, int32_t N, const rcfar_pre_params* p, 
  * the frames' N and windows are read. */
 rcfar_status rcfar_prepare(rcfar_handle h, const rcfar_frame_desc* frames, int32_t n, const rcfar_pre_params* p);
 
+/* ---- batch tuning ------------------------------------------------------- */
+
+/* How rcfar_run_batch lays its work out on the GPU. Every tuning gives the
+ * same results (bit for bit): only the schedule changes. */
+typedef struct rcfar_batch_tuning {
+  int32_t dft_kblocks_per_cta;  /* K blocks (128 samples) per band-DFT CTA; 0 = automatic (about two waves) */
+  int32_t sat_mode;             /* RCFAR_SAT_TILE_I64 (tile-local table, register-staged CFAR) or
+                                   RCFAR_SAT_I64 (table S itself, CFAR streaming it through a
+                                   bulk-copy ring; frames whose window does not fit the ring use
+                                   TILE_I64) */
+  int32_t cfar_tile_rows;       /* TILE_I64 CFAR strip: CUT rows per step and columns; 0 = automatic */
+  int32_t cfar_tile_cols;
+  double best_ms;               /* rcfar_tune_batch: time of one batch with this tuning */
+  int32_t candidates;           /* rcfar_tune_batch: tunings timed */
+  int32_t pad;
+} rcfar_batch_tuning;
+
+/* Autotuner: times rcfar_run_batch on these frames (outputs are written)
+ * under candidate tunings -- band-DFT K split {auto, 1, 2, 4, 8}, then the
+ * table mode and CFAR strip shapes with the best split -- with CUDA events
+ * on the stream, `reps` batches each after one untimed batch, and keeps the
+ * fastest in the handle for later rcfar_run_batch calls (out may be NULL).
+ * Synchronises the stream; not usable during stream capture (BAD_STATE). */
+rcfar_status rcfar_tune_batch(rcfar_handle h, const rcfar_frame_desc* frames, int32_t n, const rcfar_pre_params* p,
+                              int32_t reps, rcfar_batch_tuning* out, rcfar_stream stream);
+/* Sets (e.g. a saved tuning) or reads the handle's batch tuning.
+ * INVALID_ARG for a negative split, an unknown mode or a bad strip. */
+rcfar_status rcfar_set_batch_tuning(rcfar_handle h, const rcfar_batch_tuning* t);
+rcfar_status rcfar_get_batch_tuning(rcfar_handle h, rcfar_batch_tuning* out);
+
 /* ---- without allocation ------------------------------------------------ */
 
 /* SAT (exact TILE_I64 table) and SAT CA-CFAR of one float32 map, like

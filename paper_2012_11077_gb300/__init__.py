@@ -41,6 +41,7 @@ EXPORTS = (
     "rcfar_trace_enable", "rcfar_trace_read", "rcfar_sat_cfar_static",
     "rcfar_server_create", "rcfar_server_submit", "rcfar_server_prepare", "rcfar_server_poll", "rcfar_server_get_stats",
     "rcfar_server_now_ns", "rcfar_server_destroy", "rcfar_selftest_wait",
+    "rcfar_tune_batch", "rcfar_set_batch_tuning", "rcfar_get_batch_tuning",
 )
 
 
@@ -91,6 +92,12 @@ class rcfar_frame_desc(ctypes.Structure):
 
 
 _lib = None
+
+
+class rcfar_batch_tuning(ctypes.Structure):
+    _fields_ = [("dft_kblocks_per_cta", ctypes.c_int32), ("sat_mode", ctypes.c_int32),
+                ("cfar_tile_rows", ctypes.c_int32), ("cfar_tile_cols", ctypes.c_int32),
+                ("best_ms", ctypes.c_double), ("candidates", ctypes.c_int32), ("pad", ctypes.c_int32)]
 
 
 class rcfar_server_config(ctypes.Structure):
@@ -157,6 +164,10 @@ def lib() -> ctypes.CDLL:
             "rcfar_server_now_ns": [],
             "rcfar_server_destroy": [P],
             "rcfar_selftest_wait": [I32, I32],
+            "rcfar_tune_batch": [P, ctypes.POINTER(rcfar_frame_desc), I32, ctypes.POINTER(rcfar_pre_params), I32,
+                                 ctypes.POINTER(rcfar_batch_tuning), P],
+            "rcfar_set_batch_tuning": [P, ctypes.POINTER(rcfar_batch_tuning)],
+            "rcfar_get_batch_tuning": [P, ctypes.POINTER(rcfar_batch_tuning)],
         }
         for name, args in sig.items():
             fn = getattr(L, name)
@@ -391,3 +402,28 @@ def rcfar_server_destroy(srv: int):
 def rcfar_selftest_wait(device: int = 0, polls: int = 2000) -> int:
     """Runs the bounded-wait self-test; returns the status (RCFAR_ERR_TIMEOUT expected)."""
     return int(lib().rcfar_selftest_wait(int(device), int(polls)))
+
+
+# ---- batch tuning -------------------------------------------------------------
+
+def make_batch_tuning(dft_kblocks_per_cta: int = 0, sat_mode: int = RCFAR_SAT_TILE_I64, cfar_tile=(0, 0)):
+    return rcfar_batch_tuning(int(dft_kblocks_per_cta), int(sat_mode), int(cfar_tile[0]), int(cfar_tile[1]), 0.0, 0, 0)
+
+
+def rcfar_tune_batch(h: int, frames: Sequence[rcfar_frame_desc], params: rcfar_pre_params, reps: int = 3,
+                     stream=None) -> rcfar_batch_tuning:
+    arr = (rcfar_frame_desc * len(frames))(*frames)
+    out = rcfar_batch_tuning()
+    _check(lib().rcfar_tune_batch(h, arr, len(frames), ctypes.byref(params), int(reps), ctypes.byref(out),
+                                  _stream(stream)), "rcfar_tune_batch")
+    return out
+
+
+def rcfar_set_batch_tuning(h: int, t: rcfar_batch_tuning):
+    _check(lib().rcfar_set_batch_tuning(h, ctypes.byref(t)), "rcfar_set_batch_tuning")
+
+
+def rcfar_get_batch_tuning(h: int) -> rcfar_batch_tuning:
+    out = rcfar_batch_tuning()
+    _check(lib().rcfar_get_batch_tuning(h, ctypes.byref(out)), "rcfar_get_batch_tuning")
+    return out

@@ -230,6 +230,8 @@ struct rcfar_ctx {
   };
   std::vector<TraceRec> trace_pool;
   size_t trace_used = 0;
+  // batch schedule (rcfar_tune_batch / rcfar_set_batch_tuning)
+  rcfar_batch_tuning tuning{0, RCFAR_SAT_TILE_I64, 0, 0, 0.0, 0, 0};
 };
 
 namespace {
@@ -952,8 +954,24 @@ rcfar_status rcfar_run_batch(rcfar_handle h, const rcfar_frame_desc* frames, int
         units += (long long)g0.mtiles * g0.ntiles * g0.nblocks;
       }
       pb.dft_smem = dft_smem_for(bn_max);
-      kb_per_cta = (int)std::max<long long>(1, units / (2 * 152));  // about two waves
+      kb_per_cta = h->tuning.dft_kblocks_per_cta > 0
+                       ? h->tuning.dft_kblocks_per_cta
+                       : (int)std::max<long long>(1, units / (2 * 152));  // about two waves
     }
+    // table mode of this group: the streaming CFAR when tuned so and every
+    // frame's window fits its ring
+    int sat_mode = RCFAR_SAT_TILE_I64;
+    int ring_rows_max = 0, hcp_max = 0;
+    if (h->tuning.sat_mode == RCFAR_SAT_I64) {
+      sat_mode = RCFAR_SAT_I64;
+      for (int k = 0; k < cnt && sat_mode == RCFAR_SAT_I64; ++k) {
+        const rcfar_window& w = frames[base + k].window;
+        int rr = 0, hc = 0;
+        if (!cfar_ring_plan(w.guard_r + w.train_r, w.guard_c + w.train_c, h->smem_optin, &rr, &hc))
+          sat_mode = RCFAR_SAT_TILE_I64;
+      }
+    }
+    size_t ring_smem = 0;
     int it_stats = 0, it_dft = 0, it_norm = 0, it_cfar = 0, it_y = 0;
     int it_tile = 0, it_band = 0, it_vscan = 0;
     int cfar_mode_smem = 0, cfar_max_hc = 0;
@@ -1043,15 +1061,27 @@ rcfar_status rcfar_run_batch(rcfar_handle h, const rcfar_frame_desc* frames, int
       P.ld_det = f.ld_det;
       P.thr = f.thr;
       P.ld_thr = f.ld_thr;
-      P.mode = kBatchSatMode;
-      // tile from this frame's own window (batch composition does not matter)
-      const CfarTile t = pick_cfar_tile(kBatchSatMode, P.wr, P.wc, std::min<size_t>(h->smem_optin, 200 * 1024),
-                                        {h->cfg.cfar_tile_rows, h->cfg.cfar_tile_cols});
-      if (t.bh == 0) return RCFAR_ERR_UNSUPPORTED;
+      P.mode = sat_mode;
       P.item0 = it_cfar;
-      it_cfar += set_cfar_geometry(P, t, f.M, C);
-      cfar_mode_smem = std::max<int>(cfar_mode_smem, (int)cfar_smem_bytes(kBatchSatMode, t.bh, t.bw, P.wr, P.wc));
-      cfar_max_hc = std::max(cfar_max_hc, t.bw + 2 * P.wc + 1);
+      if (sat_mode == RCFAR_SAT_I64) {
+        int rr = 0, hc = 0;
+        cfar_ring_plan(P.wr, P.wc, h->smem_optin, &rr, &hc);
+        const size_t sm = cfar_ring_smem(rr, hc);
+        ring_smem = std::max(ring_smem, sm);
+        ring_rows_max = std::max(ring_rows_max, rr);
+        hcp_max = std::max(hcp_max, hc);
+        it_cfar += cfar_ring_geometry(P, f.M, C, rr, hc, cfar_ring_slots(sm));
+      } else {
+        // tile from this frame's own window (batch composition does not matter)
+        const CfarTile pref = h->tuning.cfar_tile_rows > 0
+                                  ? CfarTile{h->tuning.cfar_tile_rows, h->tuning.cfar_tile_cols}
+                                  : CfarTile{h->cfg.cfar_tile_rows, h->cfg.cfar_tile_cols};
+        const CfarTile t = pick_cfar_tile(sat_mode, P.wr, P.wc, std::min<size_t>(h->smem_optin, 200 * 1024), pref);
+        if (t.bh == 0) return RCFAR_ERR_UNSUPPORTED;
+        it_cfar += set_cfar_geometry(P, t, f.M, C);
+        cfar_mode_smem = std::max<int>(cfar_mode_smem, (int)cfar_smem_bytes(sat_mode, t.bh, t.bw, P.wr, P.wc));
+        cfar_max_hc = std::max(cfar_max_hc, t.bw + 2 * P.wc + 1);
+      }
     }
     cudaError_t e;
     {
@@ -1072,14 +1102,106 @@ rcfar_status rcfar_run_batch(rcfar_handle h, const rcfar_frame_desc* frames, int
     }
     if (e == cudaSuccess) {
       TraceScope t(h, "sat", s);
-      e = launch_sat(sb, kBatchSatMode, RCFAR_MAP_F32, it_tile, it_band, it_vscan, s);
+      e = launch_sat(sb, sat_mode, RCFAR_MAP_F32, it_tile, it_band, it_vscan, s);
     }
     if (e == cudaSuccess) {
       TraceScope t(h, "cfar", s);
-      e = launch_cfar(cb, kBatchSatMode, RCFAR_MAP_F32, it_cfar, (size_t)cfar_mode_smem, cfar_max_hc, s);
+      e = sat_mode == RCFAR_SAT_I64
+              ? launch_cfar_ring(cb, true, RCFAR_MAP_F32, it_cfar, ring_smem, s)
+              : launch_cfar(cb, sat_mode, RCFAR_MAP_F32, it_cfar, (size_t)cfar_mode_smem, cfar_max_hc, s);
     }
     if (e != cudaSuccess) return RCFAR_ERR_CUDA;
   }
+  return RCFAR_OK;
+}
+
+static bool valid_tuning(const rcfar_batch_tuning* t) {
+  return t && t->dft_kblocks_per_cta >= 0 && t->dft_kblocks_per_cta <= 4096 &&
+         (t->sat_mode == RCFAR_SAT_TILE_I64 || t->sat_mode == RCFAR_SAT_I64) &&
+         ((t->cfar_tile_rows == 0 && t->cfar_tile_cols == 0) ||
+          (t->cfar_tile_rows > 0 && t->cfar_tile_rows <= 16 && t->cfar_tile_cols > 0 && 256 % t->cfar_tile_cols == 0 &&
+           t->cfar_tile_rows * t->cfar_tile_cols <= 1024));
+}
+
+rcfar_status rcfar_set_batch_tuning(rcfar_handle h, const rcfar_batch_tuning* t) {
+  if (!h || !valid_tuning(t)) return RCFAR_ERR_INVALID_ARG;
+  std::lock_guard<std::mutex> lk(h->mu);
+  h->tuning = *t;
+  return RCFAR_OK;
+}
+
+rcfar_status rcfar_get_batch_tuning(rcfar_handle h, rcfar_batch_tuning* out) {
+  if (!h || !out) return RCFAR_ERR_INVALID_ARG;
+  std::lock_guard<std::mutex> lk(h->mu);
+  *out = h->tuning;
+  return RCFAR_OK;
+}
+
+// Times one tuning: one untimed batch, then reps batches between two events.
+static rcfar_status time_tuning(rcfar_handle h, const rcfar_frame_desc* frames, int n, const rcfar_pre_params* p,
+                                int reps, const rcfar_batch_tuning& t, cudaStream_t s, cudaEvent_t e0, cudaEvent_t e1,
+                                double* ms) {
+  {
+    std::lock_guard<std::mutex> lk(h->mu);
+    h->tuning = t;
+  }
+  rcfar_status st = rcfar_run_batch(h, frames, n, p, s);
+  if (st != RCFAR_OK) return st;
+  if (cudaEventRecord(e0, s) != cudaSuccess) return RCFAR_ERR_CUDA;
+  for (int r = 0; r < reps && st == RCFAR_OK; ++r) st = rcfar_run_batch(h, frames, n, p, s);
+  if (st != RCFAR_OK) return st;
+  float el = 0.f;
+  if (cudaEventRecord(e1, s) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
+      cudaEventElapsedTime(&el, e0, e1) != cudaSuccess)
+    return RCFAR_ERR_CUDA;
+  *ms = (double)el / reps;
+  return RCFAR_OK;
+}
+
+rcfar_status rcfar_tune_batch(rcfar_handle h, const rcfar_frame_desc* frames, int32_t n, const rcfar_pre_params* p,
+                              int32_t reps, rcfar_batch_tuning* out, rcfar_stream stream) {
+  if (!h || !frames || n <= 0 || reps <= 0 || reps > 100) return RCFAR_ERR_INVALID_ARG;
+  DeviceGuard dg(h->device);
+  cudaStream_t s = (cudaStream_t)stream;
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(s, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone) return RCFAR_ERR_BAD_STATE;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+    if (e0) cudaEventDestroy(e0);
+    return RCFAR_ERR_CUDA;
+  }
+  const rcfar_batch_tuning saved = h->tuning;
+  rcfar_batch_tuning best = saved;
+  best.best_ms = 1e30;
+  int timed = 0;
+  rcfar_status st = RCFAR_OK;
+  auto consider = [&](rcfar_batch_tuning t) {
+    if (st != RCFAR_OK) return;
+    double ms = 0.0;
+    st = time_tuning(h, frames, n, p, reps, t, s, e0, e1, &ms);
+    ++timed;
+    if (st == RCFAR_OK && ms < best.best_ms) {
+      best = t;
+      best.best_ms = ms;
+    }
+  };
+  // stage 1: the band-DFT K split, with the default table and CFAR
+  const int splits[] = {0, 1, 2, 4, 8};
+  for (int kb : splits) consider(rcfar_batch_tuning{kb, RCFAR_SAT_TILE_I64, 0, 0, 0.0, 0, 0});
+  // stage 2: table mode and CFAR strips with the best split
+  const int kb = best.dft_kblocks_per_cta;
+  consider(rcfar_batch_tuning{kb, RCFAR_SAT_I64, 0, 0, 0.0, 0, 0});
+  const int tiles[][2] = {{16, 64}, {8, 64}, {16, 32}, {8, 128}};
+  for (const auto& tl : tiles) consider(rcfar_batch_tuning{kb, RCFAR_SAT_TILE_I64, tl[0], tl[1], 0.0, 0, 0});
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  best.candidates = timed;
+  {
+    std::lock_guard<std::mutex> lk(h->mu);
+    h->tuning = st == RCFAR_OK ? best : saved;
+  }
+  if (st != RCFAR_OK) return st;
+  if (out) *out = best;
   return RCFAR_OK;
 }
 

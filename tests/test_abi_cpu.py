@@ -101,3 +101,13 @@ def test_product_path_does_not_import_oracle():
             if f.endswith((".py", ".cu", ".cuh", ".h")):
                 txt = open(os.path.join(dirpath, f)).read()
                 assert "import oracle" not in txt and "from oracle" not in txt, f
+
+
+def test_batch_tuning_argument_checks(rc):
+    # invalid arguments are rejected before any device work
+    import ctypes
+    L = rc.lib()
+    bad = rc.make_batch_tuning(-1)
+    assert L.rcfar_set_batch_tuning(None, ctypes.byref(bad)) == rc.RCFAR_ERR_INVALID_ARG
+    assert L.rcfar_get_batch_tuning(None, None) == rc.RCFAR_ERR_INVALID_ARG
+    assert L.rcfar_tune_batch(None, None, 0, None, 1, None, None) == rc.RCFAR_ERR_INVALID_ARG

@@ -434,3 +434,49 @@ def test_run_batch_workspace_limit(rc):
         assert e.value.status == rc.RCFAR_ERR_OUT_OF_WORKSPACE
     finally:
         rc.rcfar_destroy(small)
+
+
+def test_batch_tunings_give_identical_results(rc):
+    # every batch tuning (band-DFT split, table mode, CFAR strip) changes only
+    # the schedule: outputs are bit-identical; the autotuner keeps the fastest
+    cases = synth.mixed_batch_cases(12, seed=21, m_range=(64, 400), n_range=(256, 2048))
+    params = rc.make_pre_params(synth.FS_HZ, mean_len=5, halo_c=-1)
+    h2 = rc.rcfar_create(device=0, max_rows=512, max_cols=1100, max_n=2048, max_window=20, max_frames=16,
+                         batch_bytes=1 << 30)
+    try:
+        keep, frames, outs = [], [], []
+        for c in cases:
+            w = c.window
+            band = rc.rcfar_band_plan(c.spec.N, rc.make_pre_params(synth.FS_HZ, mean_len=5, halo_c=w.train_c + w.guard_c))
+            x = dev_t(synth.radar_frame(c.spec))
+            det = torch.empty((c.spec.M, band.cols), dtype=torch.uint8, device="cuda")
+            thr = torch.empty((c.spec.M, band.cols), dtype=torch.float32, device="cuda")
+            mp = torch.empty((c.spec.M, band.cols), dtype=torch.float32, device="cuda")
+            keep.append(x)
+            frames.append(rc.frame_desc(x, rc.make_window(w.train_r, w.train_c, w.guard_r, w.guard_c, w.pfa), det, thr, mp))
+            outs.append((det, thr, mp))
+        ref = None
+        for t in [rc.make_batch_tuning(), rc.make_batch_tuning(1), rc.make_batch_tuning(8),
+                  rc.make_batch_tuning(2, rc.RCFAR_SAT_I64), rc.make_batch_tuning(0, rc.RCFAR_SAT_TILE_I64, (8, 32))]:
+            rc.rcfar_set_batch_tuning(h2, t)
+            for d, th, mp in outs:
+                d.fill_(7)
+                th.fill_(-1.0)
+                mp.fill_(-1.0)
+            rc.rcfar_run_batch(h2, frames, params)
+            assert rc.rcfar_get_error(h2) == rc.RCFAR_OK
+            got = [(d.cpu(), th.cpu(), mp.cpu()) for d, th, mp in outs]
+            if ref is None:
+                ref = got
+            else:
+                for (a, b, c_), (a2, b2, c2) in zip(ref, got):
+                    assert torch.equal(a, a2) and torch.equal(b, b2) and torch.equal(c_, c2)
+        best = rc.rcfar_tune_batch(h2, frames, params, reps=2)
+        assert best.candidates == 10 and best.best_ms > 0
+        cur = rc.rcfar_get_batch_tuning(h2)
+        assert (cur.dft_kblocks_per_cta, cur.sat_mode) == (best.dft_kblocks_per_cta, best.sat_mode)
+        rc.rcfar_run_batch(h2, frames, params)
+        for (a, b, c_), (d, th, mp) in zip(ref, outs):
+            assert torch.equal(a, d.cpu()) and torch.equal(b, th.cpu()) and torch.equal(c_, mp.cpu())
+    finally:
+        rc.rcfar_destroy(h2)
