@@ -28,7 +28,42 @@ inline size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 struct Twiddle {
   float* Wt = nullptr;
   long long ldw = 0;
+  int npad = 0, bn = 0;
+  bool has_map = false;
+  CUtensorMap mb;  // both planes of Wt for the tensor-memory-accelerator band DFT
 };
+
+// cuTensorMapEncodeTiled, looked up once from the driver (no link to libcuda)
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+EncodeTiledFn encode_tiled() {
+  static EncodeTiledFn fn = [] {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess)
+      p = nullptr;
+    return reinterpret_cast<EncodeTiledFn>(p);
+  }();
+  return fn;
+}
+
+// Tensor map of two planes [2][rows][npad] fp32 (plane stride rows * npad):
+// boxes of 32 samples x box_rows rows x 1 plane, 128-byte swizzle, rows past
+// the end read as zeros.
+bool make_planes_map(CUtensorMap* out, const float* base, long long rows, int npad, int box_rows) {
+  EncodeTiledFn fn = encode_tiled();
+  if (!fn || (reinterpret_cast<uintptr_t>(base) & 15) || (npad % kDftBK) || box_rows < 1 || box_rows > 256)
+    return false;
+  const cuuint64_t dims[3] = {(cuuint64_t)npad, (cuuint64_t)rows, 2};
+  const cuuint64_t strides[2] = {(cuuint64_t)npad * sizeof(float), (cuuint64_t)rows * npad * sizeof(float)};
+  const cuuint32_t box[3] = {(cuuint32_t)kDftBK, (cuuint32_t)box_rows, 1};
+  const cuuint32_t elem[3] = {1, 1, 1};
+  return fn(out, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<float*>(base), dims, strides, box, elem,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
 
 // Bump allocator over a device region.
 struct Carver {
@@ -336,9 +371,33 @@ static rcfar_status get_plan(rcfar_ctx* h, int N, int c0, int C, cudaStream_t s,
     cudaFree(t.Wt);
     return RCFAR_ERR_CUDA;
   }
+  t.npad = npad;
+  t.bn = bn;
+  t.has_map = make_planes_map(&t.mb, t.Wt, t.ldw, npad, bn);
   h->plans[key] = t;
   *out = t;
   return RCFAR_OK;
+}
+
+// The band-DFT launch parameters of one frame for the TMA-fed kernel (false
+// when a tensor map cannot be made; the cp.async kernel runs instead).
+static bool make_dft_frame(DftBatch& db, int k, const PreFrameDev& F, const Twiddle& tw, const PreGeom& g) {
+  if (!tw.has_map || tw.bn != g.bn || tw.npad != g.npad) return false;
+  if (F.ylo != F.yhi + (long long)F.M * g.npad) return false;
+  if (!make_planes_map(&db.ma[k], F.yhi, F.M, g.npad, kDftBM)) return false;
+  db.mb[k] = tw.mb;
+  DftFrameDev& d = db.f[k];
+  d.kpart = F.kpart;
+  d.ldk = F.ldk;
+  d.M = F.M;
+  d.bn = g.bn;
+  d.mtiles = g.mtiles;
+  d.ntiles = g.ntiles;
+  d.kper = g.kper;
+  d.npad = g.npad;
+  d.item_dft = F.item_dft;
+  d.pad = 0;
+  return true;
 }
 
 static PreFrameDev make_pre_frame(const float* x, int M, int N, long long ldx, const rcfar_band& b, int h,
@@ -635,7 +694,7 @@ rcfar_status rcfar_preprocess(rcfar_handle h, const float* x, int32_t M, int32_t
   F.kpart = h->kpart;
   F.tile_cnt = h->tile_cnt;
   F.yhi = h->yhi;
-  F.ylo = h->ylo;
+  F.ylo = h->yhi + (long long)M * g.npad;  // the two planes back to back (the tail runs into h->ylo's room)
   F.rowmean = h->rowmean;
   F.item_stats = 0;
   F.item_dft = 0;
@@ -652,7 +711,14 @@ rcfar_status rcfar_preprocess(rcfar_handle h, const float* x, int32_t M, int32_t
   }
   if (e == cudaSuccess) {
     TraceScope t(h, "band_dft", s);
-    e = launch_band_dft(pb, g.mtiles * g.ntiles * g.splitk, s);
+    static thread_local DftBatch db;
+    db.n = 1;
+    db.dft_smem = pb.dft_smem;
+    db.status = h->status;
+    if (make_dft_frame(db, 0, F, tw, g))
+      e = launch_band_dft_tma(db, g.mtiles * g.ntiles * g.splitk, s);
+    else
+      e = launch_band_dft(pb, g.mtiles * g.ntiles * g.splitk, s);
   }
   if (e == cudaSuccess) {
     TraceScope t(h, "dft_reduce", s);
@@ -972,6 +1038,11 @@ rcfar_status rcfar_run_batch(rcfar_handle h, const rcfar_frame_desc* frames, int
       }
     }
     size_t ring_smem = 0;
+    static thread_local DftBatch db;
+    db.n = cnt;
+    db.dft_smem = pb.dft_smem;
+    db.status = h->status;
+    bool dft_tma_ok = true;
     int it_stats = 0, it_dft = 0, it_norm = 0, it_cfar = 0, it_y = 0;
     int it_tile = 0, it_band = 0, it_vscan = 0;
     int cfar_mode_smem = 0, cfar_max_hc = 0;
@@ -988,8 +1059,8 @@ rcfar_status rcfar_run_batch(rcfar_handle h, const rcfar_frame_desc* frames, int
       F.rowpart = data.take<float>((size_t)g.n_strips * f.M);
       F.strip_ab = data.take<float2>(g.n_strips);
       F.kpart = data.take<float>((size_t)g.nblocks * f.M * g.ldk);
-      F.yhi = data.take<float>((size_t)f.M * g.npad);
-      F.ylo = data.take<float>((size_t)f.M * g.npad);
+      F.yhi = data.take<float>(2 * (size_t)f.M * g.npad);  // head and tail planes back to back
+      F.ylo = F.yhi ? F.yhi + (long long)f.M * g.npad : nullptr;
       F.rowmean = data.take<float>(f.M);
       float* map = f.map;
       long long ld_map = f.ld_map;
@@ -1005,6 +1076,7 @@ rcfar_status rcfar_run_batch(rcfar_handle h, const rcfar_frame_desc* frames, int
       F.ymax = words;
       F.item_stats = it_stats;
       F.item_dft = it_dft;
+      dft_tma_ok = dft_tma_ok && F.yhi && F.kpart && make_dft_frame(db, k, F, tws[i], g);
       F.item_norm = it_norm;
       F.item_y = it_y;
       it_y += g.n_y;
@@ -1094,7 +1166,7 @@ rcfar_status rcfar_run_batch(rcfar_handle h, const rcfar_frame_desc* frames, int
     }
     if (e == cudaSuccess) {
       TraceScope t(h, "band_dft", s);
-      e = launch_band_dft(pb, it_dft, s);
+      e = dft_tma_ok ? launch_band_dft_tma(db, it_dft, s) : launch_band_dft(pb, it_dft, s);
     }
     if (e == cudaSuccess) {
       TraceScope t(h, "dft_reduce", s);

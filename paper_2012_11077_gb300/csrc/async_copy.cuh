@@ -70,4 +70,17 @@ __device__ __forceinline__ void bulk_g2s(unsigned saddr, const void* gmem, unsig
                : "memory");
 }
 
+// 3-D tiled tensor load global -> shared (box of the tensor map at
+// coordinates {c0, c1, c2}, innermost first), completing on the mbarrier
+// with its byte count; elements outside the tensor arrive as zeros.
+// tmap: generic address of a CUtensorMap in param, const or global memory.
+__device__ __forceinline__ void tma_load_3d(unsigned saddr, unsigned long long tmap, int c0, int c1, int c2,
+                                            unsigned bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], "
+      "[%5];" ::"r"(saddr),
+      "l"(tmap), "r"(c0), "r"(c1), "r"(c2), "r"(bar)
+      : "memory");
+}
+
 }  // namespace rcfar

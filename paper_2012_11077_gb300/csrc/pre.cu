@@ -198,12 +198,14 @@ __device__ __forceinline__ float2 split_tf32(float x) {
   return make_float2(__uint_as_float(hi), __uint_as_float(lo));
 }
 
-// The same split by truncation, in two integer/FP32 instructions: the head
-// keeps the top 11 significant bits (a TF32 value), the tail is the exact
-// remainder; the tensor cores read the top 19 bits of each 32-bit operand,
-// so the tail enters the products truncated to TF32 (22 bits in all).
-__device__ __forceinline__ float2 split_tf32_trunc(float x) {
-  const float hi = __uint_as_float(__float_as_uint(x) & 0xFFFFE000u);
+// The same split in three integer/FP32 instructions: the head is x rounded
+// to TF32 (nearest, ties away from zero: add half a TF32 unit to the bit
+// pattern, clear the 13 low bits), the tail the exact remainder, of either
+// sign; the tensor cores read the top 19 bits of each 32-bit operand, so the
+// tail enters the products truncated to TF32 (22 bits in all; the signed
+// tail keeps that truncation unbiased).
+__device__ __forceinline__ float2 split_tf32_fast(float x) {
+  const float hi = __uint_as_float((__float_as_uint(x) + 0x1000u) & 0xFFFFE000u);
   return make_float2(hi, x - hi);
 }
 
@@ -279,7 +281,7 @@ __global__ void __launch_bounds__(256) k_ysplit(const __grid_constant__ PreBatch
         // a full window multiplies by 1 / (2h + 1); the truncated ones at the ends divide
         const float y = cnt == 2 * h + 1 ? acc * inv_full : acc / (float)cnt;
         ymax = fmaxf(ymax, fabsf(y));
-        out = split_tf32_trunc(y - cmv);
+        out = split_tf32_fast(y - cmv);
       }
       yh[n] = out.x;
       yl[n] = out.y;
@@ -498,6 +500,171 @@ __global__ void __launch_bounds__(kDftThreads, 1) k_band_dft(const __grid_consta
   if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(tcols));
 }
 
+// The same GEMM with the operands brought in by the tensor memory
+// accelerator: one thread of warp 1 issues, per K step, four box loads
+// (y head and tail: 32 samples x 128 rows; twiddle head and tail: 32
+// samples x bn columns) that complete on the stage's mbarrier with their byte
+// count; rows past the frame arrive as zeros. Warp 0 issues the MMAs,
+// warps 2-5 drain the accumulators (warp w reads TMEM lanes 32 (w % 4) ..).
+__global__ void __launch_bounds__(kDftTmaThreads, 1) k_band_dft_tma(const __grid_constant__ DftBatch b) {
+  const int fi = find_item(b.f, b.n, (int)blockIdx.x, &DftFrameDev::item_dft);
+  const DftFrameDev& F = b.f[fi];
+  const int local = (int)blockIdx.x - F.item_dft;
+  const int per_split = F.mtiles * F.ntiles;
+  const int ks = local / per_split;
+  const int rem = local % per_split;
+  const int mt = rem / F.ntiles, nt = rem % F.ntiles;
+  const int m0 = mt * kDftBM;
+  const int bn = F.bn;
+  const int j0 = nt * bn;
+  const int kbeg = ks * F.kper;
+  const int kend = min(F.npad, kbeg + F.kper);
+  const int nk = (kend - kbeg) / kDftBK;
+  const int nblk = (nk + kDftKB - 1) / kDftKB;
+  const int blk0 = kbeg / (kDftBK * kDftKB);
+  const int stage_bytes = dft_stage_bytes(bn);
+  int stages = (b.dft_smem - 1024) / stage_bytes;
+  if (stages > kDftMaxStages) stages = kDftMaxStages;
+
+  extern __shared__ __align__(1024) unsigned char dsm[];
+  unsigned char* base = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(dsm) + 1023) & ~uintptr_t(1023));
+  __shared__ __align__(8) unsigned long long bar_full[kDftMaxStages], bar_empty[kDftMaxStages];
+  __shared__ __align__(8) unsigned long long bar_accf[2], bar_acce[2], bar_done;
+  __shared__ unsigned tmem_slot;
+  __shared__ int s_fail;
+  __shared__ int s_issued, s_consumed;  // K steps whose loads were issued / waited for by the MMA thread
+
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  unsigned tcols = 32;
+  while ((int)tcols < 2 * bn) tcols <<= 1;
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_slot)),
+                 "r"(tcols));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  if (tid == 0) {
+    for (int i = 0; i < kDftMaxStages; ++i) {
+      mbar_init(smem_u32(&bar_full[i]), 1);   // the producer's arrive.expect_tx
+      mbar_init(smem_u32(&bar_empty[i]), 1);  // the MMAs' commit
+    }
+    for (int i = 0; i < 2; ++i) {
+      mbar_init(smem_u32(&bar_accf[i]), 1);
+      mbar_init(smem_u32(&bar_acce[i]), 128);
+    }
+    mbar_init(smem_u32(&bar_done), 1);
+    s_fail = 0;
+    s_issued = 0;
+    s_consumed = 0;
+    mbar_init_fence();
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const unsigned tmem = tmem_slot;
+
+  const unsigned idesc = (1u << 4) | (2u << 7) | (2u << 10) | ((unsigned)(bn >> 3) << 17) |
+                         ((unsigned)(kDftBM >> 4) << 24);
+  if (warp == 0) {
+    if (lane == 0) {
+      for (int i = 0; i < nk; ++i) {
+        const int slot = i % stages;
+        const int bi = i / kDftKB, acc = bi & 1;
+        const bool first = (i % kDftKB) == 0;
+        if (first && bi >= 2 && !mbar_wait(smem_u32(&bar_acce[acc]), (unsigned)(((bi - 2) >> 1) & 1))) {
+          s_fail = 1;
+          break;
+        }
+        if (!mbar_wait(smem_u32(&bar_full[slot]), (unsigned)((i / stages) & 1))) {
+          s_fail = 1;
+          break;
+        }
+        s_consumed = i + 1;
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        unsigned char* st = base + slot * stage_bytes;
+        const unsigned sa_hi = smem_u32(st), sa_lo = sa_hi + kDftBM * 128;
+        const unsigned sb_hi = sa_lo + kDftBM * 128, sb_lo = sb_hi + bn * 128;
+        const unsigned dacc = tmem + (unsigned)(acc * bn);
+#pragma unroll
+        for (int kk = 0; kk < kDftBK / 8; ++kk) {
+          const unsigned off = kk * 32;
+          const unsigned long long ah = umma_desc(sa_hi + off), al = umma_desc(sa_lo + off);
+          const unsigned long long bh = umma_desc(sb_hi + off), bl = umma_desc(sb_lo + off);
+          umma_tf32(dacc, al, bh, idesc, (!first || kk > 0) ? 1u : 0u);
+          umma_tf32(dacc, ah, bl, idesc, 1u);
+          umma_tf32(dacc, ah, bh, idesc, 1u);
+        }
+        umma_commit(smem_u32(&bar_empty[slot]));
+        if ((i % kDftKB) == kDftKB - 1 || i == nk - 1) umma_commit(smem_u32(&bar_accf[acc]));
+      }
+      umma_commit(smem_u32(&bar_done));
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {
+      const unsigned long long ma = reinterpret_cast<unsigned long long>(&b.ma[fi]);
+      const unsigned long long mb = reinterpret_cast<unsigned long long>(&b.mb[fi]);
+      asm volatile("prefetch.tensormap [%0];" ::"l"(ma) : "memory");
+      asm volatile("prefetch.tensormap [%0];" ::"l"(mb) : "memory");
+      const unsigned tx = (unsigned)(2 * kDftBM * 128 + 2 * bn * 128);
+      for (int i = 0; i < nk; ++i) {
+        const int slot = i % stages;
+        if (i >= stages && !mbar_wait(smem_u32(&bar_empty[slot]), (unsigned)(((i - stages) / stages) & 1))) {
+          s_fail = 1;
+          break;
+        }
+        unsigned char* st = base + slot * stage_bytes;
+        const unsigned sa_hi = smem_u32(st), sa_lo = sa_hi + kDftBM * 128;
+        const unsigned sb_hi = sa_lo + kDftBM * 128, sb_lo = sb_hi + bn * 128;
+        const unsigned bar = smem_u32(&bar_full[slot]);
+        const int k0 = kbeg + i * kDftBK;
+        mbar_arrive_expect_tx(bar, tx);
+        tma_load_3d(sa_hi, ma, k0, m0, 0, bar);
+        tma_load_3d(sa_lo, ma, k0, m0, 1, bar);
+        tma_load_3d(sb_hi, mb, k0, j0, 0, bar);
+        tma_load_3d(sb_lo, mb, k0, j0, 1, bar);
+        s_issued = i + 1;
+      }
+    }
+  } else {
+    const int q = warp & 3;
+    const int m = m0 + 32 * q + lane;
+    for (int bi = 0; bi < nblk; ++bi) {
+      const int acc = bi & 1;
+      if (!mbar_wait(smem_u32(&bar_accf[acc]), (unsigned)((bi >> 1) & 1))) {
+        s_fail = 1;
+        break;
+      }
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      float* dst = F.kpart + ((long long)(blk0 + bi) * F.M + (m < F.M ? m : 0)) * F.ldk + j0;
+      for (int c = 0; c < bn; c += 8) {
+        unsigned r[8];
+        const unsigned taddr = tmem + ((unsigned)(32 * q) << 16) + (unsigned)(acc * bn + c);
+        asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                     : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+                     : "r"(taddr));
+        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+        if (m < F.M) {
+          float4* d4 = reinterpret_cast<float4*>(dst + c);
+          d4[0] = make_float4(__uint_as_float(r[0]), __uint_as_float(r[1]), __uint_as_float(r[2]), __uint_as_float(r[3]));
+          d4[1] = make_float4(__uint_as_float(r[4]), __uint_as_float(r[5]), __uint_as_float(r[6]), __uint_as_float(r[7]));
+        }
+      }
+      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+      mbar_arrive(smem_u32(&bar_acce[acc]));
+    }
+  }
+  __syncthreads();
+  const bool ok = mbar_wait(smem_u32(&bar_done), 0u) && !s_fail;
+  if (!ok && tid == 0) atomicOr(b.status, kStatusTimeout);
+  // after a failure, the loads issued but never waited for land before the
+  // shared memory is released (bounded waits)
+  if (tid == 32)
+    for (int i = s_consumed; i < s_issued; ++i)
+      mbar_wait(smem_u32(&bar_full[i % stages]), (unsigned)((i / stages) & 1));
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(tcols));
+}
+
 // Sum of the K blocks' partials in a fixed order with Kahan compensation
 // (deterministic, and the same however the K range was split), magnitude,
 // bin 0's mean added back, and the normalisation by max |y| ("then
@@ -573,6 +740,15 @@ cudaError_t launch_band_dft(const PreBatch& b, int blocks, cudaStream_t s) {
   cudaError_t e = ensure_smem(reinterpret_cast<const void*>(&k_band_dft), smem);
   if (e != cudaSuccess) return e;
   k_band_dft<<<blocks, kDftThreads, smem, s>>>(b);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_band_dft_tma(const DftBatch& b, int blocks, cudaStream_t s) {
+  if (blocks <= 0) return cudaSuccess;
+  const size_t smem = (size_t)b.dft_smem;
+  cudaError_t e = ensure_smem(reinterpret_cast<const void*>(&k_band_dft_tma), smem);
+  if (e != cudaSuccess) return e;
+  k_band_dft_tma<<<blocks, kDftTmaThreads, smem, s>>>(b);
   return cudaGetLastError();
 }
 

@@ -5,8 +5,10 @@
 // be captured in a CUDA graph without any host->device copy.
 #pragma once
 
+#include <cuda.h>  // CUtensorMap (the type only; the encoder is looked up at run time)
 #include <cuda_runtime.h>
 #include <cuda_fp16.h>
+#include <stddef.h>
 #include <stdint.h>
 
 #include "../../include/rcfar.h"
@@ -39,9 +41,12 @@ constexpr int kDftBK = 32;
 constexpr int kDftMaxStages = 4;
 constexpr int kDftSmemCap = 220 * 1024;
 // K block: the tensor-memory accumulator is drained every kDftKB K steps
-// (128 samples) into a partial sum; partials are added with Kahan
-// compensation (the accumulator's own adds lose precision over long runs).
-constexpr int kDftKB = 4;
+// (256 samples) into a partial sum; partials are added with Kahan
+// compensation. The accumulator's own adds lose precision in proportion to
+// the run length (measured on 1024 x 4096 frames: worst map error 4e-5 of
+// the element, floored at 1e-2 of the row peak, at 128 samples; 6e-5 at
+// 256; 1.2e-4 without draining).
+constexpr int kDftKB = 8;
 constexpr int kDftThreads = 384;  // warp 0 MMA, warps 1-7 producers, warps 8-11 drain
 // y pass: 8 rows (one per warp) x 256 samples per CTA.
 constexpr int kYRows = 8;
@@ -87,6 +92,29 @@ struct PreBatch {
   int* status;   // device status word (bounded waits)
   PreFrameDev f[kMaxBatch];
 };
+
+// Band DFT fed by the tensor memory accelerator: per frame, the tensor maps
+// of the y head/tail planes [2][M][npad] (box 32 x 128 x 1) and of the
+// twiddle head/tail planes [2][ldw][npad] (box 32 x bn x 1), both with the
+// 128-byte swizzle the MMA descriptors read. The maps are kernel parameters
+// (param space), so a launch needs no copy and is graph-capturable.
+struct DftFrameDev {
+  float* kpart;       // K-block partials [nblocks][M][ldk]
+  long long ldk;
+  int M, bn, mtiles, ntiles, kper, npad, item_dft, pad;
+};
+struct DftBatch {
+  CUtensorMap ma[kMaxBatch];
+  CUtensorMap mb[kMaxBatch];
+  DftFrameDev f[kMaxBatch];
+  int n;
+  int dft_smem;
+  int* status;
+};
+constexpr int kDftTmaThreads = 192;  // warp 0 MMA, warp 1 TMA producer, warps 2-5 drain
+static_assert(alignof(CUtensorMap) >= 64 && offsetof(DftBatch, ma) == 0 && offsetof(DftBatch, mb) % 64 == 0,
+              "tensor maps must sit 64-byte aligned in the launch parameters");
+static_assert(sizeof(DftBatch) <= 32000, "launch parameters are limited to 32 KB");
 
 struct SatMapDev {
   const void* map;
@@ -199,6 +227,7 @@ cudaError_t ensure_smem(const void* fn, size_t bytes);
 cudaError_t launch_colstats(const PreBatch& b, int blocks, cudaStream_t s);
 cudaError_t launch_ysplit(const PreBatch& b, int blocks, cudaStream_t s);
 cudaError_t launch_band_dft(const PreBatch& b, int blocks, cudaStream_t s);
+cudaError_t launch_band_dft_tma(const DftBatch& b, int blocks, cudaStream_t s);
 cudaError_t launch_dft_reduce(const PreBatch& b, int blocks, cudaStream_t s);
 cudaError_t launch_twiddles(float* Wt, long long ldw, int npad, int N, int c0, int C, cudaStream_t s);
 // bytes of one K step of the band DFT ring: A head and tail (128 rows), B head and tail (bn rows)
