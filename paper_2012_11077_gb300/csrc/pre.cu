@@ -216,6 +216,9 @@ __device__ __forceinline__ float2 split_tf32_fast(float x) {
 // (a constant only reaches bin 0; removing it keeps the FP32 rounding of the
 // large per-range offsets out of the other bins), split into TF32 head and
 // tail for the tensor-core product. Samples N..npad-1 are written as 0.
+// H: the mean filter's half length when known at compile time (the window
+// sum is unrolled), or -1 for any h.
+template <int H>
 __global__ void __launch_bounds__(256) k_ysplit(const __grid_constant__ PreBatch b) {
   const int fi = find_item(b.f, b.n, (int)blockIdx.x, &PreFrameDev::item_y);
   const PreFrameDev& F = b.f[fi];
@@ -224,7 +227,7 @@ __global__ void __launch_bounds__(256) k_ysplit(const __grid_constant__ PreBatch
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int m = rb * kYRows + warp;
   const int n0 = cbk * kYCols;
-  const int h = F.h, N = F.N;
+  const int h = H >= 0 ? H : F.h, N = F.N;
   __shared__ float seg[kYRows][kYCols + 2 * kMaxMeanHalf];
   __shared__ float red[kYRows];
   float ymax = 0.f;
@@ -268,23 +271,45 @@ __global__ void __launch_bounds__(256) k_ysplit(const __grid_constant__ PreBatch
     float* yh = F.yhi + (long long)m * F.npad;
     float* yl = F.ylo + (long long)m * F.npad;
     const float inv_full = 1.0f / (float)(2 * h + 1);
+    const float* sg = &seg[warp][lane];
+    auto window = [&](int q) {
+      float acc = 0.f;
+      if constexpr (H >= 0) {
 #pragma unroll
-    for (int q = 0; q < kYCols / 32; ++q) {
-      const int i = lane + 32 * q;
-      const int n = n0 + i;
-      if (n >= F.npad) break;
-      float2 out = make_float2(0.f, 0.f);
-      if (n < N) {
-        float acc = 0.f;
-        for (int d = 0; d <= 2 * h; ++d) acc += seg[warp][i + d];
-        const int cnt = min(n + h, N - 1) - max(n - h, 0) + 1;
-        // a full window multiplies by 1 / (2h + 1); the truncated ones at the ends divide
-        const float y = cnt == 2 * h + 1 ? acc * inv_full : acc / (float)cnt;
-        ymax = fmaxf(ymax, fabsf(y));
-        out = split_tf32_fast(y - cmv);
+        for (int d = 0; d <= 2 * H; ++d) acc += sg[32 * q + d];
+      } else {
+        for (int d = 0; d <= 2 * h; ++d) acc += sg[32 * q + d];
       }
-      yh[n] = out.x;
-      yl[n] = out.y;
+      return acc;
+    };
+    if (n0 - h >= 0 && n0 + kYCols + h <= N) {
+      // every window of this block lies inside the frame (uniform fast path)
+#pragma unroll
+      for (int q = 0; q < kYCols / 32; ++q) {
+        const int n = n0 + lane + 32 * q;
+        const float y = window(q) * inv_full;
+        ymax = fmaxf(ymax, fabsf(y));
+        const float2 out = split_tf32_fast(y - cmv);
+        yh[n] = out.x;
+        yl[n] = out.y;
+      }
+    } else {
+#pragma unroll
+      for (int q = 0; q < kYCols / 32; ++q) {
+        const int n = n0 + lane + 32 * q;
+        if (n >= F.npad) break;
+        float2 out = make_float2(0.f, 0.f);
+        if (n < N) {
+          const float acc = window(q);
+          const int cnt = min(n + h, N - 1) - max(n - h, 0) + 1;
+          // a full window multiplies by 1 / (2h + 1); the truncated ones at the ends divide
+          const float y = cnt == 2 * h + 1 ? acc * inv_full : acc / (float)cnt;
+          ymax = fmaxf(ymax, fabsf(y));
+          out = split_tf32_fast(y - cmv);
+        }
+        yh[n] = out.x;
+        yl[n] = out.y;
+      }
     }
   }
 #pragma unroll
@@ -730,7 +755,14 @@ cudaError_t launch_colstats(const PreBatch& b, int blocks, cudaStream_t s) {
 
 cudaError_t launch_ysplit(const PreBatch& b, int blocks, cudaStream_t s) {
   if (blocks <= 0) return cudaSuccess;
-  k_ysplit<<<blocks, 256, 0, s>>>(b);
+  // one half length for the whole launch (a batch shares its mean filter)
+  switch (b.f[0].h) {
+    case 1: k_ysplit<1><<<blocks, 256, 0, s>>>(b); break;
+    case 2: k_ysplit<2><<<blocks, 256, 0, s>>>(b); break;
+    case 3: k_ysplit<3><<<blocks, 256, 0, s>>>(b); break;
+    case 4: k_ysplit<4><<<blocks, 256, 0, s>>>(b); break;
+    default: k_ysplit<-1><<<blocks, 256, 0, s>>>(b); break;
+  }
   return cudaGetLastError();
 }
 
