@@ -33,10 +33,10 @@ if ROOT not in sys.path:
 
 METRIC = "SAT+CA-CFAR Gcells/s and full-chain frames/s at 1 GB300; % HBM roofline; p99 latency"
 # DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) from one ncu --set full capture
-# of each kernel as it stands: k_band_dft on the 1024x4096 frame (bench.py --profile chain); the I64
+# of each kernel as it stands: k_band_dft_tma on the 1024x4096 frame (bench.py --profile chain); the I64
 # table kernels and k_cfar_ring on a 4096x4096 map (bench.py --profile map), times 4 for the
 # 8192x8192 map (their traffic grows with the cells).
-TRAFFIC = {"band_dft": 43.76e6, "sat_i64_8192": 4 * 222.6e6, "cfar_ring_8192": 4 * 220.5e6}
+TRAFFIC = {"band_dft": 43.06e6, "sat_i64_8192": 4 * 222.6e6, "cfar_ring_8192": 4 * 220.5e6}
 RING = 16
 
 

@@ -270,7 +270,7 @@ typedef struct rcfar_batch_tuning {
 } rcfar_batch_tuning;
 
 /* Autotuner: times rcfar_run_batch on these frames (outputs are written)
- * under candidate tunings -- band-DFT K split {auto, 1, 2, 4, 8}, then the
+ * under candidate tunings -- band-DFT K split {auto, 1, 2, 4, 8, 16}, then the
  * table mode and CFAR strip shapes with the best split -- with CUDA events
  * on the stream, `reps` batches each after one untimed batch, and keeps the
  * fastest in the handle for later rcfar_run_batch calls (out may be NULL).

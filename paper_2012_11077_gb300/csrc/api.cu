@@ -1258,7 +1258,7 @@ rcfar_status rcfar_tune_batch(rcfar_handle h, const rcfar_frame_desc* frames, in
     }
   };
   // stage 1: the band-DFT K split, with the default table and CFAR
-  const int splits[] = {0, 1, 2, 4, 8};
+  const int splits[] = {0, 1, 2, 4, 8, 16};
   for (int kb : splits) consider(rcfar_batch_tuning{kb, RCFAR_SAT_TILE_I64, 0, 0, 0.0, 0, 0});
   // stage 2: table mode and CFAR strips with the best split
   const int kb = best.dft_kblocks_per_cta;
