@@ -28,6 +28,7 @@ from .preprocess import (  # noqa: F401
     detrend_fast_time,
     mean_filter_slow_time,
     normalise,
+    normalise_row_zscore,
     band_dft_magnitude,
     preprocess_frame,
 )

@@ -105,6 +105,18 @@ def normalise(Y: np.ndarray) -> np.ndarray:
     return Y / mx if mx > 0 else Y.copy()
 
 
+def normalise_row_zscore(Y: np.ndarray) -> np.ndarray:
+    """Alternative reading of "then normalized" (Sec. II.A): each range bin's
+    slow-time series scaled to zero mean and unit (population) standard
+    deviation, z[m, n] = (y[m, n] - mean_n y[m, .]) / std_n y[m, .]; a
+    constant row (std 0) becomes 0."""
+    Y = np.asarray(Y, dtype=np.float64)
+    mu = Y.mean(axis=1, keepdims=True)
+    d = Y - mu
+    sd = np.sqrt((d * d).mean(axis=1, keepdims=True))
+    return np.where(sd > 0, d / np.where(sd > 0, sd, 1.0), 0.0)
+
+
 def band_dft_magnitude(Y: np.ndarray, c0: int, c1: int) -> np.ndarray:
     """|DFT| of every slow-time signal at bins c0..c1 (Sec. II.A "FFT").
 
@@ -122,15 +134,24 @@ def band_dft_magnitude(Y: np.ndarray, c0: int, c1: int) -> np.ndarray:
 
 
 def preprocess_frame(X: np.ndarray, fs_hz: float, mean_len: int = 5, halo: int = 0,
-               f_lo_hz: float = 0.3, f_hi_hz: float = 0.8):
-    """Whole Sec. II.A chain: raw X -> band-limited magnitude map P (FP64).
+                     f_lo_hz: float = 0.3, f_hi_hz: float = 0.8, detector: str = "magnitude",
+                     normalisation: str = "global_max"):
+    """Whole Sec. II.A chain: raw X -> band-limited spectrum map P (FP64).
 
+    detector: "magnitude" (|DFT|, the paper's "FFT" map) or "square" (|DFT|^2,
+    the square-law map for which eq. 2's alpha is exact).
+    normalisation: "global_max" (divide by the frame's max |y|) or
+    "row_zscore" (normalise_row_zscore).
     Returns (P, band) with P of shape (M, band.cols).
     """
+    if detector not in ("magnitude", "square") or normalisation not in ("global_max", "row_zscore"):
+        raise ValueError("unknown detector or normalisation")
     X = np.asarray(X, dtype=np.float64)
     band = band_plan(X.shape[1], fs_hz, f_lo_hz, f_hi_hz, halo)
     Xp = detrend_fast_time(X)
     Y = mean_filter_slow_time(Xp, mean_len)
-    Y = normalise(Y)
+    Y = normalise(Y) if normalisation == "global_max" else normalise_row_zscore(Y)
     P = band_dft_magnitude(Y, band.c0, band.c1)
+    if detector == "square":
+        P = P * P
     return P, band

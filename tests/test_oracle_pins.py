@@ -273,3 +273,50 @@ def test_chain_detects_planted_respiration_targets():
         assert band.k_lo <= k <= band.k_hi
         near = np.min(np.abs(truth.target_bins - r))
         assert near <= 12, (r, truth.target_bins)
+
+
+# ---- square-law detector and per-range-bin z-score (next-step variants) ----
+
+def test_square_law_pure_tone_closed_form():
+    # a real tone a cos(2 pi k0 n / N) has |DFT| = a N / 2 at bin k0: square law (a N / 2)^2
+    N, k0, a = 256, 9, 0.75
+    n = np.arange(N)
+    Y = (a * np.cos(2 * np.pi * k0 * n / N))[None, :]
+    P = oracle.preprocess.band_dft_magnitude(Y, 0, 20)
+    assert abs(P[0, k0] - a * N / 2) < 1e-9 * N
+    spec = synth.FrameSpec(M=32, N=N, n_targets=1, seed=4)
+    X = synth.radar_frame(spec)
+    Pm, _ = oracle.preprocess_frame(X, synth.FS_HZ, 5, halo=4)
+    Ps, _ = oracle.preprocess_frame(X, synth.FS_HZ, 5, halo=4, detector="square")
+    np.testing.assert_allclose(Ps, Pm * Pm, rtol=1e-13, atol=0)
+
+
+def test_row_zscore_invariants():
+    rng = np.random.default_rng(8)
+    Y = rng.standard_normal((6, 200)) * 3.0 + 2.0
+    Y[3] = 5.0  # a constant row stays zero
+    Z = oracle.normalise_row_zscore(Y)
+    ok = np.arange(6) != 3
+    np.testing.assert_allclose(Z[ok].mean(axis=1), 0.0, atol=1e-12)
+    np.testing.assert_allclose(Z[ok].std(axis=1), 1.0, rtol=1e-12)
+    assert np.all(Z[3] == 0)
+    # invariant to a positive scale and an offset per row
+    s = rng.uniform(0.5, 4.0, size=(6, 1))
+    o = rng.uniform(-3, 3, size=(6, 1))
+    np.testing.assert_allclose(oracle.normalise_row_zscore(Y * s + o)[ok], Z[ok], atol=1e-12)
+    # Parseval on the full spectrum of a z-scored row: sum_k |Z_k|^2 = N sum_n z^2 = N^2
+    N = Y.shape[1]
+    F = np.fft.fft(Z[0])
+    assert abs(np.sum(np.abs(F) ** 2) - N * N) < 1e-8 * N * N
+
+
+def test_row_zscore_chain_is_scale_invariant():
+    # the chain is linear up to the normalisation: scaling the raw frame by a
+    # positive factor leaves every z-scored row, hence P, unchanged
+    spec = synth.FrameSpec(M=24, N=300, n_targets=2, seed=6)
+    X = synth.radar_frame(spec)
+    P1, _ = oracle.preprocess_frame(X, synth.FS_HZ, 5, halo=6, normalisation="row_zscore")
+    P2, _ = oracle.preprocess_frame(X.astype(np.float64) * 3.5, synth.FS_HZ, 5, halo=6, normalisation="row_zscore")
+    np.testing.assert_allclose(P2, P1, rtol=1e-10, atol=1e-12)
+    with pytest.raises(ValueError):
+        oracle.preprocess_frame(X, synth.FS_HZ, 5, detector="log")
