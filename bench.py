@@ -470,6 +470,44 @@ def ours(args, rank, world, local, dist):
     value = world * args.steps / (ms_max / 1e3)
     assert rc.rcfar_get_error(h) == rc.RCFAR_OK
 
+    # the chain with the square-law detector and with per-range-bin z-score
+    # normalisation (the next-step variants), captured and timed the same way
+    variants = {}
+    for vname, det_mode, norm_mode in (("square_law", 1, 0), ("row_zscore", 0, 1)):
+        pv = rc.make_pre_params(synth.FS_HZ, mean_len=case.mean_len, halo_c=case.halo_c, detector=det_mode,
+                                normalise=norm_mode)
+        bv = rc.rcfar_band_plan(N, pv)
+
+        def chain_v(i, pv=pv, bv=bv):
+            x, P, det = frames[i % RING], maps[i % RING], dets[i % RING]
+            rc.rcfar_preprocess(h, x, pv, P)
+            v = rc.rcfar_sat(h, P, value_bound=bv.value_bound, mode=rc.RCFAR_SAT_TILE_I64)
+            rc.rcfar_cfar(h, v, None, win, cut_lo, cut_hi, det)
+
+        for i in range(3):
+            chain_v(i)
+        torch.cuda.synchronize()
+        gv = []
+        with torch.cuda.stream(stream):
+            for i in range(RING):
+                g = torch.cuda.CUDAGraph()
+                with torch.cuda.graph(g, stream=stream):
+                    chain_v(i)
+                gv.append(g)
+        torch.cuda.synchronize()
+        for i in range(3):
+            gv[i % RING].replay()
+        torch.cuda.synchronize()
+        nv = max(10, args.steps // 2)
+        e0.record()
+        for i in range(nv):
+            gv[i % RING].replay()
+        e1.record()
+        torch.cuda.synchronize()
+        variants[vname] = {"frames_per_s": nv / (e0.elapsed_time(e1) / 1e3)}
+        assert rc.rcfar_get_error(h) == rc.RCFAR_OK
+        del gv
+
     # per-kernel device times (eager launches bracketed by CUDA events)
     rc.rcfar_trace_enable(h, True)
     for i in range(args.steps):
@@ -588,7 +626,7 @@ def ours(args, rank, world, local, dist):
                        "l2": "inputs larger than L2: ring of 16 distinct frames (268 MB)",
                        "parallelism": f"replicas x{world}"},
             "roofline": roofline, "kernels": step_kernels, "sat_cfar": sat_cfar, "batch": batch,
-            "serving": serving, "e2e": e2e,
+            "serving": serving, "variants": variants, "e2e": e2e,
             "cpu_baseline": cpu, "clocks": clk, "gpu_launches": launches_per_step * args.steps,
             "peaks": peaks["source"]}
     print(json.dumps(line), flush=True)

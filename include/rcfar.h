@@ -95,13 +95,24 @@ typedef struct rcfar_config {
 } rcfar_config;
 
 /* Preprocessing parameters (Sec. II.A). */
+/* Detector of the band map: the magnitude |DFT| (the paper's "FFT" map) or
+ * the square law |DFT|^2, for which eq. 2's alpha is exact on noise. */
+typedef enum rcfar_detector { RCFAR_DETECT_MAGNITUDE = 0, RCFAR_DETECT_SQUARE_LAW = 1 } rcfar_detector;
+/* "then normalized" (Sec. II.A): divide the frame by its max |y|, or scale
+ * each range bin's slow-time series to zero mean and unit standard deviation
+ * (z-score; a constant row gives a zero map row). Decisions are invariant to
+ * the global scale, not to the per-row one. */
+typedef enum rcfar_normalise { RCFAR_NORM_GLOBAL_MAX = 0, RCFAR_NORM_ROW_ZSCORE = 1 } rcfar_normalise;
+
 typedef struct rcfar_pre_params {
-  double fs_hz;     /* slow-time sampling rate (traces per second) */
-  double f_lo_hz;   /* respiration band, inclusive: 0.3 in the paper */
-  double f_hi_hz;   /* 0.8 in the paper */
-  int32_t mean_len; /* odd mean-filter length along slow time (e.g. 5) */
-  int32_t halo_c;   /* extra bins stored each side of the band (use the CFAR's guard_c + train_c);
-                       rcfar_run_batch: -1 = each frame uses its own window's guard_c + train_c */
+  double fs_hz;      /* slow-time sampling rate (traces per second) */
+  double f_lo_hz;    /* respiration band, inclusive: 0.3 in the paper */
+  double f_hi_hz;    /* 0.8 in the paper */
+  int32_t mean_len;  /* odd mean-filter length along slow time (e.g. 5) */
+  int32_t halo_c;    /* extra bins stored each side of the band (use the CFAR's guard_c + train_c);
+                        rcfar_run_batch: -1 = each frame uses its own window's guard_c + train_c */
+  int32_t detector;  /* rcfar_detector (0: magnitude) */
+  int32_t normalise; /* rcfar_normalise (0: global max) */
 } rcfar_pre_params;
 
 /* Spectral bins of a band map: map column j holds bin k = c0 + j. */
@@ -109,7 +120,7 @@ typedef struct rcfar_band {
   int32_t k_lo, k_hi; /* respiration band bins (CUT columns are k_lo-c0 .. k_hi-c0) */
   int32_t c0, c1;     /* first and last stored bin, clipped to [0, N/2] */
   int32_t cols;       /* c1 - c0 + 1 */
-  float value_bound;  /* every normalised map value is <= this (= N) */
+  float value_bound;  /* every map value is <= this: N, or N^2 for the square law (for rcfar_sat) */
 } rcfar_band;
 
 /* CFAR window (Sec. II.B): per-side counts in each dimension. The guard

@@ -30,6 +30,11 @@ RCFAR_SAT_I64 = 1
 RCFAR_SAT_NAIVE_F32 = 2
 RCFAR_SAT_TILE_I64 = 3
 
+RCFAR_DETECT_MAGNITUDE = 0
+RCFAR_DETECT_SQUARE_LAW = 1
+RCFAR_NORM_GLOBAL_MAX = 0
+RCFAR_NORM_ROW_ZSCORE = 1
+
 SAT_TILE_H = 32
 SAT_TILE_W = 128
 
@@ -60,7 +65,8 @@ class rcfar_config(ctypes.Structure):
 
 class rcfar_pre_params(ctypes.Structure):
     _fields_ = [("fs_hz", ctypes.c_double), ("f_lo_hz", ctypes.c_double), ("f_hi_hz", ctypes.c_double),
-                ("mean_len", ctypes.c_int32), ("halo_c", ctypes.c_int32)]
+                ("mean_len", ctypes.c_int32), ("halo_c", ctypes.c_int32), ("detector", ctypes.c_int32),
+                ("normalise", ctypes.c_int32)]
 
 
 class rcfar_band(ctypes.Structure):
@@ -213,11 +219,14 @@ def make_window(train_r, train_c, guard_r, guard_c, pfa) -> rcfar_window:
     return rcfar_window(int(train_r), int(train_c), int(guard_r), int(guard_c), float(pfa))
 
 
-def make_pre_params(fs_hz=20.0, f_lo_hz=0.3, f_hi_hz=0.8, mean_len=5, halo_c=0) -> rcfar_pre_params:
-    return rcfar_pre_params(float(fs_hz), float(f_lo_hz), float(f_hi_hz), int(mean_len), int(halo_c))
+def make_pre_params(fs_hz=20.0, f_lo_hz=0.3, f_hi_hz=0.8, mean_len=5, halo_c=0, detector=0,
+                    normalise=0) -> rcfar_pre_params:
+    """detector: RCFAR_DETECT_MAGNITUDE (0) or RCFAR_DETECT_SQUARE_LAW (1);
+    normalise: RCFAR_NORM_GLOBAL_MAX (0) or RCFAR_NORM_ROW_ZSCORE (1)."""
+    return rcfar_pre_params(float(fs_hz), float(f_lo_hz), float(f_hi_hz), int(mean_len), int(halo_c),
+                            int(detector), int(normalise))
 
 
-# ---------------------------------------------------------------- host-only
 def rcfar_alpha(n_ref: int, pfa: float) -> float:
     out = ctypes.c_double()
     _check(lib().rcfar_alpha(int(n_ref), float(pfa), ctypes.byref(out)), "rcfar_alpha")

@@ -247,6 +247,7 @@ struct rcfar_ctx {
   float* yhi = nullptr;
   float* ylo = nullptr;
   float* rowmean = nullptr;
+  float* rowsq = nullptr;
   // per-step SAT
   void* sat_table = nullptr;
   SatArrays sat{};
@@ -338,12 +339,16 @@ static bool band_of(int N, const rcfar_pre_params* p, rcfar_band* b) {
   b->c0 = (int)c0;
   b->c1 = (int)c1;
   b->cols = (int)(c1 - c0 + 1);
-  b->value_bound = (float)N;
+  // |sum_n y e^{-i..}| <= sum_n |y| <= N after either normalisation (global
+  // max: |y| <= 1; z-score: Cauchy-Schwarz with sum z^2 = N)
+  b->value_bound = p->detector == RCFAR_DETECT_SQUARE_LAW ? (float)N * (float)N : (float)N;
   return true;
 }
 
 static bool valid_pre(const rcfar_pre_params* p) {
-  return p && p->mean_len >= 1 && (p->mean_len & 1) && (p->mean_len - 1) / 2 <= kMaxMeanHalf;
+  return p && p->mean_len >= 1 && (p->mean_len & 1) && (p->mean_len - 1) / 2 <= kMaxMeanHalf &&
+         (p->detector == RCFAR_DETECT_MAGNITUDE || p->detector == RCFAR_DETECT_SQUARE_LAW) &&
+         (p->normalise == RCFAR_NORM_GLOBAL_MAX || p->normalise == RCFAR_NORM_ROW_ZSCORE);
 }
 
 // twiddle plan for (N, c0, C); builds it on first use
@@ -400,10 +405,13 @@ static bool make_dft_frame(DftBatch& db, int k, const PreFrameDev& F, const Twid
   return true;
 }
 
-static PreFrameDev make_pre_frame(const float* x, int M, int N, long long ldx, const rcfar_band& b, int h,
-                                  const Twiddle& tw, const PreGeom& g) {
+static PreFrameDev make_pre_frame(const float* x, int M, int N, long long ldx, const rcfar_band& b,
+                                  const rcfar_pre_params* p, const Twiddle& tw, const PreGeom& g) {
+  const int h = (p->mean_len - 1) / 2;
   PreFrameDev F;
   std::memset(&F, 0, sizeof(F));
+  F.detector = p->detector;
+  F.normalise = p->normalise;
   F.x = x;
   F.ldx = ldx;
   F.M = M;
@@ -444,6 +452,7 @@ static size_t frame_data_bytes(int M, int N, int C) {
   t += align256((size_t)g.nblocks * M * g.ldk * 4);              // K-block partials
   t += 2 * align256((size_t)M * g.npad * sizeof(float));           // yhi, ylo
   t += align256((size_t)M * sizeof(float));                        // rowmean
+  t += align256((size_t)g.ycols * M * sizeof(float));              // rowsq
   t += align256((size_t)M * round_up(C, 4) * 4);                   // map
   t += sat_bytes(M, C, kBatchSatMode);
   return t;
@@ -530,6 +539,8 @@ rcfar_status rcfar_create(const rcfar_config* cfg, rcfar_handle* out) {
   total += align256(kpart * 4);
   total += 2 * align256((size_t)R * round_up(Nm, kDftBK) * sizeof(float));  // yhi, ylo
   total += align256((size_t)R * sizeof(float));                          // rowmean
+  const size_t ycols_max = (size_t)ceil_div(round_up(Nm, kDftBK), kYCols);
+  total += align256(ycols_max * R * sizeof(float));                      // rowsq
   total += sat_bytes(R, Cm, RCFAR_SAT_I64);
   if (cudaMalloc(&h->ws, total) != cudaSuccess) {
     delete h;
@@ -554,6 +565,7 @@ rcfar_status rcfar_create(const rcfar_config* cfg, rcfar_handle* out) {
   h->yhi = cv.take<float>((size_t)R * round_up(Nm, kDftBK));
   h->ylo = cv.take<float>((size_t)R * round_up(Nm, kDftBK));
   h->rowmean = cv.take<float>(R);
+  h->rowsq = cv.take<float>(ycols_max * R);
   {
     SatGeom g = sat_geom(R, Cm);
     h->sat_table = cv.take<char>((size_t)R * g.ld_table * 8);
@@ -682,7 +694,7 @@ rcfar_status rcfar_preprocess(rcfar_handle h, const float* x, int32_t M, int32_t
   pb.status = h->status;
   pb.dft_smem = dft_smem_for(g.bn);
   PreFrameDev& F = pb.f[0];
-  F = make_pre_frame(x, M, N, ldx, b, (p->mean_len - 1) / 2, tw, g);
+  F = make_pre_frame(x, M, N, ldx, b, p, tw, g);
   F.stats = h->stats;
   F.partial = h->partial;
   F.rowpart = h->rowpart;
@@ -696,6 +708,7 @@ rcfar_status rcfar_preprocess(rcfar_handle h, const float* x, int32_t M, int32_t
   F.yhi = h->yhi;
   F.ylo = h->yhi + (long long)M * g.npad;  // the two planes back to back (the tail runs into h->ylo's room)
   F.rowmean = h->rowmean;
+  F.rowsq = h->rowsq;
   F.item_stats = 0;
   F.item_dft = 0;
   F.item_norm = 0;
@@ -1053,7 +1066,7 @@ rcfar_status rcfar_run_batch(rcfar_handle h, const rcfar_frame_desc* frames, int
       const int C = b.cols;
       const PreGeom g = pre_geom(f.M, f.N, C, kb_per_cta);
       PreFrameDev& F = pb.f[k];
-      F = make_pre_frame(f.x, f.M, f.N, f.ldx, b, (p->mean_len - 1) / 2, tws[i], g);
+      F = make_pre_frame(f.x, f.M, f.N, f.ldx, b, p, tws[i], g);
       F.stats = data.take<float2>(f.N);
       F.partial = data.take<float2>((size_t)g.n_chunks * f.N);
       F.rowpart = data.take<float>((size_t)g.n_strips * f.M);
@@ -1062,6 +1075,7 @@ rcfar_status rcfar_run_batch(rcfar_handle h, const rcfar_frame_desc* frames, int
       F.yhi = data.take<float>(2 * (size_t)f.M * g.npad);  // head and tail planes back to back
       F.ylo = F.yhi ? F.yhi + (long long)f.M * g.npad : nullptr;
       F.rowmean = data.take<float>(f.M);
+      F.rowsq = data.take<float>((size_t)g.ycols * f.M);
       float* map = f.map;
       long long ld_map = f.ld_map;
       if (!map) {
@@ -1111,7 +1125,7 @@ rcfar_status rcfar_run_batch(rcfar_handle h, const rcfar_frame_desc* frames, int
       it_tile += sg.n_bands * sg.n_chunks;
       it_band += sg.n_bands;
       it_vscan += (int)ceil_div(C, 32);
-      if (!F.stats || !F.partial || !F.rowpart || !F.strip_ab || !F.yhi || !F.ylo || !F.rowmean || !F.kpart || !map || !m.table ||
+      if (!F.stats || !F.partial || !F.rowpart || !F.strip_ab || !F.yhi || !F.ylo || !F.rowmean || !F.rowsq || !F.kpart || !map || !m.table ||
           !sat_ok || !F.strip_cnt || !F.tile_cnt || !words)
         return RCFAR_ERR_OUT_OF_WORKSPACE;
 

@@ -282,6 +282,7 @@ __global__ void __launch_bounds__(256) k_ysplit(const __grid_constant__ PreBatch
       }
       return acc;
     };
+    float sq = 0.f;  // sum of (y - c_m)^2 over this lane's samples (z-score normalisation)
     if (n0 - h >= 0 && n0 + kYCols + h <= N) {
       // every window of this block lies inside the frame (uniform fast path)
 #pragma unroll
@@ -289,7 +290,9 @@ __global__ void __launch_bounds__(256) k_ysplit(const __grid_constant__ PreBatch
         const int n = n0 + lane + 32 * q;
         const float y = window(q) * inv_full;
         ymax = fmaxf(ymax, fabsf(y));
-        const float2 out = split_tf32_fast(y - cmv);
+        const float d = y - cmv;
+        sq = fmaf(d, d, sq);
+        const float2 out = split_tf32_fast(d);
         yh[n] = out.x;
         yl[n] = out.y;
       }
@@ -305,11 +308,18 @@ __global__ void __launch_bounds__(256) k_ysplit(const __grid_constant__ PreBatch
           // a full window multiplies by 1 / (2h + 1); the truncated ones at the ends divide
           const float y = cnt == 2 * h + 1 ? acc * inv_full : acc / (float)cnt;
           ymax = fmaxf(ymax, fabsf(y));
-          out = split_tf32_fast(y - cmv);
+          const float d = y - cmv;
+          sq = fmaf(d, d, sq);
+          out = split_tf32_fast(d);
         }
         yh[n] = out.x;
         yl[n] = out.y;
       }
+    }
+    if (F.normalise == RCFAR_NORM_ROW_ZSCORE) {
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) sq += __shfl_xor_sync(0xffffffffu, sq, o);
+      if (lane == 0) F.rowsq[(long long)cbk * F.M + m] = sq;  // one slot per (block, row): fixed-order sum later
     }
   }
 #pragma unroll
@@ -703,8 +713,17 @@ __global__ void __launch_bounds__(256) k_dft_reduce(const __grid_constant__ PreB
   const int m = local / cblocks;
   const int j = (local - m * cblocks) * 256 + (int)threadIdx.x;
   if (m >= F.M || j >= F.C) return;
-  const float mx = __uint_as_float(__ldcg(F.ymax));
-  const float inv = mx > 0.f ? 1.f / mx : 1.f;
+  float inv;
+  if (F.normalise == RCFAR_NORM_ROW_ZSCORE) {
+    // z-score: 1 / std of the row's y (population std; 0 for a constant row)
+    float ss = 0.f;
+    for (int cb = 0; cb < F.ycols; ++cb) ss += __ldg(&F.rowsq[(long long)cb * F.M + m]);
+    const float sd = sqrtf(ss / (float)F.N);
+    inv = sd > 0.f ? 1.f / sd : 0.f;
+  } else {
+    const float mx = __uint_as_float(__ldcg(F.ymax));
+    inv = mx > 0.f ? 1.f / mx : 1.f;
+  }
   const long long plane = (long long)F.M * F.ldk;
   const float* src = F.kpart + (long long)m * F.ldk + 2 * j;
   float re = 0.f, im = 0.f, cr = 0.f, ci = 0.f;
@@ -724,8 +743,11 @@ __global__ void __launch_bounds__(256) k_dft_reduce(const __grid_constant__ PreB
       im = ti;
     }
   }
-  if (j == 0 && F.c0 == 0) re = fmaf((float)F.N, __ldg(&F.rowmean[m]), re);  // bin 0 gets the mean back
-  F.map[(long long)m * F.ld_map + j] = sqrtf(fmaf(re, re, im * im)) * inv;
+  // bin 0 gets the mean back (the z-scored series has none)
+  if (j == 0 && F.c0 == 0 && F.normalise != RCFAR_NORM_ROW_ZSCORE) re = fmaf((float)F.N, __ldg(&F.rowmean[m]), re);
+  // a z-scored series has zero mean: its bin 0 is exactly 0 (only rounding remains in re, im)
+  const float p2 = (F.normalise == RCFAR_NORM_ROW_ZSCORE && F.c0 + j == 0) ? 0.f : fmaf(re, re, im * im);
+  F.map[(long long)m * F.ld_map + j] = F.detector == RCFAR_DETECT_SQUARE_LAW ? p2 * (inv * inv) : sqrtf(p2) * inv;
 }
 
 __global__ void k_twiddles(float* Wt, long long ldw, int npad, int N, int c0, int C) {

@@ -65,6 +65,9 @@ struct PreFrameDev {
   float* yhi;        // [M][npad] y minus its row mean: TF32 head; zero for n >= N
   float* ylo;        // [M][npad] the TF32 tail
   float* rowmean;    // [M] the row means c_m removed from y
+  float* rowsq;      // z-score normalisation: [ycols][M] per-block sums of (y - c_m)^2
+  int detector;      // rcfar_detector
+  int normalise;     // rcfar_normalise
   int npad;          // N rounded up to kDftBK
   int bn;            // real output columns per CTA (multiple of 16, <= kDftMaxBN)
   float2* stats;        // [N] (a_n, b_n) of the fast-time line fit

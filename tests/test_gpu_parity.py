@@ -357,6 +357,46 @@ def test_preprocess_and_chain_parity(rc, h, name, case):
         assert rel_err(thr.cpu().numpy()[res_o.cut], res_o.thr[res_o.cut]).max() <= REL
 
 
+VARIANTS = [(1, 0), (0, 1), (1, 1)]  # (detector, normalise): square law, z-score, both
+
+
+@pytest.mark.parametrize("det_mode,norm_mode", VARIANTS)
+@pytest.mark.parametrize("name,case", [PRE_CASES[0], PRE_CASES[1]])
+def test_preprocess_variants_parity(rc, h, name, case, det_mode, norm_mode):
+    # square-law detector and per-range-bin z-score normalisation against the oracle
+    X = synth.radar_frame(case.spec)
+    w = case.window
+    P_o, band_o = oracle.preprocess_frame(X, synth.FS_HZ, case.mean_len, halo=case.halo_c,
+                                          detector="square" if det_mode else "magnitude",
+                                          normalisation="row_zscore" if norm_mode else "global_max")
+    res_o = ocfar.cfar_chain(P_o, band_o, w.train_r, w.train_c, w.guard_r, w.guard_c, w.pfa)
+    params = rc.make_pre_params(synth.FS_HZ, mean_len=case.mean_len, halo_c=case.halo_c, detector=det_mode,
+                                normalise=norm_mode)
+    band = rc.rcfar_band_plan(case.spec.N, params)
+    assert band.value_bound == (float(case.spec.N) ** 2 if det_mode else float(case.spec.N))
+    P = torch.empty((case.spec.M, band.cols), dtype=torch.float32, device="cuda")
+    rc.rcfar_preprocess(h, dev_t(X), params, P)
+    Pg = P.cpu().numpy()
+    e = map_err(Pg, P_o)
+    # the square law doubles the magnitude's relative error: compare its square root
+    e_mag = map_err(np.sqrt(np.maximum(Pg, 0)), np.sqrt(P_o)) if det_mode else e
+    assert e_mag.max() <= REL, (e.max(), e_mag.max())
+    view = rc.rcfar_sat(h, P, value_bound=band.value_bound)
+    det = torch.empty((case.spec.M, band.cols), dtype=torch.uint8, device="cuda")
+    rc.rcfar_cfar(h, view, P, rc.make_window(w.train_r, w.train_c, w.guard_r, w.guard_c, w.pfa),
+                  band.k_lo - band.c0, band.k_hi - band.c0, det)
+    assert rc.rcfar_get_error(h) == rc.RCFAR_OK
+    cmp = ocfar.compare_decisions(det.cpu().numpy(), res_o.det, P_o, res_o.thr, res_o.cut, margin=MARGIN)
+    assert cmp.mismatches == 0, cmp
+    # the batch path with the same parameters gives the same map and decisions
+    det_b = torch.empty_like(det)
+    map_b = torch.empty_like(P)
+    rc.rcfar_run_batch(h, [rc.frame_desc(dev_t(X), rc.make_window(w.train_r, w.train_c, w.guard_r, w.guard_c, w.pfa),
+                                         det_b, None, map_b)], params)
+    assert rc.rcfar_get_error(h) == rc.RCFAR_OK
+    assert torch.equal(map_b, P) and torch.equal(det_b, det)
+
+
 def test_preprocess_strided_input(rc, h):
     case = synth.ChainCase(synth.FrameSpec(M=200, N=300, n_targets=2, seed=9), synth.Window(4, 4, 1, 1, 1e-3))
     X = synth.radar_frame(case.spec)
