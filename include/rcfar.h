@@ -104,6 +104,13 @@ typedef enum rcfar_detector { RCFAR_DETECT_MAGNITUDE = 0, RCFAR_DETECT_SQUARE_LA
  * the global scale, not to the per-row one. */
 typedef enum rcfar_normalise { RCFAR_NORM_GLOBAL_MAX = 0, RCFAR_NORM_ROW_ZSCORE = 1 } rcfar_normalise;
 
+/* Memory order of a raw frame X (M range bins x N traces). Range-major:
+ * X[m][n] at x[m * ldx + n], ldx >= N. Trace-major, the order a radar
+ * acquires it in (one trace of M range samples after another, Sec. III):
+ * X[m][n] at x[n * ldx + m], ldx >= M; such frames are transposed once into
+ * the workspace and then take the range-major path (identical results). */
+typedef enum rcfar_x_layout { RCFAR_X_RANGE_MAJOR = 0, RCFAR_X_TRACE_MAJOR = 1 } rcfar_x_layout;
+
 typedef struct rcfar_pre_params {
   double fs_hz;      /* slow-time sampling rate (traces per second) */
   double f_lo_hz;    /* respiration band, inclusive: 0.3 in the paper */
@@ -113,6 +120,8 @@ typedef struct rcfar_pre_params {
                         rcfar_run_batch: -1 = each frame uses its own window's guard_c + train_c */
   int32_t detector;  /* rcfar_detector (0: magnitude) */
   int32_t normalise; /* rcfar_normalise (0: global max) */
+  int32_t x_layout;  /* rcfar_x_layout of the raw frames (0: range-major) */
+  int32_t pad;
 } rcfar_pre_params;
 
 /* Spectral bins of a band map: map column j holds bin k = c0 + j. */
@@ -192,12 +201,14 @@ const char* rcfar_status_string(rcfar_status s);
 
 /* ---- the per-step path ------------------------------------------------- */
 
-/* Sec. II.A: raw frame x [M][ldx] -> normalised band map [M][ld_map] with
- * band_out->cols columns. Steps, all on the GPU:
+/* Sec. II.A: raw frame x (M x N, layout p->x_layout, leading dimension ldx)
+ * -> normalised band map [M][ld_map] with band_out->cols columns. Steps, all
+ * on the GPU:
  *   x'[m,n] = x[m,n] - a_n - b_n (m - (M-1)/2)      (per-trace LS line over m)
  *   y[m,n]  = mean of x'[m, n-h..n+h] inside [0,N)   (h = (mean_len-1)/2)
- *   y      /= max |y| over the frame                  (unchanged if 0)
- *   P[m,j]  = | sum_n y[m,n] exp(-2 pi i (c0+j) n / N) |
+ *   y      /= max |y| over the frame                  (unchanged if 0; or a
+ *                                                      per-row z-score)
+ *   P[m,j]  = | sum_n y[m,n] exp(-2 pi i (c0+j) n / N) |   (or its square)
  * band_out (host pointer, may be NULL) receives the bins used. The first call
  * for a new (N, band) builds its twiddle table (one allocation). */
 rcfar_status rcfar_preprocess(rcfar_handle h, const float* x, int32_t M, int32_t N, int64_t ldx,

@@ -34,6 +34,8 @@ RCFAR_DETECT_MAGNITUDE = 0
 RCFAR_DETECT_SQUARE_LAW = 1
 RCFAR_NORM_GLOBAL_MAX = 0
 RCFAR_NORM_ROW_ZSCORE = 1
+RCFAR_X_RANGE_MAJOR = 0
+RCFAR_X_TRACE_MAJOR = 1
 
 SAT_TILE_H = 32
 SAT_TILE_W = 128
@@ -66,7 +68,7 @@ class rcfar_config(ctypes.Structure):
 class rcfar_pre_params(ctypes.Structure):
     _fields_ = [("fs_hz", ctypes.c_double), ("f_lo_hz", ctypes.c_double), ("f_hi_hz", ctypes.c_double),
                 ("mean_len", ctypes.c_int32), ("halo_c", ctypes.c_int32), ("detector", ctypes.c_int32),
-                ("normalise", ctypes.c_int32)]
+                ("normalise", ctypes.c_int32), ("x_layout", ctypes.c_int32), ("pad", ctypes.c_int32)]
 
 
 class rcfar_band(ctypes.Structure):
@@ -220,11 +222,12 @@ def make_window(train_r, train_c, guard_r, guard_c, pfa) -> rcfar_window:
 
 
 def make_pre_params(fs_hz=20.0, f_lo_hz=0.3, f_hi_hz=0.8, mean_len=5, halo_c=0, detector=0,
-                    normalise=0) -> rcfar_pre_params:
+                    normalise=0, x_layout=0) -> rcfar_pre_params:
     """detector: RCFAR_DETECT_MAGNITUDE (0) or RCFAR_DETECT_SQUARE_LAW (1);
-    normalise: RCFAR_NORM_GLOBAL_MAX (0) or RCFAR_NORM_ROW_ZSCORE (1)."""
+    normalise: RCFAR_NORM_GLOBAL_MAX (0) or RCFAR_NORM_ROW_ZSCORE (1);
+    x_layout: RCFAR_X_RANGE_MAJOR (0, frames [M][N]) or RCFAR_X_TRACE_MAJOR (1, frames [N][M])."""
     return rcfar_pre_params(float(fs_hz), float(f_lo_hz), float(f_hi_hz), int(mean_len), int(halo_c),
-                            int(detector), int(normalise))
+                            int(detector), int(normalise), int(x_layout), 0)
 
 
 def rcfar_alpha(n_ref: int, pfa: float) -> float:
@@ -279,8 +282,9 @@ def rcfar_get_error(h: int, stream=None) -> int:
 
 
 def rcfar_preprocess(h: int, x, params: rcfar_pre_params, map_out, stream=None) -> rcfar_band:
-    """x: float32 [M][N] CUDA tensor (row-major); map_out: float32 [M][>=cols]."""
-    M, N = int(x.shape[0]), int(x.shape[1])
+    """x: float32 CUDA tensor (row-major), [M][N] or, with params.x_layout = RCFAR_X_TRACE_MAJOR,
+    [N][M]; map_out: float32 [M][>=cols]."""
+    M, N = _frame_dims(x, params.x_layout == RCFAR_X_TRACE_MAJOR)
     band = rcfar_band()
     _check(lib().rcfar_preprocess(h, _ptr(x), M, N, _ld(x), ctypes.byref(params), _ptr(map_out), _ld(map_out),
                                   ctypes.byref(band), _stream(stream)), "rcfar_preprocess")
@@ -321,8 +325,14 @@ def rcfar_sat_materialize(h: int, view: rcfar_sat_view, out, stream=None):
            "rcfar_sat_materialize")
 
 
-def frame_desc(x, window: rcfar_window, det, thr=None, map_out=None) -> rcfar_frame_desc:
-    return rcfar_frame_desc(_ptr(x), int(x.shape[0]), int(x.shape[1]), _ld(x), window, _ptr(det), _ld(det),
+def _frame_dims(x, trace_major: bool):
+    """(M, N) of a raw frame tensor: [M][N], or [N][M] when trace-major."""
+    return (int(x.shape[1]), int(x.shape[0])) if trace_major else (int(x.shape[0]), int(x.shape[1]))
+
+
+def frame_desc(x, window: rcfar_window, det, thr=None, map_out=None, trace_major: bool = False) -> rcfar_frame_desc:
+    M, N = _frame_dims(x, trace_major)
+    return rcfar_frame_desc(_ptr(x), M, N, _ld(x), window, _ptr(det), _ld(det),
                             _ptr(thr), _ld(thr) if thr is not None else 0, _ptr(map_out),
                             _ld(map_out) if map_out is not None else 0)
 
@@ -370,12 +380,14 @@ def rcfar_server_create(device: int = 0, budget_bytes: int = 8 << 30, slots: int
     return out.value
 
 
-def rcfar_server_submit(srv: int, x, window: rcfar_window, det, tag: int, arrival_ns: int = 0):
+def rcfar_server_submit(srv: int, x, window: rcfar_window, det, tag: int, arrival_ns: int = 0,
+                        trace_major: bool = False):
     """x, det: host (CPU) tensors, row-major (pinned memory gives asynchronous copies); they must stay
-    alive until the frame's completion has been polled."""
+    alive until the frame's completion has been polled. trace_major: x is [N][M] (the server's
+    params must say so too)."""
     if x.device.type != "cpu" or det.device.type != "cpu":
         raise ValueError("serving takes host tensors")
-    M, N = int(x.shape[0]), int(x.shape[1])
+    M, N = _frame_dims(x, trace_major)
     req = rcfar_request(_ptr(x), M, N, _ld(x), window, _ptr(det), _ld(det), int(tag), int(arrival_ns))
     _check(lib().rcfar_server_submit(srv, ctypes.byref(req)), "rcfar_server_submit")
 

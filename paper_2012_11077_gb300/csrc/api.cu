@@ -248,6 +248,7 @@ struct rcfar_ctx {
   float* ylo = nullptr;
   float* rowmean = nullptr;
   float* rowsq = nullptr;
+  float* xt = nullptr;  // range-major copy of a trace-major frame
   // per-step SAT
   void* sat_table = nullptr;
   SatArrays sat{};
@@ -348,7 +349,13 @@ static bool band_of(int N, const rcfar_pre_params* p, rcfar_band* b) {
 static bool valid_pre(const rcfar_pre_params* p) {
   return p && p->mean_len >= 1 && (p->mean_len & 1) && (p->mean_len - 1) / 2 <= kMaxMeanHalf &&
          (p->detector == RCFAR_DETECT_MAGNITUDE || p->detector == RCFAR_DETECT_SQUARE_LAW) &&
-         (p->normalise == RCFAR_NORM_GLOBAL_MAX || p->normalise == RCFAR_NORM_ROW_ZSCORE);
+         (p->normalise == RCFAR_NORM_GLOBAL_MAX || p->normalise == RCFAR_NORM_ROW_ZSCORE) &&
+         (p->x_layout == RCFAR_X_RANGE_MAJOR || p->x_layout == RCFAR_X_TRACE_MAJOR);
+}
+
+// leading dimension a raw frame of M x N needs in the given layout
+static bool ldx_ok(const rcfar_pre_params* p, int M, int N, long long ldx) {
+  return ldx >= (p->x_layout == RCFAR_X_TRACE_MAJOR ? M : N);
 }
 
 // twiddle plan for (N, c0, C); builds it on first use
@@ -442,9 +449,10 @@ static PreFrameDev make_pre_frame(const float* x, int M, int N, long long ldx, c
 }
 
 // workspace of one frame in a batch: data, and control words zeroed per batch
-static size_t frame_data_bytes(int M, int N, int C) {
+static size_t frame_data_bytes(int M, int N, int C, int x_layout) {
   const PreGeom g = pre_geom(M, N, C);
   size_t t = 0;
+  if (x_layout == RCFAR_X_TRACE_MAJOR) t += align256((size_t)M * round_up(N, 4) * sizeof(float));  // xt
   t += align256((size_t)N * sizeof(float2));                       // stats
   t += align256((size_t)g.n_chunks * N * sizeof(float2));          // partial
   t += align256((size_t)g.n_strips * M * sizeof(float));           // rowpart
@@ -541,6 +549,7 @@ rcfar_status rcfar_create(const rcfar_config* cfg, rcfar_handle* out) {
   total += align256((size_t)R * sizeof(float));                          // rowmean
   const size_t ycols_max = (size_t)ceil_div(round_up(Nm, kDftBK), kYCols);
   total += align256(ycols_max * R * sizeof(float));                      // rowsq
+  total += align256((size_t)R * round_up(Nm, 4) * sizeof(float));        // xt
   total += sat_bytes(R, Cm, RCFAR_SAT_I64);
   if (cudaMalloc(&h->ws, total) != cudaSuccess) {
     delete h;
@@ -566,6 +575,7 @@ rcfar_status rcfar_create(const rcfar_config* cfg, rcfar_handle* out) {
   h->ylo = cv.take<float>((size_t)R * round_up(Nm, kDftBK));
   h->rowmean = cv.take<float>(R);
   h->rowsq = cv.take<float>(ycols_max * R);
+  h->xt = cv.take<float>((size_t)R * round_up(Nm, 4));
   {
     SatGeom g = sat_geom(R, Cm);
     h->sat_table = cv.take<char>((size_t)R * g.ld_table * 8);
@@ -659,7 +669,7 @@ rcfar_status rcfar_get_error(rcfar_handle h, rcfar_stream stream) {
 rcfar_status rcfar_preprocess(rcfar_handle h, const float* x, int32_t M, int32_t N, int64_t ldx,
                               const rcfar_pre_params* p, float* map, int64_t ld_map, rcfar_band* band_out,
                               rcfar_stream stream) {
-  if (!h || !x || !map || M <= 0 || N <= 0 || ldx < N || !valid_pre(p)) return RCFAR_ERR_INVALID_ARG;
+  if (!h || !x || !map || M <= 0 || N <= 0 || !valid_pre(p) || !ldx_ok(p, M, N, ldx)) return RCFAR_ERR_INVALID_ARG;
   if (p->mean_len > N) return RCFAR_ERR_INVALID_ARG;
   rcfar_band b;
   if (!band_of(N, p, &b)) return RCFAR_ERR_INVALID_ARG;
@@ -709,12 +719,26 @@ rcfar_status rcfar_preprocess(rcfar_handle h, const float* x, int32_t M, int32_t
   F.ylo = h->yhi + (long long)M * g.npad;  // the two planes back to back (the tail runs into h->ylo's room)
   F.rowmean = h->rowmean;
   F.rowsq = h->rowsq;
+  int n_tr = 0;
+  if (p->x_layout == RCFAR_X_TRACE_MAJOR) {
+    F.xsrc = x;
+    F.ldsrc = ldx;
+    F.x = h->xt;
+    F.ldx = round_up(N, 4);
+    n_tr = (int)(ceil_div(M, kTrTile) * ceil_div(N, kTrTile));
+    F.n_tr = n_tr;
+  }
+  F.item_tr = 0;
   F.item_stats = 0;
   F.item_dft = 0;
   F.item_norm = 0;
   F.item_y = 0;
-  cudaError_t e;
-  {
+  cudaError_t e = cudaSuccess;
+  if (n_tr > 0) {
+    TraceScope t(h, "transpose", s);
+    e = launch_transpose(pb, n_tr, s);
+  }
+  if (e == cudaSuccess) {
     TraceScope t(h, "colstats", s);
     e = launch_colstats(pb, g.n_strips * g.n_chunks, s);
   }
@@ -956,7 +980,7 @@ rcfar_status rcfar_batch_bytes(int32_t M, int32_t N, const rcfar_pre_params* p, 
   }
   rcfar_band b;
   if (!band_of(N, &pf, &b)) return RCFAR_ERR_INVALID_ARG;
-  *bytes_out = (int64_t)(frame_data_bytes(M, N, b.cols) + frame_ctl_bytes(M, N, b.cols));
+  *bytes_out = (int64_t)(frame_data_bytes(M, N, b.cols, p->x_layout) + frame_ctl_bytes(M, N, b.cols));
   return RCFAR_OK;
 }
 
@@ -987,7 +1011,8 @@ rcfar_status rcfar_run_batch(rcfar_handle h, const rcfar_frame_desc* frames, int
   size_t need_data = 0, need_ctl = 0;
   for (int i = 0; i < n; ++i) {
     const rcfar_frame_desc& f = frames[i];
-    if (!f.x || !f.det || f.M <= 0 || f.N <= 0 || f.ldx < f.N || !valid_window(&f.window) || p->mean_len > f.N)
+    if (!f.x || !f.det || f.M <= 0 || f.N <= 0 || !ldx_ok(p, f.M, f.N, f.ldx) || !valid_window(&f.window) ||
+        p->mean_len > f.N)
       return RCFAR_ERR_INVALID_ARG;
     rcfar_pre_params pf = *p;
     if (pf.halo_c < 0) pf.halo_c = f.window.guard_c + f.window.train_c;
@@ -999,7 +1024,7 @@ rcfar_status rcfar_run_batch(rcfar_handle h, const rcfar_frame_desc* frames, int
         f.window.guard_c + f.window.train_c > h->cfg.max_window)
       return RCFAR_ERR_UNSUPPORTED;
     need_ctl += frame_ctl_bytes(f.M, f.N, C);
-    need_data += frame_data_bytes(f.M, f.N, C);
+    need_data += frame_data_bytes(f.M, f.N, C, p->x_layout);
   }
   if (need_ctl + need_data > h->batch_bytes) return RCFAR_ERR_OUT_OF_WORKSPACE;
   // plans
@@ -1056,7 +1081,7 @@ rcfar_status rcfar_run_batch(rcfar_handle h, const rcfar_frame_desc* frames, int
     db.dft_smem = pb.dft_smem;
     db.status = h->status;
     bool dft_tma_ok = true;
-    int it_stats = 0, it_dft = 0, it_norm = 0, it_cfar = 0, it_y = 0;
+    int it_stats = 0, it_dft = 0, it_norm = 0, it_cfar = 0, it_y = 0, it_tr = 0;
     int it_tile = 0, it_band = 0, it_vscan = 0;
     int cfar_mode_smem = 0, cfar_max_hc = 0;
     for (int k = 0; k < cnt; ++k) {
@@ -1067,6 +1092,16 @@ rcfar_status rcfar_run_batch(rcfar_handle h, const rcfar_frame_desc* frames, int
       const PreGeom g = pre_geom(f.M, f.N, C, kb_per_cta);
       PreFrameDev& F = pb.f[k];
       F = make_pre_frame(f.x, f.M, f.N, f.ldx, b, p, tws[i], g);
+      F.item_tr = it_tr;
+      if (p->x_layout == RCFAR_X_TRACE_MAJOR) {
+        F.xsrc = f.x;
+        F.ldsrc = f.ldx;
+        F.ldx = round_up(f.N, 4);
+        F.x = data.take<float>((size_t)f.M * F.ldx);
+        if (!F.x) return RCFAR_ERR_OUT_OF_WORKSPACE;
+        F.n_tr = (int)(ceil_div(f.M, kTrTile) * ceil_div(f.N, kTrTile));
+        it_tr += F.n_tr;
+      }
       F.stats = data.take<float2>(f.N);
       F.partial = data.take<float2>((size_t)g.n_chunks * f.N);
       F.rowpart = data.take<float>((size_t)g.n_strips * f.M);
@@ -1169,8 +1204,12 @@ rcfar_status rcfar_run_batch(rcfar_handle h, const rcfar_frame_desc* frames, int
         cfar_max_hc = std::max(cfar_max_hc, t.bw + 2 * P.wc + 1);
       }
     }
-    cudaError_t e;
-    {
+    cudaError_t e = cudaSuccess;
+    if (it_tr > 0) {
+      TraceScope t(h, "transpose", s);
+      e = launch_transpose(pb, it_tr, s);
+    }
+    if (e == cudaSuccess) {
       TraceScope t(h, "colstats", s);
       e = launch_colstats(pb, it_stats, s);
     }

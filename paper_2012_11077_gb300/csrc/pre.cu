@@ -69,6 +69,34 @@ __device__ __forceinline__ float mean_weight(int j, int N, int h) {
   return w;
 }
 
+// Trace-major frame X[m][n] = xsrc[n * ldsrc + m] -> range-major copy
+// x[m * ldx + n]: CTA of 32 x 8 threads per 32 x 32 tile; rows of the source
+// are read and rows of the copy written 128 bytes at a time through a padded
+// shared tile. Frames given range-major (xsrc == nullptr) have no CTAs.
+__global__ void __launch_bounds__(256) k_transpose(const __grid_constant__ PreBatch b) {
+  const int fi = find_item(b.f, b.n, (int)blockIdx.x, &PreFrameDev::item_tr);
+  const PreFrameDev& F = b.f[fi];
+  const int local = (int)blockIdx.x - F.item_tr;
+  if (local >= F.n_tr || F.xsrc == nullptr) return;
+  __shared__ float t[kTrTile][kTrTile + 1];
+  const int tiles_m = (F.M + kTrTile - 1) / kTrTile;
+  const int tn = local / tiles_m, tm = local - tn * tiles_m;
+  const int m0 = tm * kTrTile, n0 = tn * kTrTile;
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+#pragma unroll
+  for (int k = 0; k < kTrTile; k += 8) {
+    const int n = n0 + ty + k, m = m0 + tx;
+    t[ty + k][tx] = (n < F.N && m < F.M) ? __ldg(F.xsrc + (long long)n * F.ldsrc + m) : 0.f;
+  }
+  __syncthreads();
+  float* out = const_cast<float*>(F.x);
+#pragma unroll
+  for (int k = 0; k < kTrTile; k += 8) {
+    const int m = m0 + ty + k, n = n0 + tx;
+    if (m < F.M && n < F.N) out[(long long)m * F.ldx + n] = t[tx][ty + k];
+  }
+}
+
 // grid: for every frame, n_strips x n_chunks CTAs of 256 threads; a chunk is
 // 64 rows (kStatsRowsPerChunk). Thread (g = warp, lane) owns rows g, g+8, ...
 // of its chunk for 4 columns; all 8 rows are loaded before any arithmetic.
@@ -768,6 +796,12 @@ __global__ void k_twiddles(float* Wt, long long ldw, int npad, int N, int c0, in
 }
 
 }  // namespace
+
+cudaError_t launch_transpose(const PreBatch& b, int blocks, cudaStream_t s) {
+  if (blocks <= 0) return cudaSuccess;
+  k_transpose<<<blocks, 256, 0, s>>>(b);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_colstats(const PreBatch& b, int blocks, cudaStream_t s) {
   if (blocks <= 0) return cudaSuccess;

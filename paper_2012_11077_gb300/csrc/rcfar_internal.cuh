@@ -66,6 +66,9 @@ struct PreFrameDev {
   float* ylo;        // [M][npad] the TF32 tail
   float* rowmean;    // [M] the row means c_m removed from y
   float* rowsq;      // z-score normalisation: [ycols][M] per-block sums of (y - c_m)^2
+  const float* xsrc; // trace-major input [N][ldsrc] transposed into x (nullptr: x is the input)
+  long long ldsrc;
+  int item_tr, n_tr; // transpose: first CTA and CTA count of this frame
   int detector;      // rcfar_detector
   int normalise;     // rcfar_normalise
   int npad;          // N rounded up to kDftBK
@@ -228,6 +231,9 @@ cudaError_t ensure_smem(const void* fn, size_t bytes);
 
 // ---- launchers (implemented in the .cu files) -------------------------------
 cudaError_t launch_colstats(const PreBatch& b, int blocks, cudaStream_t s);
+// trace-major frames [N][ldsrc] -> range-major copies [M][ldx] (32 x 32 tiles)
+cudaError_t launch_transpose(const PreBatch& b, int blocks, cudaStream_t s);
+constexpr int kTrTile = 32;
 cudaError_t launch_ysplit(const PreBatch& b, int blocks, cudaStream_t s);
 cudaError_t launch_band_dft(const PreBatch& b, int blocks, cudaStream_t s);
 cudaError_t launch_band_dft_tma(const DftBatch& b, int blocks, cudaStream_t s);

@@ -91,15 +91,18 @@ void rcfar_server_s::launch(int si) {
   for (int i = 0; i < n; ++i) {
     const rcfar_request& r = S.batch[i].r;
     float* xin = reinterpret_cast<float*>(S.dev_io + S.in_off[i]);
-    if (cudaMemcpy2DAsync(xin, (size_t)r.N * sizeof(float), r.x, (size_t)r.ldx * sizeof(float),
-                          (size_t)r.N * sizeof(float), (size_t)r.M, cudaMemcpyHostToDevice, S.stream) != cudaSuccess)
+    // packed on the device in the frame's own layout (rows of N, or of M for trace-major frames)
+    const bool tm = cfg.params.x_layout == RCFAR_X_TRACE_MAJOR;
+    const int width = tm ? r.M : r.N, height = tm ? r.N : r.M;
+    if (cudaMemcpy2DAsync(xin, (size_t)width * sizeof(float), r.x, (size_t)r.ldx * sizeof(float),
+                          (size_t)width * sizeof(float), (size_t)height, cudaMemcpyHostToDevice, S.stream) != cudaSuccess)
       st = RCFAR_ERR_CUDA;
     rcfar_frame_desc& d = S.descs[i];
     std::memset(&d, 0, sizeof(d));
     d.x = xin;
     d.M = r.M;
     d.N = r.N;
-    d.ldx = r.N;
+    d.ldx = width;
     d.window = r.window;
     d.det = reinterpret_cast<uint8_t*>(S.dev_io + S.in_cap + S.det_off[i]);
     d.ld_det = S.batch[i].C;
@@ -290,7 +293,8 @@ rcfar_status rcfar_server_create(const rcfar_server_config* cfg, rcfar_server* o
 rcfar_status rcfar_server_submit(rcfar_server srv, const rcfar_request* req) {
   if (!srv || !req) return RCFAR_ERR_INVALID_ARG;
   const rcfar_request& r = *req;
-  if (!r.x || !r.det || r.M <= 0 || r.N <= 0 || r.ldx < r.N || srv->cfg.params.mean_len > r.N)
+  const bool tm = srv->cfg.params.x_layout == RCFAR_X_TRACE_MAJOR;
+  if (!r.x || !r.det || r.M <= 0 || r.N <= 0 || r.ldx < (tm ? r.M : r.N) || srv->cfg.params.mean_len > r.N)
     return RCFAR_ERR_INVALID_ARG;
   const rcfar_window& w = r.window;
   if (w.train_r < 0 || w.train_c < 0 || w.guard_r < 0 || w.guard_c < 0 || !(w.pfa > 0.0 && w.pfa < 1.0))

@@ -520,3 +520,37 @@ def test_batch_tunings_give_identical_results(rc):
             assert torch.equal(a, d.cpu()) and torch.equal(b, th.cpu()) and torch.equal(c_, mp.cpu())
     finally:
         rc.rcfar_destroy(h2)
+
+
+@pytest.mark.parametrize("M,N", [(1024, 600), (129, 601), (40, 64)])
+def test_trace_major_input(rc, h, M, N):
+    # frames given trace by trace ([N][M], the acquisition order) give the same
+    # map and decisions as the same frames range-major, and match the oracle;
+    # 1024 x 600 is the paper's frame size (600 traces of 1024 range samples)
+    case = synth.ChainCase(synth.FrameSpec(M=M, N=N, n_targets=3, seed=M + N), synth.Window(8, 8, 2, 2, 1e-4))
+    X = synth.radar_frame(case.spec)
+    w = case.window
+    win = rc.make_window(w.train_r, w.train_c, w.guard_r, w.guard_c, w.pfa)
+    out = {}
+    for layout in (rc.RCFAR_X_RANGE_MAJOR, rc.RCFAR_X_TRACE_MAJOR):
+        params = rc.make_pre_params(synth.FS_HZ, mean_len=5, halo_c=case.halo_c, x_layout=layout)
+        band = rc.rcfar_band_plan(N, params)
+        xin = dev_t(X) if layout == rc.RCFAR_X_RANGE_MAJOR else dev_t(np.ascontiguousarray(X.T))
+        P = torch.empty((M, band.cols), dtype=torch.float32, device="cuda")
+        rc.rcfar_preprocess(h, xin, params, P)
+        view = rc.rcfar_sat(h, P, value_bound=band.value_bound)
+        det = torch.empty((M, band.cols), dtype=torch.uint8, device="cuda")
+        rc.rcfar_cfar(h, view, P, win, band.k_lo - band.c0, band.k_hi - band.c0, det)
+        # and through the batch path
+        det_b = torch.empty_like(det)
+        rc.rcfar_run_batch(h, [rc.frame_desc(xin, win, det_b, trace_major=layout == rc.RCFAR_X_TRACE_MAJOR)],
+                           rc.make_pre_params(synth.FS_HZ, mean_len=5, halo_c=-1, x_layout=layout))
+        assert rc.rcfar_get_error(h) == rc.RCFAR_OK
+        assert torch.equal(det_b, det)
+        out[layout] = (P.cpu(), det.cpu(), band)
+    (P0, d0, band), (P1, d1, _) = out[0], out[1]
+    assert torch.equal(P0, P1) and torch.equal(d0, d1)
+    P_o, band_o, res_o = oracle.run_chain(X, synth.FS_HZ, 5, w.train_r, w.train_c, w.guard_r, w.guard_c, w.pfa)
+    assert map_err(P1.numpy(), P_o).max() <= REL
+    cmp = ocfar.compare_decisions(d1.numpy(), res_o.det, P_o, res_o.thr, res_o.cut, margin=MARGIN)
+    assert cmp.mismatches == 0, cmp
