@@ -430,10 +430,10 @@ def ours(args, rank, world, local, dist):
     launches_per_step = 5
 
     def chain(i):
+        # SAT + CFAR fused (no table in device memory; decisions identical to rcfar_sat + rcfar_cfar)
         x, P, det = frames[i % RING], maps[i % RING], dets[i % RING]
         rc.rcfar_preprocess(h, x, params, P)
-        v = rc.rcfar_sat(h, P, value_bound=band.value_bound, mode=rc.RCFAR_SAT_TILE_I64)
-        rc.rcfar_cfar(h, v, None, win, cut_lo, cut_hi, det)
+        rc.rcfar_sat_cfar(h, P, band.value_bound, win, cut_lo, cut_hi, det, map_cut=False)
 
     # warm-up (also builds the twiddle plan), then capture one graph per ring slot
     for i in range(max(args.warmup, 3)):
@@ -481,8 +481,7 @@ def ours(args, rank, world, local, dist):
         def chain_v(i, pv=pv, bv=bv):
             x, P, det = frames[i % RING], maps[i % RING], dets[i % RING]
             rc.rcfar_preprocess(h, x, pv, P)
-            v = rc.rcfar_sat(h, P, value_bound=bv.value_bound, mode=rc.RCFAR_SAT_TILE_I64)
-            rc.rcfar_cfar(h, v, None, win, cut_lo, cut_hi, det)
+            rc.rcfar_sat_cfar(h, P, bv.value_bound, win, cut_lo, cut_hi, det, map_cut=False)
 
         for i in range(3):
             chain_v(i)
@@ -522,8 +521,8 @@ def ours(args, rank, world, local, dist):
 
     def chain_p(i):
         rc.rcfar_preprocess(h, xs_p[i % RING], pp, maps_p[i % RING])
-        v = rc.rcfar_sat(h, maps_p[i % RING], value_bound=bp.value_bound, mode=rc.RCFAR_SAT_TILE_I64)
-        rc.rcfar_cfar(h, v, None, win, bp.k_lo - bp.c0, bp.k_hi - bp.c0, dets_p[i % RING])
+        rc.rcfar_sat_cfar(h, maps_p[i % RING], bp.value_bound, win, bp.k_lo - bp.c0, bp.k_hi - bp.c0,
+                          dets_p[i % RING], map_cut=False)
 
     for i in range(3):
         chain_p(i)
@@ -556,6 +555,30 @@ def ours(args, rank, world, local, dist):
     trace = rc.rcfar_trace_read(h)
     rc.rcfar_trace_enable(h, False)
     step_kernels = {k: {"launches": n, "avg_us": 1e3 * t / n} for k, (n, t) in trace.items()}
+    # SAT + CFAR on the chain's band map: split (table in HBM) against fused
+    P0, d0 = maps[0], dets[0]
+    d1 = torch.empty_like(d0)
+
+    def split_sc():
+        v = rc.rcfar_sat(h, P0, value_bound=band.value_bound, mode=rc.RCFAR_SAT_TILE_I64)
+        rc.rcfar_cfar(h, v, None, win, cut_lo, cut_hi, d1)
+
+    def fused_sc():
+        rc.rcfar_sat_cfar(h, P0, band.value_bound, win, cut_lo, cut_hi, d0, map_cut=False)
+
+    chain_map = {}
+    for nm, fn in (("split_us", split_sc), ("fused_us", fused_sc)):
+        for _ in range(3):
+            fn()
+        torch.cuda.synchronize()
+        e0.record()
+        for _ in range(20):
+            fn()
+        e1.record()
+        torch.cuda.synchronize()
+        chain_map[nm] = 1e3 * e0.elapsed_time(e1) / 20
+    chain_map["decisions_identical"] = bool(torch.equal(d0, d1))
+    chain_map["map"] = f"{M}x{C} band map"
     dft_us = step_kernels["band_dft"]["avg_us"]
     # algorithmic flops of the band DFT: 2 flops x M rows x N samples x 2C real outputs (one product;
     # the kernel issues three split-TF32 products, so frac <= 1/3 by construction)
@@ -637,6 +660,24 @@ def ours(args, rank, world, local, dist):
                                  "unit": "GB/s", "frac": ach / peaks["hbm_gbs"],
                                  "traffic": TRAFFIC["cfar_ring_8192" if dom == "cfar" else "sat_i64_8192"]}}
         assert rc.rcfar_get_error(h) == rc.RCFAR_OK
+        # the same map through the fused kernel (no table in HBM; same decisions)
+        detf = torch.empty_like(detm)
+
+        def fused8():
+            rc.rcfar_sat_cfar(h, Pm, bound, wm, 0, R - 1, detf)
+
+        for _ in range(3):
+            fused8()
+        torch.cuda.synchronize()
+        e0.record()
+        for _ in range(reps):
+            fused8()
+        e1.record()
+        torch.cuda.synchronize()
+        fms = e0.elapsed_time(e1) / reps
+        sat_cfar["fused"] = {"value": cells / (fms * 1e-3) / 1e9, "unit": "Gcells/s", "ms": fms,
+                             "hbm_bytes_per_cell": 5, "decisions_identical": bool(torch.equal(detf, detm))}
+        assert rc.rcfar_get_error(h) == rc.RCFAR_OK
 
     batch = None
     if not args.no_batch:
@@ -667,7 +708,7 @@ def ours(args, rank, world, local, dist):
                        "l2": "inputs larger than L2: ring of 16 distinct frames (268 MB)",
                        "parallelism": f"replicas x{world}"},
             "roofline": roofline, "kernels": step_kernels, "sat_cfar": sat_cfar, "batch": batch,
-            "serving": serving, "variants": variants, "e2e": e2e,
+            "serving": serving, "variants": variants, "chain_sat_cfar": chain_map, "e2e": e2e,
             "cpu_baseline": cpu, "clocks": clk, "gpu_launches": launches_per_step * args.steps,
             "peaks": peaks["source"]}
     print(json.dumps(line), flush=True)

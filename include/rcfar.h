@@ -79,7 +79,8 @@ typedef enum rcfar_sat_mode {
   RCFAR_SAT_TILE_F32 = 0,
   RCFAR_SAT_I64 = 1,
   RCFAR_SAT_NAIVE_F32 = 2,
-  RCFAR_SAT_TILE_I64 = 3
+  RCFAR_SAT_TILE_I64 = 3,
+  RCFAR_SAT_FUSED = 4  /* no table in device memory (rcfar_sat_cfar); batch tuning only, not rcfar_sat */
 } rcfar_sat_mode;
 
 typedef struct rcfar_config {
@@ -240,6 +241,21 @@ rcfar_status rcfar_cfar(rcfar_handle h, const rcfar_sat_view* view, const void* 
                         int32_t cut_c_hi, uint8_t* det, int64_t ld_det, float* thr, int64_t ld_thr,
                         rcfar_stream stream);
 
+/* rcfar_sat + rcfar_cfar fused, with no table in device memory: every CTA
+ * builds the exact 64-bit integral image (eq. 3) of its block of the map plus
+ * the window halo in shared memory and takes the eq. 4 lookups there. The
+ * quantisation and fixed-point scale are those rcfar_sat uses for
+ * (value_bound > 0, the window), so the decisions and thresholds are
+ * bit-identical to rcfar_sat(TILE_I64 or I64) followed by rcfar_cfar with the
+ * same CUT source: the map's values when map_cut != 0, else the table's 1 x 1
+ * region sums. map: [rows][ld_map] of dtype (F16 values times 2^map_exp2).
+ * UNSUPPORTED when the window's halo does not fit shared memory. A value
+ * above value_bound (or NaN) is reported by rcfar_get_error as RANGE. */
+rcfar_status rcfar_sat_cfar(rcfar_handle h, const void* map, int32_t dtype, int32_t map_exp2, int32_t rows,
+                            int32_t cols, int64_t ld_map, float value_bound, const rcfar_window* w, int32_t cut_c_lo,
+                            int32_t cut_c_hi, int32_t map_cut, uint8_t* det, int64_t ld_det, float* thr,
+                            int64_t ld_thr, rcfar_stream stream);
+
 /* The same decisions with S_ref summed cell by cell over the n_ref training
  * cells (the sliding-window CA-CFAR that the SAT replaces; Sec. III, Table I
  * "CA-CFAR"). map is float32 [rows][ld_map]. */
@@ -280,10 +296,11 @@ rcfar_status rcfar_prepare(rcfar_handle h, const rcfar_frame_desc* frames, int32
  * same results (bit for bit): only the schedule changes. */
 typedef struct rcfar_batch_tuning {
   int32_t dft_kblocks_per_cta;  /* K blocks (128 samples) per band-DFT CTA; 0 = automatic (about two waves) */
-  int32_t sat_mode;             /* RCFAR_SAT_TILE_I64 (tile-local table, register-staged CFAR) or
+  int32_t sat_mode;             /* RCFAR_SAT_TILE_I64 (tile-local table, register-staged CFAR),
                                    RCFAR_SAT_I64 (table S itself, CFAR streaming it through a
-                                   bulk-copy ring; frames whose window does not fit the ring use
-                                   TILE_I64) */
+                                   bulk-copy ring) or RCFAR_SAT_FUSED (no table: each CTA builds
+                                   its block's integral image in shared memory); a group whose
+                                   windows do not fit the chosen kernel uses TILE_I64 */
   int32_t cfar_tile_rows;       /* TILE_I64 CFAR strip: CUT rows per step and columns; 0 = automatic */
   int32_t cfar_tile_cols;
   double best_ms;               /* rcfar_tune_batch: time of one batch with this tuning */
@@ -293,7 +310,7 @@ typedef struct rcfar_batch_tuning {
 
 /* Autotuner: times rcfar_run_batch on these frames (outputs are written)
  * under candidate tunings -- band-DFT K split {auto, 1, 2, 4, 8, 16}, then the
- * table mode and CFAR strip shapes with the best split -- with CUDA events
+ * table mode (TILE_I64, I64, FUSED) and CFAR strip shapes with the best split -- with CUDA events
  * on the stream, `reps` batches each after one untimed batch, and keeps the
  * fastest in the handle for later rcfar_run_batch calls (out may be NULL).
  * Synchronises the stream; not usable during stream capture (BAD_STATE). */

@@ -29,6 +29,7 @@ RCFAR_SAT_TILE_F32 = 0
 RCFAR_SAT_I64 = 1
 RCFAR_SAT_NAIVE_F32 = 2
 RCFAR_SAT_TILE_I64 = 3
+RCFAR_SAT_FUSED = 4
 
 RCFAR_DETECT_MAGNITUDE = 0
 RCFAR_DETECT_SQUARE_LAW = 1
@@ -48,7 +49,7 @@ EXPORTS = (
     "rcfar_trace_enable", "rcfar_trace_read", "rcfar_sat_cfar_static",
     "rcfar_server_create", "rcfar_server_submit", "rcfar_server_prepare", "rcfar_server_poll", "rcfar_server_get_stats",
     "rcfar_server_now_ns", "rcfar_server_destroy", "rcfar_selftest_wait",
-    "rcfar_tune_batch", "rcfar_set_batch_tuning", "rcfar_get_batch_tuning",
+    "rcfar_tune_batch", "rcfar_set_batch_tuning", "rcfar_get_batch_tuning", "rcfar_sat_cfar",
 )
 
 
@@ -176,6 +177,8 @@ def lib() -> ctypes.CDLL:
                                  ctypes.POINTER(rcfar_batch_tuning), P],
             "rcfar_set_batch_tuning": [P, ctypes.POINTER(rcfar_batch_tuning)],
             "rcfar_get_batch_tuning": [P, ctypes.POINTER(rcfar_batch_tuning)],
+            "rcfar_sat_cfar": [P, P, I32, I32, I32, I32, I64, F32, ctypes.POINTER(rcfar_window), I32, I32, I32, P, I64,
+                               P, I64, P],
         }
         for name, args in sig.items():
             fn = getattr(L, name)
@@ -448,3 +451,15 @@ def rcfar_get_batch_tuning(h: int) -> rcfar_batch_tuning:
     out = rcfar_batch_tuning()
     _check(lib().rcfar_get_batch_tuning(h, ctypes.byref(out)), "rcfar_get_batch_tuning")
     return out
+
+
+def rcfar_sat_cfar(h: int, map_t, value_bound: float, window: rcfar_window, cut_c_lo: int, cut_c_hi: int, det,
+                   thr=None, map_cut: bool = True, map_exp2: int = 0, stream=None):
+    """Fused SAT + CFAR (no table in device memory); same decisions as rcfar_sat + rcfar_cfar."""
+    import torch
+    rows, cols = int(map_t.shape[0]), int(map_t.shape[1])
+    dtype = RCFAR_MAP_F16 if map_t.dtype == torch.float16 else RCFAR_MAP_F32
+    _check(lib().rcfar_sat_cfar(h, _ptr(map_t), dtype, int(map_exp2), rows, cols, _ld(map_t), float(value_bound),
+                                ctypes.byref(window), int(cut_c_lo), int(cut_c_hi), 1 if map_cut else 0, _ptr(det),
+                                _ld(det), _ptr(thr), _ld(thr) if thr is not None else 0, _stream(stream)),
+           "rcfar_sat_cfar")

@@ -913,6 +913,48 @@ rcfar_status rcfar_cfar(rcfar_handle h, const rcfar_sat_view* view, const void* 
   return cuda_fail(e);
 }
 
+rcfar_status rcfar_sat_cfar(rcfar_handle h, const void* map, int32_t dtype, int32_t map_exp2, int32_t rows,
+                            int32_t cols, int64_t ld_map, float value_bound, const rcfar_window* w, int32_t cut_c_lo,
+                            int32_t cut_c_hi, int32_t map_cut, uint8_t* det, int64_t ld_det, float* thr,
+                            int64_t ld_thr, rcfar_stream stream) {
+  if (!h || !map || !det || rows <= 0 || cols <= 0 || ld_map < cols || ld_det < cols || !valid_window(w))
+    return RCFAR_ERR_INVALID_ARG;
+  if ((thr && ld_thr < cols) || (dtype != RCFAR_MAP_F32 && dtype != RCFAR_MAP_F16)) return RCFAR_ERR_INVALID_ARG;
+  if (!(value_bound > 0.0f) || !std::isfinite(value_bound)) return RCFAR_ERR_INVALID_ARG;
+  if (w->guard_r + w->train_r > h->cfg.max_window || w->guard_c + w->train_c > h->cfg.max_window)
+    return RCFAR_ERR_UNSUPPORTED;
+  DeviceGuard dg(h->device);
+  cudaStream_t s = (cudaStream_t)stream;
+  static thread_local CfarBatch cb;
+  cb.n = 1;
+  cb.status = h->status;
+  CfarMapDev& P = cb.m[0];
+  std::memset(&P, 0, sizeof(P));
+  P.map = map;
+  P.ld_map = ld_map;
+  P.in_scale = dtype == RCFAR_MAP_F16 ? std::ldexp(1.0f, map_exp2) : 1.0f;
+  P.rows = rows;
+  P.cols = cols;
+  fill_cfar_window(P, w, rows, cols, cut_c_lo, cut_c_hi);
+  P.det = det;
+  P.ld_det = ld_det;
+  P.thr = thr;
+  P.ld_thr = ld_thr;
+  // the scale rcfar_sat takes for this bound and handle
+  const long long wmax = h->cfg.max_window;
+  const long long max_cells = std::max<long long>((long long)kSatTileH * kSatTileW, (2 * wmax + 1) * (2 * wmax + 1));
+  P.sat_scale = sat_scale_for(value_bound, max_cells);
+  P.bound = value_bound;
+  P.item0 = 0;
+  int run = 0, bw = 0, pitch = 0;
+  size_t smem = 0;
+  if (!cfar_fused_plan(rows, cols, P.wr, P.wc, std::min<size_t>(h->smem_optin, 200 * 1024), &run, &bw, &pitch, &smem))
+    return RCFAR_ERR_UNSUPPORTED;
+  const int blocks = cfar_fused_geometry(P, rows, cols, run, bw, pitch);
+  TraceScope tr(h, "sat_cfar_fused", s);
+  return cuda_fail(launch_cfar_fused(cb, map_cut != 0, dtype, blocks, smem, s));
+}
+
 rcfar_status rcfar_cfar_direct(rcfar_handle h, const float* map, int32_t rows, int32_t cols, int64_t ld_map,
                                const rcfar_window* w, int32_t cut_c_lo, int32_t cut_c_hi, uint8_t* det,
                                int64_t ld_det, float* thr, int64_t ld_thr, rcfar_stream stream) {
@@ -1066,6 +1108,19 @@ rcfar_status rcfar_run_batch(rcfar_handle h, const rcfar_frame_desc* frames, int
     // frame's window fits its ring
     int sat_mode = RCFAR_SAT_TILE_I64;
     int ring_rows_max = 0, hcp_max = 0;
+    size_t fused_smem = 0;
+    if (h->tuning.sat_mode == RCFAR_SAT_FUSED) {
+      sat_mode = RCFAR_SAT_FUSED;
+      const size_t cap = std::min<size_t>(h->smem_optin, 200 * 1024);
+      for (int k = 0; k < cnt && sat_mode == RCFAR_SAT_FUSED; ++k) {
+        const rcfar_frame_desc& f = frames[base + k];
+        int run = 0, bw = 0, pitch = 0;
+        size_t sm = 0;
+        if (!cfar_fused_plan(f.M, bands[base + k].cols, f.window.guard_r + f.window.train_r,
+                             f.window.guard_c + f.window.train_c, cap, &run, &bw, &pitch, &sm))
+          sat_mode = RCFAR_SAT_TILE_I64;
+      }
+    }
     if (h->tuning.sat_mode == RCFAR_SAT_I64) {
       sat_mode = RCFAR_SAT_I64;
       for (int k = 0; k < cnt && sat_mode == RCFAR_SAT_I64; ++k) {
@@ -1184,7 +1239,15 @@ rcfar_status rcfar_run_batch(rcfar_handle h, const rcfar_frame_desc* frames, int
       P.ld_thr = f.ld_thr;
       P.mode = sat_mode;
       P.item0 = it_cfar;
-      if (sat_mode == RCFAR_SAT_I64) {
+      if (sat_mode == RCFAR_SAT_FUSED) {
+        int run = 0, bw = 0, pitch = 0;
+        size_t sm = 0;
+        cfar_fused_plan(f.M, C, P.wr, P.wc, std::min<size_t>(h->smem_optin, 200 * 1024), &run, &bw, &pitch, &sm);
+        fused_smem = std::max(fused_smem, sm);
+        P.sat_scale = m.scale_log2;
+        P.bound = m.bound;
+        it_cfar += cfar_fused_geometry(P, f.M, C, run, bw, pitch);
+      } else if (sat_mode == RCFAR_SAT_I64) {
         int rr = 0, hc = 0;
         cfar_ring_plan(P.wr, P.wc, h->smem_optin, &rr, &hc);
         const size_t sm = cfar_ring_smem(rr, hc);
@@ -1227,11 +1290,12 @@ rcfar_status rcfar_run_batch(rcfar_handle h, const rcfar_frame_desc* frames, int
     }
     if (e == cudaSuccess) {
       TraceScope t(h, "sat", s);
-      e = launch_sat(sb, sat_mode, RCFAR_MAP_F32, it_tile, it_band, it_vscan, s);
+      if (sat_mode != RCFAR_SAT_FUSED) e = launch_sat(sb, sat_mode, RCFAR_MAP_F32, it_tile, it_band, it_vscan, s);
     }
     if (e == cudaSuccess) {
       TraceScope t(h, "cfar", s);
-      e = sat_mode == RCFAR_SAT_I64
+      e = sat_mode == RCFAR_SAT_FUSED ? launch_cfar_fused(cb, true, RCFAR_MAP_F32, it_cfar, fused_smem, s)
+          : sat_mode == RCFAR_SAT_I64
               ? launch_cfar_ring(cb, true, RCFAR_MAP_F32, it_cfar, ring_smem, s)
               : launch_cfar(cb, sat_mode, RCFAR_MAP_F32, it_cfar, (size_t)cfar_mode_smem, cfar_max_hc, s);
     }
@@ -1242,7 +1306,7 @@ rcfar_status rcfar_run_batch(rcfar_handle h, const rcfar_frame_desc* frames, int
 
 static bool valid_tuning(const rcfar_batch_tuning* t) {
   return t && t->dft_kblocks_per_cta >= 0 && t->dft_kblocks_per_cta <= 4096 &&
-         (t->sat_mode == RCFAR_SAT_TILE_I64 || t->sat_mode == RCFAR_SAT_I64) &&
+         (t->sat_mode == RCFAR_SAT_TILE_I64 || t->sat_mode == RCFAR_SAT_I64 || t->sat_mode == RCFAR_SAT_FUSED) &&
          ((t->cfar_tile_rows == 0 && t->cfar_tile_cols == 0) ||
           (t->cfar_tile_rows > 0 && t->cfar_tile_rows <= 16 && t->cfar_tile_cols > 0 && 256 % t->cfar_tile_cols == 0 &&
            t->cfar_tile_rows * t->cfar_tile_cols <= 1024));
@@ -1316,6 +1380,7 @@ rcfar_status rcfar_tune_batch(rcfar_handle h, const rcfar_frame_desc* frames, in
   // stage 2: table mode and CFAR strips with the best split
   const int kb = best.dft_kblocks_per_cta;
   consider(rcfar_batch_tuning{kb, RCFAR_SAT_I64, 0, 0, 0.0, 0, 0});
+  consider(rcfar_batch_tuning{kb, RCFAR_SAT_FUSED, 0, 0, 0.0, 0, 0});
   const int tiles[][2] = {{16, 64}, {8, 64}, {16, 32}, {8, 128}};
   for (const auto& tl : tiles) consider(rcfar_batch_tuning{kb, RCFAR_SAT_TILE_I64, tl[0], tl[1], 0.0, 0, 0});
   cudaEventDestroy(e0);

@@ -431,6 +431,127 @@ __global__ void __launch_bounds__(kRingThreads, 1) k_cfar_ring(const __grid_cons
   if (tid == 0 && s_fail && B.status) atomicOr(B.status, kStatusTimeout);
 }
 
+// Fused SAT + CFAR (no table in device memory). A CTA owns an inner block of
+// rows [R0, R1) x columns [c0, c0 + width) and builds, in shared memory, the
+// exact 64-bit fixed-point integral image (eq. 3) of its region: table rows
+// R0 - wr - 1 .. R1 - 1 + wr and columns cb - 1 .. cb - 1 + CC - 1, with
+// region row 0 and column 0 as the zero origin (cb = c0 - wc, or 0 for a
+// strip covering the whole width). A region box sum equals the global
+// table's (box sums do not depend on the origin), so S_ref -- 8 lookups,
+// eq. 4 on the outer and guard rectangles -- and hence T and the decision are
+// bit-identical to the split path's with the same fixed-point scale.
+// Steps: quantise the region into shared memory, prefix every row (warp
+// scans), prefix every column (one thread per column), then the CUTs.
+template <bool kMapCut, typename InT>
+__global__ void __launch_bounds__(256) k_sat_cfar_fused(const __grid_constant__ CfarBatch B) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  u64* S = reinterpret_cast<u64*>(smem_raw);
+  __shared__ int s_bad;
+  const int mi = find_item(B.m, B.n, (int)blockIdx.x, &CfarMapDev::item0);
+  const CfarMapDev& P = B.m[mi];
+  const int local = (int)blockIdx.x - P.item0;
+  const int ty = local / P.tiles_x, tx = local - ty * P.tiles_x;
+  const int rows = P.rows, cols = P.cols;
+  const int R0 = ty * P.run, R1 = min(rows, R0 + P.run);
+  const int wr = P.wr, wc = P.wc, gr = P.gr, gc = P.gc;
+  const bool full = P.tiles_x == 1 && P.bw >= cols;
+  const int c0 = full ? 0 : tx * P.bw;
+  const int cw = full ? cols : min(P.bw, cols - c0);  // inner columns
+  const int cb = full ? 0 : c0 - wc;                   // table column of region column 1
+  const int RR = (R1 - R0) + 2 * wr + 1;
+  const int CC = full ? cols + 1 : cw + 2 * wc + 1;
+  const int pitch = P.hcp;
+  const int rg0 = R0 - wr - 1;  // table row of region row 0 (the origin)
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const float scalef = ldexpf(1.0f, P.sat_scale);
+  const float bound = P.bound;
+  const InT* map = reinterpret_cast<const InT*>(P.map);
+  if (tid == 0) s_bad = 0;
+
+  // 1. quantised values; the origin row and column and cells outside the map are zero
+  bool bad = false;
+  for (int idx = tid; idx < RR * CC; idx += 256) {
+    const int g = idx / CC, j = idx - g * CC;
+    const int r = rg0 + g, c = cb - 1 + j;
+    float v = 0.f;
+    if (g > 0 && j > 0 && r >= 0 && r < rows && c >= 0 && c < cols) v = ld_map_val(map + (long long)r * P.ld_map + c, P.in_scale);
+    bad |= !(fabsf(v) <= bound);
+    S[g * pitch + j] = (u64)q_from_f32(v, scalef);
+  }
+  if (bad) s_bad = 1;
+  __syncthreads();
+  // 2. row prefixes: a warp per row, 8 consecutive columns per lane (CC <= 256)
+  for (int g = warp; g < RR; g += 8) {
+    u64* row = S + g * pitch;
+    u64 v[8];
+#pragma unroll
+    for (int e = 0; e < 8; ++e) {
+      const int j = 8 * lane + e;
+      v[e] = j < CC ? row[j] : 0ull;
+    }
+#pragma unroll
+    for (int e = 1; e < 8; ++e) v[e] += v[e - 1];
+    u64 incl = v[7];
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const u64 y = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= o) incl += y;
+    }
+    const u64 excl = incl - v[7];
+#pragma unroll
+    for (int e = 0; e < 8; ++e) {
+      const int j = 8 * lane + e;
+      if (j < CC) row[j] = v[e] + excl;
+    }
+  }
+  __syncthreads();
+  // 3. column prefixes: a thread per column walks down the region
+  for (int j = tid; j < CC; j += 256) {
+    u64 acc = 0;
+#pragma unroll 4
+    for (int g = 0; g < RR; ++g) {
+      acc += S[g * pitch + j];
+      S[g * pitch + j] = acc;
+    }
+  }
+  __syncthreads();
+  // 4. the CUTs of the inner block
+  int s = P.sat_scale;
+  const float inv_s = ldexpf(1.0f, -s);
+  const float kthr = P.kthr;
+  const int inner = (R1 - R0) * cw;
+  for (int idx = tid; idx < inner; idx += 256) {
+    const int rr = idx / cw, cc = idx - rr * cw;
+    const int r = R0 + rr, c = c0 + cc;
+    unsigned char d = 0;
+    float th = 0.f;
+    if (r >= P.row_lo && r <= P.row_hi && c >= P.cut_lo && c <= P.cut_hi) {
+      const int g = r - rg0;       // region row of table row r
+      const int j = c - cb + 1;    // region column of table column c
+      const u64* ra = S + (g - wr - 1) * pitch;
+      const u64* rb = S + (g + wr) * pitch;
+      const u64* rc = S + (g - gr - 1) * pitch;
+      const u64* rd = S + (g + gr) * pitch;
+      const u64 outer = (ra[j - wc - 1] + rb[j + wc]) - (ra[j + wc] + rb[j - wc - 1]);
+      const u64 guard = (rc[j - gc - 1] + rd[j + gc]) - (rc[j + gc] + rd[j - gc - 1]);
+      const float ts = f32_from_q((long long)(outer - guard)) * kthr;  // T in fixed-point units
+      th = ts * inv_s;
+      if constexpr (kMapCut) {
+        d = ld_map_val(map + (long long)r * P.ld_map + c, P.in_scale) > th ? 1 : 0;
+      } else {
+        const u64* r1 = S + g * pitch;
+        const u64* r0 = S + (g - 1) * pitch;
+        const u64 qc = (r1[j] + r0[j - 1]) - (r0[j] + r1[j - 1]);
+        d = f32_from_q((long long)qc) > ts ? 1 : 0;
+      }
+    }
+    P.det[(long long)r * P.ld_det + c] = d;
+    if (P.thr) P.thr[(long long)r * P.ld_thr + c] = th;
+  }
+  __syncthreads();
+  if (tid == 0 && s_bad && B.status) atomicOr(B.status, kStatusRange);
+}
+
 __global__ void __launch_bounds__(256) k_cfar_direct(const __grid_constant__ CfarMapDev P) {
   extern __shared__ __align__(16) float X[];
   const int local = (int)blockIdx.x;
@@ -591,6 +712,54 @@ cudaError_t launch_cfar_ring(const CfarBatch& b, bool map_cut, int dtype, int bl
   if (!map_cut) return launch_ring_t<false, float>(b, blocks, smem, s);
   return dtype == RCFAR_MAP_F16 ? launch_ring_t<true, __half>(b, blocks, smem, s)
                                 : launch_ring_t<true, float>(b, blocks, smem, s);
+}
+
+
+bool cfar_fused_plan(int rows, int cols, int wr, int wc, size_t smem_cap, int* run, int* bw, int* pitch,
+                     size_t* smem) {
+  const bool full = cols + 1 <= kFusedMaxCols;
+  const int w = full ? cols : kRingW;
+  const int cc = full ? cols + 1 : kRingW + 2 * wc + 1;
+  if (cc > kFusedMaxCols) return false;
+  const int p = (cc + 1) & ~1;
+  // runs short enough for about two CTAs per SM (the phases of one CTA run
+  // in sequence, so the map's parallelism comes from its CTA count), long
+  // enough to amortise the 2 wr + 1 halo rows; multiples of 8, <= 64, and
+  // the region must fit
+  const long long strips = (cols + w - 1) / w;
+  int r = (int)std::min<long long>(64, std::max<long long>(8, ((long long)rows * strips / (2 * 152) + 7) / 8 * 8));
+  while (r >= 8 && (size_t)(r + 2 * wr + 1) * p * 8 > smem_cap) r -= 8;
+  if (r < 8) return false;
+  *run = r;
+  *bw = w;
+  *pitch = p;
+  *smem = (size_t)(r + 2 * wr + 1) * p * 8;
+  return true;
+}
+
+int cfar_fused_geometry(CfarMapDev& P, int rows, int cols, int run, int bw, int pitch) {
+  P.run = run;
+  P.bw = bw;
+  P.bh = 0;
+  P.hcp = pitch;
+  P.tiles_x = (cols + bw - 1) / bw;
+  return P.tiles_x * ((rows + run - 1) / run);
+}
+
+template <bool kMapCut, typename InT>
+static cudaError_t launch_fused_t(const CfarBatch& b, int blocks, size_t smem, cudaStream_t s) {
+  auto fn = k_sat_cfar_fused<kMapCut, InT>;
+  cudaError_t e = ensure_smem(reinterpret_cast<const void*>(fn), smem);
+  if (e != cudaSuccess) return e;
+  fn<<<blocks, 256, smem, s>>>(b);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_cfar_fused(const CfarBatch& b, bool map_cut, int dtype, int blocks, size_t smem, cudaStream_t s) {
+  if (blocks <= 0) return cudaSuccess;
+  const bool h = dtype == RCFAR_MAP_F16;
+  if (map_cut) return h ? launch_fused_t<true, __half>(b, blocks, smem, s) : launch_fused_t<true, float>(b, blocks, smem, s);
+  return h ? launch_fused_t<false, __half>(b, blocks, smem, s) : launch_fused_t<false, float>(b, blocks, smem, s);
 }
 
 cudaError_t launch_cfar_direct(const CfarMapDev& m, int blocks, size_t smem, cudaStream_t s) {

@@ -178,7 +178,9 @@ struct CfarMapDev {
   int run;             // rows per CTA (a multiple of bh)
   int ring_rows;       // table rows held in shared memory (a power of two; streaming kernel: NS * kRingSR)
   int mode;            // rcfar_sat_mode of the table
-  int hcp;             // streaming kernel: u64 per ring row (strip + halo, even)
+  int hcp;             // streaming kernel: u64 per ring row (strip + halo, even); fused kernel: region row pitch
+  int sat_scale;       // fused kernel: fixed-point scale s of the quantisation (as the table's)
+  float bound;         // fused kernel: |value| bound checked per cell
 };
 
 struct CfarBatch {
@@ -263,6 +265,17 @@ size_t cfar_ring_smem(int ring_rows, int hcp);
 int cfar_ring_slots(size_t smem);  // resident CTAs of the streaming kernel on this device
 int cfar_ring_geometry(CfarMapDev& P, int rows, int cols, int ring_rows, int hcp, int slots);
 cudaError_t launch_cfar_ring(const CfarBatch& b, bool map_cut, int dtype, int blocks, size_t smem, cudaStream_t s);
+
+// Fused SAT + CFAR without a table in device memory: each CTA builds the
+// exact 64-bit integral image of its region (inner run x strip plus the
+// window halo) in shared memory and takes the eq. 4 lookups there. Strips
+// cover the whole width when it fits (cols + 1 <= kFusedMaxCols), else
+// kRingW columns plus halo. Returns false if no run fits shared memory.
+constexpr int kFusedMaxCols = 256;
+bool cfar_fused_plan(int rows, int cols, int wr, int wc, size_t smem_cap, int* run, int* bw, int* pitch,
+                     size_t* smem);
+int cfar_fused_geometry(CfarMapDev& P, int rows, int cols, int run, int bw, int pitch);
+cudaError_t launch_cfar_fused(const CfarBatch& b, bool map_cut, int dtype, int blocks, size_t smem, cudaStream_t s);
 size_t cfar_direct_smem_bytes(int bh, int bw, int wr, int wc);
 
 }  // namespace rcfar

@@ -497,7 +497,8 @@ def test_batch_tunings_give_identical_results(rc):
             outs.append((det, thr, mp))
         ref = None
         for t in [rc.make_batch_tuning(), rc.make_batch_tuning(1), rc.make_batch_tuning(8),
-                  rc.make_batch_tuning(2, rc.RCFAR_SAT_I64), rc.make_batch_tuning(0, rc.RCFAR_SAT_TILE_I64, (8, 32))]:
+                  rc.make_batch_tuning(2, rc.RCFAR_SAT_I64), rc.make_batch_tuning(0, rc.RCFAR_SAT_TILE_I64, (8, 32)),
+                  rc.make_batch_tuning(0, rc.RCFAR_SAT_FUSED)]:
             rc.rcfar_set_batch_tuning(h2, t)
             for d, th, mp in outs:
                 d.fill_(7)
@@ -512,7 +513,7 @@ def test_batch_tunings_give_identical_results(rc):
                 for (a, b, c_), (a2, b2, c2) in zip(ref, got):
                     assert torch.equal(a, a2) and torch.equal(b, b2) and torch.equal(c_, c2)
         best = rc.rcfar_tune_batch(h2, frames, params, reps=2)
-        assert best.candidates == 11 and best.best_ms > 0
+        assert best.candidates == 12 and best.best_ms > 0
         cur = rc.rcfar_get_batch_tuning(h2)
         assert (cur.dft_kblocks_per_cta, cur.sat_mode) == (best.dft_kblocks_per_cta, best.sat_mode)
         rc.rcfar_run_batch(h2, frames, params)
@@ -554,3 +555,37 @@ def test_trace_major_input(rc, h, M, N):
     assert map_err(P1.numpy(), P_o).max() <= REL
     cmp = ocfar.compare_decisions(d1.numpy(), res_o.det, P_o, res_o.thr, res_o.cut, margin=MARGIN)
     assert cmp.mismatches == 0, cmp
+
+
+@pytest.mark.parametrize("shape,win,cut", CFAR_CASES + [((300, 1030), (16, 16, 4, 4, 1e-6), (30, 1000))])
+@pytest.mark.parametrize("map_cut", [True, False])
+def test_fused_sat_cfar_equals_split(rc, h, shape, win, cut, map_cut):
+    # the fused kernel (no table in device memory, per-block integral images)
+    # gives exactly the split path's decisions and thresholds, on narrow maps
+    # (one strip) and wide ones (strips plus halo)
+    P = cfar_map(shape, seed=shape[0] + 7 * shape[1])
+    rows, cols = shape
+    lo, hi = cut if cut is not None else (0, cols - 1)
+    w = rc.make_window(*win)
+    bound = float(P.max())
+    Pt = dev_t(P)
+    view = rc.rcfar_sat(h, Pt, value_bound=bound, mode=rc.RCFAR_SAT_TILE_I64)
+    d1 = torch.full((rows, cols), 7, dtype=torch.uint8, device="cuda")
+    t1 = torch.full((rows, cols), -1.0, dtype=torch.float32, device="cuda")
+    rc.rcfar_cfar(h, view, Pt if map_cut else None, w, lo, hi, d1, t1)
+    d2 = torch.full((rows, cols), 7, dtype=torch.uint8, device="cuda")
+    t2 = torch.full((rows, cols), -1.0, dtype=torch.float32, device="cuda")
+    rc.rcfar_sat_cfar(h, Pt, bound, w, lo, hi, d2, t2, map_cut=map_cut)
+    assert rc.rcfar_get_error(h) == rc.RCFAR_OK
+    assert torch.equal(d1, d2) and torch.equal(t1, t2)
+    ref = ocfar.cfar_direct(P.astype(np.float64), *win, cut_cols=cut)
+    cmp = ocfar.compare_decisions(d2.cpu().numpy(), ref.det, P, ref.thr, ref.cut, margin=MARGIN)
+    assert cmp.mismatches == 0, cmp
+
+
+def test_fused_sat_cfar_range_error(rc, h):
+    P = torch.ones((64, 64), device="cuda")
+    P[10, 10] = 1e9
+    d = torch.empty((64, 64), dtype=torch.uint8, device="cuda")
+    rc.rcfar_sat_cfar(h, P, 100.0, rc.make_window(4, 4, 1, 1, 1e-3), 0, 63, d)
+    assert rc.rcfar_get_error(h) == rc.RCFAR_ERR_RANGE
