@@ -50,7 +50,7 @@ constexpr int kDftKB = 8;
 constexpr int kDftThreads = 384;  // warp 0 MMA, warps 1-7 producers, warps 8-11 drain
 // y pass: 8 rows (one per warp) x 256 samples per CTA.
 constexpr int kYRows = 8;
-constexpr int kYCols = 256;
+constexpr int kYCols = 512;
 
 struct PreFrameDev {
   const float* x;
