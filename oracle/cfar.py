@@ -244,3 +244,136 @@ def run_chain(X: np.ndarray, fs_hz: float, mean_len: int, train_r: int, train_c:
     P, band = preprocess_frame(X, fs_hz, mean_len, halo=train_c + guard_c)
     res = cfar_chain(P, band, train_r, train_c, guard_r, guard_c, pfa, method)
     return P, band, res
+
+
+# ---- greatest-of / smallest-of CFAR (next-step variants; not in the paper) ----
+#
+# Reading (recorded in the design notes): the training cells are split along
+# range into a leading half (the outer window's rows r - wr .. r - 1 minus the
+# guard rows r - gr .. r - 1) and a lagging half (rows r + 1 .. r + wr minus
+# r + 1 .. r + gr); the training cells of the CUT's own row belong to
+# neither. Each half holds n = wr (2 wc + 1) - gr (2 gc + 1) cells.
+# GO: T = t * max(S_lead, S_lag); SO: T = t * min(S_lead, S_lag), with t the
+# multiplier of the half SUM that gives the requested Pfa on iid exponential
+# (square-law) noise of any mean: for X, Y ~ Gamma(n, 1) independent and the
+# CUT ~ Exp(1), P(CUT > t min(X, Y)) = E[exp(-t min(X, Y))]
+#   = 2 sum_{k=0}^{n-1} C(n-1+k, k) (2 + t)^-(n+k)
+# and, with 1 - F of Gamma(n, 1) written as the tail of a Poisson sum,
+#   P(CUT > t max(X, Y)) = 2 sum_{k>=n} C(n-1+k, k) (2 + t)^-(n+k),
+# a series of positive terms (no cancellation); the two laws add up to
+# E[e^{-tX}] + E[e^{-tY}] = 2 (1 + t)^-n.
+
+GO, SO = "go", "so"
+
+
+def half_cells(train_r: int, train_c: int, guard_r: int, guard_c: int) -> int:
+    wr, wc = guard_r + train_r, guard_c + train_c
+    return wr * (2 * wc + 1) - guard_r * (2 * guard_c + 1)
+
+
+def _log_term(n: int, k: int, l2t: float) -> float:
+    from math import lgamma
+    return lgamma(n + k) - lgamma(k + 1) - lgamma(n) - (n + k) * l2t
+
+
+def pfa_smallest_of(t: float, n: int) -> float:
+    """P(CUT > t min(X, Y)) for CUT ~ Exp(1), X, Y ~ Gamma(n, 1)."""
+    if n <= 0 or t < 0:
+        raise ValueError("need n > 0 and t >= 0")
+    from math import exp, log
+    l2t = log(2.0 + t)
+    return 2.0 * sum(exp(_log_term(n, k, l2t)) for k in range(n))
+
+
+def pfa_greatest_of(t: float, n: int) -> float:
+    """P(CUT > t max(X, Y)): the series over k >= n, summed until its terms,
+    which shrink by (n + k) / ((k + 1)(2 + t)) < 1 from there on, are below
+    1e-18 of the total."""
+    if n <= 0 or t < 0:
+        raise ValueError("need n > 0 and t >= 0")
+    from math import exp, log
+    l2t = log(2.0 + t)
+    acc, k = 0.0, n
+    while True:
+        term = exp(_log_term(n, k, l2t))
+        acc += term
+        k += 1
+        if (n + k) < (k + 1) * (2.0 + t) and term <= 1e-18 * acc:
+            break
+    return 2.0 * acc
+
+
+def go_so_factor(kind: str, n: int, pfa: float) -> float:
+    """Multiplier t of the half sum for the requested Pfa (bisection in FP64;
+    both false-alarm laws decrease in t)."""
+    if kind not in (GO, SO) or n <= 0 or not (0.0 < pfa < 1.0):
+        raise ValueError("bad GO/SO request")
+    f = pfa_greatest_of if kind == GO else pfa_smallest_of
+    lo, hi = 0.0, 1.0
+    while f(hi, n) > pfa:
+        hi *= 2.0
+    for _ in range(200):
+        mid = 0.5 * (lo + hi)
+        if f(mid, n) > pfa:
+            lo = mid
+        else:
+            hi = mid
+        if hi - lo <= 1e-15 * hi:
+            break
+    return 0.5 * (lo + hi)
+
+
+def _halves_direct(P, rs, cs, train_r, train_c, guard_r, guard_c):
+    wr, wc = guard_r + train_r, guard_c + train_c
+    lead = np.zeros(rs.shape)
+    lag = np.zeros(rs.shape)
+    for dr in range(1, wr + 1):
+        for dc in range(-wc, wc + 1):
+            if dr <= guard_r and abs(dc) <= guard_c:
+                continue
+            lead += P[rs - dr, cs + dc]
+            lag += P[rs + dr, cs + dc]
+    return lead, lag
+
+
+def cfar_go_so_direct(P: np.ndarray, kind: str, train_r: int, train_c: int, guard_r: int, guard_c: int,
+                      pfa: float, cut_cols: Optional[Tuple[int, int]] = None) -> CfarResult:
+    """GO / SO CFAR with each half summed cell by cell (FP64)."""
+    P = np.asarray(P, dtype=np.float64)
+    n = half_cells(train_r, train_c, guard_r, guard_c)
+    t = go_so_factor(kind, n, pfa)
+    mask = _cut_mask(P.shape, train_r, train_c, guard_r, guard_c, cut_cols)
+    det = np.zeros(P.shape, dtype=np.uint8)
+    thr = np.zeros(P.shape, dtype=np.float64)
+    if not mask.any():
+        return CfarResult(det, thr, mask)
+    rs, cs = np.nonzero(mask)
+    lead, lag = _halves_direct(P, rs, cs, train_r, train_c, guard_r, guard_c)
+    T = t * (np.maximum(lead, lag) if kind == GO else np.minimum(lead, lag))
+    thr[rs, cs] = T
+    det[rs, cs] = (P[rs, cs] > T).astype(np.uint8)
+    return CfarResult(det, thr, mask)
+
+
+def cfar_go_so_sat(P: np.ndarray, kind: str, train_r: int, train_c: int, guard_r: int, guard_c: int,
+                   pfa: float, cut_cols: Optional[Tuple[int, int]] = None, S: Optional[np.ndarray] = None) -> CfarResult:
+    """GO / SO CFAR with each half from eq. 4 on the eq. 3 table: half =
+    A(outer rows of the half) - A(guard rows of the half)."""
+    P = np.asarray(P, dtype=np.float64)
+    if S is None:
+        S = sat(P)
+    wr, wc = guard_r + train_r, guard_c + train_c
+    n = half_cells(train_r, train_c, guard_r, guard_c)
+    t = go_so_factor(kind, n, pfa)
+    mask = _cut_mask(P.shape, train_r, train_c, guard_r, guard_c, cut_cols)
+    det = np.zeros(P.shape, dtype=np.uint8)
+    thr = np.zeros(P.shape, dtype=np.float64)
+    if not mask.any():
+        return CfarResult(det, thr, mask)
+    rs, cs = np.nonzero(mask)
+    lead = box_sum(S, rs - wr, rs - 1, cs - wc, cs + wc) - box_sum(S, rs - guard_r, rs - 1, cs - guard_c, cs + guard_c)
+    lag = box_sum(S, rs + 1, rs + wr, cs - wc, cs + wc) - box_sum(S, rs + 1, rs + guard_r, cs - guard_c, cs + guard_c)
+    T = t * (np.maximum(lead, lag) if kind == GO else np.minimum(lead, lag))
+    thr[rs, cs] = T
+    det[rs, cs] = (P[rs, cs] > T).astype(np.uint8)
+    return CfarResult(det, thr, mask)

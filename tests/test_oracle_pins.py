@@ -320,3 +320,124 @@ def test_row_zscore_chain_is_scale_invariant():
     np.testing.assert_allclose(P2, P1, rtol=1e-10, atol=1e-12)
     with pytest.raises(ValueError):
         oracle.preprocess_frame(X, synth.FS_HZ, 5, detector="log")
+
+
+# ------------------------------------------------------------ greatest-of / smallest-of CFAR
+def _law_by_quadrature(t, n, kind):
+    # E[exp(-t Z)], Z = min or max of two iid Gamma(n, 1), from the order
+    # statistic densities 2 f (1 - F) and 2 f F, integrated numerically.
+    from scipy import integrate, stats
+    g = stats.gamma(n)
+    if kind == ocfar.SO:
+        dens = lambda x: 2.0 * g.pdf(x) * g.sf(x)
+    else:
+        dens = lambda x: 2.0 * g.pdf(x) * g.cdf(x)
+    val, _ = integrate.quad(lambda x: math.exp(-t * x) * dens(x), 0.0, np.inf, limit=400, epsabs=0, epsrel=1e-11)
+    return val
+
+
+@pytest.mark.parametrize("n", [1, 3, 12, 40])
+def test_go_so_law_matches_quadrature(n):
+    pytest.importorskip("scipy")
+    for t in (0.05, 0.3, 1.0, 4.0):
+        so = ocfar.pfa_smallest_of(t, n)
+        go = ocfar.pfa_greatest_of(t, n)
+        assert abs(so - _law_by_quadrature(t, n, ocfar.SO)) <= 1e-8 * so + 1e-300
+        assert abs(go - _law_by_quadrature(t, n, ocfar.GO)) <= 1e-8 * go + 1e-300
+        assert go < so  # the larger half sum gives the higher threshold
+
+
+def test_go_so_factor_inverts_law_and_limits():
+    for n, pfa in [(1, 1e-2), (20, 1e-3), (112, 1e-4), (800, 1e-6)]:
+        tg = ocfar.go_so_factor(ocfar.GO, n, pfa)
+        ts = ocfar.go_so_factor(ocfar.SO, n, pfa)
+        assert abs(ocfar.pfa_greatest_of(tg, n) - pfa) <= 1e-10 * pfa
+        assert abs(ocfar.pfa_smallest_of(ts, n) - pfa) <= 1e-10 * pfa
+        assert ts > tg > 0
+    # n = 1: min of two Exp(1) is Exp(2), so P_SO = 2 / (2 + t) and t = 2 / pfa - 2
+    assert abs(ocfar.go_so_factor(ocfar.SO, 1, 0.01) - 198.0) < 1e-9
+    # many cells: min, max and the mean of each half concentrate at n, so
+    # n t -> -ln(pfa), the cell-averaging limit
+    for kind in (ocfar.GO, ocfar.SO):
+        nt = 4000 * ocfar.go_so_factor(kind, 4000, 1e-3)
+        assert abs(nt - (-math.log(1e-3))) < 0.05 * -math.log(1e-3)
+    # the two halves plus the CUT row's 2 T_c training cells make up the ring
+    for tr, tc, gr, gc in [(4, 4, 1, 1), (3, 5, 1, 2), (16, 16, 4, 4), (2, 7, 0, 3)]:
+        assert 2 * ocfar.half_cells(tr, tc, gr, gc) + 2 * tc == ocfar.n_ref(tr, tc, gr, gc)
+    assert ocfar.half_cells(3, 5, 1, 2) == 4 * 15 - 1 * 5
+
+
+def test_go_so_halves_by_hand():
+    # 9 x 9 map, one interior CUT at (4, 4) with train 2 / guard 1 on both axes
+    # (outer half-sizes 3): cells in the CUT's row never count; a cell in rows
+    # 1..3 outside the guard box counts in the leading half only.
+    tr, gd = 2, 1
+    t_go = ocfar.go_so_factor(ocfar.GO, ocfar.half_cells(tr, tr, gd, gd), 1e-3)
+    for kind in (ocfar.GO, ocfar.SO):
+        P = np.zeros((7, 7))
+        P[3, 3] = 1e-30
+        P[3, 0] = 5.0  # CUT row training cell: in neither half
+        for fn in (ocfar.cfar_go_so_direct, ocfar.cfar_go_so_sat):
+            res = fn(P, kind, tr, tr, gd, gd, 1e-3)
+            assert res.cut.sum() == 1 and res.thr[3, 3] == 0.0 and res.det[3, 3] == 1
+        P[1, 3] = 2.0  # leading half, outside the guard rows
+        P[2, 3] = 100.0  # inside the guard box: ignored
+        P[6, 6] = 0.5  # lagging half corner
+        for fn in (ocfar.cfar_go_so_direct, ocfar.cfar_go_so_sat):
+            res = fn(P, kind, tr, tr, gd, gd, 1e-3)
+            want = 2.0 if kind == ocfar.GO else 0.5
+            t = ocfar.go_so_factor(kind, ocfar.half_cells(tr, tr, gd, gd), 1e-3)
+            assert abs(res.thr[3, 3] - t * want) <= 1e-12 * t * want
+    assert t_go > 0
+
+
+def test_go_so_direct_equals_sat_random_maps():
+    rng = np.random.default_rng(21)
+    for kind in (ocfar.GO, ocfar.SO):
+        for shape, win in [((40, 50), (3, 2, 1, 2, 1e-2)), ((64, 31), (8, 8, 2, 2, 1e-4)),
+                           ((25, 25), (4, 4, 0, 0, 1e-1))]:
+            P = rng.exponential(size=shape)
+            P[rng.integers(0, shape[0], 5), rng.integers(0, shape[1], 5)] += 30
+            d = ocfar.cfar_go_so_direct(P, kind, *win)
+            s = ocfar.cfar_go_so_sat(P, kind, *win)
+            np.testing.assert_allclose(s.thr, d.thr, rtol=1e-12, atol=1e-12)
+            cmp = ocfar.compare_decisions(s.det, d.det, P, d.thr, d.cut, margin=1e-9)
+            assert cmp.mismatches == 0
+            base = s.det
+            np.testing.assert_array_equal(ocfar.cfar_go_so_sat(P * 2.0 ** 9, kind, *win).det, base)
+
+
+def test_go_so_clutter_edge_behaviour():
+    # A step in the noise level along rows: GO takes the noisier half, so its
+    # threshold is never below the cell-averaging one near the edge and it
+    # raises no more alarms there. SO takes the quieter half, so a target
+    # beside a strong interferer in one half stays detected where cell
+    # averaging loses it.
+    rng = np.random.default_rng(22)
+    P = rng.exponential(size=(80, 60))
+    P[40:] *= 100.0
+    go = ocfar.cfar_go_so_sat(P, ocfar.GO, 6, 6, 1, 1, 1e-3)
+    ca = ocfar.cfar_sat(P, 6, 6, 1, 1, 1e-3)
+    assert go.det.sum() <= ca.det.sum()
+    Q = rng.exponential(size=(60, 60))
+    Q[30, 30] += 60.0
+    Q[33, 27:34] += 4000.0  # interferer inside the lagging half only
+    so = ocfar.cfar_go_so_sat(Q, ocfar.SO, 6, 6, 1, 1, 1e-4)
+    ca = ocfar.cfar_sat(Q, 6, 6, 1, 1, 1e-4)
+    assert so.det[30, 30] == 1 and ca.det[30, 30] == 0
+
+
+@pytest.mark.parametrize("kind", ["go", "so"])
+def test_go_so_monte_carlo_false_alarm_rate(kind):
+    # Disjoint windows on an iid Exp(1) map: independent Bernoulli(Pfa) CUTs.
+    pfa, shape, (tr, tc, gr, gc) = 1e-2, (2200, 2200), (4, 4, 1, 1)
+    P = synth.square_law_map(*shape, n_targets=0, seed=23).astype(np.float64)
+    res = ocfar.cfar_go_so_sat(P, kind, tr, tc, gr, gc, pfa)
+    w = tr + gr
+    stride = 2 * w + 1
+    sel = res.det[w:shape[0] - w:stride, w:shape[1] - w:stride]
+    n = sel.size
+    k = int(sel.sum())
+    mu = n * pfa
+    sd = math.sqrt(n * pfa * (1 - pfa))
+    assert abs(k - mu) < 5 * sd, (k, mu, sd)
