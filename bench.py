@@ -470,6 +470,31 @@ def ours(args, rank, world, local, dist):
     value = world * args.steps / (ms_max / 1e3)
     assert rc.rcfar_get_error(h) == rc.RCFAR_OK
 
+    def graph_rate(fn):
+        """frames/s of fn(i) captured as one CUDA graph per ring slot and replayed."""
+        for i in range(3):
+            fn(i)
+        torch.cuda.synchronize()
+        gv = []
+        with torch.cuda.stream(stream):
+            for i in range(RING):
+                g = torch.cuda.CUDAGraph()
+                with torch.cuda.graph(g, stream=stream):
+                    fn(i)
+                gv.append(g)
+        torch.cuda.synchronize()
+        for i in range(3):
+            gv[i % RING].replay()
+        torch.cuda.synchronize()
+        nv = max(10, args.steps // 2)
+        e0.record()
+        for i in range(nv):
+            gv[i % RING].replay()
+        e1.record()
+        torch.cuda.synchronize()
+        assert rc.rcfar_get_error(h) == rc.RCFAR_OK
+        return {"frames_per_s": nv / (e0.elapsed_time(e1) / 1e3)}
+
     # the chain with the square-law detector and with per-range-bin z-score
     # normalisation (the next-step variants), captured and timed the same way
     variants = {}
@@ -483,29 +508,18 @@ def ours(args, rank, world, local, dist):
             rc.rcfar_preprocess(h, x, pv, P)
             rc.rcfar_sat_cfar(h, P, bv.value_bound, win, cut_lo, cut_hi, det, map_cut=False)
 
-        for i in range(3):
-            chain_v(i)
-        torch.cuda.synchronize()
-        gv = []
-        with torch.cuda.stream(stream):
-            for i in range(RING):
-                g = torch.cuda.CUDAGraph()
-                with torch.cuda.graph(g, stream=stream):
-                    chain_v(i)
-                gv.append(g)
-        torch.cuda.synchronize()
-        for i in range(3):
-            gv[i % RING].replay()
-        torch.cuda.synchronize()
-        nv = max(10, args.steps // 2)
-        e0.record()
-        for i in range(nv):
-            gv[i % RING].replay()
-        e1.record()
-        torch.cuda.synchronize()
-        variants[vname] = {"frames_per_s": nv / (e0.elapsed_time(e1) / 1e3)}
-        assert rc.rcfar_get_error(h) == rc.RCFAR_OK
-        del gv
+        variants[vname] = graph_rate(chain_v)
+
+    # greatest-of / smallest-of thresholds on the same chain
+    for vname, kind in (("greatest_of", rc.RCFAR_CFAR_GO), ("smallest_of", rc.RCFAR_CFAR_SO)):
+        wk = rc.make_window(w.train_r, w.train_c, w.guard_r, w.guard_c, w.pfa, kind=kind)
+
+        def chain_k(i, wk=wk):
+            x, P, det = frames[i % RING], maps[i % RING], dets[i % RING]
+            rc.rcfar_preprocess(h, x, params, P)
+            rc.rcfar_sat_cfar(h, P, band.value_bound, wk, cut_lo, cut_hi, det, map_cut=False)
+
+        variants[vname] = graph_rate(chain_k)
 
     # the paper's own frame size, 600 traces of 1024 range samples, given trace
     # by trace ([N][M], the acquisition order)
@@ -524,29 +538,7 @@ def ours(args, rank, world, local, dist):
         rc.rcfar_sat_cfar(h, maps_p[i % RING], bp.value_bound, win, bp.k_lo - bp.c0, bp.k_hi - bp.c0,
                           dets_p[i % RING], map_cut=False)
 
-    for i in range(3):
-        chain_p(i)
-    torch.cuda.synchronize()
-    gp = []
-    with torch.cuda.stream(stream):
-        for i in range(RING):
-            g = torch.cuda.CUDAGraph()
-            with torch.cuda.graph(g, stream=stream):
-                chain_p(i)
-            gp.append(g)
-    torch.cuda.synchronize()
-    for i in range(3):
-        gp[i % RING].replay()
-    torch.cuda.synchronize()
-    nv = max(10, args.steps // 2)
-    e0.record()
-    for i in range(nv):
-        gp[i % RING].replay()
-    e1.record()
-    torch.cuda.synchronize()
-    variants["paper_frame_1024x600_trace_major"] = {"frames_per_s": nv / (e0.elapsed_time(e1) / 1e3)}
-    assert rc.rcfar_get_error(h) == rc.RCFAR_OK
-    del gp
+    variants["paper_frame_1024x600_trace_major"] = graph_rate(chain_p)
 
     # per-kernel device times (eager launches bracketed by CUDA events)
     rc.rcfar_trace_enable(h, True)
@@ -677,6 +669,24 @@ def ours(args, rank, world, local, dist):
         fms = e0.elapsed_time(e1) / reps
         sat_cfar["fused"] = {"value": cells / (fms * 1e-3) / 1e9, "unit": "Gcells/s", "ms": fms,
                              "hbm_bytes_per_cell": 5, "decisions_identical": bool(torch.equal(detf, detm))}
+        assert rc.rcfar_get_error(h) == rc.RCFAR_OK
+        # greatest-of thresholds on the same table path (16 lookups per CUT instead of 8)
+        wg = rc.make_window(16, 16, 4, 4, 1e-6, kind=rc.RCFAR_CFAR_GO)
+
+        def satcfar_go():
+            v = rc.rcfar_sat(h, Pm, value_bound=bound, mode=rc.RCFAR_SAT_I64)
+            rc.rcfar_cfar(h, v, Pm, wg, 0, R - 1, detf)
+
+        for _ in range(3):
+            satcfar_go()
+        torch.cuda.synchronize()
+        e0.record()
+        for _ in range(reps):
+            satcfar_go()
+        e1.record()
+        torch.cuda.synchronize()
+        gms = e0.elapsed_time(e1) / reps
+        sat_cfar["greatest_of"] = {"value": cells / (gms * 1e-3) / 1e9, "unit": "Gcells/s", "ms": gms}
         assert rc.rcfar_get_error(h) == rc.RCFAR_OK
 
     batch = None

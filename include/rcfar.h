@@ -133,13 +133,34 @@ typedef struct rcfar_band {
   float value_bound;  /* every map value is <= this: N, or N^2 for the square law (for rcfar_sat) */
 } rcfar_band;
 
+/* How the reference cells set the threshold.
+ * CA: cell averaging (Sec. II.B, eqs. 1-2): T = (alpha / n_ref) S_ref over
+ *     the whole training ring, alpha = n_ref (Pfa^(-1/n_ref) - 1).
+ * GO / SO (greatest-of / smallest-of; not in the paper, built on the same
+ *     eq. 3 table and eq. 4 lookups): the training ring is split along range
+ *     into a leading half (rows r - W_r .. r - 1 without the guard rows
+ *     r - guard_r .. r - 1) and a lagging half (rows r + 1 .. r + W_r without
+ *     r + 1 .. r + guard_r); the training cells in the CUT's own row belong to
+ *     neither. Each half has n = W_r (2 W_c + 1) - guard_r (2 guard_c + 1)
+ *     cells, and T = t * max (GO) or t * min (SO) of the two half sums, with t
+ *     the factor for which iid exponential noise gives false-alarm
+ *     probability exactly Pfa (rcfar_threshold_factor). */
+typedef enum rcfar_cfar_kind {
+  RCFAR_CFAR_CA = 0,
+  RCFAR_CFAR_GO = 1,
+  RCFAR_CFAR_SO = 2
+} rcfar_cfar_kind;
+
 /* CFAR window (Sec. II.B): per-side counts in each dimension. The guard
  * rectangle [r-guard_r, r+guard_r] x [c-guard_c, c+guard_c] contains the CUT;
- * training cells fill the ring out to half-sizes guard+train. */
+ * training cells fill the ring out to half-sizes guard+train
+ * (W_r = guard_r + train_r, W_c = guard_c + train_c). */
 typedef struct rcfar_window {
   int32_t train_r, train_c;
   int32_t guard_r, guard_c;
-  double pfa; /* false-alarm probability, 0 < pfa < 1 */
+  double pfa;       /* false-alarm probability, 0 < pfa < 1 */
+  int32_t kind;     /* rcfar_cfar_kind (0: cell averaging) */
+  int32_t reserved; /* must be 0 */
 } rcfar_window;
 
 /* Description of a summed-area table produced by rcfar_sat. The arrays live
@@ -188,6 +209,13 @@ rcfar_status rcfar_destroy(rcfar_handle h);
 rcfar_status rcfar_alpha(int32_t n_ref, double pfa, double* alpha_out);
 /* n_ref = (2(g_r+t_r)+1)(2(g_c+t_c)+1) - (2g_r+1)(2g_c+1) (Sec. II.B "N"). */
 rcfar_status rcfar_n_ref(const rcfar_window* w, int32_t* n_ref_out);
+/* The factor the kernels multiply the reference statistic by, computed on the
+ * host in FP64: CA: alpha / n_ref (applied to S_ref); GO / SO: t (applied to
+ * the larger / smaller half sum), found by bisection on the false-alarm law
+ * of the kind (relative accuracy 1e-13). cells_out (may be NULL): n_ref for
+ * CA, the cells of one half for GO / SO. An invalid window (including a GO /
+ * SO window with empty halves) is RCFAR_ERR_INVALID_ARG. */
+rcfar_status rcfar_threshold_factor(const rcfar_window* w, double* factor_out, int32_t* cells_out);
 /* Respiration band of a length-N slow-time transform (Sec. II.A, 0.3-0.8 Hz):
  * k_lo = ceil(f_lo N / fs), k_hi = floor(f_hi N / fs) (inclusive; values
  * within 1e-9 of an integer count as that integer), c0 = max(0, k_lo - halo_c),
@@ -235,7 +263,10 @@ rcfar_status rcfar_sat(rcfar_handle h, const void* map, int32_t dtype, int32_t m
  * table lookups A = L1 + L4 - (L2 + L3); T = alpha * S_ref / n_ref;
  * det = 1 (H1) iff CUT > T (CUT == T decides H0). Every other cell gets
  * det = 0 and thr = 0. det is uint8 [rows][ld_det]; thr (optional, NULL) is
- * float [rows][ld_thr]. Zero interior CUTs is valid (all-zero det). */
+ * float [rows][ld_thr]. Zero interior CUTs is valid (all-zero det).
+ * GO / SO windows (w->kind): each half sum is A(rows of the half, outer
+ * columns) - A(its guard rows, guard columns), from the same table rows, and
+ * T = t * max or min of the two; every table mode supports them. */
 rcfar_status rcfar_cfar(rcfar_handle h, const rcfar_sat_view* view, const void* map, int32_t dtype,
                         int32_t map_exp2, int64_t ld_map, const rcfar_window* w, int32_t cut_c_lo,
                         int32_t cut_c_hi, uint8_t* det, int64_t ld_det, float* thr, int64_t ld_thr,

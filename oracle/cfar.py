@@ -231,9 +231,13 @@ def compare_decisions(det: np.ndarray, det_ref: np.ndarray, P_ref: np.ndarray, t
 
 
 def cfar_chain(P: np.ndarray, band, train_r: int, train_c: int, guard_r: int, guard_c: int, pfa: float,
-               method: str = "sat") -> CfarResult:
-    """CFAR on a band map: CUT columns restricted to the respiration band bins."""
+               method: str = "sat", kind: str = "ca") -> CfarResult:
+    """CFAR on a band map: CUT columns restricted to the respiration band bins.
+    kind: "ca" (Sec. II.B) or the greatest-of / smallest-of variants "go", "so"."""
     cut_cols = (band.k_lo - band.c0, band.k_hi - band.c0)
+    if kind != "ca":
+        fn = cfar_go_so_sat if method == "sat" else cfar_go_so_direct
+        return fn(P, kind, train_r, train_c, guard_r, guard_c, pfa, cut_cols=cut_cols)
     fn = cfar_sat if method == "sat" else cfar_direct
     return fn(P, train_r, train_c, guard_r, guard_c, pfa, cut_cols=cut_cols)
 

@@ -37,6 +37,9 @@ RCFAR_NORM_GLOBAL_MAX = 0
 RCFAR_NORM_ROW_ZSCORE = 1
 RCFAR_X_RANGE_MAJOR = 0
 RCFAR_X_TRACE_MAJOR = 1
+RCFAR_CFAR_CA = 0
+RCFAR_CFAR_GO = 1
+RCFAR_CFAR_SO = 2
 
 SAT_TILE_H = 32
 SAT_TILE_W = 128
@@ -50,6 +53,7 @@ EXPORTS = (
     "rcfar_server_create", "rcfar_server_submit", "rcfar_server_prepare", "rcfar_server_poll", "rcfar_server_get_stats",
     "rcfar_server_now_ns", "rcfar_server_destroy", "rcfar_selftest_wait",
     "rcfar_tune_batch", "rcfar_set_batch_tuning", "rcfar_get_batch_tuning", "rcfar_sat_cfar",
+    "rcfar_threshold_factor",
 )
 
 
@@ -79,7 +83,8 @@ class rcfar_band(ctypes.Structure):
 
 class rcfar_window(ctypes.Structure):
     _fields_ = [("train_r", ctypes.c_int32), ("train_c", ctypes.c_int32), ("guard_r", ctypes.c_int32),
-                ("guard_c", ctypes.c_int32), ("pfa", ctypes.c_double)]
+                ("guard_c", ctypes.c_int32), ("pfa", ctypes.c_double), ("kind", ctypes.c_int32),
+                ("reserved", ctypes.c_int32)]
 
 
 class rcfar_sat_view(ctypes.Structure):
@@ -146,6 +151,7 @@ def lib() -> ctypes.CDLL:
             "rcfar_destroy": [P],
             "rcfar_alpha": [I32, F64, ctypes.POINTER(F64)],
             "rcfar_n_ref": [ctypes.POINTER(rcfar_window), ctypes.POINTER(I32)],
+            "rcfar_threshold_factor": [ctypes.POINTER(rcfar_window), ctypes.POINTER(F64), ctypes.POINTER(I32)],
             "rcfar_band_plan": [I32, ctypes.POINTER(rcfar_pre_params), ctypes.POINTER(rcfar_band)],
             "rcfar_sat_scale": [F32, I64, ctypes.POINTER(I32)],
             "rcfar_status_string": [ctypes.c_int],
@@ -220,8 +226,9 @@ def _ld(t) -> int:
     return int(t.stride(0))
 
 
-def make_window(train_r, train_c, guard_r, guard_c, pfa) -> rcfar_window:
-    return rcfar_window(int(train_r), int(train_c), int(guard_r), int(guard_c), float(pfa))
+def make_window(train_r, train_c, guard_r, guard_c, pfa, kind=RCFAR_CFAR_CA) -> rcfar_window:
+    """kind: RCFAR_CFAR_CA (cell averaging), RCFAR_CFAR_GO or RCFAR_CFAR_SO."""
+    return rcfar_window(int(train_r), int(train_c), int(guard_r), int(guard_c), float(pfa), int(kind), 0)
 
 
 def make_pre_params(fs_hz=20.0, f_lo_hz=0.3, f_hi_hz=0.8, mean_len=5, halo_c=0, detector=0,
@@ -243,6 +250,16 @@ def rcfar_n_ref(window: rcfar_window) -> int:
     out = ctypes.c_int32()
     _check(lib().rcfar_n_ref(ctypes.byref(window), ctypes.byref(out)), "rcfar_n_ref")
     return out.value
+
+
+def rcfar_threshold_factor(window: rcfar_window):
+    """(factor, cells): alpha / n_ref and n_ref for cell averaging; the
+    half-sum factor t and the cells of one half for greatest-of / smallest-of."""
+    f = ctypes.c_double()
+    n = ctypes.c_int32()
+    _check(lib().rcfar_threshold_factor(ctypes.byref(window), ctypes.byref(f), ctypes.byref(n)),
+           "rcfar_threshold_factor")
+    return f.value, n.value
 
 
 def rcfar_band_plan(N: int, params: rcfar_pre_params) -> rcfar_band:

@@ -313,12 +313,106 @@ struct DeviceGuard {
 
 bool valid_window(const rcfar_window* w) {
   return w && w->train_r >= 0 && w->train_c >= 0 && w->guard_r >= 0 && w->guard_c >= 0 &&
-         w->pfa > 0.0 && w->pfa < 1.0 && n_ref_of(*w) > 0;
+         w->pfa > 0.0 && w->pfa < 1.0 && n_ref_of(*w) > 0 && w->reserved == 0 &&
+         (w->kind == RCFAR_CFAR_CA ||
+          ((w->kind == RCFAR_CFAR_GO || w->kind == RCFAR_CFAR_SO) &&
+           (long long)(w->guard_r + w->train_r) * (2LL * (w->guard_c + w->train_c) + 1) -
+                   (long long)w->guard_r * (2LL * w->guard_c + 1) > 0));
 }
 
 }  // namespace
 
 static double alpha_of(int n_ref, double pfa) { return (double)n_ref * (std::pow(pfa, -1.0 / (double)n_ref) - 1.0); }
+
+// Greatest-of / smallest-of false-alarm laws on iid exponential noise. The
+// half sums X, Y are Gamma(n, 1) and the CUT Exp(1), so P(CUT > t Z) =
+// E[exp(-t Z)] for Z = min(X, Y) or max(X, Y). Writing the Gamma(n, 1)
+// distribution function as a Poisson tail and integrating term by term gives
+// 2 sum_k u_k with u_k = C(n-1+k, k) (2+t)^-(n+k): the terms k < n make the
+// smallest-of law, the terms k >= n the greatest-of law. The terms follow
+// u_{k+1} = u_k (n+k) / ((k+1)(2+t)) from u_0 = (2+t)^-n; they are summed
+// relative to u_0 with a running rescale (they can span thousands of decades)
+// until they shrink below 1e-18 of the tail sum, and the laws are returned
+// as natural logarithms.
+static void go_so_log_laws(int n, double t, double* log_so, double* log_go) {
+  const double q = 2.0 + t;
+  double u = 1.0, lo = 0.0, hi = 0.0, shift = -(double)n * std::log(q);
+  constexpr double kBig = 1e250, kSmall = 1e-250;
+  for (long long k = 0;; ++k) {
+    if (k < n) lo += u; else hi += u;
+    const double ratio = (double)(n + k) / ((double)(k + 1) * q);
+    if (k >= n && ratio < 1.0 && u <= 1e-18 * hi) break;
+    u *= ratio;
+    if (u > kBig) {
+      u *= kSmall;
+      lo *= kSmall;
+      hi *= kSmall;
+      shift -= std::log(kSmall);
+    }
+  }
+  const double l2 = std::log(2.0) + shift;
+  *log_so = lo > 0.0 ? std::log(lo) + l2 : -INFINITY;
+  *log_go = hi > 0.0 ? std::log(hi) + l2 : -INFINITY;
+}
+
+// t with law(t) = pfa by bisection: both laws fall from 1 (t = 0) to 0.
+static double go_so_factor_of(int kind, int n, double pfa) {
+  const double target = std::log(pfa);
+  auto law = [&](double t) {
+    double a, b;
+    go_so_log_laws(n, t, &a, &b);
+    return kind == RCFAR_CFAR_SO ? a : b;
+  };
+  double lo = 0.0, hi = 1.0;
+  while (law(hi) > target && hi < 1e300) hi *= 2.0;
+  for (int it = 0; it < 200 && hi - lo > 1e-14 * hi; ++it) {
+    const double mid = 0.5 * (lo + hi);
+    if (law(mid) > target) lo = mid; else hi = mid;
+  }
+  return 0.5 * (lo + hi);
+}
+
+static long long half_cells_of(const rcfar_window& w) {
+  const long long wr = w.guard_r + w.train_r, wc = w.guard_c + w.train_c;
+  return wr * (2 * wc + 1) - (long long)w.guard_r * (2LL * w.guard_c + 1);
+}
+
+namespace rcfar {
+bool window_factor(const rcfar_window& w, double* factor, int* cells) {
+  if (w.train_r < 0 || w.train_c < 0 || w.guard_r < 0 || w.guard_c < 0 || !(w.pfa > 0.0 && w.pfa < 1.0) ||
+      w.reserved != 0)
+    return false;
+  if (w.kind == RCFAR_CFAR_CA) {
+    const int nr = n_ref_of(w);
+    if (nr <= 0) return false;
+    *factor = alpha_of(nr, w.pfa) / (double)nr;
+    if (cells) *cells = nr;
+    return true;
+  }
+  if (w.kind != RCFAR_CFAR_GO && w.kind != RCFAR_CFAR_SO) return false;
+  const long long n = half_cells_of(w);
+  if (n <= 0 || n > (1 << 24)) return false;
+  // the bisection costs up to a few hundred microseconds for large windows;
+  // batches and servers ask for the same few windows again and again
+  struct Entry {
+    int kind, n;
+    double pfa, factor;
+  };
+  static thread_local Entry cache[8] = {};
+  static thread_local int next = 0;
+  double f = -1.0;
+  for (const Entry& e : cache)
+    if (e.n == (int)n && e.kind == w.kind && e.pfa == w.pfa) f = e.factor;
+  if (f < 0.0) {
+    f = go_so_factor_of(w.kind, (int)n, w.pfa);
+    cache[next] = Entry{w.kind, (int)n, w.pfa, f};
+    next = (next + 1) % 8;
+  }
+  *factor = f;
+  if (cells) *cells = (int)n;
+  return true;
+}
+}  // namespace rcfar
 
 static bool band_of(int N, const rcfar_pre_params* p, rcfar_band* b) {
   if (!p || N <= 0 || !(p->fs_hz > 0.0) || !(p->f_lo_hz >= 0.0) || !(p->f_hi_hz >= p->f_lo_hz) || p->halo_c < 0)
@@ -497,6 +591,14 @@ rcfar_status rcfar_n_ref(const rcfar_window* w, int32_t* n_ref_out) {
   if (!w || !n_ref_out || w->train_r < 0 || w->train_c < 0 || w->guard_r < 0 || w->guard_c < 0)
     return RCFAR_ERR_INVALID_ARG;
   *n_ref_out = n_ref_of(*w);
+  return RCFAR_OK;
+}
+
+rcfar_status rcfar_threshold_factor(const rcfar_window* w, double* factor_out, int32_t* cells_out) {
+  if (!w || !factor_out || !valid_window(w)) return RCFAR_ERR_INVALID_ARG;
+  int cells = 0;
+  if (!window_factor(*w, factor_out, &cells)) return RCFAR_ERR_INVALID_ARG;
+  if (cells_out) *cells_out = cells;
   return RCFAR_OK;
 }
 
@@ -849,8 +951,10 @@ static void fill_cfar_window(CfarMapDev& P, const rcfar_window* w, int rows, int
   P.wc = w->guard_c + w->train_c;
   P.gr = w->guard_r;
   P.gc = w->guard_c;
-  const int nr = n_ref_of(*w);
-  P.kthr = (float)(alpha_of(nr, w->pfa) / (double)nr);
+  double k = 0.0;
+  window_factor(*w, &k, nullptr);  // the window was validated
+  P.kthr = (float)k;
+  P.kind = w->kind;
   P.row_lo = P.wr;
   P.row_hi = rows - 1 - P.wr;
   P.cut_lo = std::max(P.wc, cut_c_lo);

@@ -51,6 +51,29 @@ table_value(const CfarMapDev& P, int r, int c, float scalef) {
   }
 }
 
+// Sum over table rows (top, bot] and the columns within w of the CUT's
+// column, by eq. 4; both pointers are at the CUT's column.
+template <typename SV>
+__device__ __forceinline__ SV box_rows(const SV* top, const SV* bot, int w) {
+  return (top[-w - 1] + bot[w]) - (top[w] + bot[-w - 1]);
+}
+__device__ __forceinline__ bool sv_greater(u64 a, u64 b) { return (long long)a > (long long)b; }
+__device__ __forceinline__ bool sv_greater(float a, float b) { return a > b; }
+
+// Greatest-of / smallest-of statistic: the larger (greatest) or smaller of
+// the leading half (rows r - wr .. r - 1 minus the guard rows r - gr .. r - 1
+// within gc columns) and the lagging half (rows r + 1 .. r + wr minus
+// r + 1 .. r + gr). Row pointers at the CUT's column: ra = r - wr - 1,
+// r0 = r - 1, rc = r - gr - 1 (leading); r1 = r, rd = r + gr, rb = r + wr
+// (lagging). With gr = 0 the guard boxes are empty (rc = r0, rd = r1).
+template <typename SV>
+__device__ __forceinline__ SV go_so_stat(bool greatest, const SV* ra, const SV* rb, const SV* rc, const SV* rd,
+                                         const SV* r1, const SV* r0, int wc, int gc) {
+  const SV lead = box_rows(ra, r0, wc) - box_rows(rc, r0, gc);
+  const SV lag = box_rows(r1, rb, wc) - box_rows(r1, rd, gc);
+  return sv_greater(lead, lag) == greatest ? lead : lag;
+}
+
 // SAT CFAR over a strip of bw columns and a run of rows (P.bh CUT rows per
 // step, P.run rows per CTA). The table rows the lookups need live in a ring
 // of ring_rows (a power of two >= bh + 2 wr + 1) rows of HC = bw + 2 wc + 1
@@ -119,6 +142,7 @@ __global__ void __launch_bounds__(256) k_cfar(const __grid_constant__ CfarBatch 
   const bool col_cut = col_ok && c >= P.cut_lo && c <= P.cut_hi;
   const int ca = cc, cb = cc + 2 * wc + 1, cg = cc + wc - gc, cd = cc + wc + gc + 1, cm = cc + wc + 1;
   const float kthr = P.kthr;
+  const int kind = P.kind;
   const float kk = kthr * ldexpf(1.0f, -s);
   const float inv_s = ldexpf(1.0f, -s);
   const InT* map = reinterpret_cast<const InT*>(P.map);
@@ -155,10 +179,17 @@ __global__ void __launch_bounds__(256) k_cfar(const __grid_constant__ CfarBatch 
         const SV* Sb = S + ((g + wr) & rmask) * HC;       // row r + wr
         const SV* Sc = S + ((g - gr - 1) & rmask) * HC;   // row r - gr - 1
         const SV* Sd = S + ((g + gr) & rmask) * HC;       // row r + gr
-        // eq. 4: A = L1 + L4 - (L2 + L3) for the outer and the guard rectangle
-        const SV outer = (Sa[ca] + Sb[cb]) - (Sa[cb] + Sb[ca]);
-        const SV guard = (Sc[cg] + Sd[cd]) - (Sc[cd] + Sd[cg]);
-        const SV ref = outer - guard;
+        SV ref;
+        if (kind == RCFAR_CFAR_CA) {
+          // eq. 4: A = L1 + L4 - (L2 + L3) for the outer and the guard rectangle
+          const SV outer = (Sa[ca] + Sb[cb]) - (Sa[cb] + Sb[ca]);
+          const SV guard = (Sc[cg] + Sd[cd]) - (Sc[cd] + Sd[cg]);
+          ref = outer - guard;
+        } else {
+          const SV* S1 = S + (g & rmask) * HC + cm;        // row r at the CUT's column
+          const SV* S0 = S + ((g - 1) & rmask) * HC + cm;  // row r - 1
+          ref = go_so_stat(kind == RCFAR_CFAR_GO, Sa + cm, Sb + cm, Sc + cm, Sd + cm, S1, S0, wc, gc);
+        }
         if constexpr (kExact) {
           // T = (alpha / n_ref) * S_ref in fixed-point units; the CUT value
           // comes from the map when one is given, else from the exact table
@@ -200,6 +231,7 @@ __device__ __forceinline__ u64 ref_sum(const u64* ra, const u64* rb, const u64* 
   const u64 neg = (ra[wc] + rb[-wc - 1]) + (rc[-gc - 1] + rd[gc]);
   return pos - neg;
 }
+
 
 // SAT CFAR streaming an exact global table S (I64 mode: S is eq. 3 itself in
 // 64-bit fixed point, so a lookup is one load). A CTA owns a strip of
@@ -294,6 +326,7 @@ __global__ void __launch_bounds__(kRingThreads, 1) k_cfar_ring(const __grid_cons
     for (int q = 0; q < min(nq, NS); ++q) issue(q);
 
   const float kthr = P.kthr;
+  const int kind = P.kind;
   int s = 0;
   if (work) s = __ldcg(P.scale_dev);
   const float inv_s = ldexpf(1.0f, -s);
@@ -360,11 +393,23 @@ __global__ void __launch_bounds__(kRingThreads, 1) k_cfar_ring(const __grid_cons
         const u64* rd = rrow(3);  // row r + gr
         const u64* r1 = rrow(4);  // row r
         const u64* r0 = rrow(5);  // row r - 1
+        long long st[4];  // reference statistic in fixed point
+        if (kind == RCFAR_CFAR_CA) {
+#pragma unroll
+          for (int k = 0; k < 4; ++k) st[k] = (long long)ref_sum(ra + 32 * k, rb + 32 * k, rc + 32 * k, rd + 32 * k, wc, gc);
+        } else {
+          const bool greatest = kind == RCFAR_CFAR_GO;
+#pragma unroll
+          for (int k = 0; k < 4; ++k) {
+            const int o = 32 * k;
+            st[k] = (long long)go_so_stat(greatest, ra + o, rb + o, rc + o, rd + o, r1 + o, r0 + o, wc, gc);
+          }
+        }
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
           const int o = 32 * k;
-          const float ts = f32_from_q((long long)ref_sum(ra + o, rb + o, rc + o, rd + o, wc, gc)) * kthr;
-          th[k] = ts * inv_s;  // T (eq. 2 with A = S_ref / n_ref)
+          const float ts = f32_from_q(st[k]) * kthr;
+          th[k] = ts * inv_s;  // T (eq. 2 with A = S_ref / n_ref, or t times a half sum)
           if constexpr (kMapCut) {
             d[k] = cut[k] > th[k];
           } else {
@@ -519,6 +564,7 @@ __global__ void __launch_bounds__(256) k_sat_cfar_fused(const __grid_constant__ 
   int s = P.sat_scale;
   const float inv_s = ldexpf(1.0f, -s);
   const float kthr = P.kthr;
+  const int kind = P.kind;
   const int inner = (R1 - R0) * cw;
   for (int idx = tid; idx < inner; idx += 256) {
     const int rr = idx / cw, cc = idx - rr * cw;
@@ -527,21 +573,21 @@ __global__ void __launch_bounds__(256) k_sat_cfar_fused(const __grid_constant__ 
     float th = 0.f;
     if (r >= P.row_lo && r <= P.row_hi && c >= P.cut_lo && c <= P.cut_hi) {
       const int g = r - rg0;       // region row of table row r
-      const int j = c - cb + 1;    // region column of table column c
-      const u64* ra = S + (g - wr - 1) * pitch;
-      const u64* rb = S + (g + wr) * pitch;
-      const u64* rc = S + (g - gr - 1) * pitch;
-      const u64* rd = S + (g + gr) * pitch;
-      const u64 outer = (ra[j - wc - 1] + rb[j + wc]) - (ra[j + wc] + rb[j - wc - 1]);
-      const u64 guard = (rc[j - gc - 1] + rd[j + gc]) - (rc[j + gc] + rd[j - gc - 1]);
-      const float ts = f32_from_q((long long)(outer - guard)) * kthr;  // T in fixed-point units
+      const u64* cutc = S + (c - cb + 1);  // region column of table column c
+      const u64* ra = cutc + (g - wr - 1) * pitch;
+      const u64* rb = cutc + (g + wr) * pitch;
+      const u64* rc = cutc + (g - gr - 1) * pitch;
+      const u64* rd = cutc + (g + gr) * pitch;
+      const u64* r1 = cutc + g * pitch;
+      const u64* r0 = cutc + (g - 1) * pitch;
+      const u64 st = kind == RCFAR_CFAR_CA ? ref_sum(ra, rb, rc, rd, wc, gc)
+                                           : go_so_stat(kind == RCFAR_CFAR_GO, ra, rb, rc, rd, r1, r0, wc, gc);
+      const float ts = f32_from_q((long long)st) * kthr;  // T in fixed-point units
       th = ts * inv_s;
       if constexpr (kMapCut) {
         d = ld_map_val(map + (long long)r * P.ld_map + c, P.in_scale) > th ? 1 : 0;
       } else {
-        const u64* r1 = S + g * pitch;
-        const u64* r0 = S + (g - 1) * pitch;
-        const u64 qc = (r1[j] + r0[j - 1]) - (r0[j] + r1[j - 1]);
+        const u64 qc = (r1[0] + r0[-1]) - (r0[0] + r1[-1]);
         d = f32_from_q((long long)qc) > ts ? 1 : 0;
       }
     }
@@ -578,7 +624,9 @@ __global__ void __launch_bounds__(256) k_cfar_direct(const __grid_constant__ Cfa
     unsigned char d = 0;
     float t = 0.f;
     if (r >= P.row_lo && r <= P.row_hi && c >= P.cut_lo && c <= P.cut_hi) {
-      float sum = 0.f;
+      // cell averaging: every training cell; greatest-of / smallest-of: the
+      // rows above the CUT (leading half) and below it (lagging half) apart
+      float sum = 0.f, lead = 0.f, lag = 0.f;
       for (int dr = -wr; dr <= wr; ++dr) {
         const float* row = X + (rr + wr + dr) * HC + cc + wc;
         float rs = 0.f;
@@ -589,8 +637,12 @@ __global__ void __launch_bounds__(256) k_cfar_direct(const __grid_constant__ Cfa
           for (int dc = -wc; dc <= wc; ++dc) rs += row[dc];
         }
         sum += rs;
+        if (dr < 0) lead += rs;
+        if (dr > 0) lag += rs;
       }
-      t = sum * P.kthr;
+      const float stat = P.kind == RCFAR_CFAR_CA ? sum
+                         : P.kind == RCFAR_CFAR_GO ? fmaxf(lead, lag) : fminf(lead, lag);
+      t = stat * P.kthr;
       d = X[(rr + wr) * HC + cc + wc] > t ? 1 : 0;
     }
     P.det[(long long)r * P.ld_det + c] = d;

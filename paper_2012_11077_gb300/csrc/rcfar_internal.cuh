@@ -165,7 +165,8 @@ struct CfarMapDev {
   float in_scale;
   int rows, cols;
   int wr, wc, gr, gc;  // outer and guard half-sizes
-  float kthr;          // alpha / n_ref
+  float kthr;          // CA: alpha / n_ref; GO / SO: the half-sum factor t
+  int kind;            // rcfar_cfar_kind
   int cut_lo, cut_hi;  // CUT column range (after the interior clip)
   int row_lo, row_hi;  // CUT row range
   unsigned char* det;
@@ -272,6 +273,10 @@ cudaError_t launch_cfar_ring(const CfarBatch& b, bool map_cut, int dtype, int bl
 // cover the whole width when it fits (cols + 1 <= kFusedMaxCols), else
 // kRingW columns plus halo. Returns false if no run fits shared memory.
 constexpr int kFusedMaxCols = 256;
+// Threshold factor of a window (host, FP64): alpha / n_ref for cell
+// averaging, the half-sum factor t for greatest-of / smallest-of; cells gets
+// n_ref or the cells of one half. False for an invalid window.
+bool window_factor(const rcfar_window& w, double* factor, int* cells);
 bool cfar_fused_plan(int rows, int cols, int wr, int wc, size_t smem_cap, int* run, int* bw, int* pitch,
                      size_t* smem);
 int cfar_fused_geometry(CfarMapDev& P, int rows, int cols, int run, int bw, int pitch);

@@ -297,8 +297,8 @@ rcfar_status rcfar_server_submit(rcfar_server srv, const rcfar_request* req) {
   if (!r.x || !r.det || r.M <= 0 || r.N <= 0 || r.ldx < (tm ? r.M : r.N) || srv->cfg.params.mean_len > r.N)
     return RCFAR_ERR_INVALID_ARG;
   const rcfar_window& w = r.window;
-  if (w.train_r < 0 || w.train_c < 0 || w.guard_r < 0 || w.guard_c < 0 || !(w.pfa > 0.0 && w.pfa < 1.0))
-    return RCFAR_ERR_INVALID_ARG;
+  double factor = 0.0;
+  if (rcfar_threshold_factor(&w, &factor, nullptr) != RCFAR_OK) return RCFAR_ERR_INVALID_ARG;
   if (r.M > srv->cfg.max_rows || r.N > srv->cfg.max_n || w.guard_r + w.train_r > srv->cfg.max_window ||
       w.guard_c + w.train_c > srv->cfg.max_window)
     return RCFAR_ERR_UNSUPPORTED;

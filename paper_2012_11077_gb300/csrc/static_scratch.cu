@@ -76,7 +76,8 @@ extern "C" rcfar_status rcfar_sat_cfar_static(const float* map, int32_t rows, in
     return RCFAR_ERR_INVALID_ARG;
   const int wr = w->guard_r + w->train_r, wc = w->guard_c + w->train_c;
   const long long n_ref = (2LL * wr + 1) * (2LL * wc + 1) - (2LL * w->guard_r + 1) * (2LL * w->guard_c + 1);
-  if (n_ref <= 0) return RCFAR_ERR_INVALID_ARG;
+  double kfac = 0.0;
+  if (n_ref <= 0 || !window_factor(*w, &kfac, nullptr)) return RCFAR_ERR_INVALID_ARG;
 
   // scratch layout: control words | table int64 | col_tot | row_carry | row_tot | col_carry
   const int n_bands = (int)cdiv(rows, kSatTileH), n_chunks = (int)cdiv(cols, kSatTileW);
@@ -170,7 +171,8 @@ extern "C" rcfar_status rcfar_sat_cfar_static(const float* map, int32_t rows, in
   P.wc = wc;
   P.gr = w->guard_r;
   P.gc = w->guard_c;
-  P.kthr = (float)((double)n_ref * (std::pow(w->pfa, -1.0 / (double)n_ref) - 1.0) / (double)n_ref);
+  P.kthr = (float)kfac;
+  P.kind = w->kind;
   P.row_lo = wr;
   P.row_hi = rows - 1 - wr;
   P.cut_lo = std::max(wc, cut_c_lo);

@@ -111,3 +111,34 @@ def test_batch_tuning_argument_checks(rc):
     assert L.rcfar_set_batch_tuning(None, ctypes.byref(bad)) == rc.RCFAR_ERR_INVALID_ARG
     assert L.rcfar_get_batch_tuning(None, None) == rc.RCFAR_ERR_INVALID_ARG
     assert L.rcfar_tune_batch(None, None, 0, None, 1, None, None) == rc.RCFAR_ERR_INVALID_ARG
+
+
+def test_threshold_factor_matches_oracle(rc):
+    # the library's greatest-of / smallest-of factor (scaled term recurrence)
+    # against the oracle's (log-gamma terms), and cell averaging's alpha / n_ref
+    for tr, tc, gr, gc, pfa in [(16, 16, 4, 4, 1e-6), (4, 4, 1, 1, 1e-2), (2, 7, 0, 3, 1e-3), (1, 1, 1, 1, 0.1),
+                                (32, 32, 8, 8, 1e-8), (1, 0, 0, 0, 0.25)]:
+        for kind, okind in ((rc.RCFAR_CFAR_GO, ocfar.GO), (rc.RCFAR_CFAR_SO, ocfar.SO)):
+            f, n = rc.rcfar_threshold_factor(rc.make_window(tr, tc, gr, gc, pfa, kind))
+            assert n == ocfar.half_cells(tr, tc, gr, gc)
+            o = ocfar.go_so_factor(okind, n, pfa)
+            assert abs(f - o) <= 1e-12 * o, (kind, tr, tc, gr, gc, pfa, f, o)
+        f, n = rc.rcfar_threshold_factor(rc.make_window(tr, tc, gr, gc, pfa))
+        assert n == ocfar.n_ref(tr, tc, gr, gc)
+        assert abs(f - ocfar.alpha(n, pfa) / n) <= 1e-14 * f
+
+
+def test_window_kind_checks(rc):
+    L = rc.lib()
+    import ctypes
+    f = ctypes.c_double()
+    bad = [rc.make_window(4, 4, 1, 1, 1e-3, kind=3), rc.make_window(0, 2, 0, 1, 1e-3, kind=rc.RCFAR_CFAR_GO)]
+    w = rc.make_window(4, 4, 1, 1, 1e-3)
+    w.reserved = 1
+    bad.append(w)
+    for w in bad:
+        assert L.rcfar_threshold_factor(ctypes.byref(w), ctypes.byref(f), None) == rc.RCFAR_ERR_INVALID_ARG
+    # the same columns-only window is valid for cell averaging (its training
+    # cells all lie in the CUT's row, which neither half holds)
+    ok = rc.make_window(0, 2, 0, 1, 1e-3)
+    assert L.rcfar_threshold_factor(ctypes.byref(ok), ctypes.byref(f), None) == rc.RCFAR_OK
