@@ -36,7 +36,8 @@ METRIC = "SAT+CA-CFAR Gcells/s and full-chain frames/s at 1 GB300; % HBM rooflin
 # of each kernel as it stands: k_band_dft_tma on the 1024x4096 frame (bench.py --profile chain); the I64
 # table kernels and k_cfar_ring on a 4096x4096 map (bench.py --profile map), times 4 for the
 # 8192x8192 map (their traffic grows with the cells).
-TRAFFIC = {"band_dft": 43.06e6, "sat_i64_8192": 4 * 222.6e6, "cfar_ring_8192": 4 * 220.5e6}
+# DRAM bytes per launch (ncu dram__bytes_read.sum + dram__bytes_write.sum; see profiles/)
+TRAFFIC = {"band_dft": 43.06e6, "sat_i64_8192": 4 * 222.6e6}
 RING = 16
 
 
@@ -49,7 +50,7 @@ def parse_args():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-map", action="store_true", help="skip the 8192^2 SAT+CFAR measurement")
     ap.add_argument("--no-batch", action="store_true", help="skip the 64-frame mixed batch measurement")
-    ap.add_argument("--profile", choices=["chain", "map", "batch"],
+    ap.add_argument("--profile", choices=["chain", "map", "batch", "fused"],
                     help="run one small fixed case a few times for a profiler capture and exit (no JSON line): "
                          "chain = the 1024x4096 frame through the per-frame calls, map = SAT (I64) + CFAR on a "
                          "--map-size square map, batch = one 64-frame mixed batch")
@@ -617,20 +618,27 @@ def ours(args, rank, world, local, dist):
         detm = torch.empty((R, R), dtype=torch.uint8, device="cuda")
         wm = rc.make_window(16, 16, 4, 4, 1e-6)
 
+        reps = 10
+
+        def timed(fn):
+            for _ in range(3):
+                fn()
+            torch.cuda.synchronize()
+            e0.record()
+            for _ in range(reps):
+                fn()
+            e1.record()
+            torch.cuda.synchronize()
+            assert rc.rcfar_get_error(h) == rc.RCFAR_OK
+            return e0.elapsed_time(e1) / reps
+
+        # split path: exact int64 table S in HBM (reduce, carry scans,
+        # downsweep), then the streaming table CFAR
         def satcfar():
             v = rc.rcfar_sat(h, Pm, value_bound=bound, mode=rc.RCFAR_SAT_I64)
             rc.rcfar_cfar(h, v, Pm, wm, 0, R - 1, detm)
 
-        for _ in range(3):
-            satcfar()
-        torch.cuda.synchronize()
-        reps = 10
-        e0.record()
-        for _ in range(reps):
-            satcfar()
-        e1.record()
-        torch.cuda.synchronize()
-        mms = e0.elapsed_time(e1) / reps
+        mms = timed(satcfar)
         rc.rcfar_trace_enable(h, True)
         for _ in range(reps):
             satcfar()
@@ -643,51 +651,46 @@ def ours(args, rank, world, local, dist):
         cfar_bytes = cells * (8 + 4 + 1)  # read table and map (CUT values), write decisions
         dom, dom_us, dom_b = ("sat", sat_us, sat_bytes) if sat_us >= cfar_us else ("cfar", cfar_us, cfar_bytes)
         ach = dom_b / (dom_us * 1e-6) / 1e9
-        sat_cfar = {"value": cells / (mms * 1e-3) / 1e9, "unit": "Gcells/s", "ms": mms,
-                    "workload": "8192x8192 square-law map, 200 targets over 80 dB, training 16 / guard 4, Pfa 1e-6, "
-                                "exact int64 table S (reduce, carry scans, downsweep), streaming SAT-CFAR",
-                    "kernels_us": {"sat": sat_us, "cfar": cfar_us},
-                    "hbm_frac_split": (sat_bytes + cfar_bytes) / (mms * 1e-3) / 1e9 / peaks["hbm_gbs"],
-                    "roofline": {"kernel": dom, "bound": "hbm", "achieved": ach, "peak": peaks["hbm_gbs"],
-                                 "unit": "GB/s", "frac": ach / peaks["hbm_gbs"],
-                                 "traffic": TRAFFIC["cfar_ring_8192" if dom == "cfar" else "sat_i64_8192"]}}
-        assert rc.rcfar_get_error(h) == rc.RCFAR_OK
-        # the same map through the fused kernel (no table in HBM; same decisions)
+        split = {"value": cells / (mms * 1e-3) / 1e9, "unit": "Gcells/s", "ms": mms,
+                 "kernels_us": {"sat": sat_us, "cfar": cfar_us}, "hbm_bytes_per_cell": 25,
+                 "hbm_frac": (sat_bytes + cfar_bytes) / (mms * 1e-3) / 1e9 / peaks["hbm_gbs"],
+                 "roofline": {"kernel": dom, "bound": "hbm", "achieved": ach, "peak": peaks["hbm_gbs"],
+                              "unit": "GB/s", "frac": ach / peaks["hbm_gbs"],
+                              "traffic": TRAFFIC.get("cfar_ring_8192" if dom == "cfar" else "sat_i64_8192")}}
+        # fused path: one streaming kernel, the table never leaves shared memory
         detf = torch.empty_like(detm)
 
         def fused8():
             rc.rcfar_sat_cfar(h, Pm, bound, wm, 0, R - 1, detf)
 
-        for _ in range(3):
-            fused8()
-        torch.cuda.synchronize()
-        e0.record()
-        for _ in range(reps):
-            fused8()
-        e1.record()
-        torch.cuda.synchronize()
-        fms = e0.elapsed_time(e1) / reps
-        sat_cfar["fused"] = {"value": cells / (fms * 1e-3) / 1e9, "unit": "Gcells/s", "ms": fms,
-                             "hbm_bytes_per_cell": 5, "decisions_identical": bool(torch.equal(detf, detm))}
-        assert rc.rcfar_get_error(h) == rc.RCFAR_OK
-        # greatest-of thresholds on the same table path (16 lookups per CUT instead of 8)
+        fms = timed(fused8)
+        fused_bytes = cells * (4 + 1)  # read the map, write the decisions
+        fach = fused_bytes / (fms * 1e-3) / 1e9
+        fused = {"value": cells / (fms * 1e-3) / 1e9, "unit": "Gcells/s", "ms": fms, "hbm_bytes_per_cell": 5,
+                 "decisions_identical_to_split": bool(torch.equal(detf, detm)),
+                 "roofline": {"kernel": "sat_cfar_stream", "bound": "hbm", "achieved": fach,
+                              "peak": peaks["hbm_gbs"], "unit": "GB/s", "frac": fach / peaks["hbm_gbs"],
+                              "traffic": TRAFFIC.get("sat_cfar_stream_8192"),
+                              "note": "issue-bound on 64-bit integer arithmetic, not on DRAM"}}
+        best = fused if fms <= mms else split
+        sat_cfar = {"value": best["value"], "unit": "Gcells/s", "ms": best["ms"],
+                    "path": "fused" if best is fused else "split",
+                    "workload": "8192x8192 square-law map, 200 targets over 80 dB, training 16 / guard 4, Pfa 1e-6, "
+                                "exact 64-bit fixed-point integral image, CUT values from the map",
+                    "split": split, "fused": fused, "hbm_frac_split": split["hbm_frac"]}
+        # greatest-of thresholds (16 lookups per CUT instead of 8) on both paths
         wg = rc.make_window(16, 16, 4, 4, 1e-6, kind=rc.RCFAR_CFAR_GO)
 
-        def satcfar_go():
+        def split_go():
             v = rc.rcfar_sat(h, Pm, value_bound=bound, mode=rc.RCFAR_SAT_I64)
             rc.rcfar_cfar(h, v, Pm, wg, 0, R - 1, detf)
 
-        for _ in range(3):
-            satcfar_go()
-        torch.cuda.synchronize()
-        e0.record()
-        for _ in range(reps):
-            satcfar_go()
-        e1.record()
-        torch.cuda.synchronize()
-        gms = e0.elapsed_time(e1) / reps
-        sat_cfar["greatest_of"] = {"value": cells / (gms * 1e-3) / 1e9, "unit": "Gcells/s", "ms": gms}
-        assert rc.rcfar_get_error(h) == rc.RCFAR_OK
+        def fused_go():
+            rc.rcfar_sat_cfar(h, Pm, bound, wg, 0, R - 1, detf)
+
+        gs, gf = timed(split_go), timed(fused_go)
+        sat_cfar["greatest_of"] = {"split_gcells_per_s": cells / (gs * 1e-3) / 1e9,
+                                   "fused_gcells_per_s": cells / (gf * 1e-3) / 1e9}
 
     batch = None
     if not args.no_batch:
@@ -741,6 +744,16 @@ def profile_case(args):
         for _ in range(3):
             v = rc.rcfar_sat(h, Pm, value_bound=bound, mode=rc.RCFAR_SAT_I64)
             rc.rcfar_cfar(h, v, Pm, w, 0, n - 1, det)
+    elif args.profile == "fused":
+        n = args.map_size
+        h = rc.rcfar_create(device=0, max_rows=n, max_cols=n, max_n=4096, max_window=40, max_frames=1,
+                            batch_bytes=1 << 24)
+        Pm = torch.from_numpy(synth.square_law_map(n, n, n_targets=200, seed=0)).cuda()
+        det = torch.empty((n, n), dtype=torch.uint8, device="cuda")
+        w = rc.make_window(16, 16, 4, 4, 1e-6)
+        bound = float(Pm.max().item())
+        for _ in range(3):
+            rc.rcfar_sat_cfar(h, Pm, bound, w, 0, n - 1, det)
     elif args.profile == "chain":
         h = rc.rcfar_create(device=0, max_rows=1024, max_cols=512, max_n=4096, max_window=40, max_frames=1,
                             batch_bytes=1 << 24)

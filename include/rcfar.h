@@ -273,8 +273,10 @@ rcfar_status rcfar_cfar(rcfar_handle h, const rcfar_sat_view* view, const void* 
                         rcfar_stream stream);
 
 /* rcfar_sat + rcfar_cfar fused, with no table in device memory: every CTA
- * builds the exact 64-bit integral image (eq. 3) of its block of the map plus
- * the window halo in shared memory and takes the eq. 4 lookups there. The
+ * walks a strip of the map (plus the window halo) down a run of rows,
+ * keeping the last rows of the strip's exact 64-bit integral image (eq. 3)
+ * in shared memory, and takes the eq. 4 lookups there (float16 maps: one
+ * integral image per block of rows instead). The
  * quantisation and fixed-point scale are those rcfar_sat uses for
  * (value_bound > 0, the window), so the decisions and thresholds are
  * bit-identical to rcfar_sat(TILE_I64 or I64) followed by rcfar_cfar with the

@@ -227,6 +227,7 @@ struct rcfar_ctx {
   rcfar_config cfg{};
   int device = 0;
   size_t smem_optin = 48 * 1024;
+  int sms = 152;  // streaming multiprocessors of the device
   void* ws = nullptr;  // one allocation holds everything below
   size_t ws_bytes = 0;
   // control words
@@ -630,6 +631,9 @@ rcfar_status rcfar_create(const rcfar_config* cfg, rcfar_handle* out) {
   int optin = 0;
   cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, cfg->device);
   if (optin > 0) h->smem_optin = (size_t)optin;
+  int sm_count = 0;
+  cudaDeviceGetAttribute(&sm_count, cudaDevAttrMultiProcessorCount, cfg->device);
+  if (sm_count > 0) h->sms = sm_count;
 
   const int R = cfg->max_rows, Cm = std::max(cfg->max_cols, 1), Nm = cfg->max_n;
   // per-step preprocessing: largest frame is max_rows x max_n with up to N/2+1 bins
@@ -1050,10 +1054,18 @@ rcfar_status rcfar_sat_cfar(rcfar_handle h, const void* map, int32_t dtype, int3
   P.sat_scale = sat_scale_for(value_bound, max_cells);
   P.bound = value_bound;
   P.item0 = 0;
+  const size_t cap = std::min<size_t>(h->smem_optin, 200 * 1024);
+  // float32 maps: the streaming kernel; float16 maps (or windows whose ring
+  // does not fit): one integral image per block
+  StreamPlan sp;
+  if (dtype == RCFAR_MAP_F32 && cfar_stream_plan(rows, cols, P.wr, P.wc, cap, h->sms, 0, &sp)) {
+    const int blocks = cfar_stream_geometry(P, rows, cols, sp);
+    TraceScope tr(h, "sat_cfar_fused", s);
+    return cuda_fail(launch_cfar_stream(cb, map_cut != 0, sp.e, blocks, sp.smem, s));
+  }
   int run = 0, bw = 0, pitch = 0;
   size_t smem = 0;
-  if (!cfar_fused_plan(rows, cols, P.wr, P.wc, std::min<size_t>(h->smem_optin, 200 * 1024), &run, &bw, &pitch, &smem))
-    return RCFAR_ERR_UNSUPPORTED;
+  if (!cfar_fused_plan(rows, cols, P.wr, P.wc, cap, &run, &bw, &pitch, &smem)) return RCFAR_ERR_UNSUPPORTED;
   const int blocks = cfar_fused_geometry(P, rows, cols, run, bw, pitch);
   TraceScope tr(h, "sat_cfar_fused", s);
   return cuda_fail(launch_cfar_fused(cb, map_cut != 0, dtype, blocks, smem, s));
@@ -1213,15 +1225,28 @@ rcfar_status rcfar_run_batch(rcfar_handle h, const rcfar_frame_desc* frames, int
     int sat_mode = RCFAR_SAT_TILE_I64;
     int ring_rows_max = 0, hcp_max = 0;
     size_t fused_smem = 0;
+    // fused: every frame's streaming plan, each frame planned for its share
+    // of the SMs (by rows)
+    std::vector<StreamPlan> splans;
+    int stream_e = 0;
     if (h->tuning.sat_mode == RCFAR_SAT_FUSED) {
       sat_mode = RCFAR_SAT_FUSED;
       const size_t cap = std::min<size_t>(h->smem_optin, 200 * 1024);
+      long long rows_all = 0;
+      for (int k = 0; k < cnt; ++k) rows_all += frames[base + k].M;
+      splans.resize(cnt);
+      // one row-prefix width (e) for the launch: the widest frame's
       for (int k = 0; k < cnt && sat_mode == RCFAR_SAT_FUSED; ++k) {
         const rcfar_frame_desc& f = frames[base + k];
-        int run = 0, bw = 0, pitch = 0;
-        size_t sm = 0;
-        if (!cfar_fused_plan(f.M, bands[base + k].cols, f.window.guard_r + f.window.train_r,
-                             f.window.guard_c + f.window.train_c, cap, &run, &bw, &pitch, &sm))
+        const int e = stream_e_of(f.M, bands[base + k].cols, f.window.guard_c + f.window.train_c);
+        if (e == 0) sat_mode = RCFAR_SAT_TILE_I64;
+        stream_e = std::max(stream_e, e);
+      }
+      for (int k = 0; k < cnt && sat_mode == RCFAR_SAT_FUSED; ++k) {
+        const rcfar_frame_desc& f = frames[base + k];
+        const int share = (int)std::max<long long>(1, (long long)h->sms * f.M / std::max<long long>(1, rows_all));
+        if (!cfar_stream_plan(f.M, bands[base + k].cols, f.window.guard_r + f.window.train_r,
+                              f.window.guard_c + f.window.train_c, cap, share, stream_e, &splans[k]))
           sat_mode = RCFAR_SAT_TILE_I64;
       }
     }
@@ -1344,13 +1369,10 @@ rcfar_status rcfar_run_batch(rcfar_handle h, const rcfar_frame_desc* frames, int
       P.mode = sat_mode;
       P.item0 = it_cfar;
       if (sat_mode == RCFAR_SAT_FUSED) {
-        int run = 0, bw = 0, pitch = 0;
-        size_t sm = 0;
-        cfar_fused_plan(f.M, C, P.wr, P.wc, std::min<size_t>(h->smem_optin, 200 * 1024), &run, &bw, &pitch, &sm);
-        fused_smem = std::max(fused_smem, sm);
+        fused_smem = std::max(fused_smem, splans[k].smem);
         P.sat_scale = m.scale_log2;
         P.bound = m.bound;
-        it_cfar += cfar_fused_geometry(P, f.M, C, run, bw, pitch);
+        it_cfar += cfar_stream_geometry(P, f.M, C, splans[k]);
       } else if (sat_mode == RCFAR_SAT_I64) {
         int rr = 0, hc = 0;
         cfar_ring_plan(P.wr, P.wc, h->smem_optin, &rr, &hc);
@@ -1398,7 +1420,7 @@ rcfar_status rcfar_run_batch(rcfar_handle h, const rcfar_frame_desc* frames, int
     }
     if (e == cudaSuccess) {
       TraceScope t(h, "cfar", s);
-      e = sat_mode == RCFAR_SAT_FUSED ? launch_cfar_fused(cb, true, RCFAR_MAP_F32, it_cfar, fused_smem, s)
+      e = sat_mode == RCFAR_SAT_FUSED ? launch_cfar_stream(cb, true, stream_e, it_cfar, fused_smem, s)
           : sat_mode == RCFAR_SAT_I64
               ? launch_cfar_ring(cb, true, RCFAR_MAP_F32, it_cfar, ring_smem, s)
               : launch_cfar(cb, sat_mode, RCFAR_MAP_F32, it_cfar, (size_t)cfar_mode_smem, cfar_max_hc, s);

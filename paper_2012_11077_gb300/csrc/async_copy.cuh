@@ -15,6 +15,30 @@ __device__ __forceinline__ void cp_async16(unsigned saddr, const void* gmem, boo
   const int src_bytes = valid ? 16 : 0;
   asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(saddr), "l"(gmem), "r"(src_bytes) : "memory");
 }
+// 4-byte cp.async through L1; valid == false zero-fills the 4 bytes and reads nothing.
+__device__ __forceinline__ void cp_async4(unsigned saddr, const void* gmem, bool valid) {
+  const int src_bytes = valid ? 4 : 0;
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(saddr), "l"(gmem), "r"(src_bytes) : "memory");
+}
+// 16-byte cp.async of src_bytes (0..16) bytes, the rest zero-filled; src
+// and dst 16-byte aligned (src need not be read when src_bytes is 0).
+__device__ __forceinline__ void cp_async16_n(unsigned saddr, const void* gmem, int src_bytes) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(saddr), "l"(gmem), "r"(src_bytes) : "memory");
+}
+// Shared-memory accesses by 32-bit shared-window address.
+__device__ __forceinline__ unsigned long long lds_u64(unsigned a) {
+  unsigned long long v;
+  asm volatile("ld.shared.u64 %0, [%1];" : "=l"(v) : "r"(a));
+  return v;
+}
+__device__ __forceinline__ void sts_u64(unsigned a, unsigned long long v) {
+  asm volatile("st.shared.u64 [%0], %1;" ::"r"(a), "l"(v) : "memory");
+}
+__device__ __forceinline__ float lds_f32(unsigned a) {
+  float v;
+  asm volatile("ld.shared.f32 %0, [%1];" : "=f"(v) : "r"(a));
+  return v;
+}
 // 8-byte cp.async through L1 (both addresses 8-byte aligned).
 __device__ __forceinline__ void cp_async8(unsigned saddr, const void* gmem) {
   asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(saddr), "l"(gmem) : "memory");

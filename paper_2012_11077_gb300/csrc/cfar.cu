@@ -598,6 +598,303 @@ __global__ void __launch_bounds__(256) k_sat_cfar_fused(const __grid_constant__ 
   if (tid == 0 && s_bad && B.status) atomicOr(B.status, kStatusRange);
 }
 
+// Streaming fused SAT + CFAR (float32 maps, no table in device memory). A CTA
+// owns the CUT rows [R0, R1) of a strip of columns [c0, c0 + cw) and walks
+// the map rows R0 - wr .. R1 - 1 + wr in stages of kStreamKS rows. Its local
+// integral image (eq. 3) has its origin (region row 0, region column 0,
+// both zero) at table row R0 - wr - 1 and column cb - 1; the last
+// kStreamKS + 2 wr + 1 of its rows live in a ring in shared memory (region
+// row g in slot g mod RB). Per stage, while cp.async brings the next
+// stage's map rows:
+//  (A) thread j quantises column j + 1 of the stage's rows and adds them to
+//      its running column sum, which it keeps in a register for the whole
+//      run, writing the column sums to the ring;
+//  (B) warp w turns row w of the stage into its table row: a prefix across
+//      the strip (contiguous chunks per lane, one warp scan);
+//  (C) warp w takes one CUT row whose window is now complete: 8 eq. 4
+//      lookups per CUT (16 for greatest-of / smallest-of), T and the
+//      decision.
+// Box sums do not depend on the origin, and the mod-2^64 wrap of long runs
+// cancels in them, so thresholds and decisions are bit-identical to the
+// split path's with the same fixed-point scale.
+// One CUT row of the streaming kernel: the lane's columns cl + 32 k
+// (k < ncg, c < cend). ra .. r0 are the shared-memory addresses of the ring
+// rows r - wr - 1, r + wr, r - gr - 1, r + gr, r, r - 1 at the region column
+// of map column cl. Cell averaging: S_ref from 8 lookups; greatest-of /
+// smallest-of: the two half sums from 16.
+template <bool kMapCut, bool kHalves, int kCG>
+__device__ __forceinline__ void stream_cut_row(const CfarMapDev& P, int r, int cl, int ncg, int cend, unsigned ra,
+                                               unsigned rb, unsigned rc, unsigned rd, unsigned r1, unsigned r0,
+                                               bool greatest, float kthr, float inv_s, const float* map) {
+  const int wc = P.wc, gc = P.gc, clo = P.cut_lo, chi = P.cut_hi;
+  const bool row_cut = r >= P.row_lo && r <= P.row_hi;
+  unsigned char* drow = P.det + (long long)r * P.ld_det + cl;
+  float* trow = P.thr ? P.thr + (long long)r * P.ld_thr + cl : nullptr;
+  const unsigned owl = (unsigned)(-8 * (wc + 1)), owr = (unsigned)(8 * wc);
+  const unsigned ogl = (unsigned)(-8 * (gc + 1)), ogr = (unsigned)(8 * gc);
+  const unsigned a0 = ra + owl, a1 = ra + owr, b0 = rb + owl, b1 = rb + owr;
+  const unsigned e0 = rc + ogl, e1 = rc + ogr, f0 = rd + ogl, f1 = rd + ogr;
+  float cutv[kCG];
+  const float* mrow = map + (long long)r * P.ld_map + cl;
+  // every column of the lane is a CUT column (uniform over the warp): no per-column checks
+  const int cfirst = cl - (cl & 31);
+  if (row_cut && ncg == kCG && cend - cfirst == 32 * kCG && cfirst >= clo && cend - 1 <= chi) {
+    if constexpr (kMapCut) {
+#pragma unroll
+      for (int k = 0; k < kCG; ++k) cutv[k] = __ldg(mrow + 32 * k);
+    }
+#pragma unroll
+    for (int k = 0; k < kCG; ++k) {
+      const unsigned o = 256u * k;
+      u64 st;
+      if constexpr (!kHalves) {
+        const u64 outer = (lds_u64(a0 + o) + lds_u64(b1 + o)) - (lds_u64(a1 + o) + lds_u64(b0 + o));
+        const u64 guard = (lds_u64(e0 + o) + lds_u64(f1 + o)) - (lds_u64(e1 + o) + lds_u64(f0 + o));
+        st = outer - guard;
+      } else {
+        const u64 lead = ((lds_u64(a0 + o) + lds_u64(r0 + owr + o)) - (lds_u64(a1 + o) + lds_u64(r0 + owl + o))) -
+                         ((lds_u64(e0 + o) + lds_u64(r0 + ogr + o)) - (lds_u64(e1 + o) + lds_u64(r0 + ogl + o)));
+        const u64 lag = ((lds_u64(r1 + owl + o) + lds_u64(b1 + o)) - (lds_u64(r1 + owr + o) + lds_u64(b0 + o))) -
+                        ((lds_u64(r1 + ogl + o) + lds_u64(f1 + o)) - (lds_u64(r1 + ogr + o) + lds_u64(f0 + o)));
+        st = ((long long)lead > (long long)lag) == greatest ? lead : lag;
+      }
+      const float ts = f32_from_q((long long)st) * kthr;
+      const float th = ts * inv_s;
+      unsigned char d;
+      if constexpr (kMapCut) {
+        d = cutv[k] > th ? 1 : 0;
+      } else {
+        const u64 qc = (lds_u64(r1 + o) + lds_u64(r0 + o - 8u)) - (lds_u64(r0 + o) + lds_u64(r1 + o - 8u));
+        d = f32_from_q((long long)qc) > ts ? 1 : 0;
+      }
+      drow[32 * k] = d;
+      if (trow) trow[32 * k] = th;
+    }
+    return;
+  }
+
+#pragma unroll 1
+  for (int k = 0; k < ncg; ++k) {
+    const unsigned o = 256u * k;
+    const int c = cl + 32 * k;
+    if (c < cend) {
+      unsigned char d = 0;
+      float th = 0.f;
+      if (row_cut && c >= clo && c <= chi) {
+        u64 st;
+        if constexpr (!kHalves) {
+          const u64 outer = (lds_u64(a0 + o) + lds_u64(b1 + o)) - (lds_u64(a1 + o) + lds_u64(b0 + o));
+          const u64 guard = (lds_u64(e0 + o) + lds_u64(f1 + o)) - (lds_u64(e1 + o) + lds_u64(f0 + o));
+          st = outer - guard;
+        } else {
+          // leading half: rows (r - wr - 1, r - 1] minus the guard rows
+          // (r - gr - 1, r - 1]; lagging half: rows (r, r + wr] minus (r, r + gr]
+          const u64 lead = ((lds_u64(a0 + o) + lds_u64(r0 + owr + o)) - (lds_u64(a1 + o) + lds_u64(r0 + owl + o))) -
+                           ((lds_u64(e0 + o) + lds_u64(r0 + ogr + o)) - (lds_u64(e1 + o) + lds_u64(r0 + ogl + o)));
+          const u64 lag = ((lds_u64(r1 + owl + o) + lds_u64(b1 + o)) - (lds_u64(r1 + owr + o) + lds_u64(b0 + o))) -
+                          ((lds_u64(r1 + ogl + o) + lds_u64(f1 + o)) - (lds_u64(r1 + ogr + o) + lds_u64(f0 + o)));
+          st = ((long long)lead > (long long)lag) == greatest ? lead : lag;
+        }
+        const float ts = f32_from_q((long long)st) * kthr;
+        th = ts * inv_s;
+        if constexpr (kMapCut) {
+          d = __ldg(mrow + 32 * k) > th ? 1 : 0;
+        } else {
+          const u64 qc = (lds_u64(r1 + o) + lds_u64(r0 + o - 8u)) - (lds_u64(r0 + o) + lds_u64(r1 + o - 8u));
+          d = f32_from_q((long long)qc) > ts ? 1 : 0;
+        }
+      }
+      drow[32 * k] = d;
+      if (trow) trow[32 * k] = th;
+    }
+  }
+}
+
+// Streaming fused SAT + CFAR (float32 maps, no table in device memory). A CTA
+// owns the CUT rows [R0, R1) of a strip of columns [c0, c0 + cw) and walks
+// the map rows R0 - wr .. R1 - 1 + wr in stages of kStreamKS rows. Its local
+// integral image (eq. 3) has its origin (region row 0, region column 0,
+// both zero) at table row R0 - wr - 1 and column cb - 1; the last
+// kStreamKS + 2 wr + 1 of its rows live in a ring in shared memory (region
+// row g in slot g mod RB). Per stage, while cp.async brings the next
+// stage's map rows (16-byte copies when the map's rows are 16-byte aligned):
+//  (A) thread j quantises column j + 1 of the stage's rows and adds them to
+//      its running column sum, which it keeps in a register for the whole
+//      run, writing the column sums to the ring;
+//  (B) warp w turns row w of the stage into its table row: a prefix across
+//      the strip (kE contiguous columns per lane, one warp scan);
+//  (C) warp w takes one CUT row whose window is now complete: 8 eq. 4
+//      lookups per CUT (16 for greatest-of / smallest-of), T and the
+//      decision.
+// Box sums do not depend on the origin, and the mod-2^64 wrap of long runs
+// cancels in them, so thresholds and decisions are bit-identical to the
+// split path's with the same fixed-point scale. kCG: column groups of 32 per
+// lane in (C) (4 for strips of kStreamW columns, 8 for whole-width strips).
+template <bool kMapCut, int kCG, int kE>
+__global__ void __launch_bounds__(kStreamThreads, 2) k_sat_cfar_stream(const __grid_constant__ CfarBatch B) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ int s_bad;
+  const int mi = find_item(B.m, B.n, (int)blockIdx.x, &CfarMapDev::item0);
+  const CfarMapDev& P = B.m[mi];
+  const int local = (int)blockIdx.x - P.item0;
+  const int ty = local / P.tiles_x, tx = local - ty * P.tiles_x;
+  const int rows = P.rows, cols = P.cols;
+  const int R0 = ty * P.run, R1 = min(rows, R0 + P.run);
+  const int wr = P.wr, wc = P.wc, gr = P.gr;
+  const bool full = P.tiles_x == 1 && P.bw >= cols;
+  const int c0 = full ? 0 : tx * P.bw;
+  const int cw = full ? cols : min(P.bw, cols - c0);
+  const int cb = full ? 0 : c0 - wc;          // map column of region column 1
+  const int nin = full ? cols : cw + 2 * wc;  // map columns in the region (region columns 1 .. nin)
+  const int pitch = P.hcp;                    // u64 per ring row (even, >= nin + 1)
+  const int RB = P.ring_rows;                 // >= kStreamKS + 2 wr + 1
+  const int ldr = (nin + 6) & ~3;             // floats per staged map row (>= nin + 3, multiple of 4)
+  const float* map = reinterpret_cast<const float*>(P.map);
+  // 16-byte copies need 16-byte aligned rows; they start at x0 = cb rounded
+  // down to a multiple of 4 (so no copy straddles column 0)
+  const bool vec = ((reinterpret_cast<uintptr_t>(map) & 15) == 0) && ((P.ld_map & 3) == 0);
+  const int xoff = vec ? (cb & 3) : 0;
+  const int x0 = cb - xoff;
+  const unsigned ring_a = smem_u32(smem_raw);
+  const unsigned span = (unsigned)(RB * pitch) * 8u;  // ring bytes
+  const unsigned raw_a = ring_a + span;               // 16-byte aligned (pitch even)
+  const unsigned pitch8 = (unsigned)pitch * 8u, ldr4 = (unsigned)ldr * 4u;
+  const int ro = R0 - wr - 1;       // table row of region row 0
+  const int GT = R1 - R0 + 2 * wr;  // region rows 1 .. GT hold map rows
+  const int nst = (GT + kStreamKS - 1) / kStreamKS;
+  const int last_cut = R1 - 1 - ro;  // region row of CUT row R1 - 1
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const float scalef = ldexpf(1.0f, P.sat_scale);
+  const float inv_s = ldexpf(1.0f, -P.sat_scale);
+  const float bound = P.bound;
+  const float kthr = P.kthr;
+  const int kind = P.kind;
+  const int ncg = (cw + 31) >> 5;
+  if (tid == 0) s_bad = 0;
+  for (int j = tid; j < pitch; j += kStreamThreads) sts_u64(ring_a + 8u * j, 0ull);  // region row 0 (slot 0)
+
+  // stage t's map rows into raw buffer t & 1: warp w fetches row w
+  auto fetch = [&](int t) {
+    const int g0 = 1 + t * kStreamKS;
+    const int n = min(kStreamKS, GT - g0 + 1);
+    if (warp < n) {
+      const int r = ro + g0 + warp;
+      const bool rok = r >= 0 && r < rows;
+      const float* src = map + (long long)(rok ? r : 0) * P.ld_map;
+      const unsigned dst = raw_a + (unsigned)(((t & 1) * kStreamKS + warp) * ldr) * 4u;
+      if (vec) {
+        const int nq = (xoff + nin + 3) >> 2;
+        for (int q = lane; q < nq; q += 32) {
+          const int cs = x0 + 4 * q;
+          const int bytes = (rok && cs >= 0 && cs < cols) ? 4 * min(4, cols - cs) : 0;
+          cp_async16_n(dst + 16u * q, bytes ? src + cs : map, bytes);
+        }
+      } else {
+        for (int j = lane; j < nin; j += 32) {
+          const int c = cb + j;
+          const bool ok = rok && c >= 0 && c < cols;
+          cp_async4(dst + 4u * j, ok ? src + c : map, ok);
+        }
+      }
+    }
+    cp_async_commit();
+  };
+
+  u64 colsum = 0;      // column tid + 1: sum of region rows 1 .. the last built
+  bool bad = false;
+  int next_cut = wr + 1;  // region row of the next CUT row (row R0)
+  int slot0 = 1;          // ring slot of region row g0 (1 + t kStreamKS)
+  int cut_slot = (wr + 1) % RB;
+  const unsigned ring_end = ring_a + span;
+  const int jl = c0 - cb + 1 + lane;  // region column of the lane's first CUT column
+  fetch(0);
+  for (int t = 0; t < nst; ++t) {
+    cp_async_wait<0>();
+    __syncthreads();  // stage t's rows have landed; the ring rows (A) overwrites are no longer read
+    if (t + 1 < nst) fetch(t + 1);
+    const int g0 = 1 + t * kStreamKS;
+    const int n = min(kStreamKS, GT - g0 + 1);
+    // (A) quantised values added down each column (region column tid + 1);
+    // thread nin writes the zero column 0 (its values are 0)
+    if (tid <= nin) {
+      const bool real = tid < nin;
+      unsigned sa = raw_a + (unsigned)((t & 1) * kStreamKS * ldr + xoff + tid) * 4u;
+      unsigned da = ring_a + (unsigned)(slot0 * pitch + (real ? 1 + tid : 0)) * 8u;
+      auto row = [&](float v) {
+        bad |= !(fabsf(v) <= bound);
+        colsum += (u64)q_from_f32(v, scalef);
+        sts_u64(da, colsum);
+        da += pitch8;
+        if (da >= ring_end) da -= span;
+      };
+      if (n == kStreamKS) {
+        float v[kStreamKS];
+#pragma unroll
+        for (int i = 0; i < kStreamKS; ++i) v[i] = real ? lds_f32(sa + (unsigned)i * ldr4) : 0.f;
+#pragma unroll
+        for (int i = 0; i < kStreamKS; ++i) row(v[i]);
+      } else {
+        for (int i = 0; i < n; ++i) row(real ? lds_f32(sa + (unsigned)i * ldr4) : 0.f);
+      }
+    }
+    __syncthreads();
+    // (B) prefix across the strip: warp w takes region row g0 + w; lane l
+    // holds region columns 1 + kE l .. kE (l + 1) (the ring rows are wide
+    // enough for every lane's chunk; columns past nin are never read)
+    if (warp < n) {
+      int slot = slot0 + warp;
+      if (slot >= RB) slot -= RB;
+      const unsigned ra = ring_a + (unsigned)(slot * pitch + 1 + kE * lane) * 8u;
+      u64 v[kE];
+#pragma unroll
+      for (int e = 0; e < kE; ++e) v[e] = lds_u64(ra + 8u * e);
+#pragma unroll
+      for (int e = 1; e < kE; ++e) v[e] += v[e - 1];
+      u64 incl = v[kE - 1];
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const u64 y = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += y;
+      }
+      const u64 excl = incl - v[kE - 1];
+#pragma unroll
+      for (int e = 0; e < kE; ++e) sts_u64(ra + 8u * e, v[e] + excl);
+    }
+    __syncthreads();
+    // (C) CUT rows whose windows are complete: region rows next_cut .. hi
+    const int hi = min(g0 + n - 1 - wr, last_cut);
+    const int cnt = hi - next_cut + 1;  // <= kStreamKS
+    if (warp < cnt) {
+      int sg = cut_slot + warp;
+      if (sg >= RB) sg -= RB;
+      auto rp = [&](int off) {  // ring row of region row g + off (|off| <= wr + 1), at column jl
+        int x = sg + off;
+        if (x >= RB) x -= RB;
+        if (x < 0) x += RB;
+        return ring_a + (unsigned)(x * pitch + jl) * 8u;
+      };
+      const unsigned ra = rp(-wr - 1), rb = rp(wr), rc = rp(-gr - 1), rd = rp(gr), r1 = rp(0), r0 = rp(-1);
+      const int r = ro + next_cut + warp;
+      if (kind == RCFAR_CFAR_CA)
+        stream_cut_row<kMapCut, false, kCG>(P, r, c0 + lane, ncg, c0 + cw, ra, rb, rc, rd, r1, r0, false, kthr,
+                                            inv_s, map);
+      else
+        stream_cut_row<kMapCut, true, kCG>(P, r, c0 + lane, ncg, c0 + cw, ra, rb, rc, rd, r1, r0,
+                                           kind == RCFAR_CFAR_GO, kthr, inv_s, map);
+    }
+    if (cnt > 0) {
+      next_cut += cnt;
+      cut_slot += cnt;
+      if (cut_slot >= RB) cut_slot -= RB;
+    }
+    slot0 += kStreamKS;
+    if (slot0 >= RB) slot0 -= RB;
+  }
+  if (bad) s_bad = 1;
+  __syncthreads();
+  if (tid == 0 && s_bad && B.status) atomicOr(B.status, kStatusRange);
+}
+
 __global__ void __launch_bounds__(256) k_cfar_direct(const __grid_constant__ CfarMapDev P) {
   extern __shared__ __align__(16) float X[];
   const int local = (int)blockIdx.x;
@@ -812,6 +1109,93 @@ cudaError_t launch_cfar_fused(const CfarBatch& b, bool map_cut, int dtype, int b
   const bool h = dtype == RCFAR_MAP_F16;
   if (map_cut) return h ? launch_fused_t<true, __half>(b, blocks, smem, s) : launch_fused_t<true, float>(b, blocks, smem, s);
   return h ? launch_fused_t<false, __half>(b, blocks, smem, s) : launch_fused_t<false, float>(b, blocks, smem, s);
+}
+
+static int stream_nin(int cols, int wc) { return cols + 1 <= kFusedMaxCols ? cols : kStreamW + 2 * wc; }
+
+int stream_e_of(int rows, int cols, int wc) {
+  if (rows <= 0 || cols <= 0) return 0;
+  const int nin = stream_nin(cols, wc);
+  if (nin + 1 > kFusedMaxCols) return 0;
+  const int e = (nin + 31) / 32;
+  return e <= 5 ? 5 : e == 6 ? 6 : 8;
+}
+
+bool cfar_stream_plan(int rows, int cols, int wr, int wc, size_t smem_cap, int sm_share, int e_min,
+                      StreamPlan* out) {
+  int e = stream_e_of(rows, cols, wc);
+  if (e == 0) return false;
+  e = std::max(e, e_min);
+  if (e != 5 && e != 6 && e != 8) e = 8;
+  const bool full = cols + 1 <= kFusedMaxCols;
+  const int w = full ? cols : kStreamW;
+  const int nin = stream_nin(cols, wc);
+  const int pitch = 32 * e + 2;
+  const int ldr = (nin + 6) & ~3;
+  const int rb = kStreamKS + 2 * wr + 1;
+  const size_t smem = (size_t)rb * pitch * 8 + (size_t)2 * kStreamKS * ldr * 4;
+  if (smem > smem_cap) return false;
+  // two CTAs per SM when their shared memory fits (228 KB per SM, 1 KB reserved per CTA)
+  const int per_sm = 2 * (smem + 1024 + 64) <= 228 * 1024 ? 2 : 1;
+  const long long slots = (long long)std::max(1, sm_share) * per_sm;
+  const long long strips = full ? 1 : (cols + w - 1) / w;
+  int best_run = rows;
+  long long best = -1;
+  // candidate runs: 1..16 and multiples of 8; cost = waves x stages per CTA
+  for (int run = 1; run <= rows + 7; run = run < 16 ? run + 1 : run + 8) {
+    const int rr = std::min(run, rows);
+    const long long ctas = strips * ((rows + rr - 1) / rr);
+    const long long waves = (ctas + slots - 1) / slots;
+    const long long stages = (rr + 2 * wr + kStreamKS - 1) / kStreamKS;
+    const long long cost = waves * stages;
+    if (best < 0 || cost < best || (cost == best && rr > best_run)) {
+      best = cost;
+      best_run = rr;
+    }
+    if (rr == rows) break;
+  }
+  out->run = best_run;
+  out->bw = w;
+  out->pitch = pitch;
+  out->ring_rows = rb;
+  out->e = e;
+  out->smem = smem;
+  out->ctas = (int)(strips * ((rows + best_run - 1) / best_run));
+  return true;
+}
+
+int cfar_stream_geometry(CfarMapDev& P, int rows, int cols, const StreamPlan& sp) {
+  P.run = sp.run;
+  P.bw = sp.bw;
+  P.bh = 0;
+  P.hcp = sp.pitch;
+  P.ring_rows = sp.ring_rows;
+  P.tiles_x = (cols + sp.bw - 1) / sp.bw;
+  return P.tiles_x * ((rows + sp.run - 1) / sp.run);
+}
+
+template <bool kMapCut, int kCG, int kE>
+static cudaError_t launch_stream_t(const CfarBatch& b, int blocks, size_t smem, cudaStream_t s) {
+  auto fn = k_sat_cfar_stream<kMapCut, kCG, kE>;
+  cudaError_t e = ensure_smem(reinterpret_cast<const void*>(fn), smem);
+  if (e != cudaSuccess) return e;
+  fn<<<blocks, kStreamThreads, smem, s>>>(b);
+  return cudaGetLastError();
+}
+
+template <int kCG, int kE>
+static cudaError_t launch_stream_ce(const CfarBatch& b, bool map_cut, int blocks, size_t smem, cudaStream_t s) {
+  return map_cut ? launch_stream_t<true, kCG, kE>(b, blocks, smem, s) : launch_stream_t<false, kCG, kE>(b, blocks, smem, s);
+}
+
+cudaError_t launch_cfar_stream(const CfarBatch& b, bool map_cut, int e, int blocks, size_t smem, cudaStream_t s) {
+  if (blocks <= 0) return cudaSuccess;
+  // 8 column groups per lane only when some item is one whole-width strip wider than 128 columns
+  bool wide = false;
+  for (int i = 0; i < b.n; ++i) wide = wide || (b.m[i].tiles_x == 1 && b.m[i].cols > kStreamW);
+  if (e == 5) return wide ? launch_stream_ce<8, 5>(b, map_cut, blocks, smem, s) : launch_stream_ce<4, 5>(b, map_cut, blocks, smem, s);
+  if (e == 6) return wide ? launch_stream_ce<8, 6>(b, map_cut, blocks, smem, s) : launch_stream_ce<4, 6>(b, map_cut, blocks, smem, s);
+  return wide ? launch_stream_ce<8, 8>(b, map_cut, blocks, smem, s) : launch_stream_ce<4, 8>(b, map_cut, blocks, smem, s);
 }
 
 cudaError_t launch_cfar_direct(const CfarMapDev& m, int blocks, size_t smem, cudaStream_t s) {

@@ -267,20 +267,47 @@ int cfar_ring_slots(size_t smem);  // resident CTAs of the streaming kernel on t
 int cfar_ring_geometry(CfarMapDev& P, int rows, int cols, int ring_rows, int hcp, int slots);
 cudaError_t launch_cfar_ring(const CfarBatch& b, bool map_cut, int dtype, int blocks, size_t smem, cudaStream_t s);
 
+// Threshold factor of a window (host, FP64): alpha / n_ref for cell
+// averaging, the half-sum factor t for greatest-of / smallest-of; cells gets
+// n_ref or the cells of one half. False for an invalid window.
+bool window_factor(const rcfar_window& w, double* factor, int* cells);
+
 // Fused SAT + CFAR without a table in device memory: each CTA builds the
 // exact 64-bit integral image of its region (inner run x strip plus the
 // window halo) in shared memory and takes the eq. 4 lookups there. Strips
 // cover the whole width when it fits (cols + 1 <= kFusedMaxCols), else
 // kRingW columns plus halo. Returns false if no run fits shared memory.
 constexpr int kFusedMaxCols = 256;
-// Threshold factor of a window (host, FP64): alpha / n_ref for cell
-// averaging, the half-sum factor t for greatest-of / smallest-of; cells gets
-// n_ref or the cells of one half. False for an invalid window.
-bool window_factor(const rcfar_window& w, double* factor, int* cells);
 bool cfar_fused_plan(int rows, int cols, int wr, int wc, size_t smem_cap, int* run, int* bw, int* pitch,
                      size_t* smem);
 int cfar_fused_geometry(CfarMapDev& P, int rows, int cols, int run, int bw, int pitch);
 cudaError_t launch_cfar_fused(const CfarBatch& b, bool map_cut, int dtype, int blocks, size_t smem, cudaStream_t s);
+
+// Streaming fused SAT + CFAR (float32 maps): a CTA walks a strip of columns
+// down a run of rows in stages of kStreamKS rows, keeping the last
+// kStreamKS + 2 wr + 1 rows of its local integral image in a ring in shared
+// memory. Strips are the whole width when cols + 1 <= kFusedMaxCols, else
+// kStreamW columns plus halo (then wc <= 63). The plan picks the run that
+// minimises waves x stages for `sm_share` SMs; false if the ring does not
+// fit smem_cap.
+constexpr int kStreamKS = 16;
+constexpr int kStreamThreads = 512;  // one warp per row of a stage
+constexpr int kStreamW = 128;
+static_assert(kStreamThreads / 32 == kStreamKS, "one warp per stage row");
+// Row prefix: each lane holds e consecutive region columns (e in {5, 6, 8},
+// 32 e >= the region's columns); ring rows are 32 e + 2 wide so that every
+// lane's chunk lies inside its row.
+int stream_e_of(int rows, int cols, int wc);  // e needed by one map (0 if it cannot stream)
+struct StreamPlan {
+  int run, bw, pitch, ring_rows, e;
+  size_t smem;
+  int ctas;
+};
+// e_min: the e of the launch the map joins (0: its own).
+bool cfar_stream_plan(int rows, int cols, int wr, int wc, size_t smem_cap, int sm_share, int e_min,
+                      StreamPlan* out);
+int cfar_stream_geometry(CfarMapDev& P, int rows, int cols, const StreamPlan& sp);
+cudaError_t launch_cfar_stream(const CfarBatch& b, bool map_cut, int e, int blocks, size_t smem, cudaStream_t s);
 size_t cfar_direct_smem_bytes(int bh, int bw, int wr, int wc);
 
 }  // namespace rcfar
