@@ -233,8 +233,11 @@ def compare_decisions(det: np.ndarray, det_ref: np.ndarray, P_ref: np.ndarray, t
 def cfar_chain(P: np.ndarray, band, train_r: int, train_c: int, guard_r: int, guard_c: int, pfa: float,
                method: str = "sat", kind: str = "ca") -> CfarResult:
     """CFAR on a band map: CUT columns restricted to the respiration band bins.
-    kind: "ca" (Sec. II.B) or the greatest-of / smallest-of variants "go", "so"."""
+    kind: "ca" (Sec. II.B), or the greatest-of / smallest-of / ordered-statistic
+    variants "go", "so", "os" (default rank)."""
     cut_cols = (band.k_lo - band.c0, band.k_hi - band.c0)
+    if kind == OS:
+        return cfar_os_direct(P, train_r, train_c, guard_r, guard_c, pfa, cut_cols=cut_cols)
     if kind != "ca":
         fn = cfar_go_so_sat if method == "sat" else cfar_go_so_direct
         return fn(P, kind, train_r, train_c, guard_r, guard_c, pfa, cut_cols=cut_cols)
@@ -380,4 +383,74 @@ def cfar_go_so_sat(P: np.ndarray, kind: str, train_r: int, train_c: int, guard_r
     T = t * (np.maximum(lead, lag) if kind == GO else np.minimum(lead, lag))
     thr[rs, cs] = T
     det[rs, cs] = (P[rs, cs] > T).astype(np.uint8)
+    return CfarResult(det, thr, mask)
+
+
+# ---- ordered-statistic CFAR (next-step variant; not in the paper) ----
+#
+# Reading (recorded in the design notes): the reference set is the same
+# training ring as cell averaging (n_ref cells); T = alpha * X_(k), X_(k)
+# the k-th smallest reference value (1-based), k = ceil(3 n_ref / 4) unless
+# given. For iid exponential noise the k-th order statistic of n cells is a
+# sum of independent exponentials with rates n, n-1, ..., n-k+1 (Renyi), so
+#   P(CUT > alpha X_(k)) = prod_{i=0}^{k-1} (n - i) / (n - i + alpha),
+# which falls monotonically in alpha; alpha comes by bisection. An order
+# statistic is not a region sum, so this variant cannot use the eq. 3 table.
+OS = "os"
+
+
+def os_rank_default(nref: int) -> int:
+    return -(-3 * nref // 4)
+
+
+def pfa_ordered_statistic(alpha: float, n: int, k: int) -> float:
+    """P(CUT > alpha X_(k)) for n iid Exp(1) reference cells (log-space product)."""
+    if not (1 <= k <= n) or alpha < 0:
+        raise ValueError("need 1 <= k <= n and alpha >= 0")
+    from math import exp, log1p
+    return exp(-sum(log1p(alpha / (n - i)) for i in range(k)))
+
+
+def os_factor(n: int, k: int, pfa: float) -> float:
+    """alpha with pfa_ordered_statistic(alpha, n, k) = pfa (bisection in FP64)."""
+    if not (0.0 < pfa < 1.0):
+        raise ValueError("need 0 < pfa < 1")
+    lo, hi = 0.0, 1.0
+    while pfa_ordered_statistic(hi, n, k) > pfa:
+        hi *= 2.0
+    for _ in range(200):
+        mid = 0.5 * (lo + hi)
+        if pfa_ordered_statistic(mid, n, k) > pfa:
+            lo = mid
+        else:
+            hi = mid
+        if hi - lo <= 1e-15 * hi:
+            break
+    return 0.5 * (lo + hi)
+
+
+def cfar_os_direct(P: np.ndarray, train_r: int, train_c: int, guard_r: int, guard_c: int, pfa: float,
+                   k: Optional[int] = None, cut_cols: Optional[Tuple[int, int]] = None) -> CfarResult:
+    """OS CFAR: the k-th smallest of each CUT's n_ref training cells, times alpha (FP64)."""
+    P = np.asarray(P, dtype=np.float64)
+    nref = n_ref(train_r, train_c, guard_r, guard_c)
+    if k is None or k == 0:
+        k = os_rank_default(nref)
+    alpha_os = os_factor(nref, k, pfa)
+    wr, wc = guard_r + train_r, guard_c + train_c
+    yy, xx = np.mgrid[-wr:wr + 1, -wc:wc + 1]
+    ring = ~((np.abs(yy) <= guard_r) & (np.abs(xx) <= guard_c))
+    dr, dc = yy[ring], xx[ring]
+    mask = _cut_mask(P.shape, train_r, train_c, guard_r, guard_c, cut_cols)
+    det = np.zeros(P.shape, dtype=np.uint8)
+    thr = np.zeros(P.shape, dtype=np.float64)
+    rs, cs = np.nonzero(mask)
+    for start in range(0, rs.size, 4096):  # chunks keep the gathered windows small
+        r = rs[start:start + 4096, None]
+        c = cs[start:start + 4096, None]
+        cells = P[r + dr[None, :], c + dc[None, :]]
+        xk = np.partition(cells, k - 1, axis=1)[:, k - 1]
+        T = alpha_os * xk
+        thr[rs[start:start + 4096], cs[start:start + 4096]] = T
+        det[rs[start:start + 4096], cs[start:start + 4096]] = (P[rs[start:start + 4096], cs[start:start + 4096]] > T)
     return CfarResult(det, thr, mask)

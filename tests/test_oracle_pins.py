@@ -441,3 +441,67 @@ def test_go_so_monte_carlo_false_alarm_rate(kind):
     mu = n * pfa
     sd = math.sqrt(n * pfa * (1 - pfa))
     assert abs(k - mu) < 5 * sd, (k, mu, sd)
+
+
+# ------------------------------------------------------------ ordered-statistic CFAR
+@pytest.mark.parametrize("n,k", [(8, 6), (72, 54), (112, 84), (400, 1), (400, 400)])
+def test_os_law_matches_beta_function_form(n, k):
+    # X_(k) = -ln(1 - U_(k)) with U_(k) ~ Beta(k, n - k + 1), so
+    # E[exp(-a X_(k))] = E[(1 - U)^a] = B(k, n - k + 1 + a) / B(k, n - k + 1)
+    special = pytest.importorskip("scipy.special")
+    for a in (0.01, 0.5, 3.0, 40.0):
+        want = math.exp(special.betaln(k, n - k + 1 + a) - special.betaln(k, n - k + 1))
+        got = ocfar.pfa_ordered_statistic(a, n, k)
+        assert abs(got - want) <= 1e-10 * want
+
+
+def test_os_factor_inverts_law_and_closed_forms():
+    for n, k, pfa in [(8, 6, 1e-2), (112, 84, 1e-4), (1600, 1200, 1e-6)]:
+        a = ocfar.os_factor(n, k, pfa)
+        assert abs(ocfar.pfa_ordered_statistic(a, n, k) - pfa) <= 1e-10 * pfa
+    # k = 1: X_(1) ~ Exp(n), P = n / (n + a)
+    assert abs(ocfar.os_factor(50, 1, 0.01) - 50 * 99) <= 1e-8 * 50 * 99
+    assert ocfar.os_rank_default(112) == 84 and ocfar.os_rank_default(8) == 6 and ocfar.os_rank_default(1) == 1
+
+
+def test_os_hand_example():
+    # 5 x 5 map, train 1 / guard 0: the ring of the centre CUT holds 1..8, so
+    # X_(6) = 6 and T = alpha 6
+    P = np.zeros((5, 5))
+    ring = [(1, 1), (1, 2), (1, 3), (2, 1), (2, 3), (3, 1), (3, 2), (3, 3)]
+    vals = [5.0, 2.0, 8.0, 1.0, 7.0, 3.0, 6.0, 4.0]
+    for (r, c), v in zip(ring, vals):
+        P[r, c] = v
+    a = ocfar.os_factor(8, 6, 1e-2)
+    P[2, 2] = 6.0 * a * 1.01
+    res = ocfar.cfar_os_direct(P, 1, 1, 0, 0, 1e-2)
+    assert res.cut.sum() == 9
+    assert abs(res.thr[2, 2] - 6.0 * a) <= 1e-12 * a and res.det[2, 2] == 1
+    res = ocfar.cfar_os_direct(P, 1, 1, 0, 0, 1e-2, k=2)
+    assert abs(res.thr[2, 2] - 2.0 * ocfar.os_factor(8, 2, 1e-2)) <= 1e-12 * res.thr[2, 2]
+
+
+def test_os_robust_to_one_interferer_and_scale_invariant():
+    rng = np.random.default_rng(31)
+    Q = rng.exponential(size=(60, 60))
+    Q[30, 30] += 60.0
+    Q[33, 27] += 1e5  # one strong cell in the CUT's window
+    os_ = ocfar.cfar_os_direct(Q, 6, 6, 1, 1, 1e-4)
+    ca = ocfar.cfar_sat(Q, 6, 6, 1, 1, 1e-4)
+    assert os_.det[30, 30] == 1 and ca.det[30, 30] == 0
+    np.testing.assert_array_equal(ocfar.cfar_os_direct(Q * 2.0 ** 7, 6, 6, 1, 1, 1e-4).det, os_.det)
+
+
+def test_os_monte_carlo_false_alarm_rate():
+    # disjoint windows on an iid Exp(1) map: independent Bernoulli(Pfa) CUTs
+    pfa, shape, (tr, tc, gr, gc) = 2e-2, (1100, 1100), (4, 4, 1, 1)
+    P = synth.square_law_map(*shape, n_targets=0, seed=33).astype(np.float64)
+    res = ocfar.cfar_os_direct(P, tr, tc, gr, gc, pfa)
+    w = tr + gr
+    stride = 2 * w + 1
+    sel = res.det[w:shape[0] - w:stride, w:shape[1] - w:stride]
+    n = sel.size
+    k = int(sel.sum())
+    mu = n * pfa
+    sd = math.sqrt(n * pfa * (1 - pfa))
+    assert abs(k - mu) < 5 * sd, (k, mu, sd)
