@@ -144,11 +144,20 @@ typedef struct rcfar_band {
  *     neither. Each half has n = W_r (2 W_c + 1) - guard_r (2 guard_c + 1)
  *     cells, and T = t * max (GO) or t * min (SO) of the two half sums, with t
  *     the factor for which iid exponential noise gives false-alarm
- *     probability exactly Pfa (rcfar_threshold_factor). */
+ *     probability exactly Pfa (rcfar_threshold_factor).
+ * OS (ordered statistic; not in the paper, and not a region sum, so it
+ *     cannot use the eq. 3 table): T = alpha_os * X_(k), X_(k) the k-th
+ *     smallest of the n_ref training cells (k = os_rank, default
+ *     ceil(3 n_ref / 4)), alpha_os such that iid exponential noise gives
+ *     false-alarm probability exactly Pfa:
+ *     prod_{i<k} (n_ref - i) / (n_ref - i + alpha_os) = Pfa. Run by
+ *     rcfar_cfar_direct and by the batched chain (rcfar_run_batch, the
+ *     server), n_ref <= 2048; the table-based calls return UNSUPPORTED. */
 typedef enum rcfar_cfar_kind {
   RCFAR_CFAR_CA = 0,
   RCFAR_CFAR_GO = 1,
-  RCFAR_CFAR_SO = 2
+  RCFAR_CFAR_SO = 2,
+  RCFAR_CFAR_OS = 3
 } rcfar_cfar_kind;
 
 /* CFAR window (Sec. II.B): per-side counts in each dimension. The guard
@@ -160,7 +169,7 @@ typedef struct rcfar_window {
   int32_t guard_r, guard_c;
   double pfa;       /* false-alarm probability, 0 < pfa < 1 */
   int32_t kind;     /* rcfar_cfar_kind (0: cell averaging) */
-  int32_t reserved; /* must be 0 */
+  int32_t os_rank;  /* OS: rank k (1..n_ref, 0: ceil(3 n_ref / 4)); other kinds: must be 0 */
 } rcfar_window;
 
 /* Description of a summed-area table produced by rcfar_sat. The arrays live
@@ -213,7 +222,8 @@ rcfar_status rcfar_n_ref(const rcfar_window* w, int32_t* n_ref_out);
  * host in FP64: CA: alpha / n_ref (applied to S_ref); GO / SO: t (applied to
  * the larger / smaller half sum), found by bisection on the false-alarm law
  * of the kind (relative accuracy 1e-13). cells_out (may be NULL): n_ref for
- * CA, the cells of one half for GO / SO. An invalid window (including a GO /
+ * CA, the cells of one half for GO / SO. OS: alpha_os (applied to the k-th
+ * smallest training cell), cells = n_ref. An invalid window (including a GO /
  * SO window with empty halves) is RCFAR_ERR_INVALID_ARG. */
 rcfar_status rcfar_threshold_factor(const rcfar_window* w, double* factor_out, int32_t* cells_out);
 /* Respiration band of a length-N slow-time transform (Sec. II.A, 0.3-0.8 Hz):
@@ -291,7 +301,9 @@ rcfar_status rcfar_sat_cfar(rcfar_handle h, const void* map, int32_t dtype, int3
 
 /* The same decisions with S_ref summed cell by cell over the n_ref training
  * cells (the sliding-window CA-CFAR that the SAT replaces; Sec. III, Table I
- * "CA-CFAR"). map is float32 [rows][ld_map]. */
+ * "CA-CFAR"). map is float32 [rows][ld_map]. Also the OS variant: the k-th
+ * smallest training cell of each CUT, selected exactly (a bitwise search
+ * over the order-preserving 32-bit keys of the cells). */
 rcfar_status rcfar_cfar_direct(rcfar_handle h, const float* map, int32_t rows, int32_t cols,
                                int64_t ld_map, const rcfar_window* w, int32_t cut_c_lo,
                                int32_t cut_c_hi, uint8_t* det, int64_t ld_det, float* thr,

@@ -40,6 +40,7 @@ RCFAR_X_TRACE_MAJOR = 1
 RCFAR_CFAR_CA = 0
 RCFAR_CFAR_GO = 1
 RCFAR_CFAR_SO = 2
+RCFAR_CFAR_OS = 3
 
 SAT_TILE_H = 32
 SAT_TILE_W = 128
@@ -84,7 +85,7 @@ class rcfar_band(ctypes.Structure):
 class rcfar_window(ctypes.Structure):
     _fields_ = [("train_r", ctypes.c_int32), ("train_c", ctypes.c_int32), ("guard_r", ctypes.c_int32),
                 ("guard_c", ctypes.c_int32), ("pfa", ctypes.c_double), ("kind", ctypes.c_int32),
-                ("reserved", ctypes.c_int32)]
+                ("os_rank", ctypes.c_int32)]
 
 
 class rcfar_sat_view(ctypes.Structure):
@@ -226,9 +227,10 @@ def _ld(t) -> int:
     return int(t.stride(0))
 
 
-def make_window(train_r, train_c, guard_r, guard_c, pfa, kind=RCFAR_CFAR_CA) -> rcfar_window:
-    """kind: RCFAR_CFAR_CA (cell averaging), RCFAR_CFAR_GO or RCFAR_CFAR_SO."""
-    return rcfar_window(int(train_r), int(train_c), int(guard_r), int(guard_c), float(pfa), int(kind), 0)
+def make_window(train_r, train_c, guard_r, guard_c, pfa, kind=RCFAR_CFAR_CA, os_rank=0) -> rcfar_window:
+    """kind: RCFAR_CFAR_CA (cell averaging), RCFAR_CFAR_GO, RCFAR_CFAR_SO or RCFAR_CFAR_OS;
+    os_rank: the OS rank k (0: ceil(3 n_ref / 4))."""
+    return rcfar_window(int(train_r), int(train_c), int(guard_r), int(guard_c), float(pfa), int(kind), int(os_rank))
 
 
 def make_pre_params(fs_hz=20.0, f_lo_hz=0.3, f_hi_hz=0.8, mean_len=5, halo_c=0, detector=0,
@@ -254,7 +256,8 @@ def rcfar_n_ref(window: rcfar_window) -> int:
 
 def rcfar_threshold_factor(window: rcfar_window):
     """(factor, cells): alpha / n_ref and n_ref for cell averaging; the
-    half-sum factor t and the cells of one half for greatest-of / smallest-of."""
+    half-sum factor t and the cells of one half for greatest-of / smallest-of;
+    alpha_os and n_ref for the ordered statistic."""
     f = ctypes.c_double()
     n = ctypes.c_int32()
     _check(lib().rcfar_threshold_factor(ctypes.byref(window), ctypes.byref(f), ctypes.byref(n)),

@@ -313,12 +313,19 @@ struct DeviceGuard {
 };
 
 bool valid_window(const rcfar_window* w) {
-  return w && w->train_r >= 0 && w->train_c >= 0 && w->guard_r >= 0 && w->guard_c >= 0 &&
-         w->pfa > 0.0 && w->pfa < 1.0 && n_ref_of(*w) > 0 && w->reserved == 0 &&
-         (w->kind == RCFAR_CFAR_CA ||
-          ((w->kind == RCFAR_CFAR_GO || w->kind == RCFAR_CFAR_SO) &&
-           (long long)(w->guard_r + w->train_r) * (2LL * (w->guard_c + w->train_c) + 1) -
-                   (long long)w->guard_r * (2LL * w->guard_c + 1) > 0));
+  if (!w || w->train_r < 0 || w->train_c < 0 || w->guard_r < 0 || w->guard_c < 0 || !(w->pfa > 0.0 && w->pfa < 1.0))
+    return false;
+  const int nr = n_ref_of(*w);
+  if (nr <= 0) return false;
+  switch (w->kind) {
+    case RCFAR_CFAR_CA: return w->os_rank == 0;
+    case RCFAR_CFAR_GO:
+    case RCFAR_CFAR_SO:
+      return w->os_rank == 0 && (long long)(w->guard_r + w->train_r) * (2LL * (w->guard_c + w->train_c) + 1) -
+                                        (long long)w->guard_r * (2LL * w->guard_c + 1) > 0;
+    case RCFAR_CFAR_OS: return w->os_rank >= 0 && w->os_rank <= nr;
+  }
+  return false;
 }
 
 }  // namespace
@@ -373,6 +380,38 @@ static double go_so_factor_of(int kind, int n, double pfa) {
   return 0.5 * (lo + hi);
 }
 
+// Ordered-statistic law on iid exponential noise: the k-th smallest of n
+// Exp(1) cells is a sum of independent exponentials with rates n, n-1, ...,
+// n-k+1, so P(CUT > a X_(k)) = prod_{i<k} (n-i) / (n-i+a); its logarithm,
+// accumulated as a product with a rescale, falls monotonically in a.
+static double os_log_law(int n, int k, double a) {
+  double prod = 1.0, logacc = 0.0;
+  for (int i = 0; i < k; ++i) {
+    prod *= (double)(n - i) / ((double)(n - i) + a);
+    if (prod < 1e-200) {
+      logacc += std::log(prod);
+      prod = 1.0;
+    }
+  }
+  return logacc + std::log(prod);
+}
+
+static double os_factor_of(int n, int k, double pfa) {
+  const double target = std::log(pfa);
+  double lo = 0.0, hi = 1.0;
+  while (os_log_law(n, k, hi) > target && hi < 1e300) hi *= 2.0;
+  for (int it = 0; it < 200 && hi - lo > 1e-14 * hi; ++it) {
+    const double mid = 0.5 * (lo + hi);
+    if (os_log_law(n, k, mid) > target) lo = mid; else hi = mid;
+  }
+  return 0.5 * (lo + hi);
+}
+
+static int os_rank_of(const rcfar_window& w) {
+  const int nr = n_ref_of(w);
+  return w.os_rank > 0 ? w.os_rank : (3 * nr + 3) / 4;
+}
+
 static long long half_cells_of(const rcfar_window& w) {
   const long long wr = w.guard_r + w.train_r, wc = w.guard_c + w.train_c;
   return wr * (2 * wc + 1) - (long long)w.guard_r * (2LL * w.guard_c + 1);
@@ -380,33 +419,42 @@ static long long half_cells_of(const rcfar_window& w) {
 
 namespace rcfar {
 bool window_factor(const rcfar_window& w, double* factor, int* cells) {
-  if (w.train_r < 0 || w.train_c < 0 || w.guard_r < 0 || w.guard_c < 0 || !(w.pfa > 0.0 && w.pfa < 1.0) ||
-      w.reserved != 0)
+  if (w.train_r < 0 || w.train_c < 0 || w.guard_r < 0 || w.guard_c < 0 || !(w.pfa > 0.0 && w.pfa < 1.0))
     return false;
+  const int nr = n_ref_of(w);
+  if (nr <= 0) return false;
+  if (w.kind != RCFAR_CFAR_OS && w.os_rank != 0) return false;
   if (w.kind == RCFAR_CFAR_CA) {
-    const int nr = n_ref_of(w);
-    if (nr <= 0) return false;
     *factor = alpha_of(nr, w.pfa) / (double)nr;
     if (cells) *cells = nr;
     return true;
   }
-  if (w.kind != RCFAR_CFAR_GO && w.kind != RCFAR_CFAR_SO) return false;
-  const long long n = half_cells_of(w);
+  long long n = 0;
+  int k = 0;
+  if (w.kind == RCFAR_CFAR_GO || w.kind == RCFAR_CFAR_SO) {
+    n = half_cells_of(w);
+  } else if (w.kind == RCFAR_CFAR_OS) {
+    n = nr;
+    k = os_rank_of(w);
+    if (w.os_rank < 0 || k > nr) return false;
+  } else {
+    return false;
+  }
   if (n <= 0 || n > (1 << 24)) return false;
   // the bisection costs up to a few hundred microseconds for large windows;
   // batches and servers ask for the same few windows again and again
   struct Entry {
-    int kind, n;
+    int kind, n, k;
     double pfa, factor;
   };
   static thread_local Entry cache[8] = {};
   static thread_local int next = 0;
   double f = -1.0;
   for (const Entry& e : cache)
-    if (e.n == (int)n && e.kind == w.kind && e.pfa == w.pfa) f = e.factor;
+    if (e.n == (int)n && e.kind == w.kind && e.k == k && e.pfa == w.pfa) f = e.factor;
   if (f < 0.0) {
-    f = go_so_factor_of(w.kind, (int)n, w.pfa);
-    cache[next] = Entry{w.kind, (int)n, w.pfa, f};
+    f = w.kind == RCFAR_CFAR_OS ? os_factor_of((int)n, k, w.pfa) : go_so_factor_of(w.kind, (int)n, w.pfa);
+    cache[next] = Entry{w.kind, (int)n, k, w.pfa, f};
     next = (next + 1) % 8;
   }
   *factor = f;
@@ -959,6 +1007,8 @@ static void fill_cfar_window(CfarMapDev& P, const rcfar_window* w, int rows, int
   window_factor(*w, &k, nullptr);  // the window was validated
   P.kthr = (float)k;
   P.kind = w->kind;
+  P.n_ref = n_ref_of(*w);
+  P.os_rank = w->kind == RCFAR_CFAR_OS ? os_rank_of(*w) : 0;
   P.row_lo = P.wr;
   P.row_hi = rows - 1 - P.wr;
   P.cut_lo = std::max(P.wc, cut_c_lo);
@@ -975,7 +1025,8 @@ rcfar_status rcfar_cfar(rcfar_handle h, const rcfar_sat_view* view, const void* 
     return RCFAR_ERR_INVALID_ARG;
   rcfar_status st = check_view(h, view);
   if (st != RCFAR_OK) return st;
-  if (w->guard_r + w->train_r > h->cfg.max_window || w->guard_c + w->train_c > h->cfg.max_window)
+  if (w->guard_r + w->train_r > h->cfg.max_window || w->guard_c + w->train_c > h->cfg.max_window ||
+      w->kind == RCFAR_CFAR_OS)
     return RCFAR_ERR_UNSUPPORTED;
   DeviceGuard dg(h->device);
   cudaStream_t s = (cudaStream_t)stream;
@@ -1029,7 +1080,8 @@ rcfar_status rcfar_sat_cfar(rcfar_handle h, const void* map, int32_t dtype, int3
     return RCFAR_ERR_INVALID_ARG;
   if ((thr && ld_thr < cols) || (dtype != RCFAR_MAP_F32 && dtype != RCFAR_MAP_F16)) return RCFAR_ERR_INVALID_ARG;
   if (!(value_bound > 0.0f) || !std::isfinite(value_bound)) return RCFAR_ERR_INVALID_ARG;
-  if (w->guard_r + w->train_r > h->cfg.max_window || w->guard_c + w->train_c > h->cfg.max_window)
+  if (w->guard_r + w->train_r > h->cfg.max_window || w->guard_c + w->train_c > h->cfg.max_window ||
+      w->kind == RCFAR_CFAR_OS)
     return RCFAR_ERR_UNSUPPORTED;
   DeviceGuard dg(h->device);
   cudaStream_t s = (cudaStream_t)stream;
@@ -1093,6 +1145,18 @@ rcfar_status rcfar_cfar_direct(rcfar_handle h, const float* map, int32_t rows, i
   P.ld_det = ld_det;
   P.thr = thr;
   P.ld_thr = ld_thr;
+  if (w->kind == RCFAR_CFAR_OS) {
+    const size_t smem = cfar_os_smem(P.wr, P.wc, P.n_ref);
+    if (P.n_ref > kOsMaxRef || smem > std::min<size_t>(h->smem_optin, 200 * 1024)) return RCFAR_ERR_UNSUPPORTED;
+    static thread_local CfarBatch ob;
+    ob.n = 1;
+    ob.status = h->status;
+    ob.m[0] = P;
+    ob.m[0].item0 = 0;
+    const int blocks = cfar_os_geometry(ob.m[0], rows, cols);
+    TraceScope tr(h, "cfar_os", s);
+    return cuda_fail(launch_cfar_os(ob, P.n_ref, blocks, smem, s));
+  }
   int bh = 32, bw = 64;
   while (cfar_direct_smem_bytes(bh, bw, P.wr, P.wc) > std::min<size_t>(h->smem_optin, 200 * 1024) && bw > 8) {
     if (bw > bh) bw /= 2; else bh /= 2;
@@ -1181,6 +1245,11 @@ rcfar_status rcfar_run_batch(rcfar_handle h, const rcfar_frame_desc* frames, int
         f.window.guard_r + f.window.train_r > h->cfg.max_window ||
         f.window.guard_c + f.window.train_c > h->cfg.max_window)
       return RCFAR_ERR_UNSUPPORTED;
+    if (f.window.kind == RCFAR_CFAR_OS &&
+        (n_ref_of(f.window) > kOsMaxRef ||
+         cfar_os_smem(f.window.guard_r + f.window.train_r, f.window.guard_c + f.window.train_c, n_ref_of(f.window)) >
+             std::min<size_t>(h->smem_optin, 200 * 1024)))
+      return RCFAR_ERR_UNSUPPORTED;
     need_ctl += frame_ctl_bytes(f.M, f.N, C);
     need_data += frame_data_bytes(f.M, f.N, C, p->x_layout);
   }
@@ -1200,12 +1269,18 @@ rcfar_status rcfar_run_batch(rcfar_handle h, const rcfar_frame_desc* frames, int
   static thread_local CfarBatch cb;
   for (int base = 0; base < n; base += kMaxBatch) {
     const int cnt = std::min(kMaxBatch, n - base);
+    // ordered-statistic frames skip the table: their maps go to the OS kernel
+    static thread_local CfarBatch ob;
+    int n_sat = 0, n_os = 0;
+    for (int k = 0; k < cnt; ++k) (frames[base + k].window.kind == RCFAR_CFAR_OS ? n_os : n_sat) += 1;
     pb.n = cnt;
     pb.status = h->status;
-    sb.n = cnt;
-    cb.n = cnt;
+    sb.n = n_sat;
+    cb.n = n_sat;
+    ob.n = n_os;
     cb.status = h->status;
     sb.status = h->status;
+    ob.status = h->status;
     int kb_per_cta = 1;
     {
       int bn_max = 16;
@@ -1238,12 +1313,14 @@ rcfar_status rcfar_run_batch(rcfar_handle h, const rcfar_frame_desc* frames, int
       // one row-prefix width (e) for the launch: the widest frame's
       for (int k = 0; k < cnt && sat_mode == RCFAR_SAT_FUSED; ++k) {
         const rcfar_frame_desc& f = frames[base + k];
+        if (f.window.kind == RCFAR_CFAR_OS) continue;
         const int e = stream_e_of(f.M, bands[base + k].cols, f.window.guard_c + f.window.train_c);
         if (e == 0) sat_mode = RCFAR_SAT_TILE_I64;
         stream_e = std::max(stream_e, e);
       }
       for (int k = 0; k < cnt && sat_mode == RCFAR_SAT_FUSED; ++k) {
         const rcfar_frame_desc& f = frames[base + k];
+        if (f.window.kind == RCFAR_CFAR_OS) continue;
         const int share = (int)std::max<long long>(1, (long long)h->sms * f.M / std::max<long long>(1, rows_all));
         if (!cfar_stream_plan(f.M, bands[base + k].cols, f.window.guard_r + f.window.train_r,
                               f.window.guard_c + f.window.train_c, cap, share, stream_e, &splans[k]))
@@ -1254,6 +1331,7 @@ rcfar_status rcfar_run_batch(rcfar_handle h, const rcfar_frame_desc* frames, int
       sat_mode = RCFAR_SAT_I64;
       for (int k = 0; k < cnt && sat_mode == RCFAR_SAT_I64; ++k) {
         const rcfar_window& w = frames[base + k].window;
+        if (w.kind == RCFAR_CFAR_OS) continue;
         int rr = 0, hc = 0;
         if (!cfar_ring_plan(w.guard_r + w.train_r, w.guard_c + w.train_c, h->smem_optin, &rr, &hc))
           sat_mode = RCFAR_SAT_TILE_I64;
@@ -1267,6 +1345,8 @@ rcfar_status rcfar_run_batch(rcfar_handle h, const rcfar_frame_desc* frames, int
     bool dft_tma_ok = true;
     int it_stats = 0, it_dft = 0, it_norm = 0, it_cfar = 0, it_y = 0, it_tr = 0;
     int it_tile = 0, it_band = 0, it_vscan = 0;
+    int i_sat = 0, i_os = 0, it_os = 0, os_nref = 0;  // table items, OS items, OS CTAs
+    size_t os_smem = 0;
     int cfar_mode_smem = 0, cfar_max_hc = 0;
     for (int k = 0; k < cnt; ++k) {
       const int i = base + k;
@@ -1316,9 +1396,31 @@ rcfar_status rcfar_run_batch(rcfar_handle h, const rcfar_frame_desc* frames, int
       it_stats += g.n_strips * g.n_chunks;
       it_dft += g.mtiles * g.ntiles * g.splitk;
       it_norm += g.n_norm;
+      if (!F.stats || !F.partial || !F.rowpart || !F.strip_ab || !F.yhi || !F.ylo || !F.rowmean || !F.rowsq ||
+          !F.kpart || !map || !F.strip_cnt || !F.tile_cnt || !words)
+        return RCFAR_ERR_OUT_OF_WORKSPACE;
+      if (f.window.kind == RCFAR_CFAR_OS) {
+        CfarMapDev& Q = ob.m[i_os++];
+        std::memset(&Q, 0, sizeof(Q));
+        Q.map = map;
+        Q.ld_map = ld_map;
+        Q.in_scale = 1.0f;
+        Q.rows = f.M;
+        Q.cols = C;
+        fill_cfar_window(Q, &f.window, f.M, C, b.k_lo - b.c0, b.k_hi - b.c0);
+        Q.det = f.det;
+        Q.ld_det = f.ld_det;
+        Q.thr = f.thr;
+        Q.ld_thr = f.ld_thr;
+        Q.item0 = it_os;
+        it_os += cfar_os_geometry(Q, f.M, C);
+        os_smem = std::max(os_smem, cfar_os_smem(Q.wr, Q.wc, Q.n_ref));
+        os_nref = std::max(os_nref, Q.n_ref);
+        continue;
+      }
 
       const SatGeom sg = sat_geom(f.M, C);
-      SatMapDev& m = sb.m[k];
+      SatMapDev& m = sb.m[i_sat];
       std::memset(&m, 0, sizeof(m));
       m.map = map;
       m.ld = ld_map;
@@ -1348,7 +1450,7 @@ rcfar_status rcfar_run_batch(rcfar_handle h, const rcfar_frame_desc* frames, int
           !sat_ok || !F.strip_cnt || !F.tile_cnt || !words)
         return RCFAR_ERR_OUT_OF_WORKSPACE;
 
-      CfarMapDev& P = cb.m[k];
+      CfarMapDev& P = cb.m[i_sat];
       std::memset(&P, 0, sizeof(P));
       P.table = m.table;
       P.ld_table = m.ld_table;
@@ -1392,6 +1494,7 @@ rcfar_status rcfar_run_batch(rcfar_handle h, const rcfar_frame_desc* frames, int
         cfar_mode_smem = std::max<int>(cfar_mode_smem, (int)cfar_smem_bytes(sat_mode, t.bh, t.bw, P.wr, P.wc));
         cfar_max_hc = std::max(cfar_max_hc, t.bw + 2 * P.wc + 1);
       }
+      ++i_sat;
     }
     cudaError_t e = cudaSuccess;
     if (it_tr > 0) {
@@ -1424,6 +1527,10 @@ rcfar_status rcfar_run_batch(rcfar_handle h, const rcfar_frame_desc* frames, int
           : sat_mode == RCFAR_SAT_I64
               ? launch_cfar_ring(cb, true, RCFAR_MAP_F32, it_cfar, ring_smem, s)
               : launch_cfar(cb, sat_mode, RCFAR_MAP_F32, it_cfar, (size_t)cfar_mode_smem, cfar_max_hc, s);
+    }
+    if (e == cudaSuccess && it_os > 0) {
+      TraceScope t(h, "cfar_os", s);
+      e = launch_cfar_os(ob, os_nref, it_os, os_smem, s);
     }
     if (e != cudaSuccess) return RCFAR_ERR_CUDA;
   }

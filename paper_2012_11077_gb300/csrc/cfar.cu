@@ -895,6 +895,123 @@ __global__ void __launch_bounds__(kStreamThreads, 2) k_sat_cfar_stream(const __g
   if (tid == 0 && s_bad && B.status) atomicOr(B.status, kStatusRange);
 }
 
+// Ordered-statistic CFAR. A CTA holds the map tile of kOsRows x 32 CUTs plus
+// the window halo in shared memory, and the offsets of the n_ref training
+// cells (outer box minus guard box) relative to the CUT. Warp w takes CUT row
+// w, one CUT at a time: lane l loads training cells l, l + 32, ... as
+// order-preserving 32-bit keys into registers (kNK per lane), and the warp
+// finds the k-th smallest key by building it bit by bit from the top: a bit
+// is set when fewer than k keys lie below the key with that bit set
+// (per-lane counts, one warp reduction per bit; bits above the first one in
+// which the window's smallest and largest keys differ are taken from them).
+// T = alpha_os X_(k); lane c keeps column c's result and the warp stores
+// its row of decisions at the end.
+__device__ __forceinline__ unsigned os_key(float v) {
+  const unsigned b = __float_as_uint(v);
+  return (b & 0x80000000u) ? ~b : (b | 0x80000000u);
+}
+__device__ __forceinline__ float os_value(unsigned k) {
+  return __uint_as_float((k & 0x80000000u) ? (k & 0x7fffffffu) : ~k);
+}
+
+template <int kNK>
+__global__ void __launch_bounds__(256, 2) k_cfar_os(const __grid_constant__ CfarBatch B) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int mi = find_item(B.m, B.n, (int)blockIdx.x, &CfarMapDev::item0);
+  const CfarMapDev& P = B.m[mi];
+  const int local = (int)blockIdx.x - P.item0;
+  const int ty = local / P.tiles_x, tx = local - ty * P.tiles_x;
+  const int r0 = ty * kOsRows, c0 = tx * 32;
+  const int wr = P.wr, wc = P.wc, gr = P.gr, gc = P.gc;
+  const int HR = kOsRows + 2 * wr, HC = 32 + 2 * wc;
+  const int nref = P.n_ref, kr = P.os_rank;
+  float* X = reinterpret_cast<float*>(smem_raw);
+  int* offs = reinterpret_cast<int*>(X + HR * HC);
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const float* map = reinterpret_cast<const float*>(P.map);
+  for (int i = tid; i < HR * HC; i += 256) {
+    const int hr = i / HC, hc = i - hr * HC;
+    const int r = r0 - wr + hr, c = c0 - wc + hc;
+    X[i] = (r >= 0 && r < P.rows && c >= 0 && c < P.cols) ? __ldg(map + (long long)r * P.ld_map + c) : 0.f;
+  }
+  // training cell i -> (dr, dc): rows above the guard box (full width), the
+  // guard rows (left and right of the guard box), rows below
+  {
+    const int W = 2 * wc + 1, side = wc - gc;
+    const int top = (wr - gr) * W, mid = (2 * gr + 1) * 2 * side;
+    for (int i = tid; i < nref; i += 256) {
+      int dr, dc;
+      if (i < top) {
+        dr = -wr + i / W;
+        dc = -wc + i % W;
+      } else if (i < top + mid) {
+        const int j = i - top;
+        dr = -gr + j / (2 * side);
+        const int q = j % (2 * side);
+        dc = q < side ? -wc + q : gc + 1 + (q - side);
+      } else {
+        const int j = i - top - mid;
+        dr = gr + 1 + j / W;
+        dc = -wc + j % W;
+      }
+      offs[i] = dr * HC + dc;
+    }
+  }
+  __syncthreads();
+  const int r = r0 + warp;
+  unsigned char my_d = 0;
+  float my_t = 0.f;
+  if (r < P.rows && r >= P.row_lo && r <= P.row_hi) {
+    const float alpha = P.kthr;
+    for (int cc = 0; cc < 32; ++cc) {
+      const int c = c0 + cc;
+      if (c < P.cut_lo || c > P.cut_hi || c >= P.cols) continue;  // uniform over the warp
+      const float* ctr = X + (warp + wr) * HC + (cc + wc);
+      unsigned key[kNK];
+      unsigned mn = 0xffffffffu, mx = 0u;
+#pragma unroll
+      for (int m = 0; m < kNK; ++m) {
+        const int i = lane + 32 * m;
+        key[m] = i < nref ? os_key(ctr[offs[i]]) : 0xffffffffu;
+        if (i < nref) {
+          mn = min(mn, key[m]);
+          mx = max(mx, key[m]);
+        }
+      }
+      mn = __reduce_min_sync(0xffffffffu, mn);
+      mx = __reduce_max_sync(0xffffffffu, mx);
+      // bits above the highest differing bit of mn and mx are common to every key
+      const unsigned diff = mn ^ mx;
+      const int top = diff ? 31 - __clz(diff) : -1;
+      unsigned t = top >= 0 ? (mn & ~((2u << top) - 1u)) : mn;
+      if (top == 31) t = 0u;
+      for (int b = top; b >= 0; --b) {
+        const unsigned cand = t | (1u << b);
+        int n0 = 0, n1 = 0, n2 = 0, n3 = 0;
+#pragma unroll
+        for (int m = 0; m < kNK; m += 4) {
+          n0 += key[m] < cand;
+          if (m + 1 < kNK) n1 += key[m + 1] < cand;
+          if (m + 2 < kNK) n2 += key[m + 2] < cand;
+          if (m + 3 < kNK) n3 += key[m + 3] < cand;
+        }
+        const int below = (int)__reduce_add_sync(0xffffffffu, (unsigned)((n0 + n1) + (n2 + n3)));
+        if (below < kr) t = cand;
+      }
+      const float T = alpha * os_value(t);
+      if (lane == cc) {
+        my_t = T;
+        my_d = ctr[0] > T ? 1 : 0;
+      }
+    }
+  }
+  const int c = c0 + lane;
+  if (r < P.rows && c < P.cols) {
+    P.det[(long long)r * P.ld_det + c] = my_d;
+    if (P.thr) P.thr[(long long)r * P.ld_thr + c] = my_t;
+  }
+}
+
 __global__ void __launch_bounds__(256) k_cfar_direct(const __grid_constant__ CfarMapDev P) {
   extern __shared__ __align__(16) float X[];
   const int local = (int)blockIdx.x;
@@ -1196,6 +1313,40 @@ cudaError_t launch_cfar_stream(const CfarBatch& b, bool map_cut, int e, int bloc
   if (e == 5) return wide ? launch_stream_ce<8, 5>(b, map_cut, blocks, smem, s) : launch_stream_ce<4, 5>(b, map_cut, blocks, smem, s);
   if (e == 6) return wide ? launch_stream_ce<8, 6>(b, map_cut, blocks, smem, s) : launch_stream_ce<4, 6>(b, map_cut, blocks, smem, s);
   return wide ? launch_stream_ce<8, 8>(b, map_cut, blocks, smem, s) : launch_stream_ce<4, 8>(b, map_cut, blocks, smem, s);
+}
+
+int cfar_os_geometry(CfarMapDev& P, int rows, int cols) {
+  P.tiles_x = (cols + 31) / 32;
+  P.bh = kOsRows;
+  P.bw = 32;
+  return P.tiles_x * ((rows + kOsRows - 1) / kOsRows);
+}
+
+size_t cfar_os_smem(int wr, int wc, int n_ref) {
+  return (size_t)(kOsRows + 2 * wr) * (32 + 2 * wc) * 4 + (size_t)n_ref * 4;
+}
+
+template <int kNK>
+static cudaError_t launch_os_t(const CfarBatch& b, int blocks, size_t smem, cudaStream_t s) {
+  auto fn = k_cfar_os<kNK>;
+  cudaError_t e = ensure_smem(reinterpret_cast<const void*>(fn), smem);
+  if (e != cudaSuccess) return e;
+  fn<<<blocks, 256, smem, s>>>(b);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_cfar_os(const CfarBatch& b, int max_n_ref, int blocks, size_t smem, cudaStream_t s) {
+  if (blocks <= 0) return cudaSuccess;
+  const int nk = (max_n_ref + 31) / 32;
+  if (nk <= 8) return launch_os_t<8>(b, blocks, smem, s);
+  if (nk <= 16) return launch_os_t<16>(b, blocks, smem, s);
+  if (nk <= 24) return launch_os_t<24>(b, blocks, smem, s);
+  if (nk <= 32) return launch_os_t<32>(b, blocks, smem, s);
+  if (nk <= 40) return launch_os_t<40>(b, blocks, smem, s);
+  if (nk <= 48) return launch_os_t<48>(b, blocks, smem, s);
+  if (nk <= 56) return launch_os_t<56>(b, blocks, smem, s);
+  if (nk <= 64) return launch_os_t<64>(b, blocks, smem, s);
+  return cudaErrorInvalidValue;
 }
 
 cudaError_t launch_cfar_direct(const CfarMapDev& m, int blocks, size_t smem, cudaStream_t s) {

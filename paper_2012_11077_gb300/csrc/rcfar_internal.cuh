@@ -167,6 +167,8 @@ struct CfarMapDev {
   int wr, wc, gr, gc;  // outer and guard half-sizes
   float kthr;          // CA: alpha / n_ref; GO / SO: the half-sum factor t
   int kind;            // rcfar_cfar_kind
+  int os_rank;         // OS: rank k of the order statistic (1-based)
+  int n_ref;           // training cells per CUT
   int cut_lo, cut_hi;  // CUT column range (after the interior clip)
   int row_lo, row_hi;  // CUT row range
   unsigned char* det;
@@ -308,6 +310,14 @@ bool cfar_stream_plan(int rows, int cols, int wr, int wc, size_t smem_cap, int s
                       StreamPlan* out);
 int cfar_stream_geometry(CfarMapDev& P, int rows, int cols, const StreamPlan& sp);
 cudaError_t launch_cfar_stream(const CfarBatch& b, bool map_cut, int e, int blocks, size_t smem, cudaStream_t s);
+
+// Ordered-statistic CFAR on float32 maps: CTAs of kOsRows x 32 CUTs, one warp
+// per CUT row; each CUT's k-th smallest training cell is selected exactly.
+constexpr int kOsRows = 8;
+constexpr int kOsMaxRef = 2048;  // training cells per CUT (64 per lane)
+int cfar_os_geometry(CfarMapDev& P, int rows, int cols);  // CTAs of one map
+size_t cfar_os_smem(int wr, int wc, int n_ref);
+cudaError_t launch_cfar_os(const CfarBatch& b, int max_n_ref, int blocks, size_t smem, cudaStream_t s);
 size_t cfar_direct_smem_bytes(int bh, int bw, int wr, int wc);
 
 }  // namespace rcfar

@@ -78,6 +78,7 @@ extern "C" rcfar_status rcfar_sat_cfar_static(const float* map, int32_t rows, in
   const long long n_ref = (2LL * wr + 1) * (2LL * wc + 1) - (2LL * w->guard_r + 1) * (2LL * w->guard_c + 1);
   double kfac = 0.0;
   if (n_ref <= 0 || !window_factor(*w, &kfac, nullptr)) return RCFAR_ERR_INVALID_ARG;
+  if (w->kind == RCFAR_CFAR_OS) return RCFAR_ERR_UNSUPPORTED;  // an order statistic is not a region sum
 
   // scratch layout: control words | table int64 | col_tot | row_carry | row_tot | col_carry
   const int n_bands = (int)cdiv(rows, kSatTileH), n_chunks = (int)cdiv(cols, kSatTileW);

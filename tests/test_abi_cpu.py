@@ -132,13 +132,22 @@ def test_window_kind_checks(rc):
     L = rc.lib()
     import ctypes
     f = ctypes.c_double()
-    bad = [rc.make_window(4, 4, 1, 1, 1e-3, kind=3), rc.make_window(0, 2, 0, 1, 1e-3, kind=rc.RCFAR_CFAR_GO)]
-    w = rc.make_window(4, 4, 1, 1, 1e-3)
-    w.reserved = 1
-    bad.append(w)
+    bad = [rc.make_window(4, 4, 1, 1, 1e-3, kind=4), rc.make_window(0, 2, 0, 1, 1e-3, kind=rc.RCFAR_CFAR_GO)]
+    bad.append(rc.make_window(4, 4, 1, 1, 1e-3, os_rank=3))  # a rank for a non-OS window
+    bad.append(rc.make_window(4, 4, 1, 1, 1e-3, kind=rc.RCFAR_CFAR_OS, os_rank=113))  # above n_ref = 112
     for w in bad:
         assert L.rcfar_threshold_factor(ctypes.byref(w), ctypes.byref(f), None) == rc.RCFAR_ERR_INVALID_ARG
     # the same columns-only window is valid for cell averaging (its training
     # cells all lie in the CUT's row, which neither half holds)
     ok = rc.make_window(0, 2, 0, 1, 1e-3)
     assert L.rcfar_threshold_factor(ctypes.byref(ok), ctypes.byref(f), None) == rc.RCFAR_OK
+
+
+def test_os_factor_matches_oracle(rc):
+    for tr, tc, gr, gc, pfa, k in [(4, 4, 1, 1, 1e-3, 0), (16, 16, 4, 4, 1e-6, 0), (1, 1, 0, 0, 1e-2, 0),
+                                   (8, 8, 2, 2, 1e-4, 1), (8, 8, 2, 2, 1e-4, 416), (3, 5, 1, 2, 1e-2, 20)]:
+        f, n = rc.rcfar_threshold_factor(rc.make_window(tr, tc, gr, gc, pfa, kind=rc.RCFAR_CFAR_OS, os_rank=k))
+        assert n == ocfar.n_ref(tr, tc, gr, gc)
+        kk = k or ocfar.os_rank_default(n)
+        o = ocfar.os_factor(n, kk, pfa)
+        assert abs(f - o) <= 1e-12 * o, (tr, tc, gr, gc, pfa, k, f, o)

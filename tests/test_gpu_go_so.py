@@ -305,3 +305,123 @@ def test_server_go_so_frames(rc):
     finally:
         rc.rcfar_server_destroy(srv)
         rc.rcfar_destroy(h1)
+
+
+# ------------------------------------------------------------ ordered statistic
+OS_CASES = CASES[:3] + CASES[4:] + [((200, 150), (4, 4, 1, 1, 1e-3), None)]
+
+
+@pytest.mark.parametrize("shape,win,cut", OS_CASES)
+@pytest.mark.parametrize("rank", ["default", "first", "last"])
+def test_os_direct_parity(rc, h, shape, win, cut, rank):
+    # the k-th smallest is selected exactly, so the threshold is alpha_os times
+    # the oracle's own cell value (one FP32 rounding of alpha and one of the product)
+    P = edge_map(shape, seed=7 * shape[0] + shape[1])
+    rows, cols = shape
+    nref = ocfar.n_ref(*win[:4])
+    k = {"default": 0, "first": 1, "last": nref}[rank]
+    det = torch.full((rows, cols), 7, dtype=torch.uint8, device="cuda")
+    thr = torch.full((rows, cols), -1.0, dtype=torch.float32, device="cuda")
+    lo, hi = cut if cut is not None else (0, cols - 1)
+    rc.rcfar_cfar_direct(h, dev_t(P), rc.make_window(*win, kind=rc.RCFAR_CFAR_OS, os_rank=k), lo, hi, det, thr)
+    assert rc.rcfar_get_error(h) == rc.RCFAR_OK
+    ref = ocfar.cfar_os_direct(P.astype(np.float64), *win, k=k, cut_cols=cut)
+    det, thr = det.cpu().numpy(), thr.cpu().numpy()
+    assert np.all(det[~ref.cut] == 0) and np.all(thr[~ref.cut] == 0)
+    cmp = ocfar.compare_decisions(det, ref.det, P, ref.thr, ref.cut, margin=MARGIN)
+    assert cmp.mismatches == 0, cmp
+    if ref.cut.any():
+        o = ref.thr[ref.cut]
+        assert np.all(np.abs(thr[ref.cut] - o) <= 2.5e-7 * np.abs(o) + 1e-30)
+
+
+def test_os_negative_values_and_ties(rc, h):
+    # signed values (the keys must order negatives below positives) and a map
+    # of small integers (many equal cells: the rank counts duplicates)
+    rng = np.random.default_rng(5)
+    for P in (rng.standard_normal((90, 120)).astype(np.float32),
+              rng.integers(0, 6, size=(90, 120)).astype(np.float32)):
+        for k in (0, 1, 30, 72):
+            w = rc.make_window(4, 4, 1, 1, 1e-2, kind=rc.RCFAR_CFAR_OS, os_rank=k)
+            det = torch.empty((90, 120), dtype=torch.uint8, device="cuda")
+            thr = torch.empty((90, 120), dtype=torch.float32, device="cuda")
+            rc.rcfar_cfar_direct(h, dev_t(P), w, 0, 119, det, thr)
+            ref = ocfar.cfar_os_direct(P.astype(np.float64), 4, 4, 1, 1, 1e-2, k=k)
+            t = thr.cpu().numpy()[ref.cut]
+            o = ref.thr[ref.cut]
+            assert np.all(np.abs(t - o) <= 2.5e-7 * np.abs(o) + 1e-30), k
+            cmp = ocfar.compare_decisions(det.cpu().numpy(), ref.det, P, ref.thr, ref.cut, margin=MARGIN)
+            assert cmp.mismatches == 0, (k, cmp)
+    assert rc.rcfar_get_error(h) == rc.RCFAR_OK
+
+
+def test_os_hand_example_and_table_paths_unsupported(rc, h):
+    P = np.zeros((5, 5), dtype=np.float32)
+    for (r, c), v in zip([(1, 1), (1, 2), (1, 3), (2, 1), (2, 3), (3, 1), (3, 2), (3, 3)],
+                         [5.0, 2.0, 8.0, 1.0, 7.0, 3.0, 6.0, 4.0]):
+        P[r, c] = v
+    w = rc.make_window(1, 1, 0, 0, 1e-2, kind=rc.RCFAR_CFAR_OS)
+    a, n = rc.rcfar_threshold_factor(w)
+    assert n == 8
+    P[2, 2] = 6.0 * a * 1.01
+    Pt = dev_t(P)
+    det = torch.zeros((5, 5), dtype=torch.uint8, device="cuda")
+    thr = torch.zeros((5, 5), dtype=torch.float32, device="cuda")
+    rc.rcfar_cfar_direct(h, Pt, w, 0, 4, det, thr)
+    assert abs(float(thr[2, 2]) - 6.0 * a) <= 1e-6 * a and int(det[2, 2]) == 1 and int(det.sum()) == 1
+    view = rc.rcfar_sat(h, Pt, value_bound=1e6, mode=rc.RCFAR_SAT_I64)
+    for call in (lambda: rc.rcfar_cfar(h, view, Pt, w, 0, 4, det),
+                 lambda: rc.rcfar_sat_cfar(h, Pt, 1e6, w, 0, 4, det),
+                 lambda: rc.rcfar_sat_cfar_static(Pt, 1e6, w, 0, 4, det)):
+        with pytest.raises(rc.RcfarError) as e:
+            call()
+        assert e.value.status == rc.RCFAR_ERR_UNSUPPORTED
+
+
+def test_batch_with_os_frames(rc):
+    # ordered-statistic frames in a batch with cell-averaging and greatest-of
+    # frames: every tuning gives identical outputs and each frame matches the
+    # FP64 chain of its kind
+    cases = synth.mixed_batch_cases(8, seed=41, m_range=(64, 256), n_range=(256, 1200))
+    params = rc.make_pre_params(synth.FS_HZ, mean_len=5, halo_c=-1)
+    h2 = rc.rcfar_create(device=0, max_rows=512, max_cols=1100, max_n=2048, max_window=20, max_frames=16,
+                         batch_bytes=1 << 30)
+    kinds = [(rc.RCFAR_CFAR_OS, "os"), (rc.RCFAR_CFAR_CA, "ca"), (rc.RCFAR_CFAR_OS, "os"), (rc.RCFAR_CFAR_GO, "go")]
+    try:
+        keep, frames, outs = [], [], []
+        for i, c in enumerate(cases):
+            w = c.window
+            band = rc.rcfar_band_plan(c.spec.N, rc.make_pre_params(synth.FS_HZ, mean_len=5,
+                                                                   halo_c=w.train_c + w.guard_c))
+            X = synth.radar_frame(c.spec)
+            x = dev_t(X)
+            det = torch.empty((c.spec.M, band.cols), dtype=torch.uint8, device="cuda")
+            thr = torch.empty((c.spec.M, band.cols), dtype=torch.float32, device="cuda")
+            win = rc.make_window(w.train_r, w.train_c, w.guard_r, w.guard_c, w.pfa, kind=kinds[i % 4][0])
+            keep.append((X, x, win))
+            frames.append(rc.frame_desc(x, win, det, thr))
+            outs.append((det, thr))
+        ref = None
+        for t in [rc.make_batch_tuning(), rc.make_batch_tuning(2, rc.RCFAR_SAT_I64),
+                  rc.make_batch_tuning(0, rc.RCFAR_SAT_FUSED)]:
+            rc.rcfar_set_batch_tuning(h2, t)
+            for d, th in outs:
+                d.fill_(7)
+                th.fill_(-1.0)
+            rc.rcfar_run_batch(h2, frames, params)
+            assert rc.rcfar_get_error(h2) == rc.RCFAR_OK
+            got = [(d.cpu(), th.cpu()) for d, th in outs]
+            if ref is None:
+                ref = got
+            else:
+                for (a, b), (a2, b2) in zip(ref, got):
+                    assert torch.equal(a, a2) and torch.equal(b, b2)
+        for i, (c, (X, x, win), (d, th)) in enumerate(zip(cases, keep, ref)):
+            w = c.window
+            P_o, band_o = oracle.preprocess_frame(X, synth.FS_HZ, 5, halo=w.train_c + w.guard_c)
+            res = oracle.cfar_chain(P_o, band_o, w.train_r, w.train_c, w.guard_r, w.guard_c, w.pfa,
+                                    kind=kinds[i % 4][1])
+            cmp = ocfar.compare_decisions(d.numpy(), res.det, P_o, res.thr, res.cut, margin=MARGIN)
+            assert cmp.mismatches == 0, (i, cmp)
+    finally:
+        rc.rcfar_destroy(h2)
