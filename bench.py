@@ -522,6 +522,17 @@ def ours(args, rank, world, local, dist):
 
         variants[vname] = graph_rate(chain_k)
 
+    # ordered-statistic thresholds on the same chain (an order statistic is not
+    # a region sum: the map goes to the direct selection kernel)
+    wos = rc.make_window(w.train_r, w.train_c, w.guard_r, w.guard_c, w.pfa, kind=rc.RCFAR_CFAR_OS)
+
+    def chain_os(i):
+        x, P, det = frames[i % RING], maps[i % RING], dets[i % RING]
+        rc.rcfar_preprocess(h, x, params, P)
+        rc.rcfar_cfar_direct(h, P, wos, cut_lo, cut_hi, det)
+
+    variants["ordered_statistic"] = graph_rate(chain_os)
+
     # the paper's own frame size, 600 traces of 1024 range samples, given trace
     # by trace ([N][M], the acquisition order)
     pp = rc.make_pre_params(synth.FS_HZ, mean_len=case.mean_len, halo_c=case.halo_c,
@@ -559,8 +570,14 @@ def ours(args, rank, world, local, dist):
     def fused_sc():
         rc.rcfar_sat_cfar(h, P0, band.value_bound, win, cut_lo, cut_hi, d0, map_cut=False)
 
+    def direct_sc():  # the cell-by-cell CA-CFAR the SAT replaces (Table I's "CA-CFAR")
+        rc.rcfar_cfar_direct(h, P0, win, cut_lo, cut_hi, d1)
+
+    def os_sc():
+        rc.rcfar_cfar_direct(h, P0, wos, cut_lo, cut_hi, d1)
+
     chain_map = {}
-    for nm, fn in (("split_us", split_sc), ("fused_us", fused_sc)):
+    for nm, fn in (("direct_us", direct_sc), ("os_us", os_sc), ("split_us", split_sc), ("fused_us", fused_sc)):
         for _ in range(3):
             fn()
         torch.cuda.synchronize()
