@@ -37,7 +37,8 @@ METRIC = "SAT+CA-CFAR Gcells/s and full-chain frames/s at 1 GB300; % HBM rooflin
 # table kernels and k_cfar_ring on a 4096x4096 map (bench.py --profile map), times 4 for the
 # 8192x8192 map (their traffic grows with the cells).
 # DRAM bytes per launch (ncu dram__bytes_read.sum + dram__bytes_write.sum; see profiles/)
-TRAFFIC = {"band_dft": 43.06e6, "sat_i64_8192": 4 * 222.6e6}
+TRAFFIC = {"band_dft": 43.03e6, "sat_i64_8192": 4 * 222.6e6, "cfar_ring_8192": 4 * 221.4e6,
+           "sat_cfar_stream_8192": 320.5e6}
 RING = 16
 
 
@@ -50,7 +51,7 @@ def parse_args():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-map", action="store_true", help="skip the 8192^2 SAT+CFAR measurement")
     ap.add_argument("--no-batch", action="store_true", help="skip the 64-frame mixed batch measurement")
-    ap.add_argument("--profile", choices=["chain", "map", "batch", "fused"],
+    ap.add_argument("--profile", choices=["chain", "map", "batch", "fused", "os"],
                     help="run one small fixed case a few times for a profiler capture and exit (no JSON line): "
                          "chain = the 1024x4096 frame through the per-frame calls, map = SAT (I64) + CFAR on a "
                          "--map-size square map, batch = one 64-frame mixed batch")
@@ -771,7 +772,7 @@ def profile_case(args):
         bound = float(Pm.max().item())
         for _ in range(3):
             rc.rcfar_sat_cfar(h, Pm, bound, w, 0, n - 1, det)
-    elif args.profile == "chain":
+    elif args.profile in ("chain", "os"):
         h = rc.rcfar_create(device=0, max_rows=1024, max_cols=512, max_n=4096, max_window=40, max_frames=1,
                             batch_bytes=1 << 24)
         case = synth.large_frame_case(0)
@@ -781,11 +782,15 @@ def profile_case(args):
         P = torch.empty((case.spec.M, band.cols), device="cuda")
         det = torch.empty((case.spec.M, band.cols), dtype=torch.uint8, device="cuda")
         w = case.window
-        win = rc.make_window(w.train_r, w.train_c, w.guard_r, w.guard_c, w.pfa)
+        kind = rc.RCFAR_CFAR_OS if args.profile == "os" else rc.RCFAR_CFAR_CA
+        win = rc.make_window(w.train_r, w.train_c, w.guard_r, w.guard_c, w.pfa, kind=kind)
         for _ in range(3):
             rc.rcfar_preprocess(h, x, params, P)
-            v = rc.rcfar_sat(h, P, value_bound=band.value_bound, mode=rc.RCFAR_SAT_TILE_I64)
-            rc.rcfar_cfar(h, v, P, win, band.k_lo - band.c0, band.k_hi - band.c0, det)
+            if kind == rc.RCFAR_CFAR_OS:
+                rc.rcfar_cfar_direct(h, P, win, band.k_lo - band.c0, band.k_hi - band.c0, det)
+            else:
+                rc.rcfar_sat_cfar(h, P, band.value_bound, win, band.k_lo - band.c0, band.k_hi - band.c0, det,
+                                  map_cut=False)
     else:
         h = rc.rcfar_create(device=0, max_rows=1024, max_cols=1024, max_n=4096, max_window=32, max_frames=64,
                             batch_bytes=3 << 30)
