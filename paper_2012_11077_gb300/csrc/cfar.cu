@@ -83,6 +83,8 @@ __device__ __forceinline__ SV go_so_stat(bool greatest, const SV* ra, const SV* 
 // rows per step).
 template <int MODE, typename InT, int HG>
 __global__ void __launch_bounds__(256) k_cfar(const __grid_constant__ CfarBatch B) {
+  pdl_trigger();
+  pdl_wait();
   typedef typename std::conditional<MODE == RCFAR_SAT_NAIVE_F32, float, u64>::type SV;
   constexpr bool kExact = MODE != RCFAR_SAT_TILE_F32 && MODE != RCFAR_SAT_NAIVE_F32;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -250,6 +252,8 @@ __device__ __forceinline__ u64 ref_sum(const u64* ra, const u64* rb, const u64* 
 // without per-cell checks.
 template <bool kMapCut, typename InT>
 __global__ void __launch_bounds__(kRingThreads, 1) k_cfar_ring(const __grid_constant__ CfarBatch B) {
+  pdl_trigger();
+  pdl_wait();
   extern __shared__ __align__(16) unsigned char smem_raw[];
   u64* bars = reinterpret_cast<u64*>(smem_raw);
   u64* ring = reinterpret_cast<u64*>(smem_raw + kRingBarBytes);
@@ -489,6 +493,8 @@ __global__ void __launch_bounds__(kRingThreads, 1) k_cfar_ring(const __grid_cons
 // scans), prefix every column (one thread per column), then the CUTs.
 template <bool kMapCut, typename InT>
 __global__ void __launch_bounds__(256) k_sat_cfar_fused(const __grid_constant__ CfarBatch B) {
+  pdl_trigger();
+  pdl_wait();
   extern __shared__ __align__(16) unsigned char smem_raw[];
   u64* S = reinterpret_cast<u64*>(smem_raw);
   __shared__ int s_bad;
@@ -732,6 +738,7 @@ __device__ __forceinline__ void stream_cut_row(const CfarMapDev& P, int r, int c
 // lane in (C) (4 for strips of kStreamW columns, 8 for whole-width strips).
 template <bool kMapCut, int kCG, int kE>
 __global__ void __launch_bounds__(kStreamThreads, 2) k_sat_cfar_stream(const __grid_constant__ CfarBatch B) {
+  pdl_trigger();
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ int s_bad;
   const int mi = find_item(B.m, B.n, (int)blockIdx.x, &CfarMapDev::item0);
@@ -807,6 +814,7 @@ __global__ void __launch_bounds__(kStreamThreads, 2) k_sat_cfar_stream(const __g
   int cut_slot = (wr + 1) % RB;
   const unsigned ring_end = ring_a + span;
   const int jl = c0 - cb + 1 + lane;  // region column of the lane's first CUT column
+  pdl_wait();  // the set-up above overlaps the previous kernel
   fetch(0);
   for (int t = 0; t < nst; ++t) {
     cp_async_wait<0>();
@@ -916,6 +924,8 @@ __device__ __forceinline__ float os_value(unsigned k) {
 
 template <int kNK>
 __global__ void __launch_bounds__(256, 2) k_cfar_os(const __grid_constant__ CfarBatch B) {
+  pdl_trigger();
+  pdl_wait();
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int mi = find_item(B.m, B.n, (int)blockIdx.x, &CfarMapDev::item0);
   const CfarMapDev& P = B.m[mi];
@@ -1013,6 +1023,8 @@ __global__ void __launch_bounds__(256, 2) k_cfar_os(const __grid_constant__ Cfar
 }
 
 __global__ void __launch_bounds__(256) k_cfar_direct(const __grid_constant__ CfarMapDev P) {
+  pdl_trigger();
+  pdl_wait();
   extern __shared__ __align__(16) float X[];
   const int local = (int)blockIdx.x;
   const int ty = local / P.tiles_x, tx = local % P.tiles_x;
@@ -1086,8 +1098,7 @@ static cudaError_t launch_cfar_t(const CfarBatch& b, int blocks, size_t smem, in
   auto fn = max_hc <= 128 ? k_cfar<MODE, InT, 4> : k_cfar<MODE, InT, 8>;
   cudaError_t e = ensure_smem(reinterpret_cast<const void*>(fn), smem);
   if (e != cudaSuccess) return e;
-  fn<<<blocks, 256, smem, s>>>(b);
-  return cudaGetLastError();
+  return launch_pdl(fn, blocks, 256, smem, s, b);
 }
 
 cudaError_t launch_cfar(const CfarBatch& b, int mode, int dtype, int blocks, size_t smem, int max_hc, cudaStream_t s) {
@@ -1169,8 +1180,7 @@ static cudaError_t launch_ring_t(const CfarBatch& b, int blocks, size_t smem, cu
   auto fn = k_cfar_ring<kMapCut, InT>;
   cudaError_t e = ensure_smem(reinterpret_cast<const void*>(fn), smem);
   if (e != cudaSuccess) return e;
-  fn<<<blocks, kRingThreads, smem, s>>>(b);
-  return cudaGetLastError();
+  return launch_pdl(fn, blocks, kRingThreads, smem, s, b);
 }
 
 cudaError_t launch_cfar_ring(const CfarBatch& b, bool map_cut, int dtype, int blocks, size_t smem, cudaStream_t s) {
@@ -1217,8 +1227,7 @@ static cudaError_t launch_fused_t(const CfarBatch& b, int blocks, size_t smem, c
   auto fn = k_sat_cfar_fused<kMapCut, InT>;
   cudaError_t e = ensure_smem(reinterpret_cast<const void*>(fn), smem);
   if (e != cudaSuccess) return e;
-  fn<<<blocks, 256, smem, s>>>(b);
-  return cudaGetLastError();
+  return launch_pdl(fn, blocks, 256, smem, s, b);
 }
 
 cudaError_t launch_cfar_fused(const CfarBatch& b, bool map_cut, int dtype, int blocks, size_t smem, cudaStream_t s) {
@@ -1296,8 +1305,7 @@ static cudaError_t launch_stream_t(const CfarBatch& b, int blocks, size_t smem, 
   auto fn = k_sat_cfar_stream<kMapCut, kCG, kE>;
   cudaError_t e = ensure_smem(reinterpret_cast<const void*>(fn), smem);
   if (e != cudaSuccess) return e;
-  fn<<<blocks, kStreamThreads, smem, s>>>(b);
-  return cudaGetLastError();
+  return launch_pdl(fn, blocks, kStreamThreads, smem, s, b);
 }
 
 template <int kCG, int kE>
@@ -1331,8 +1339,7 @@ static cudaError_t launch_os_t(const CfarBatch& b, int blocks, size_t smem, cuda
   auto fn = k_cfar_os<kNK>;
   cudaError_t e = ensure_smem(reinterpret_cast<const void*>(fn), smem);
   if (e != cudaSuccess) return e;
-  fn<<<blocks, 256, smem, s>>>(b);
-  return cudaGetLastError();
+  return launch_pdl(fn, blocks, 256, smem, s, b);
 }
 
 cudaError_t launch_cfar_os(const CfarBatch& b, int max_n_ref, int blocks, size_t smem, cudaStream_t s) {
@@ -1353,8 +1360,7 @@ cudaError_t launch_cfar_direct(const CfarMapDev& m, int blocks, size_t smem, cud
   if (blocks <= 0) return cudaSuccess;
   cudaError_t e = ensure_smem(reinterpret_cast<const void*>(&k_cfar_direct), smem);
   if (e != cudaSuccess) return e;
-  k_cfar_direct<<<blocks, 256, smem, s>>>(m);
-  return cudaGetLastError();
+  return launch_pdl(k_cfar_direct, blocks, 256, smem, s, m);
 }
 
 }  // namespace rcfar

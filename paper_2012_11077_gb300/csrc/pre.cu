@@ -74,6 +74,8 @@ __device__ __forceinline__ float mean_weight(int j, int N, int h) {
 // are read and rows of the copy written 128 bytes at a time through a padded
 // shared tile. Frames given range-major (xsrc == nullptr) have no CTAs.
 __global__ void __launch_bounds__(256) k_transpose(const __grid_constant__ PreBatch b) {
+  pdl_trigger();
+  pdl_wait();
   const int fi = find_item(b.f, b.n, (int)blockIdx.x, &PreFrameDev::item_tr);
   const PreFrameDev& F = b.f[fi];
   const int local = (int)blockIdx.x - F.item_tr;
@@ -101,6 +103,8 @@ __global__ void __launch_bounds__(256) k_transpose(const __grid_constant__ PreBa
 // 64 rows (kStatsRowsPerChunk). Thread (g = warp, lane) owns rows g, g+8, ...
 // of its chunk for 4 columns; all 8 rows are loaded before any arithmetic.
 __global__ void __launch_bounds__(256, 4) k_colstats(const __grid_constant__ PreBatch b) {
+  pdl_trigger();
+  pdl_wait();
   const int fi = find_item(b.f, b.n, (int)blockIdx.x, &PreFrameDev::item_stats);
   const PreFrameDev& F = b.f[fi];
   const int local = (int)blockIdx.x - F.item_stats;
@@ -248,6 +252,8 @@ __device__ __forceinline__ float2 split_tf32_fast(float x) {
 // sum is unrolled), or -1 for any h.
 template <int H>
 __global__ void __launch_bounds__(256) k_ysplit(const __grid_constant__ PreBatch b) {
+  pdl_trigger();
+  pdl_wait();
   const int fi = find_item(b.f, b.n, (int)blockIdx.x, &PreFrameDev::item_y);
   const PreFrameDev& F = b.f[fi];
   const int local = (int)blockIdx.x - F.item_y;
@@ -396,6 +402,8 @@ __device__ __forceinline__ void umma_commit(unsigned bar) {
 // kStatusTimeout and the CTA still drains its MMAs, frees its tensor memory
 // and returns.
 __global__ void __launch_bounds__(kDftThreads, 1) k_band_dft(const __grid_constant__ PreBatch b) {
+  pdl_trigger();
+  pdl_wait();
   const int fi = find_item(b.f, b.n, (int)blockIdx.x, &PreFrameDev::item_dft);
   const PreFrameDev& F = b.f[fi];
   const int local = (int)blockIdx.x - F.item_dft;
@@ -570,6 +578,7 @@ __global__ void __launch_bounds__(kDftThreads, 1) k_band_dft(const __grid_consta
 // count; rows past the frame arrive as zeros. Warp 0 issues the MMAs,
 // warps 2-5 drain the accumulators (warp w reads TMEM lanes 32 (w % 4) ..).
 __global__ void __launch_bounds__(kDftTmaThreads, 1) k_band_dft_tma(const __grid_constant__ DftBatch b) {
+  pdl_trigger();
   const int fi = find_item(b.f, b.n, (int)blockIdx.x, &DftFrameDev::item_dft);
   const DftFrameDev& F = b.f[fi];
   const int local = (int)blockIdx.x - F.item_dft;
@@ -624,6 +633,7 @@ __global__ void __launch_bounds__(kDftTmaThreads, 1) k_band_dft_tma(const __grid
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const unsigned tmem = tmem_slot;
+  pdl_wait();  // the tensor-memory allocation and barriers above overlap the previous kernel
 
   const unsigned idesc = (1u << 4) | (2u << 7) | (2u << 10) | ((unsigned)(bn >> 3) << 17) |
                          ((unsigned)(kDftBM >> 4) << 24);
@@ -734,6 +744,8 @@ __global__ void __launch_bounds__(kDftTmaThreads, 1) k_band_dft_tma(const __grid
 // normalized": the DFT is linear, so this equals transforming y / max|y|).
 // Grid: per frame, rows x ceil(C / 256) CTAs; one thread per map cell.
 __global__ void __launch_bounds__(256) k_dft_reduce(const __grid_constant__ PreBatch b) {
+  pdl_trigger();
+  pdl_wait();
   const int fi = find_item(b.f, b.n, (int)blockIdx.x, &PreFrameDev::item_norm);
   const PreFrameDev& F = b.f[fi];
   const int local = (int)blockIdx.x - F.item_norm;
@@ -799,27 +811,24 @@ __global__ void k_twiddles(float* Wt, long long ldw, int npad, int N, int c0, in
 
 cudaError_t launch_transpose(const PreBatch& b, int blocks, cudaStream_t s) {
   if (blocks <= 0) return cudaSuccess;
-  k_transpose<<<blocks, 256, 0, s>>>(b);
-  return cudaGetLastError();
+  return launch_pdl(k_transpose, blocks, 256, 0, s, b);
 }
 
 cudaError_t launch_colstats(const PreBatch& b, int blocks, cudaStream_t s) {
   if (blocks <= 0) return cudaSuccess;
-  k_colstats<<<blocks, 256, 0, s>>>(b);
-  return cudaGetLastError();
+  return launch_pdl(k_colstats, blocks, 256, 0, s, b);
 }
 
 cudaError_t launch_ysplit(const PreBatch& b, int blocks, cudaStream_t s) {
   if (blocks <= 0) return cudaSuccess;
   // one half length for the whole launch (a batch shares its mean filter)
   switch (b.f[0].h) {
-    case 1: k_ysplit<1><<<blocks, 256, 0, s>>>(b); break;
-    case 2: k_ysplit<2><<<blocks, 256, 0, s>>>(b); break;
-    case 3: k_ysplit<3><<<blocks, 256, 0, s>>>(b); break;
-    case 4: k_ysplit<4><<<blocks, 256, 0, s>>>(b); break;
-    default: k_ysplit<-1><<<blocks, 256, 0, s>>>(b); break;
+    case 1: return launch_pdl(k_ysplit<1>, blocks, 256, 0, s, b);
+    case 2: return launch_pdl(k_ysplit<2>, blocks, 256, 0, s, b);
+    case 3: return launch_pdl(k_ysplit<3>, blocks, 256, 0, s, b);
+    case 4: return launch_pdl(k_ysplit<4>, blocks, 256, 0, s, b);
+    default: return launch_pdl(k_ysplit<-1>, blocks, 256, 0, s, b);
   }
-  return cudaGetLastError();
 }
 
 cudaError_t launch_band_dft(const PreBatch& b, int blocks, cudaStream_t s) {
@@ -827,8 +836,7 @@ cudaError_t launch_band_dft(const PreBatch& b, int blocks, cudaStream_t s) {
   const size_t smem = (size_t)b.dft_smem;
   cudaError_t e = ensure_smem(reinterpret_cast<const void*>(&k_band_dft), smem);
   if (e != cudaSuccess) return e;
-  k_band_dft<<<blocks, kDftThreads, smem, s>>>(b);
-  return cudaGetLastError();
+  return launch_pdl(k_band_dft, blocks, kDftThreads, smem, s, b);
 }
 
 cudaError_t launch_band_dft_tma(const DftBatch& b, int blocks, cudaStream_t s) {
@@ -836,14 +844,12 @@ cudaError_t launch_band_dft_tma(const DftBatch& b, int blocks, cudaStream_t s) {
   const size_t smem = (size_t)b.dft_smem;
   cudaError_t e = ensure_smem(reinterpret_cast<const void*>(&k_band_dft_tma), smem);
   if (e != cudaSuccess) return e;
-  k_band_dft_tma<<<blocks, kDftTmaThreads, smem, s>>>(b);
-  return cudaGetLastError();
+  return launch_pdl(k_band_dft_tma, blocks, kDftTmaThreads, smem, s, b);
 }
 
 cudaError_t launch_dft_reduce(const PreBatch& b, int blocks, cudaStream_t s) {
   if (blocks <= 0) return cudaSuccess;
-  k_dft_reduce<<<blocks, 256, 0, s>>>(b);
-  return cudaGetLastError();
+  return launch_pdl(k_dft_reduce, blocks, 256, 0, s, b);
 }
 
 cudaError_t launch_twiddles(float* Wt, long long ldw, int npad, int N, int c0, int C, cudaStream_t s) {

@@ -5,7 +5,8 @@
 // be captured in a CUDA graph without any host->device copy.
 #pragma once
 
-#include <cuda.h>  // CUtensorMap (the type only; the encoder is looked up at run time)
+#include <cuda.h>
+#include <utility>  // CUtensorMap (the type only; the encoder is looked up at run time)
 #include <cuda_runtime.h>
 #include <cuda_fp16.h>
 #include <stddef.h>
@@ -233,6 +234,32 @@ __device__ __forceinline__ int find_item(const T* arr, int n, int item, int T::*
 
 // Raise a kernel's dynamic shared-memory limit once per (kernel, device).
 cudaError_t ensure_smem(const void* fn, size_t bytes);
+
+// Programmatic dependent launch. A kernel launched by launch_pdl may begin
+// while its predecessor on the stream is still running: it calls pdl_trigger()
+// first (so that its own successor may launch once all of its CTAs have
+// started) and pdl_wait() before its first access to global memory, which
+// returns once the predecessor has completed and its writes are visible.
+// Since every such kernel waits before touching global memory, each one also
+// runs after all earlier kernels on the stream. Both are no-ops for kernels
+// launched without the attribute.
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
+template <typename... KArgs, typename... Args>
+cudaError_t launch_pdl(void (*fn)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s, Args&&... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, fn, std::forward<Args>(args)...);
+}
 
 // ---- launchers (implemented in the .cu files) -------------------------------
 cudaError_t launch_colstats(const PreBatch& b, int blocks, cudaStream_t s);

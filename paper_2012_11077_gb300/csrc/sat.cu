@@ -125,6 +125,8 @@ struct SatTypes {
 // Pass 1: one CTA per tile (warp w: rows 4w..4w+3, lane: columns 4l..4l+3).
 template <int MODE, typename InT>
 __global__ void __launch_bounds__(256) k_sat_tile(const __grid_constant__ SatBatch B) {
+  pdl_trigger();
+  pdl_wait();
   typedef typename SatTypes<MODE>::Acc Acc;
   typedef typename SatTypes<MODE>::Loc Loc;
   __shared__ Loc s_wt[8][kSatTileW];
@@ -299,6 +301,8 @@ __device__ __forceinline__ int sat_scale_of(const SatMapDev& Mp, float* bound) {
 // 4l..4l+3); exact row totals -> row_tot, column totals -> col_tot.
 template <typename InT>
 __global__ void __launch_bounds__(256) k_sat_reduce(const __grid_constant__ SatBatch B) {
+  pdl_trigger();
+  pdl_wait();
   __shared__ u64 s_col[8][kSatTileW];
   const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
   const int mi = find_item(B.m, B.n, (int)blockIdx.x, &SatMapDev::item_tile);
@@ -360,6 +364,8 @@ __global__ void __launch_bounds__(256) k_sat_reduce(const __grid_constant__ SatB
 // barrier).
 template <typename InT>
 __global__ void __launch_bounds__(256, 3) k_sat_down(const __grid_constant__ SatBatch B, int total_tiles) {
+  pdl_trigger();
+  pdl_wait();
   __shared__ __align__(16) InT s_map[2][kSatTileH][kSatTileW];
   __shared__ u64 s_wt[8][kSatTileW];
   const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
@@ -481,6 +487,8 @@ __device__ __forceinline__ Acc block_excl_scan(Acc x, Acc* s_warp, Acc* total) {
 // the warps before it.
 template <typename Acc>
 __global__ void __launch_bounds__(256) k_sat_hscan(const __grid_constant__ SatBatch B) {
+  pdl_trigger();
+  pdl_wait();
   __shared__ Acc s_warp[8];
   __shared__ Acc s_run[8][32];
   const int mi = find_item(B.m, B.n, (int)blockIdx.x, &SatMapDev::item_band);
@@ -532,6 +540,8 @@ __global__ void __launch_bounds__(256) k_sat_hscan(const __grid_constant__ SatBa
 // CTA = 32 columns (lane) x 32 groups of consecutive bands (warp).
 template <typename Acc>
 __global__ void __launch_bounds__(1024) k_sat_vscan(const __grid_constant__ SatBatch B) {
+  pdl_trigger();
+  pdl_wait();
   __shared__ Acc s_tot[32][32];
   const int mi = find_item(B.m, B.n, (int)blockIdx.x, &SatMapDev::item_vscan);
   const SatMapDev& Mp = B.m[mi];
@@ -561,6 +571,8 @@ __global__ void __launch_bounds__(1024) k_sat_vscan(const __grid_constant__ SatB
 // I64 and NAIVE_F32: fold the carries into the tile-local table in place.
 template <int MODE>
 __global__ void __launch_bounds__(256) k_sat_finalize(const __grid_constant__ SatBatch B) {
+  pdl_trigger();
+  pdl_wait();
   typedef typename SatTypes<MODE>::Acc Acc;
   typedef typename SatTypes<MODE>::Loc Loc;
   const int mi = find_item(B.m, B.n, (int)blockIdx.x, &SatMapDev::item_tile);
@@ -654,23 +666,23 @@ cudaError_t launch_map_max(const void* map, int dtype, float in_scale, int rows,
 template <int MODE, typename InT>
 static cudaError_t launch_sat_t(const SatBatch& b, int tiles, int bands, int vscans, cudaStream_t s) {
   typedef typename SatTypes<MODE>::Acc Acc;
+  cudaError_t e;
   if constexpr (MODE == RCFAR_SAT_I64) {
-    k_sat_reduce<InT><<<tiles, 256, 0, s>>>(b);
-    k_sat_hscan<Acc><<<bands, 256, 0, s>>>(b);
-    k_sat_vscan<Acc><<<vscans, 1024, 0, s>>>(b);
+    if ((e = launch_pdl(k_sat_reduce<InT>, tiles, 256, 0, s, b)) != cudaSuccess) return e;
+    if ((e = launch_pdl(k_sat_hscan<Acc>, bands, 256, 0, s, b)) != cudaSuccess) return e;
+    if ((e = launch_pdl(k_sat_vscan<Acc>, vscans, 1024, 0, s, b)) != cudaSuccess) return e;
     // grid-stride: about three resident CTAs per SM, each streaming tiles
     int dev = 0, sms = 152;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     const int grid = tiles < 3 * sms ? tiles : 3 * sms;
-    k_sat_down<InT><<<grid, 256, 0, s>>>(b, tiles);
-    return cudaGetLastError();
+    return launch_pdl(k_sat_down<InT>, grid, 256, 0, s, b, tiles);
   }
-  k_sat_tile<MODE, InT><<<tiles, 256, 0, s>>>(b);
-  k_sat_hscan<Acc><<<bands, 256, 0, s>>>(b);
-  k_sat_vscan<Acc><<<vscans, 1024, 0, s>>>(b);
-  if constexpr (MODE == RCFAR_SAT_NAIVE_F32) k_sat_finalize<MODE><<<tiles, 256, 0, s>>>(b);
-  return cudaGetLastError();
+  if ((e = launch_pdl(k_sat_tile<MODE, InT>, tiles, 256, 0, s, b)) != cudaSuccess) return e;
+  if ((e = launch_pdl(k_sat_hscan<Acc>, bands, 256, 0, s, b)) != cudaSuccess) return e;
+  if ((e = launch_pdl(k_sat_vscan<Acc>, vscans, 1024, 0, s, b)) != cudaSuccess) return e;
+  if constexpr (MODE == RCFAR_SAT_NAIVE_F32) return launch_pdl(k_sat_finalize<MODE>, tiles, 256, 0, s, b);
+  return cudaSuccess;
 }
 
 cudaError_t launch_sat(const SatBatch& b, int mode, int dtype, int tiles, int bands, int vscans, cudaStream_t s) {
