@@ -270,7 +270,7 @@ def test_batch_mixed_kinds_all_tunings(rc):
         rc.rcfar_destroy(h2)
 
 
-def test_server_go_so_frames(rc):
+def test_server_go_so_os_frames(rc):
     params = rc.make_pre_params(synth.FS_HZ, mean_len=5, halo_c=-1)
     srv = rc.rcfar_server_create(device=0, budget_bytes=128 << 20, slots=2, max_batch_frames=4, max_rows=256,
                                  max_n=1024, max_window=20, params=params)
@@ -282,7 +282,7 @@ def test_server_go_so_frames(rc):
             c = synth.ChainCase(synth.FrameSpec(M=128 + 16 * i, N=512, n_targets=2, seed=40 + i),
                                 synth.Window(8, 8, 2, 2, 1e-4))
             x = torch.from_numpy(synth.radar_frame(c.spec)).pin_memory()
-            w = rc.make_window(8, 8, 2, 2, 1e-4, kind=1 + i % 2)
+            w = rc.make_window(8, 8, 2, 2, 1e-4, kind=1 + i % 3)  # GO, SO, OS
             C = rc.rcfar_band_plan(512, rc.make_pre_params(synth.FS_HZ, mean_len=5, halo_c=10)).cols
             det = torch.full((c.spec.M, C), 7, dtype=torch.uint8).pin_memory()
             rc.rcfar_server_submit(srv, x, w, det, tag=i)

@@ -589,3 +589,26 @@ def test_fused_sat_cfar_range_error(rc, h):
     d = torch.empty((64, 64), dtype=torch.uint8, device="cuda")
     rc.rcfar_sat_cfar(h, P, 100.0, rc.make_window(4, 4, 1, 1, 1e-3), 0, 63, d)
     assert rc.rcfar_get_error(h) == rc.RCFAR_ERR_RANGE
+
+
+@pytest.mark.parametrize("win", [(8, 8, 2, 2, 1e-4), (30, 30, 6, 6, 1e-4)])
+def test_fused_sat_cfar_f16_and_wide_windows(rc, h, win):
+    # float16 maps (one integral image per block of rows) and a window whose
+    # ring does not fit the streaming kernel's shared memory take the blocked
+    # fused kernel; both equal the split path bit for bit
+    P = synth.square_law_map(300, 700, n_targets=40, dyn_range_db=40.0, seed=5)
+    rows, cols = P.shape
+    for dtype, exp2 in ((torch.float32, 0), (torch.float16, int(math.ceil(math.log2(P.max() / 60000.0))))):
+        Ps = (P / 2.0 ** exp2).astype(np.float16 if dtype == torch.float16 else np.float32)
+        Pt = dev_t(Ps)
+        bound = float(Ps.astype(np.float64).max() * 2.0 ** exp2)
+        w = rc.make_window(*win)
+        view = rc.rcfar_sat(h, Pt, value_bound=bound, mode=rc.RCFAR_SAT_TILE_I64, map_exp2=exp2)
+        d1 = torch.full((rows, cols), 7, dtype=torch.uint8, device="cuda")
+        t1 = torch.full((rows, cols), -1.0, dtype=torch.float32, device="cuda")
+        rc.rcfar_cfar(h, view, Pt, w, 0, cols - 1, d1, t1, map_exp2=exp2)
+        d2 = torch.full((rows, cols), 7, dtype=torch.uint8, device="cuda")
+        t2 = torch.full((rows, cols), -1.0, dtype=torch.float32, device="cuda")
+        rc.rcfar_sat_cfar(h, Pt, bound, w, 0, cols - 1, d2, t2, map_exp2=exp2)
+        assert rc.rcfar_get_error(h) == rc.RCFAR_OK
+        assert torch.equal(d1, d2) and torch.equal(t1, t2), (dtype, win)
