@@ -724,11 +724,11 @@ __device__ __forceinline__ void stream_cut_row(const CfarMapDev& P, int r, int c
 // kStreamKS + 2 wr + 1 of its rows live in a ring in shared memory (region
 // row g in slot g mod RB). Per stage, while cp.async brings the next
 // stage's map rows (16-byte copies when the map's rows are 16-byte aligned):
-//  (A) thread j quantises column j + 1 of the stage's rows and adds them to
-//      its running column sum, which it keeps in a register for the whole
-//      run, writing the column sums to the ring;
-//  (B) warp w turns row w of the stage into its table row: a prefix across
-//      the strip (kE contiguous columns per lane, one warp scan);
+//  (A) warp w quantises row w of the stage and prefixes it across the strip
+//      (kE contiguous columns per lane, one warp scan) into the ring;
+//  (B) thread j adds each new row's prefix to column j + 1's running sum,
+//      which it keeps in a register for the whole run (eq. 3 as
+//      S(g, .) = S(g - 1, .) + H(g, .));
 //  (C) warp w takes one CUT row whose window is now complete: 8 eq. 4
 //      lookups per CUT (16 for greatest-of / smallest-of), T and the
 //      decision.
@@ -765,7 +765,7 @@ __global__ void __launch_bounds__(kStreamThreads, 2) k_sat_cfar_stream(const __g
   const unsigned ring_a = smem_u32(smem_raw);
   const unsigned span = (unsigned)(RB * pitch) * 8u;  // ring bytes
   const unsigned raw_a = ring_a + span;               // 16-byte aligned (pitch even)
-  const unsigned pitch8 = (unsigned)pitch * 8u, ldr4 = (unsigned)ldr * 4u;
+  const unsigned pitch8 = (unsigned)pitch * 8u;
   const int ro = R0 - wr - 1;       // table row of region row 0
   const int GT = R1 - R0 + 2 * wr;  // region rows 1 .. GT hold map rows
   const int nst = (GT + kStreamKS - 1) / kStreamKS;
@@ -822,40 +822,22 @@ __global__ void __launch_bounds__(kStreamThreads, 2) k_sat_cfar_stream(const __g
     if (t + 1 < nst) fetch(t + 1);
     const int g0 = 1 + t * kStreamKS;
     const int n = min(kStreamKS, GT - g0 + 1);
-    // (A) quantised values added down each column (region column tid + 1);
-    // thread nin writes the zero column 0 (its values are 0)
-    if (tid <= nin) {
-      const bool real = tid < nin;
-      unsigned sa = raw_a + (unsigned)((t & 1) * kStreamKS * ldr + xoff + tid) * 4u;
-      unsigned da = ring_a + (unsigned)(slot0 * pitch + (real ? 1 + tid : 0)) * 8u;
-      auto row = [&](float v) {
-        bad |= !(fabsf(v) <= bound);
-        colsum += (u64)q_from_f32(v, scalef);
-        sts_u64(da, colsum);
-        da += pitch8;
-        if (da >= ring_end) da -= span;
-      };
-      if (n == kStreamKS) {
-        float v[kStreamKS];
-#pragma unroll
-        for (int i = 0; i < kStreamKS; ++i) v[i] = real ? lds_f32(sa + (unsigned)i * ldr4) : 0.f;
-#pragma unroll
-        for (int i = 0; i < kStreamKS; ++i) row(v[i]);
-      } else {
-        for (int i = 0; i < n; ++i) row(real ? lds_f32(sa + (unsigned)i * ldr4) : 0.f);
-      }
-    }
-    __syncthreads();
-    // (B) prefix across the strip: warp w takes region row g0 + w; lane l
-    // holds region columns 1 + kE l .. kE (l + 1) (the ring rows are wide
-    // enough for every lane's chunk; columns past nin are never read)
+    // (A) warp w: stage row w quantised and prefixed across the strip (lane l
+    // holds region columns 1 + kE l .. kE (l + 1), one warp scan): the row's
+    // own prefix H(g, .) goes to the ring (columns past nin are never read)
     if (warp < n) {
       int slot = slot0 + warp;
       if (slot >= RB) slot -= RB;
       const unsigned ra = ring_a + (unsigned)(slot * pitch + 1 + kE * lane) * 8u;
+      const unsigned rr = raw_a + (unsigned)(((t & 1) * kStreamKS + warp) * ldr + xoff + kE * lane) * 4u;
+      const int lim = nin - kE * lane;  // this lane's columns inside the region
       u64 v[kE];
 #pragma unroll
-      for (int e = 0; e < kE; ++e) v[e] = lds_u64(ra + 8u * e);
+      for (int e = 0; e < kE; ++e) {
+        const float x = e < lim ? lds_f32(rr + 4u * e) : 0.f;
+        bad |= !(fabsf(x) <= bound);
+        v[e] = (u64)q_from_f32(x, scalef);
+      }
 #pragma unroll
       for (int e = 1; e < kE; ++e) v[e] += v[e - 1];
       u64 incl = v[kE - 1];
@@ -867,6 +849,19 @@ __global__ void __launch_bounds__(kStreamThreads, 2) k_sat_cfar_stream(const __g
       const u64 excl = incl - v[kE - 1];
 #pragma unroll
       for (int e = 0; e < kE; ++e) sts_u64(ra + 8u * e, v[e] + excl);
+      if (lane == 0) sts_u64(ra - 8u, 0ull);  // region column 0
+    }
+    __syncthreads();
+    // (B) eq. 3 down the columns: S(g, .) = S(g - 1, .) + H(g, .); thread j
+    // keeps column j + 1's running sum in a register for the whole run
+    if (tid < nin) {
+      unsigned da = ring_a + (unsigned)(slot0 * pitch + 1 + tid) * 8u;
+      for (int i2 = 0; i2 < n; ++i2) {
+        colsum += lds_u64(da);
+        sts_u64(da, colsum);
+        da += pitch8;
+        if (da >= ring_end) da -= span;
+      }
     }
     __syncthreads();
     // (C) CUT rows whose windows are complete: region rows next_cut .. hi
