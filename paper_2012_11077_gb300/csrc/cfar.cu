@@ -814,6 +814,7 @@ __global__ void __launch_bounds__(kStreamThreads, 2) k_sat_cfar_stream(const __g
   int cut_slot = (wr + 1) % RB;
   const unsigned ring_end = ring_a + span;
   const int jl = c0 - cb + 1 + lane;  // region column of the lane's first CUT column
+  const unsigned lane_base = ring_a + (unsigned)jl * 8u;
   pdl_wait();  // the set-up above overlaps the previous kernel
   fetch(0);
   for (int t = 0; t < nst; ++t) {
@@ -870,13 +871,19 @@ __global__ void __launch_bounds__(kStreamThreads, 2) k_sat_cfar_stream(const __g
     if (warp < cnt) {
       int sg = cut_slot + warp;
       if (sg >= RB) sg -= RB;
-      auto rp = [&](int off) {  // ring row of region row g + off (|off| <= wr + 1), at column jl
+      // ring rows of region rows g + off at column jl (0 <= sg < RB, |off| <= wr + 1 < RB)
+      auto rp_below = [&](int off) {  // off < 0
+        int x = sg + off;
+        if (x < 0) x += RB;
+        return lane_base + (unsigned)x * pitch8;
+      };
+      auto rp_above = [&](int off) {  // off >= 0
         int x = sg + off;
         if (x >= RB) x -= RB;
-        if (x < 0) x += RB;
-        return ring_a + (unsigned)(x * pitch + jl) * 8u;
+        return lane_base + (unsigned)x * pitch8;
       };
-      const unsigned ra = rp(-wr - 1), rb = rp(wr), rc = rp(-gr - 1), rd = rp(gr), r1 = rp(0), r0 = rp(-1);
+      const unsigned ra = rp_below(-wr - 1), rb = rp_above(wr), rc = rp_below(-gr - 1), rd = rp_above(gr);
+      const unsigned r1 = lane_base + (unsigned)sg * pitch8, r0 = rp_below(-1);
       const int r = ro + next_cut + warp;
       if (kind == RCFAR_CFAR_CA)
         stream_cut_row<kMapCut, false, kCG>(P, r, c0 + lane, ncg, c0 + cw, ra, rb, rc, rd, r1, r0, false, kthr,
