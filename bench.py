@@ -38,7 +38,7 @@ METRIC = "SAT+CA-CFAR Gcells/s and full-chain frames/s at 1 GB300; % HBM rooflin
 # 8192x8192 map (their traffic grows with the cells).
 # DRAM bytes per launch (ncu dram__bytes_read.sum + dram__bytes_write.sum; see profiles/)
 TRAFFIC = {"band_dft": 43.03e6, "sat_i64_8192": 4 * 222.6e6, "cfar_ring_8192": 4 * 221.4e6,
-           "sat_cfar_stream_8192": 320.5e6}
+           "sat_cfar_stream_8192": 320.7e6}
 RING = 16
 
 

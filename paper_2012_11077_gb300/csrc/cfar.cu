@@ -604,25 +604,6 @@ __global__ void __launch_bounds__(256) k_sat_cfar_fused(const __grid_constant__ 
   if (tid == 0 && s_bad && B.status) atomicOr(B.status, kStatusRange);
 }
 
-// Streaming fused SAT + CFAR (float32 maps, no table in device memory). A CTA
-// owns the CUT rows [R0, R1) of a strip of columns [c0, c0 + cw) and walks
-// the map rows R0 - wr .. R1 - 1 + wr in stages of kStreamKS rows. Its local
-// integral image (eq. 3) has its origin (region row 0, region column 0,
-// both zero) at table row R0 - wr - 1 and column cb - 1; the last
-// kStreamKS + 2 wr + 1 of its rows live in a ring in shared memory (region
-// row g in slot g mod RB). Per stage, while cp.async brings the next
-// stage's map rows:
-//  (A) thread j quantises column j + 1 of the stage's rows and adds them to
-//      its running column sum, which it keeps in a register for the whole
-//      run, writing the column sums to the ring;
-//  (B) warp w turns row w of the stage into its table row: a prefix across
-//      the strip (contiguous chunks per lane, one warp scan);
-//  (C) warp w takes one CUT row whose window is now complete: 8 eq. 4
-//      lookups per CUT (16 for greatest-of / smallest-of), T and the
-//      decision.
-// Box sums do not depend on the origin, and the mod-2^64 wrap of long runs
-// cancels in them, so thresholds and decisions are bit-identical to the
-// split path's with the same fixed-point scale.
 // One CUT row of the streaming kernel: the lane's columns cl + 32 k
 // (k < ncg, c < cend). ra .. r0 are the shared-memory addresses of the ring
 // rows r - wr - 1, r + wr, r - gr - 1, r + gr, r, r - 1 at the region column
