@@ -83,7 +83,7 @@ struct Carver {
 // Per-frame preprocessing geometry (depends on the frame's own shape only,
 // so a frame is computed the same way alone and inside any batch).
 struct PreGeom {
-  int n_strips, n_chunks, rows_per_chunk;
+  int n_strips, n_chunks;
   int mtiles, ntiles, splitk, kper, bn, nblocks;
   int n_norm;
   int npad, ycols, n_y;
@@ -110,7 +110,6 @@ inline int dft_smem_for(int bn) {
 PreGeom pre_geom(int M, int N, int C, int kblocks_per_cta = 0) {
   PreGeom g;
   g.n_strips = (int)ceil_div(N, kStatsStrip);
-  g.rows_per_chunk = kStatsRows;
   g.n_chunks = (int)ceil_div(M, kStatsRows);
   g.npad = (int)round_up(N, kDftBK);
   g.ycols = (int)ceil_div(g.npad, kYCols);
@@ -578,7 +577,7 @@ static PreFrameDev make_pre_frame(const float* x, int M, int N, long long ldx, c
   F.npad = g.npad;
   F.ycols = g.ycols;
   F.bn = g.bn;
-  F.rows_per_chunk = g.rows_per_chunk;
+  F.chunks_per_cta = 1;
   F.n_chunks = g.n_chunks;
   F.n_strips = g.n_strips;
   F.mtiles = g.mtiles;
@@ -1343,6 +1342,17 @@ rcfar_status rcfar_run_batch(rcfar_handle h, const rcfar_frame_desc* frames, int
     db.dft_smem = pb.dft_smem;
     db.status = h->status;
     bool dft_tma_ok = true;
+    // column statistics: several 64-row chunks per CTA when the batch has
+    // chunks for more than two waves of CTAs at two chunks each (fewer
+    // hand-offs between CTAs; the results do not depend on it)
+    int stats_cpc = 1;
+    {
+      long long chunks = 0;
+      for (int k = 0; k < cnt; ++k)
+        chunks += ceil_div(frames[base + k].N, kStatsStrip) * ceil_div(frames[base + k].M, kStatsRows);
+      const long long wave = 4LL * std::max(1, h->sms);
+      while (stats_cpc < 4 && chunks / (2 * stats_cpc) >= 2 * wave) stats_cpc *= 2;
+    }
     int it_stats = 0, it_dft = 0, it_norm = 0, it_cfar = 0, it_y = 0, it_tr = 0;
     int it_tile = 0, it_band = 0, it_vscan = 0;
     int i_sat = 0, i_os = 0, it_os = 0, os_nref = 0;  // table items, OS items, OS CTAs
@@ -1393,7 +1403,8 @@ rcfar_status rcfar_run_batch(rcfar_handle h, const rcfar_frame_desc* frames, int
       F.item_norm = it_norm;
       F.item_y = it_y;
       it_y += g.n_y;
-      it_stats += g.n_strips * g.n_chunks;
+      F.chunks_per_cta = stats_cpc;
+      it_stats += g.n_strips * (int)ceil_div(g.n_chunks, stats_cpc);
       it_dft += g.mtiles * g.ntiles * g.splitk;
       it_norm += g.n_norm;
       if (!F.stats || !F.partial || !F.rowpart || !F.strip_ab || !F.yhi || !F.ylo || !F.rowmean || !F.rowsq ||

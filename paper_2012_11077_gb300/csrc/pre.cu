@@ -99,9 +99,12 @@ __global__ void __launch_bounds__(256) k_transpose(const __grid_constant__ PreBa
   }
 }
 
-// grid: for every frame, n_strips x n_chunks CTAs of 256 threads; a chunk is
-// 64 rows (kStatsRowsPerChunk). Thread (g = warp, lane) owns rows g, g+8, ...
-// of its chunk for 4 columns; all 8 rows are loaded before any arithmetic.
+// grid: for every frame, n_strips x n_groups CTAs of 256 threads; a CTA takes
+// chunks_per_cta consecutive chunks of 64 rows (kStatsRowsPerChunk) of one
+// 128-column strip, n_groups = ceil(n_chunks / chunks_per_cta). Per chunk,
+// thread (g = warp, lane) owns rows g, g+8, ... for 4 columns; all 8 rows
+// are loaded before any arithmetic. Every chunk writes its own partial
+// column sums, so the results do not depend on chunks_per_cta.
 __global__ void __launch_bounds__(256, 4) k_colstats(const __grid_constant__ PreBatch b) {
   pdl_trigger();
   pdl_wait();
@@ -109,88 +112,93 @@ __global__ void __launch_bounds__(256, 4) k_colstats(const __grid_constant__ Pre
   const PreFrameDev& F = b.f[fi];
   const int local = (int)blockIdx.x - F.item_stats;
   const int strip = local % F.n_strips;
-  const int chunk = local / F.n_strips;
+  const int group = local / F.n_strips;
+  const int ch0 = group * F.chunks_per_cta;
+  const int ch1 = min(F.n_chunks, ch0 + F.chunks_per_cta);
   const int lane = threadIdx.x & 31, g = threadIdx.x >> 5;
   const int col0 = strip * kStatsStrip + lane * 4;
-  const int r0 = chunk * kStatsRowsPerChunk;
   const bool vec = ((F.ldx & 3) == 0) && ((reinterpret_cast<uintptr_t>(F.x) & 15) == 0);
-
-  float v[8][4];
-#pragma unroll
-  for (int i = 0; i < 8; ++i) {
-    const int m = r0 + g + 8 * i;
-    if (m < F.M) {
-      load4_masked(F.x + (long long)m * F.ldx, col0, F.N, vec, v[i]);
-    } else {
-#pragma unroll
-      for (int k = 0; k < 4; ++k) v[i][k] = 0.f;
-    }
-  }
   float wj[4];
 #pragma unroll
   for (int k = 0; k < 4; ++k) wj[k] = mean_weight(col0 + k, F.N, F.h);
-  float sx[4] = {0.f, 0.f, 0.f, 0.f}, smx[4] = {0.f, 0.f, 0.f, 0.f};
-  float rs[8];
-#pragma unroll
-  for (int i = 0; i < 8; ++i) {
-    const float dm = (float)(r0 + g + 8 * i) - F.mbar;
-    rs[i] = 0.f;
-#pragma unroll
-    for (int k = 0; k < 4; ++k) {
-      sx[k] += v[i][k];
-      smx[k] = fmaf(dm, v[i][k], smx[k]);
-      rs[i] = fmaf(wj[k], v[i][k], rs[i]);
-    }
-  }
-  // row sums over the strip (sum_j w_j x[m, j]): reduce the 8 rows across the warp
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1)
-#pragma unroll
-    for (int i = 0; i < 8; ++i) rs[i] += __shfl_xor_sync(0xffffffffu, rs[i], o);
-  if (lane < 8) {
-    float mine = rs[0];
-#pragma unroll
-    for (int i = 1; i < 8; ++i)
-      if (lane == i) mine = rs[i];
-    const int m = r0 + g + 8 * lane;
-    if (m < F.M) F.rowpart[(long long)strip * F.M + m] = mine;
-  }
-
   __shared__ float2 red[8][kStatsStrip];
   __shared__ bool is_last;
+
+  for (int chunk = ch0; chunk < ch1; ++chunk) {
+    const int r0 = chunk * kStatsRowsPerChunk;
+    float v[8][4];
 #pragma unroll
-  for (int k = 0; k < 4; ++k) red[g][lane * 4 + k] = make_float2(sx[k], smx[k]);
-  __syncthreads();
-  if (threadIdx.x < kStatsStrip) {
-    const int c = strip * kStatsStrip + threadIdx.x;
-    float2 t = red[0][threadIdx.x];
+    for (int i = 0; i < 8; ++i) {
+      const int m = r0 + g + 8 * i;
+      if (m < F.M) {
+        load4_masked(F.x + (long long)m * F.ldx, col0, F.N, vec, v[i]);
+      } else {
 #pragma unroll
-    for (int gg = 1; gg < 8; ++gg) {
-      t.x += red[gg][threadIdx.x].x;
-      t.y += red[gg][threadIdx.x].y;
+        for (int k = 0; k < 4; ++k) v[i][k] = 0.f;
+      }
     }
-    if (c < F.N) F.partial[(long long)chunk * F.N + c] = t;
+    float sx[4] = {0.f, 0.f, 0.f, 0.f}, smx[4] = {0.f, 0.f, 0.f, 0.f};
+    float rs[8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+      const float dm = (float)(r0 + g + 8 * i) - F.mbar;
+      rs[i] = 0.f;
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        sx[k] += v[i][k];
+        smx[k] = fmaf(dm, v[i][k], smx[k]);
+        rs[i] = fmaf(wj[k], v[i][k], rs[i]);
+      }
+    }
+    // row sums over the strip (sum_j w_j x[m, j]): reduce the 8 rows across the warp
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+      for (int i = 0; i < 8; ++i) rs[i] += __shfl_xor_sync(0xffffffffu, rs[i], o);
+    if (lane < 8) {
+      float mine = rs[0];
+#pragma unroll
+      for (int i = 1; i < 8; ++i)
+        if (lane == i) mine = rs[i];
+      const int m = r0 + g + 8 * lane;
+      if (m < F.M) F.rowpart[(long long)strip * F.M + m] = mine;
+    }
+#pragma unroll
+    for (int k = 0; k < 4; ++k) red[g][lane * 4 + k] = make_float2(sx[k], smx[k]);
+    __syncthreads();
+    if (threadIdx.x < kStatsStrip) {
+      const int c = strip * kStatsStrip + threadIdx.x;
+      float2 t = red[0][threadIdx.x];
+#pragma unroll
+      for (int gg = 1; gg < 8; ++gg) {
+        t.x += red[gg][threadIdx.x].x;
+        t.y += red[gg][threadIdx.x].y;
+      }
+      if (c < F.N) F.partial[(long long)chunk * F.N + c] = t;
+    }
+    __syncthreads();  // red is rewritten by the next chunk
   }
   __threadfence();
   __syncthreads();
   if (threadIdx.x == 0) {
-    const unsigned old = atomicAdd(&F.strip_cnt[strip], 1u);
-    is_last = (old == (unsigned)F.n_chunks - 1u);
+    const unsigned nch = (unsigned)(ch1 - ch0);
+    const unsigned old = atomicAdd(&F.strip_cnt[strip], nch);
+    is_last = (old + nch == (unsigned)F.n_chunks);
   }
   __syncthreads();
   if (is_last) {
     __threadfence();
-    __shared__ float2 ab[kStatsStrip];
+    __shared__ float2 ab[kStatsStrip / 32];
     if (threadIdx.x < kStatsStrip) {
       const int c = strip * kStatsStrip + threadIdx.x;
       float2 st = make_float2(0.f, 0.f);
       if (c < F.N) {
         float2 t = make_float2(0.f, 0.f);
-        for (int ch0 = 0; ch0 < F.n_chunks; ch0 += 8) {  // fixed order: deterministic
+        for (int cb = 0; cb < F.n_chunks; cb += 8) {  // fixed order: deterministic
           float2 p[8];
 #pragma unroll
           for (int u = 0; u < 8; ++u)
-            p[u] = (ch0 + u < F.n_chunks) ? __ldcg(&F.partial[(long long)(ch0 + u) * F.N + c]) : make_float2(0.f, 0.f);
+            p[u] = (cb + u < F.n_chunks) ? __ldcg(&F.partial[(long long)(cb + u) * F.N + c]) : make_float2(0.f, 0.f);
 #pragma unroll
           for (int u = 0; u < 8; ++u) {
             t.x += p[u].x;
@@ -200,13 +208,22 @@ __global__ void __launch_bounds__(256, 4) k_colstats(const __grid_constant__ Pre
         st = make_float2(t.x * F.inv_M, t.y * F.inv_D);
         F.stats[c] = st;
       }
+      // (sum_j w_j a_j, sum_j w_j b_j) over the strip: a fixed shuffle tree per warp of 32
+      // columns, then the four warps' sums in order
       const float w = mean_weight(c, F.N, F.h);
-      ab[threadIdx.x] = make_float2(w * st.x, w * st.y);
+      float2 t = make_float2(w * st.x, w * st.y);
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        t.x += __shfl_xor_sync(0xffffffffu, t.x, o);
+        t.y += __shfl_xor_sync(0xffffffffu, t.y, o);
+      }
+      if (lane == 0) ab[g] = t;
     }
     __syncthreads();
     if (threadIdx.x == 0) {
-      float2 t = make_float2(0.f, 0.f);
-      for (int i = 0; i < kStatsStrip; ++i) {
+      float2 t = ab[0];
+#pragma unroll
+      for (int i = 1; i < kStatsStrip / 32; ++i) {
         t.x += ab[i].x;
         t.y += ab[i].y;
       }
@@ -241,7 +258,7 @@ __device__ __forceinline__ float2 split_tf32_fast(float x) {
   return make_float2(hi, x - hi);
 }
 
-// y pass: one warp per frame row, 256 samples per CTA column block.
+// y pass: one warp per frame row, kYCols samples per CTA column block.
 //   x'[m,n] = x[m,n] - a_n - b_n (m - mbar)       (detrend)
 //   y[m,n]  = mean of x'[m, n-h..n+h] in [0, N)    (mean filter)
 // records max |y| and writes y - c_m, where c_m is the row's slow-time mean

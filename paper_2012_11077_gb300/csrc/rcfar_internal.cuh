@@ -32,7 +32,7 @@ constexpr int kSatTileW = 128;  // columns per chunk (32 lanes x 4)
 
 // ---- preprocessing ----------------------------------------------------------
 constexpr int kStatsStrip = 128;         // columns per column-statistics CTA
-constexpr int kStatsRowsPerChunk = 64;   // rows per column-statistics CTA (8 warps x 8)
+constexpr int kStatsRowsPerChunk = 64;   // rows per column-statistics chunk (8 warps x 8)
 
 // Band DFT GEMM on tcgen05: 128 rows (TMEM lanes) x up to 256 real outputs
 // (TMEM columns) per CTA, K steps of 32 samples (one 128-byte swizzle row).
@@ -49,7 +49,7 @@ constexpr int kDftSmemCap = 220 * 1024;
 // 256; 1.2e-4 without draining).
 constexpr int kDftKB = 8;
 constexpr int kDftThreads = 384;  // warp 0 MMA, warps 1-7 producers, warps 8-11 drain
-// y pass: 8 rows (one per warp) x 256 samples per CTA.
+// y pass: 8 rows (one per warp) x kYCols samples per CTA.
 constexpr int kYRows = 8;
 constexpr int kYCols = 512;
 
@@ -86,7 +86,7 @@ struct PreFrameDev {
   int nblocks;          // npad / (32 * kDftKB), rounded up
   long long ldk;
   unsigned* tile_cnt;   // [mtiles * ntiles] arrival counters (self-resetting)
-  int rows_per_chunk, n_chunks, n_strips;
+  int chunks_per_cta, n_chunks, n_strips;  // k_colstats: CTAs per frame n_strips x ceil(n_chunks / chunks_per_cta)
   int mtiles, ntiles, splitk, kper;
   int item_stats, item_dft, item_norm, item_y;  // first CTA of this frame in each launch
   int n_norm;                                    // CTAs of this frame in k_dft_reduce
