@@ -127,7 +127,7 @@ PreGeom pre_geom(int M, int N, int C, int kblocks_per_cta = 0) {
   g.kper = (int)round_up(ceil_div(g.npad, sk), kblk);
   g.splitk = (int)ceil_div(g.npad, g.kper);
   g.ldk = g.ldw;
-  g.n_norm = M * (int)ceil_div(C, 256);  // k_dft_reduce: one thread per map cell
+  g.n_norm = (int)ceil_div((long long)M * C, 256);  // k_dft_reduce: one thread per map cell
   return g;
 }
 

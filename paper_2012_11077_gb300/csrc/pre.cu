@@ -759,17 +759,18 @@ __global__ void __launch_bounds__(kDftTmaThreads, 1) k_band_dft_tma(const __grid
 // (deterministic, and the same however the K range was split), magnitude,
 // bin 0's mean added back, and the normalisation by max |y| ("then
 // normalized": the DFT is linear, so this equals transforming y / max|y|).
-// Grid: per frame, rows x ceil(C / 256) CTAs; one thread per map cell.
+// Grid: per frame, ceil(M C / 256) CTAs; one thread per map cell.
 __global__ void __launch_bounds__(256) k_dft_reduce(const __grid_constant__ PreBatch b) {
   pdl_trigger();
   pdl_wait();
   const int fi = find_item(b.f, b.n, (int)blockIdx.x, &PreFrameDev::item_norm);
   const PreFrameDev& F = b.f[fi];
   const int local = (int)blockIdx.x - F.item_norm;
-  const int cblocks = (F.C + 255) / 256;
-  const int m = local / cblocks;
-  const int j = (local - m * cblocks) * 256 + (int)threadIdx.x;
-  if (m >= F.M || j >= F.C) return;
+  // cells in row-major order, 256 per CTA (a CTA may span several rows)
+  const long long cell = (long long)local * 256 + threadIdx.x;
+  if (cell >= (long long)F.M * F.C) return;
+  const int m = (int)(cell / F.C);
+  const int j = (int)(cell - (long long)m * F.C);
   float inv;
   if (F.normalise == RCFAR_NORM_ROW_ZSCORE) {
     // z-score: 1 / std of the row's y (population std; 0 for a constant row)
