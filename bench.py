@@ -45,7 +45,7 @@ RING = 16
 def parse_args():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--steps", type=int, default=1000)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -240,7 +240,12 @@ def reference_arm(args, rank):
 
 
 # ---------------------------------------------------------------- batching
-def batch_measure(rc, torch, synth, local, rank, n_frames=64, reps=5):
+def sat_mode_name(rc, mode: int) -> str:
+    return {rc.RCFAR_SAT_I64: "I64 (streaming CFAR)", rc.RCFAR_SAT_TILE_I64: "TILE_I64",
+            rc.RCFAR_SAT_FUSED: "FUSED (streaming SAT + CFAR)"}.get(mode, str(mode))
+
+
+def batch_measure(rc, torch, synth, local, rank, n_frames=64, reps=10):
     """64 frames of uneven size and window: one rcfar_run_batch (graph-captured)
     against looping the per-frame path (rcfar_preprocess, rcfar_sat,
     rcfar_cfar) over the same frames; both produce the same decisions."""
@@ -319,7 +324,7 @@ def batch_measure(rc, torch, synth, local, rank, n_frames=64, reps=5):
             "speedup_vs_per_frame": t_single / t_batch,
             "kernels_us": {k: 1e3 * t / n for k, (n, t) in tr.items()},
             "tuning": {"dft_kblocks_per_cta": tuning.dft_kblocks_per_cta,
-                       "sat_mode": "I64 (streaming CFAR)" if tuning.sat_mode == rc.RCFAR_SAT_I64 else "TILE_I64",
+                       "sat_mode": sat_mode_name(rc, tuning.sat_mode),
                        "cfar_tile": [tuning.cfar_tile_rows, tuning.cfar_tile_cols],
                        "candidates": tuning.candidates, "best_ms": tuning.best_ms},
             "samples_per_s": samples / (t_batch * 1e-3),
@@ -593,6 +598,45 @@ def ours(args, rank, world, local, dist):
 
     variants["paper_frame_1024x600_trace_major"] = graph_rate(chain_p)
 
+    # the same 1024 x 4096 frames eight at a time through rcfar_run_batch (one
+    # graph per batch, autotuned schedule): the throughput form of this workload
+    hb = rc.rcfar_create(device=local, max_rows=M, max_cols=1024, max_n=N, max_window=32, max_frames=8,
+                         batch_bytes=1 << 30)
+    pbatch = rc.make_pre_params(synth.FS_HZ, mean_len=case.mean_len, halo_c=-1)
+    dets_b = [torch.empty((M, C), dtype=torch.uint8, device="cuda") for _ in range(RING)]
+    groups = [[rc.frame_desc(frames[j], win, dets_b[j]) for j in range(g0, g0 + 8)] for g0 in range(0, RING, 8)]
+    rc.rcfar_prepare(hb, groups[0], pbatch)
+    tuning_b = rc.rcfar_tune_batch(hb, groups[0], pbatch, reps=3)
+    gb = []
+    with torch.cuda.stream(stream):
+        for grp in groups:
+            rc.rcfar_run_batch(hb, grp, pbatch)
+            stream.synchronize()
+            g = torch.cuda.CUDAGraph()
+            with torch.cuda.graph(g, stream=stream):
+                rc.rcfar_run_batch(hb, grp, pbatch)
+            gb.append(g)
+    torch.cuda.synchronize()
+    for i in range(3):
+        gb[i % len(gb)].replay()
+    torch.cuda.synchronize()
+    nb_rep = max(6, args.steps // 8)
+    e0.record()
+    for i in range(nb_rep):
+        gb[i % len(gb)].replay()
+    e1.record()
+    torch.cuda.synchronize()
+    assert rc.rcfar_get_error(hb) == rc.RCFAR_OK
+    for i in range(RING):
+        chain(i)
+    torch.cuda.synchronize()
+    chain_batched = {"frames_per_batch": 8, "frames_per_s": 8 * nb_rep / (e0.elapsed_time(e1) / 1e3),
+                     "decisions_identical_to_per_frame": all(torch.equal(dets_b[j], dets[j]) for j in range(RING)),
+                     "tuning": {"dft_kblocks_per_cta": tuning_b.dft_kblocks_per_cta,
+                                "sat_mode": sat_mode_name(rc, tuning_b.sat_mode),
+                                "best_ms": tuning_b.best_ms}}
+    rc.rcfar_destroy(hb)
+
     # per-kernel device times (eager launches bracketed by CUDA events)
     rc.rcfar_trace_enable(h, True)
     for i in range(args.steps):
@@ -785,7 +829,8 @@ def ours(args, rank, world, local, dist):
                        "l2": "inputs larger than L2: ring of 16 distinct frames (268 MB)",
                        "parallelism": f"replicas x{world}"},
             "roofline": roofline, "kernels": step_kernels, "sat_cfar": sat_cfar, "batch": batch,
-            "serving": serving, "variants": variants, "chain_sat_cfar": chain_map, "e2e": e2e,
+            "serving": serving, "variants": variants, "chain_batched": chain_batched, "chain_sat_cfar": chain_map,
+            "e2e": e2e,
             "cpu_baseline": cpu, "clocks": clk, "gpu_launches": launches_per_step * args.steps,
             "peaks": peaks["source"]}
     print(json.dumps(line), flush=True)
