@@ -154,3 +154,44 @@ def test_serving_destroy_completes_queued_frames(rc):
     rc.rcfar_server_destroy(srv)  # returns once every queued frame has run
     for x, det in keep:
         assert int((det == 7).sum()) == 0  # every decision byte was written (0 or 1)
+
+
+def test_serving_padded_host_rows(rc):
+    """Frames whose host rows are padded (ldx > N, odd and even pitches) take the
+    pitched copy; frames without padding the linear one. Both give the frame's
+    decisions run alone from a contiguous device copy."""
+    arrivals, drones, variants, cases = synth.serving_stream(
+        n_requests=8, n_drones=2, rate_hz=1e6, seed=21, m_range=(64, 200), n_range=(256, 900), n_variants=2)
+    srv = rc.rcfar_server_create(device=0, budget_bytes=128 << 20, slots=2, max_batch_frames=4, max_rows=200,
+                                 max_n=900, max_window=20, params=params_of(rc))
+    subs = []
+    try:
+        for i, (d, v) in enumerate(zip(drones, variants)):
+            c = cases[int(d)][int(v)]
+            X = torch.from_numpy(synth.radar_frame(c.spec))
+            pad = (0, 13, 4, 1)[i % 4]
+            wide = torch.zeros((c.spec.M, c.spec.N + pad), dtype=torch.float32).pin_memory()
+            wide[:, :c.spec.N] = X
+            x = wide[:, :c.spec.N]
+            assert x.stride(0) == c.spec.N + pad
+            det = torch.full((c.spec.M, band_cols(rc, c.spec.N, c.window)), 7, dtype=torch.uint8).pin_memory()
+            subs.append((X, c.window, det, wide))
+            rc.rcfar_server_submit(srv, x, win_of(rc, c.window), det, tag=i)
+        done = {}
+        deadline = time.time() + 60
+        while len(done) < len(subs) and time.time() < deadline:
+            for cpl in rc.rcfar_server_poll(srv, 64, 100):
+                done[cpl.tag] = cpl
+    finally:
+        rc.rcfar_server_destroy(srv)
+    assert len(done) == len(subs) and all(cpl.status == rc.RCFAR_OK for cpl in done.values())
+    h = rc.rcfar_create(device=0, max_rows=200, max_cols=520, max_n=900, max_window=20, max_frames=1,
+                        batch_bytes=64 << 20)
+    try:
+        for X, w, det, _ in subs:
+            det1 = torch.empty(det.shape, dtype=torch.uint8, device="cuda")
+            rc.rcfar_run_batch(h, [rc.frame_desc(X.cuda(), win_of(rc, w), det1)], params_of(rc))
+            assert torch.equal(det, det1.cpu())
+        assert rc.rcfar_get_error(h) == rc.RCFAR_OK
+    finally:
+        rc.rcfar_destroy(h)
