@@ -26,7 +26,7 @@ inline long long round_up(long long a, long long b) { return ceil_div(a, b) * b;
 inline size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 struct Twiddle {
-  float* Wt = nullptr;
+  __half* Wt = nullptr;
   long long ldw = 0;
   int npad = 0, bn = 0;
   bool has_map = false;
@@ -49,18 +49,18 @@ EncodeTiledFn encode_tiled() {
   return fn;
 }
 
-// Tensor map of two planes [2][rows][npad] fp32 (plane stride rows * npad):
-// boxes of 32 samples x box_rows rows x 1 plane, 128-byte swizzle, rows past
-// the end read as zeros.
-bool make_planes_map(CUtensorMap* out, const float* base, long long rows, int npad, int box_rows) {
+// Tensor map of two planes [2][rows][npad] FP16 (plane stride rows * npad):
+// boxes of kDftBK samples (128 bytes) x box_rows rows x 1 plane, 128-byte
+// swizzle, rows past the end read as zeros.
+bool make_planes_map(CUtensorMap* out, const __half* base, long long rows, int npad, int box_rows) {
   EncodeTiledFn fn = encode_tiled();
   if (!fn || (reinterpret_cast<uintptr_t>(base) & 15) || (npad % kDftBK) || box_rows < 1 || box_rows > 256)
     return false;
   const cuuint64_t dims[3] = {(cuuint64_t)npad, (cuuint64_t)rows, 2};
-  const cuuint64_t strides[2] = {(cuuint64_t)npad * sizeof(float), (cuuint64_t)rows * npad * sizeof(float)};
+  const cuuint64_t strides[2] = {(cuuint64_t)npad * sizeof(__half), (cuuint64_t)rows * npad * sizeof(__half)};
   const cuuint32_t box[3] = {(cuuint32_t)kDftBK, (cuuint32_t)box_rows, 1};
   const cuuint32_t elem[3] = {1, 1, 1};
-  return fn(out, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<float*>(base), dims, strides, box, elem,
+  return fn(out, CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 3, const_cast<__half*>(base), dims, strides, box, elem,
             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
@@ -118,9 +118,8 @@ PreGeom pre_geom(int M, int N, int C, int kblocks_per_cta = 0) {
   dft_cols(C, &g.ntiles, &g.bn);
   g.ldw = (long long)g.ntiles * g.bn;
   const int tiles = g.mtiles * g.ntiles;
-  // about one CTA per SM for a frame on its own; every split keeps >= 4 K steps
   // about one CTA per SM for a frame on its own (one wave); splits are whole K blocks
-  const int kblk = kDftBK * kDftKB;
+  const int kblk = kDftBlock;
   g.nblocks = (int)ceil_div(g.npad, kblk);
   int sk = kblocks_per_cta > 0 ? (int)ceil_div(g.nblocks, kblocks_per_cta) : std::max(1, 152 / tiles);
   if (sk > g.nblocks) sk = g.nblocks;
@@ -244,8 +243,9 @@ struct rcfar_ctx {
   float* kpart = nullptr;
   size_t kpart_floats = 0;
   void* kpart_own = nullptr;  // separately allocated K-block partials (grown on demand)
-  float* yhi = nullptr;
-  float* ylo = nullptr;
+  __half* yhi = nullptr;
+  __half* ylo = nullptr;
+  float* yscale = nullptr;
   float* rowmean = nullptr;
   float* rowsq = nullptr;
   float* xt = nullptr;  // range-major copy of a trace-major frame
@@ -517,7 +517,7 @@ static rcfar_status get_plan(rcfar_ctx* h, int N, int c0, int C, cudaStream_t s,
   dft_cols(C, &ntiles, &bn);
   t.ldw = (long long)ntiles * bn;
   const int npad = (int)round_up(N, kDftBK);
-  const size_t bytes = 2 * (size_t)t.ldw * npad * sizeof(float);  // head and tail planes
+  const size_t bytes = 2 * (size_t)t.ldw * npad * sizeof(__half);  // head and tail planes
   if (cudaMalloc(&t.Wt, bytes) != cudaSuccess) return RCFAR_ERR_CUDA;
   cudaError_t e = cudaMemsetAsync(t.Wt, 0, bytes, s);  // padding rows and columns stay zero
   if (e == cudaSuccess) e = launch_twiddles(t.Wt, t.ldw, npad, N, c0, C, s);
@@ -542,6 +542,7 @@ static bool make_dft_frame(DftBatch& db, int k, const PreFrameDev& F, const Twid
   db.mb[k] = tw.mb;
   DftFrameDev& d = db.f[k];
   d.kpart = F.kpart;
+  d.yscale = F.yscale;
   d.ldk = F.ldk;
   d.M = F.M;
   d.bn = g.bn;
@@ -600,7 +601,8 @@ static size_t frame_data_bytes(int M, int N, int C, int x_layout) {
   t += align256((size_t)g.n_strips * M * sizeof(float));           // rowpart
   t += align256((size_t)g.n_strips * sizeof(float2));              // strip_ab
   t += align256((size_t)g.nblocks * M * g.ldk * 4);              // K-block partials
-  t += 2 * align256((size_t)M * g.npad * sizeof(float));           // yhi, ylo
+  t += 2 * align256((size_t)M * g.npad * sizeof(__half));          // yhi, ylo
+  t += align256((size_t)g.nblocks * M * sizeof(float));            // yscale
   t += align256((size_t)M * sizeof(float));                        // rowmean
   t += align256((size_t)g.ycols * M * sizeof(float));              // rowsq
   t += align256((size_t)M * round_up(C, 4) * 4);                   // map
@@ -698,7 +700,9 @@ rcfar_status rcfar_create(const rcfar_config* cfg, rcfar_handle* out) {
   total += align256((size_t)max_strips * 4);
   total += align256((size_t)max_tiles * 4);
   total += align256(kpart * 4);
-  total += 2 * align256((size_t)R * round_up(Nm, kDftBK) * sizeof(float));  // yhi, ylo
+  total += 2 * align256((size_t)R * round_up(Nm, kDftBK) * sizeof(__half));  // yhi, ylo
+  const size_t nblocks_max = (size_t)ceil_div(round_up(Nm, kDftBK), kDftBlock);
+  total += align256(nblocks_max * R * sizeof(float));                     // yscale
   total += align256((size_t)R * sizeof(float));                          // rowmean
   const size_t ycols_max = (size_t)ceil_div(round_up(Nm, kDftBK), kYCols);
   total += align256(ycols_max * R * sizeof(float));                      // rowsq
@@ -724,8 +728,9 @@ rcfar_status rcfar_create(const rcfar_config* cfg, rcfar_handle* out) {
   h->tile_cnt = cv.take<unsigned>(max_tiles);
   h->kpart = cv.take<float>(kpart);
   h->kpart_floats = kpart;
-  h->yhi = cv.take<float>((size_t)R * round_up(Nm, kDftBK));
-  h->ylo = cv.take<float>((size_t)R * round_up(Nm, kDftBK));
+  h->yhi = cv.take<__half>((size_t)R * round_up(Nm, kDftBK));
+  h->ylo = cv.take<__half>((size_t)R * round_up(Nm, kDftBK));
+  h->yscale = cv.take<float>(nblocks_max * R);
   h->rowmean = cv.take<float>(R);
   h->rowsq = cv.take<float>(ycols_max * R);
   h->xt = cv.take<float>((size_t)R * round_up(Nm, 4));
@@ -870,6 +875,7 @@ rcfar_status rcfar_preprocess(rcfar_handle h, const float* x, int32_t M, int32_t
   F.tile_cnt = h->tile_cnt;
   F.yhi = h->yhi;
   F.ylo = h->yhi + (long long)M * g.npad;  // the two planes back to back (the tail runs into h->ylo's room)
+  F.yscale = h->yscale;
   F.rowmean = h->rowmean;
   F.rowsq = h->rowsq;
   int n_tr = 0;
@@ -1381,8 +1387,9 @@ rcfar_status rcfar_run_batch(rcfar_handle h, const rcfar_frame_desc* frames, int
       F.rowpart = data.take<float>((size_t)g.n_strips * f.M);
       F.strip_ab = data.take<float2>(g.n_strips);
       F.kpart = data.take<float>((size_t)g.nblocks * f.M * g.ldk);
-      F.yhi = data.take<float>(2 * (size_t)f.M * g.npad);  // head and tail planes back to back
+      F.yhi = data.take<__half>(2 * (size_t)f.M * g.npad);  // head and tail planes back to back
       F.ylo = F.yhi ? F.yhi + (long long)f.M * g.npad : nullptr;
+      F.yscale = data.take<float>((size_t)g.nblocks * f.M);
       F.rowmean = data.take<float>(f.M);
       F.rowsq = data.take<float>((size_t)g.ycols * f.M);
       float* map = f.map;
@@ -1407,8 +1414,8 @@ rcfar_status rcfar_run_batch(rcfar_handle h, const rcfar_frame_desc* frames, int
       it_stats += g.n_strips * (int)ceil_div(g.n_chunks, stats_cpc);
       it_dft += g.mtiles * g.ntiles * g.splitk;
       it_norm += g.n_norm;
-      if (!F.stats || !F.partial || !F.rowpart || !F.strip_ab || !F.yhi || !F.ylo || !F.rowmean || !F.rowsq ||
-          !F.kpart || !map || !F.strip_cnt || !F.tile_cnt || !words)
+      if (!F.stats || !F.partial || !F.rowpart || !F.strip_ab || !F.yhi || !F.ylo || !F.yscale || !F.rowmean ||
+          !F.rowsq || !F.kpart || !map || !F.strip_cnt || !F.tile_cnt || !words)
         return RCFAR_ERR_OUT_OF_WORKSPACE;
       if (f.window.kind == RCFAR_CFAR_OS) {
         CfarMapDev& Q = ob.m[i_os++];
@@ -1457,7 +1464,8 @@ rcfar_status rcfar_run_batch(rcfar_handle h, const rcfar_frame_desc* frames, int
       it_tile += sg.n_bands * sg.n_chunks;
       it_band += sg.n_bands;
       it_vscan += (int)ceil_div(C, 32);
-      if (!F.stats || !F.partial || !F.rowpart || !F.strip_ab || !F.yhi || !F.ylo || !F.rowmean || !F.rowsq || !F.kpart || !map || !m.table ||
+      if (!F.stats || !F.partial || !F.rowpart || !F.strip_ab || !F.yhi || !F.ylo || !F.yscale || !F.rowmean || !F.rowsq ||
+          !F.kpart || !map || !m.table ||
           !sat_ok || !F.strip_cnt || !F.tile_cnt || !words)
         return RCFAR_ERR_OUT_OF_WORKSPACE;
 

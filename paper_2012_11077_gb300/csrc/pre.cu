@@ -5,9 +5,10 @@
 //                linear trend subtraction"; also the pieces of each row's
 //                slow-time mean of y (see k_ysplit).
 //   k_ysplit   : detrend + slow-time mean filter + max|y|; writes y minus
-//                its row mean, split into TF32 head and tail.
+//                its row mean, scaled per (row, K block) by a power of two
+//                into the FP16 range and split into FP16 head and tail.
 //   k_band_dft : band DFT as a GEMM of y [M x N] with the twiddle matrix
-//                [N x 2C] on the tcgen05 tensor cores (split TF32, three
+//                [N x 2C] on the tcgen05 tensor cores (split FP16, three
 //                products, accumulator in tensor memory), then the magnitude;
 //                split-K for small frames. Each row's
 //                mean c_m was removed from y and N c_m is added back to bin
@@ -19,7 +20,7 @@
 //   DFT is linear, so this equals transforming y / max|y|.
 //   k_twiddles : twiddle matrix W[n][2j] = cos(2 pi t/N), W[n][2j+1] = -sin,
 //                t = (c0 + j) n mod N, computed once per (N, band) in FP64 and
-//                stored split into TF32 head and tail.
+//                stored split into FP16 head and tail.
 #include "rcfar_internal.cuh"
 #include "async_copy.cuh"
 
@@ -234,28 +235,23 @@ __global__ void __launch_bounds__(256, 4) k_colstats(const __grid_constant__ Pre
   if (local == 0 && threadIdx.x == 0) *F.ymax = 0u;
 }
 
-__device__ __forceinline__ unsigned to_tf32(float x) {
-  unsigned r;
-  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
-  return r;
+// Power-of-two shift s that brings a K block of y into the FP16 range:
+// mx 2^s < 2^14 for the block's largest magnitude mx (0 for an all-zero or
+// non-finite block; |s| <= 100 keeps 2^s and 2^-s normal FP32 numbers).
+__device__ __forceinline__ int fp16_shift(float mx) {
+  if (!(mx > 0.f) || !(mx <= 3.0e38f)) return 0;
+  int e;
+  frexpf(mx, &e);  // mx = f 2^e, 1/2 <= f < 1
+  return max(-100, min(100, 14 - e));
 }
 
-// x as a TF32 head plus a TF32 tail (about 22 significant bits together).
-__device__ __forceinline__ float2 split_tf32(float x) {
-  const unsigned hi = to_tf32(x);
-  const unsigned lo = to_tf32(x - __uint_as_float(hi));
-  return make_float2(__uint_as_float(hi), __uint_as_float(lo));
-}
-
-// The same split in three integer/FP32 instructions: the head is x rounded
-// to TF32 (nearest, ties away from zero: add half a TF32 unit to the bit
-// pattern, clear the 13 low bits), the tail the exact remainder, of either
-// sign; the tensor cores read the top 19 bits of each 32-bit operand, so the
-// tail enters the products truncated to TF32 (22 bits in all; the signed
-// tail keeps that truncation unbiased).
-__device__ __forceinline__ float2 split_tf32_fast(float x) {
-  const float hi = __uint_as_float((__float_as_uint(x) + 0x1000u) & 0xFFFFE000u);
-  return make_float2(hi, x - hi);
+// x as an FP16 head plus an FP16 tail (about 22 significant bits together):
+// the head is x rounded to FP16, the tail the rounded remainder (x - head is
+// exact in FP32).
+__device__ __forceinline__ void split_f16(float x, __half* h, __half* t) {
+  const __half hh = __float2half_rn(x);
+  *h = hh;
+  *t = __float2half_rn(x - __half2float(hh));
 }
 
 // y pass: one warp per frame row, kYCols samples per CTA column block.
@@ -263,12 +259,13 @@ __device__ __forceinline__ float2 split_tf32_fast(float x) {
 //   y[m,n]  = mean of x'[m, n-h..n+h] in [0, N)    (mean filter)
 // records max |y| and writes y - c_m, where c_m is the row's slow-time mean
 // (a constant only reaches bin 0; removing it keeps the FP32 rounding of the
-// large per-range offsets out of the other bins), split into TF32 head and
-// tail for the tensor-core product. Samples N..npad-1 are written as 0.
+// large per-range offsets out of the other bins), scaled per K block of 256
+// samples by a power of two into the FP16 range and split into FP16 head and
+// tail for the tensor-core product (the scale is recorded per (row, block)). Samples N..npad-1 are written as 0.
 // H: the mean filter's half length when known at compile time (the window
 // sum is unrolled), or -1 for any h.
 template <int H>
-__global__ void __launch_bounds__(256) k_ysplit(const __grid_constant__ PreBatch b) {
+__global__ void __launch_bounds__(256, 4) k_ysplit(const __grid_constant__ PreBatch b) {
   pdl_trigger();
   pdl_wait();
   const int fi = find_item(b.f, b.n, (int)blockIdx.x, &PreFrameDev::item_y);
@@ -319,8 +316,8 @@ __global__ void __launch_bounds__(256) k_ysplit(const __grid_constant__ PreBatch
       if (i < kYCols + 2 * h) seg[warp][i] = xv[u] - sv[u].x - sv[u].y * dm;
     }
     __syncwarp();
-    float* yh = F.yhi + (long long)m * F.npad;
-    float* yl = F.ylo + (long long)m * F.npad;
+    __half* yh = F.yhi + (long long)m * F.npad;
+    __half* yl = F.ylo + (long long)m * F.npad;
     const float inv_full = 1.0f / (float)(2 * h + 1);
     const float* sg = &seg[warp][lane];
     auto window = [&](int q) {
@@ -333,26 +330,24 @@ __global__ void __launch_bounds__(256) k_ysplit(const __grid_constant__ PreBatch
       }
       return acc;
     };
+    constexpr int kQ = kYCols / 32;
+    float dv[kQ];    // y - c_m of the lane's samples n0 + lane + 32 q (0 past the frame)
     float sq = 0.f;  // sum of (y - c_m)^2 over this lane's samples (z-score normalisation)
     if (n0 - h >= 0 && n0 + kYCols + h <= N) {
       // every window of this block lies inside the frame (uniform fast path)
 #pragma unroll
-      for (int q = 0; q < kYCols / 32; ++q) {
-        const int n = n0 + lane + 32 * q;
+      for (int q = 0; q < kQ; ++q) {
         const float y = window(q) * inv_full;
         ymax = fmaxf(ymax, fabsf(y));
         const float d = y - cmv;
         sq = fmaf(d, d, sq);
-        const float2 out = split_tf32_fast(d);
-        yh[n] = out.x;
-        yl[n] = out.y;
+        dv[q] = d;
       }
     } else {
 #pragma unroll
-      for (int q = 0; q < kYCols / 32; ++q) {
+      for (int q = 0; q < kQ; ++q) {
         const int n = n0 + lane + 32 * q;
-        if (n >= F.npad) break;
-        float2 out = make_float2(0.f, 0.f);
+        dv[q] = 0.f;
         if (n < N) {
           const float acc = window(q);
           const int cnt = min(n + h, N - 1) - max(n - h, 0) + 1;
@@ -361,11 +356,34 @@ __global__ void __launch_bounds__(256) k_ysplit(const __grid_constant__ PreBatch
           ymax = fmaxf(ymax, fabsf(y));
           const float d = y - cmv;
           sq = fmaf(d, d, sq);
-          out = split_tf32_fast(d);
+          dv[q] = d;
         }
-        yh[n] = out.x;
-        yl[n] = out.y;
       }
+    }
+    // the block's two K blocks (q < kQ / 2 and q >= kQ / 2), each scaled by
+    // its own power of two into the FP16 range, split into head and tail
+    float mx0 = 0.f, mx1 = 0.f;
+#pragma unroll
+    for (int q = 0; q < kQ; ++q) {
+      if (q < kQ / 2) mx0 = fmaxf(mx0, fabsf(dv[q]));
+      else mx1 = fmaxf(mx1, fabsf(dv[q]));
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      mx0 = fmaxf(mx0, __shfl_xor_sync(0xffffffffu, mx0, o));
+      mx1 = fmaxf(mx1, __shfl_xor_sync(0xffffffffu, mx1, o));
+    }
+    const int s0 = fp16_shift(mx0), s1 = fp16_shift(mx1);
+    const float f0 = ldexpf(1.0f, s0), f1 = ldexpf(1.0f, s1);
+#pragma unroll
+    for (int q = 0; q < kQ; ++q) {
+      const int n = n0 + lane + 32 * q;
+      if (n < F.npad) split_f16(dv[q] * (q < kQ / 2 ? f0 : f1), &yh[n], &yl[n]);
+    }
+    if (lane == 0) {
+      const int blk = 2 * cbk;
+      if (blk < F.nblocks) F.yscale[(long long)blk * F.M + m] = ldexpf(1.0f, -s0);
+      if (blk + 1 < F.nblocks) F.yscale[(long long)(blk + 1) * F.M + m] = ldexpf(1.0f, -s1);
     }
     if (F.normalise == RCFAR_NORM_ROW_ZSCORE) {
 #pragma unroll
@@ -385,18 +403,18 @@ __global__ void __launch_bounds__(256) k_ysplit(const __grid_constant__ PreBatch
 }
 
 // Shared-memory matrix descriptor of a K-major operand tile whose rows are
-// 128 bytes (32 TF32 values) stored with the 128-byte swizzle: 8-row groups
+// 128 bytes (64 FP16 values) stored with the 128-byte swizzle: 8-row groups
 // 1024 bytes apart (SBO), layout SWIZZLE_128B, descriptor version 1.
 __device__ __forceinline__ unsigned long long umma_desc(unsigned saddr) {
   return (unsigned long long)((saddr >> 4) & 0x3FFFu) | (1ull << 16) | ((unsigned long long)(1024 >> 4) << 32) |
          (1ull << 46) | (2ull << 61);
 }
 
-__device__ __forceinline__ void umma_tf32(unsigned tmem_d, unsigned long long a, unsigned long long b, unsigned idesc,
-                                          unsigned accumulate) {
+__device__ __forceinline__ void umma_f16(unsigned tmem_d, unsigned long long a, unsigned long long b, unsigned idesc,
+                                         unsigned accumulate) {
   asm volatile(
       "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
-      " tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem_d),
+      " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem_d),
       "l"(a), "l"(b), "r"(idesc), "r"(accumulate));
 }
 
@@ -405,13 +423,13 @@ __device__ __forceinline__ void umma_commit(unsigned bar) {
 }
 
 // Band DFT as a GEMM on the 5th-generation tensor cores: (yhi + ylo) [M x npad]
-// times (Whi + Wlo)^T [npad x ldw] in TF32, three products per K step
+// times (Whi + Wlo)^T [npad x ldw] in FP16, three products per K step
 // (tail*head + head*tail + head*head, about 22 bits per product). One CTA per
 // (128-row tile, bn-column tile, K split), 12 warps:
 //   warp 0     issues the MMAs (one thread) into tensor memory;
-//   warps 1-7  stage K steps of 32 samples with cp.async into a ring of
+//   warps 1-7  stage K steps of 64 samples with cp.async into a ring of
 //              stages in the 128-byte-swizzled K-major layout the MMA reads;
-//   warps 8-11 drain the accumulator every kDftKB K steps (a K block of 128
+//   warps 8-11 drain the accumulator every kDftKB K steps (a K block of 256
 //              samples) into that block's partial sums in global memory.
 // Two accumulators alternate, so the MMAs of block b+1 run while block b is
 // drained. k_dft_reduce adds the blocks' partials in a fixed order with
@@ -431,7 +449,7 @@ __global__ void __launch_bounds__(kDftThreads, 1) k_band_dft(const __grid_consta
   const int m0 = mt * kDftBM;
   const int bn = F.bn;
   const int j0 = nt * bn;  // real output column
-  const int kbeg = ks * F.kper;  // a multiple of 32 * kDftKB
+  const int kbeg = ks * F.kper;  // a multiple of kDftBlock
   const int kend = min(F.npad, kbeg + F.kper);
   const int nk = (kend - kbeg) / kDftBK;
   const int nblk = (nk + kDftKB - 1) / kDftKB;
@@ -473,8 +491,9 @@ __global__ void __launch_bounds__(kDftThreads, 1) k_band_dft(const __grid_consta
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const unsigned tmem = tmem_slot;
 
-  const unsigned idesc = (1u << 4) | (2u << 7) | (2u << 10) | ((unsigned)(bn >> 3) << 17) |
-                         ((unsigned)(kDftBM >> 4) << 24);
+  // instruction descriptor: D FP32 (bits 4-5 = 1), A and B FP16 (bits 7-9, 10-12 = 0),
+  // both K-major, N >> 3 at bit 17, M >> 4 at bit 24
+  const unsigned idesc = (1u << 4) | ((unsigned)(bn >> 3) << 17) | ((unsigned)(kDftBM >> 4) << 24);
   if (warp == 0) {
     if (lane == 0) {
       for (int i = 0; i < nk; ++i) {
@@ -495,13 +514,13 @@ __global__ void __launch_bounds__(kDftThreads, 1) k_band_dft(const __grid_consta
         const unsigned sb_hi = sa_lo + kDftBM * 128, sb_lo = sb_hi + bn * 128;
         const unsigned dacc = tmem + (unsigned)(acc * bn);
 #pragma unroll
-        for (int kk = 0; kk < kDftBK / 8; ++kk) {
-          const unsigned off = kk * 32;  // 8 TF32 values along K
+        for (int kk = 0; kk < kDftBK / 16; ++kk) {
+          const unsigned off = kk * 32;  // 16 FP16 values along K
           const unsigned long long ah = umma_desc(sa_hi + off), al = umma_desc(sa_lo + off);
           const unsigned long long bh = umma_desc(sb_hi + off), bl = umma_desc(sb_lo + off);
-          umma_tf32(dacc, al, bh, idesc, (!first || kk > 0) ? 1u : 0u);
-          umma_tf32(dacc, ah, bl, idesc, 1u);
-          umma_tf32(dacc, ah, bh, idesc, 1u);
+          umma_f16(dacc, al, bh, idesc, (!first || kk > 0) ? 1u : 0u);
+          umma_f16(dacc, ah, bl, idesc, 1u);
+          umma_f16(dacc, ah, bh, idesc, 1u);
         }
         umma_commit(smem_u32(&bar_empty[slot]));  // the slot is free once these MMAs finish
         if ((i % kDftKB) == kDftKB - 1 || i == nk - 1) umma_commit(smem_u32(&bar_accf[acc]));  // block done
@@ -526,15 +545,15 @@ __global__ void __launch_bounds__(kDftThreads, 1) k_band_dft(const __grid_consta
         const int rr = id >> 3, c = id & 7;
         const int m = m0 + rr;
         const bool ok = m < F.M;
-        const long long off = (long long)(ok ? m : 0) * F.npad + k0 + 4 * c;
+        const long long off = (long long)(ok ? m : 0) * F.npad + k0 + 8 * c;
         const unsigned sw = rr * 128 + ((c ^ (rr & 7)) << 4);
         cp_async16(sa_hi + sw, F.yhi + off, ok);
         cp_async16(sa_lo + sw, F.ylo + off, ok);
       }
-      const float* wb = F.Wt + (long long)j0 * F.npad + k0;
+      const __half* wb = F.Wt + (long long)j0 * F.npad + k0;
       for (int id = ptid; id < bn * 8; id += 224) {  // B: bn rows (output columns) x 8 chunks
         const int rr = id >> 3, c = id & 7;
-        const float* src = wb + (long long)rr * F.npad + 4 * c;
+        const __half* src = wb + (long long)rr * F.npad + 8 * c;
         const unsigned sw = rr * 128 + ((c ^ (rr & 7)) << 4);
         cp_async16(sb_hi + sw, src, true);
         cp_async16(sb_lo + sw, src + plane, true);
@@ -563,6 +582,8 @@ __global__ void __launch_bounds__(kDftThreads, 1) k_band_dft(const __grid_consta
       }
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
       float* dst = F.kpart + ((long long)(blk0 + bi) * F.M + (m < F.M ? m : 0)) * F.ldk + j0;
+      // back to the units of y: the block's rows were scaled by 2^s(m, block) (exact)
+      const float f = m < F.M ? __ldg(F.yscale + (long long)(blk0 + bi) * F.M + m) : 0.f;
       for (int c = 0; c < bn; c += 8) {
         unsigned r[8];
         const unsigned taddr = tmem + ((unsigned)(32 * q) << 16) + (unsigned)(acc * bn + c);
@@ -572,8 +593,10 @@ __global__ void __launch_bounds__(kDftThreads, 1) k_band_dft(const __grid_consta
         asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
         if (m < F.M) {
           float4* d4 = reinterpret_cast<float4*>(dst + c);
-          d4[0] = make_float4(__uint_as_float(r[0]), __uint_as_float(r[1]), __uint_as_float(r[2]), __uint_as_float(r[3]));
-          d4[1] = make_float4(__uint_as_float(r[4]), __uint_as_float(r[5]), __uint_as_float(r[6]), __uint_as_float(r[7]));
+          d4[0] = make_float4(__uint_as_float(r[0]) * f, __uint_as_float(r[1]) * f, __uint_as_float(r[2]) * f,
+                              __uint_as_float(r[3]) * f);
+          d4[1] = make_float4(__uint_as_float(r[4]) * f, __uint_as_float(r[5]) * f, __uint_as_float(r[6]) * f,
+                              __uint_as_float(r[7]) * f);
         }
       }
       asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -590,7 +613,7 @@ __global__ void __launch_bounds__(kDftThreads, 1) k_band_dft(const __grid_consta
 
 // The same GEMM with the operands brought in by the tensor memory
 // accelerator: one thread of warp 1 issues, per K step, four box loads
-// (y head and tail: 32 samples x 128 rows; twiddle head and tail: 32
+// (y head and tail: 64 samples x 128 rows; twiddle head and tail: 64
 // samples x bn columns) that complete on the stage's mbarrier with their byte
 // count; rows past the frame arrive as zeros. Warp 0 issues the MMAs,
 // warps 2-5 drain the accumulators (warp w reads TMEM lanes 32 (w % 4) ..).
@@ -652,8 +675,9 @@ __global__ void __launch_bounds__(kDftTmaThreads, 1) k_band_dft_tma(const __grid
   const unsigned tmem = tmem_slot;
   pdl_wait();  // the tensor-memory allocation and barriers above overlap the previous kernel
 
-  const unsigned idesc = (1u << 4) | (2u << 7) | (2u << 10) | ((unsigned)(bn >> 3) << 17) |
-                         ((unsigned)(kDftBM >> 4) << 24);
+  // instruction descriptor: D FP32 (bits 4-5 = 1), A and B FP16 (bits 7-9, 10-12 = 0),
+  // both K-major, N >> 3 at bit 17, M >> 4 at bit 24
+  const unsigned idesc = (1u << 4) | ((unsigned)(bn >> 3) << 17) | ((unsigned)(kDftBM >> 4) << 24);
   if (warp == 0) {
     if (lane == 0) {
       for (int i = 0; i < nk; ++i) {
@@ -675,13 +699,13 @@ __global__ void __launch_bounds__(kDftTmaThreads, 1) k_band_dft_tma(const __grid
         const unsigned sb_hi = sa_lo + kDftBM * 128, sb_lo = sb_hi + bn * 128;
         const unsigned dacc = tmem + (unsigned)(acc * bn);
 #pragma unroll
-        for (int kk = 0; kk < kDftBK / 8; ++kk) {
-          const unsigned off = kk * 32;
+        for (int kk = 0; kk < kDftBK / 16; ++kk) {
+          const unsigned off = kk * 32;  // 16 FP16 values along K
           const unsigned long long ah = umma_desc(sa_hi + off), al = umma_desc(sa_lo + off);
           const unsigned long long bh = umma_desc(sb_hi + off), bl = umma_desc(sb_lo + off);
-          umma_tf32(dacc, al, bh, idesc, (!first || kk > 0) ? 1u : 0u);
-          umma_tf32(dacc, ah, bl, idesc, 1u);
-          umma_tf32(dacc, ah, bh, idesc, 1u);
+          umma_f16(dacc, al, bh, idesc, (!first || kk > 0) ? 1u : 0u);
+          umma_f16(dacc, ah, bl, idesc, 1u);
+          umma_f16(dacc, ah, bh, idesc, 1u);
         }
         umma_commit(smem_u32(&bar_empty[slot]));
         if ((i % kDftKB) == kDftKB - 1 || i == nk - 1) umma_commit(smem_u32(&bar_accf[acc]));
@@ -725,6 +749,8 @@ __global__ void __launch_bounds__(kDftTmaThreads, 1) k_band_dft_tma(const __grid
       }
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
       float* dst = F.kpart + ((long long)(blk0 + bi) * F.M + (m < F.M ? m : 0)) * F.ldk + j0;
+      // back to the units of y: the block's rows were scaled by 2^s(m, block) (exact)
+      const float f = m < F.M ? __ldg(F.yscale + (long long)(blk0 + bi) * F.M + m) : 0.f;
       for (int c = 0; c < bn; c += 8) {
         unsigned r[8];
         const unsigned taddr = tmem + ((unsigned)(32 * q) << 16) + (unsigned)(acc * bn + c);
@@ -734,8 +760,10 @@ __global__ void __launch_bounds__(kDftTmaThreads, 1) k_band_dft_tma(const __grid
         asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
         if (m < F.M) {
           float4* d4 = reinterpret_cast<float4*>(dst + c);
-          d4[0] = make_float4(__uint_as_float(r[0]), __uint_as_float(r[1]), __uint_as_float(r[2]), __uint_as_float(r[3]));
-          d4[1] = make_float4(__uint_as_float(r[4]), __uint_as_float(r[5]), __uint_as_float(r[6]), __uint_as_float(r[7]));
+          d4[0] = make_float4(__uint_as_float(r[0]) * f, __uint_as_float(r[1]) * f, __uint_as_float(r[2]) * f,
+                              __uint_as_float(r[3]) * f);
+          d4[1] = make_float4(__uint_as_float(r[4]) * f, __uint_as_float(r[5]) * f, __uint_as_float(r[6]) * f,
+                              __uint_as_float(r[7]) * f);
         }
       }
       asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -808,7 +836,7 @@ __global__ void __launch_bounds__(256) k_dft_reduce(const __grid_constant__ PreB
   F.map[(long long)m * F.ld_map + j] = F.detector == RCFAR_DETECT_SQUARE_LAW ? p2 * (inv * inv) : sqrtf(p2) * inv;
 }
 
-__global__ void k_twiddles(float* Wt, long long ldw, int npad, int N, int c0, int C) {
+__global__ void k_twiddles(__half* Wt, long long ldw, int npad, int N, int c0, int C) {
   const long long total = (long long)N * C;
   const long long plane = ldw * npad;
   for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < total;
@@ -817,11 +845,12 @@ __global__ void k_twiddles(float* Wt, long long ldw, int npad, int N, int c0, in
     const long long t = ((long long)(c0 + j) * n) % N;
     double s, c;
     sincospi(2.0 * (double)t / (double)N, &s, &c);
-    const float2 cs = split_tf32((float)c), sn = split_tf32((float)(-s));
-    Wt[(long long)(2 * j) * npad + n] = cs.x;
-    Wt[plane + (long long)(2 * j) * npad + n] = cs.y;
-    Wt[(long long)(2 * j + 1) * npad + n] = sn.x;
-    Wt[plane + (long long)(2 * j + 1) * npad + n] = sn.y;
+    // FP16 head and tail of the FP64 value (the tail is the rounded remainder)
+    const __half ch = __double2half(c), sh = __double2half(-s);
+    Wt[(long long)(2 * j) * npad + n] = ch;
+    Wt[plane + (long long)(2 * j) * npad + n] = __double2half(c - (double)__half2float(ch));
+    Wt[(long long)(2 * j + 1) * npad + n] = sh;
+    Wt[plane + (long long)(2 * j + 1) * npad + n] = __double2half(-s - (double)__half2float(sh));
   }
 }
 
@@ -870,7 +899,7 @@ cudaError_t launch_dft_reduce(const PreBatch& b, int blocks, cudaStream_t s) {
   return launch_pdl(k_dft_reduce, blocks, 256, 0, s, b);
 }
 
-cudaError_t launch_twiddles(float* Wt, long long ldw, int npad, int N, int c0, int C, cudaStream_t s) {
+cudaError_t launch_twiddles(__half* Wt, long long ldw, int npad, int N, int c0, int C, cudaStream_t s) {
   const long long total = (long long)N * C;
   int blocks = (int)((total + 255) / 256);
   if (blocks > 4096) blocks = 4096;

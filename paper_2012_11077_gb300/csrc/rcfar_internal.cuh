@@ -35,10 +35,11 @@ constexpr int kStatsStrip = 128;         // columns per column-statistics CTA
 constexpr int kStatsRowsPerChunk = 64;   // rows per column-statistics chunk (8 warps x 8)
 
 // Band DFT GEMM on tcgen05: 128 rows (TMEM lanes) x up to 256 real outputs
-// (TMEM columns) per CTA, K steps of 32 samples (one 128-byte swizzle row).
+// (TMEM columns) per CTA, K steps of 64 samples (one 128-byte swizzle row of
+// FP16 head or tail values).
 constexpr int kDftBM = 128;
 constexpr int kDftMaxBN = 256;
-constexpr int kDftBK = 32;
+constexpr int kDftBK = 64;
 constexpr int kDftMaxStages = 4;
 constexpr int kDftSmemCap = 220 * 1024;
 // K block: the tensor-memory accumulator is drained every kDftKB K steps
@@ -46,12 +47,16 @@ constexpr int kDftSmemCap = 220 * 1024;
 // compensation. The accumulator's own adds lose precision in proportion to
 // the run length (measured on 1024 x 4096 frames: worst map error 4e-5 of
 // the element, floored at 1e-2 of the row peak, at 128 samples; 6e-5 at
-// 256; 1.2e-4 without draining).
-constexpr int kDftKB = 8;
+// 256; 1.2e-4 without draining). Each (row, K block) of y carries its own
+// power-of-two scale into the FP16 range (the y pass writes it, the
+// reduction divides it out).
+constexpr int kDftKB = 4;
+constexpr int kDftBlock = kDftBK * kDftKB;  // samples per K block
 constexpr int kDftThreads = 384;  // warp 0 MMA, warps 1-7 producers, warps 8-11 drain
-// y pass: 8 rows (one per warp) x kYCols samples per CTA.
+// y pass: 8 rows (one per warp) x kYCols samples per CTA (two K blocks).
 constexpr int kYRows = 8;
 constexpr int kYCols = 512;
+static_assert(kYCols == 2 * kDftBlock, "a y-pass column block holds two K blocks");
 
 struct PreFrameDev {
   const float* x;
@@ -60,11 +65,12 @@ struct PreFrameDev {
   int c0, C;  // stored bins c0 .. c0 + C - 1
   int h;      // mean filter half length
   float mbar, inv_M, inv_D;
-  const float* Wt;   // twiddles, transposed and split: head [ldw][npad] then tail [ldw][npad];
-                     // row 2j = cos, 2j+1 = -sin of bin c0+j (TF32 bit patterns); zero padded
+  const __half* Wt;  // twiddles, transposed and split: head [ldw][npad] then tail [ldw][npad];
+                     // row 2j = cos, 2j+1 = -sin of bin c0+j (FP16 head and tail); zero padded
   long long ldw;     // real output columns incl. padding = ntiles * bn
-  float* yhi;        // [M][npad] y minus its row mean: TF32 head; zero for n >= N
-  float* ylo;        // [M][npad] the TF32 tail
+  __half* yhi;       // [M][npad] (y minus its row mean) x 2^s(m, K block): FP16 head; zero for n >= N
+  __half* ylo;       // [M][npad] the FP16 tail
+  float* yscale;     // [nblocks][M] 2^-s(m, K block), by which the drain multiplies each partial
   float* rowmean;    // [M] the row means c_m removed from y
   float* rowsq;      // z-score normalisation: [ycols][M] per-block sums of (y - c_m)^2
   const float* xsrc; // trace-major input [N][ldsrc] transposed into x (nullptr: x is the input)
@@ -83,7 +89,7 @@ struct PreFrameDev {
   float* map;           // [M][ld_map] the normalised band map
   long long ld_map;
   float* kpart;         // K-block partial sums [nblocks][M][ldk] (ldk = ldw)
-  int nblocks;          // npad / (32 * kDftKB), rounded up
+  int nblocks;          // npad / kDftBlock, rounded up
   long long ldk;
   unsigned* tile_cnt;   // [mtiles * ntiles] arrival counters (self-resetting)
   int chunks_per_cta, n_chunks, n_strips;  // k_colstats: CTAs per frame n_strips x ceil(n_chunks / chunks_per_cta)
@@ -106,7 +112,8 @@ struct PreBatch {
 // 128-byte swizzle the MMA descriptors read. The maps are kernel parameters
 // (param space), so a launch needs no copy and is graph-capturable.
 struct DftFrameDev {
-  float* kpart;       // K-block partials [nblocks][M][ldk]
+  float* kpart;         // K-block partials [nblocks][M][ldk]
+  const float* yscale;  // [nblocks][M] 2^-s(m, block): the drain writes partials in the units of y
   long long ldk;
   int M, bn, mtiles, ntiles, kper, npad, item_dft, pad;
 };
@@ -270,7 +277,7 @@ cudaError_t launch_ysplit(const PreBatch& b, int blocks, cudaStream_t s);
 cudaError_t launch_band_dft(const PreBatch& b, int blocks, cudaStream_t s);
 cudaError_t launch_band_dft_tma(const DftBatch& b, int blocks, cudaStream_t s);
 cudaError_t launch_dft_reduce(const PreBatch& b, int blocks, cudaStream_t s);
-cudaError_t launch_twiddles(float* Wt, long long ldw, int npad, int N, int c0, int C, cudaStream_t s);
+cudaError_t launch_twiddles(__half* Wt, long long ldw, int npad, int N, int c0, int C, cudaStream_t s);
 // bytes of one K step of the band DFT ring: A head and tail (128 rows), B head and tail (bn rows)
 __host__ __device__ inline int dft_stage_bytes(int bn) { return 2 * kDftBM * 128 + 2 * bn * 128; }
 
