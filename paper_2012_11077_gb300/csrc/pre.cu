@@ -15,7 +15,7 @@
 //                0 only: a constant contributes to no other bin, and removing
 //                it keeps the FP32 rounding of the large per-range DC offsets
 //                out of the small bins.
-//   k_dft_reduce: sums the K splits' partials (fixed order), magnitude.
+//   k_dft_reduce: sums the K blocks' partials (fixed order), magnitude.
 //   Normalisation ("then normalized") divides the magnitude by max|y|: the
 //   DFT is linear, so this equals transforming y / max|y|.
 //   k_twiddles : twiddle matrix W[n][2j] = cos(2 pi t/N), W[n][2j+1] = -sin,

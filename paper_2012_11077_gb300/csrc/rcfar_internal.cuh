@@ -45,11 +45,11 @@ constexpr int kDftSmemCap = 220 * 1024;
 // K block: the tensor-memory accumulator is drained every kDftKB K steps
 // (256 samples) into a partial sum; partials are added with Kahan
 // compensation. The accumulator's own adds lose precision in proportion to
-// the run length (measured on 1024 x 4096 frames: worst map error 4e-5 of
-// the element, floored at 1e-2 of the row peak, at 128 samples; 6e-5 at
-// 256; 1.2e-4 without draining). Each (row, K block) of y carries its own
-// power-of-two scale into the FP16 range (the y pass writes it, the
-// reduction divides it out).
+// the run length (measured on 1024 x 4096 frames with TF32 operands: worst
+// map error 4e-5 of the element, floored at 1e-2 of the row peak, at 128
+// samples; 6e-5 at 256; 1.2e-4 without draining; 4.0e-5 at 256 with the FP16
+// operands). Each (row, K block) of y carries its own power-of-two scale
+// into the FP16 range (the y pass writes it, the drain divides it out).
 constexpr int kDftKB = 4;
 constexpr int kDftBlock = kDftBK * kDftKB;  // samples per K block
 constexpr int kDftThreads = 384;  // warp 0 MMA, warps 1-7 producers, warps 8-11 drain
