@@ -280,6 +280,23 @@ __global__ void __launch_bounds__(256, 4) k_ysplit(const __grid_constant__ PreBa
   __shared__ float red[kYRows];
   float ymax = 0.f;
   if (m < F.M) {
+    const float* xr = F.x + (long long)m * F.ldx;
+    // fast layout: the whole block and its halo inside the frame, rows 16-byte
+    // aligned, the filter length known at compile time; its samples are
+    // loaded first, so their latency overlaps the row mean's
+    constexpr int kPad = H >= 0 ? (H + 3) / 4 * 4 : 0;  // halo rounded up to whole float4
+    constexpr int kG = (kYCols + 2 * kPad) / 4;         // float4 groups of the fast layout's span
+    constexpr int kGL = (kG + 31) / 32;
+    const bool vec = ((F.ldx & 3) == 0) && ((reinterpret_cast<uintptr_t>(F.x) & 15) == 0);
+    const bool fastv = H >= 0 && vec && n0 - kPad >= 0 && n0 + kYCols + kPad <= N;  // uniform over the CTA
+    float4 xq[kGL];
+    if (fastv) {
+#pragma unroll
+      for (int u = 0; u < kGL; ++u) {
+        const int g = lane + 32 * u;
+        xq[u] = g < kG ? __ldg(reinterpret_cast<const float4*>(xr + n0 - kPad + 4 * g)) : make_float4(0.f, 0.f, 0.f, 0.f);
+      }
+    }
     // row mean c_m = (sum_j w_j x[m,j] - sum_j w_j a_j - (m - mbar) sum_j w_j b_j) / N
     float rs = 0.f, A = 0.f, Bv = 0.f;
     for (int sI = lane; sI < F.n_strips; sI += 32) {
@@ -297,66 +314,124 @@ __global__ void __launch_bounds__(256, 4) k_ysplit(const __grid_constant__ PreBa
     const float dm = (float)m - F.mbar;
     const float cmv = (rs - A - dm * Bv) / (float)N;
     if (cbk == 0 && lane == 0) F.rowmean[m] = cmv;
-    // x' over [n0 - h, n0 + 256 + h): all loads issued before any store
-    const float* xr = F.x + (long long)m * F.ldx;
-    constexpr int kSeg = (kYCols + 2 * kMaxMeanHalf) / 32;
-    float xv[kSeg];
-    float2 sv[kSeg];
-#pragma unroll
-    for (int u = 0; u < kSeg; ++u) {
-      const int i = lane + 32 * u;
-      const int n = n0 - h + i;
-      const bool ok = i < kYCols + 2 * h && n >= 0 && n < N;
-      xv[u] = ok ? __ldg(xr + n) : 0.f;
-      sv[u] = ok ? __ldg(&F.stats[n]) : make_float2(0.f, 0.f);
-    }
-#pragma unroll
-    for (int u = 0; u < kSeg; ++u) {
-      const int i = lane + 32 * u;
-      if (i < kYCols + 2 * h) seg[warp][i] = xv[u] - sv[u].x - sv[u].y * dm;
-    }
-    __syncwarp();
     __half* yh = F.yhi + (long long)m * F.npad;
     __half* yl = F.ylo + (long long)m * F.npad;
     const float inv_full = 1.0f / (float)(2 * h + 1);
-    const float* sg = &seg[warp][lane];
-    auto window = [&](int q) {
-      float acc = 0.f;
-      if constexpr (H >= 0) {
-#pragma unroll
-        for (int d = 0; d <= 2 * H; ++d) acc += sg[32 * q + d];
-      } else {
-        for (int d = 0; d <= 2 * h; ++d) acc += sg[32 * q + d];
-      }
-      return acc;
-    };
     constexpr int kQ = kYCols / 32;
-    float dv[kQ];    // y - c_m of the lane's samples n0 + lane + 32 q (0 past the frame)
+    // dv[k]: y - c_m of the lane's k-th sample (0 past the frame); k < kQ / 2
+    // lie in the block's first K block. Fast layout: sample n0 + 4 lane +
+    // 128 (k / 4) + k % 4; general layout: sample n0 + lane + 32 k.
+    float dv[kQ];
     float sq = 0.f;  // sum of (y - c_m)^2 over this lane's samples (z-score normalisation)
-    if (n0 - h >= 0 && n0 + kYCols + h <= N) {
-      // every window of this block lies inside the frame (uniform fast path)
+    if (fastv) {
+      // seg[w][i] = x' at column n0 - kPad + i: 16-byte loads of the
+      // statistics, 16-byte stores (all loads issued before any store)
+      float4 sa[kGL], sb[kGL];
+      const float4* st4 = reinterpret_cast<const float4*>(F.stats);  // two (a, b) pairs per float4
 #pragma unroll
-      for (int q = 0; q < kQ; ++q) {
-        const float y = window(q) * inv_full;
-        ymax = fmaxf(ymax, fabsf(y));
-        const float d = y - cmv;
-        sq = fmaf(d, d, sq);
-        dv[q] = d;
+      for (int u = 0; u < kGL; ++u) {
+        const int g = lane + 32 * u;
+        if (g < kG) {
+          const int c = n0 - kPad + 4 * g;
+          sa[u] = __ldg(st4 + c / 2);
+          sb[u] = __ldg(st4 + c / 2 + 1);
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < kGL; ++u) {
+        const int g = lane + 32 * u;
+        if (g < kG) {
+          float4 o;
+          o.x = xq[u].x - sa[u].x - sa[u].y * dm;
+          o.y = xq[u].y - sa[u].z - sa[u].w * dm;
+          o.z = xq[u].z - sb[u].x - sb[u].y * dm;
+          o.w = xq[u].w - sb[u].z - sb[u].w * dm;
+          *reinterpret_cast<float4*>(&seg[warp][4 * g]) = o;
+        }
+      }
+      __syncwarp();
+      // four consecutive outputs per lane and group: their windows from
+      // kPad / 2 + 1 aligned 16-byte reads, each summed in the general
+      // layout's order
+#pragma unroll
+      for (int qq = 0; qq < kQ / 4; ++qq) {
+        const int base = 4 * lane + 128 * qq;
+        float v[2 * kPad + 4];
+#pragma unroll
+        for (int r = 0; r < (2 * kPad + 4) / 4; ++r) {
+          const float4 t = *reinterpret_cast<const float4*>(&seg[warp][base + 4 * r]);
+          v[4 * r] = t.x;
+          v[4 * r + 1] = t.y;
+          v[4 * r + 2] = t.z;
+          v[4 * r + 3] = t.w;
+        }
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+          float acc = 0.f;
+#pragma unroll
+          for (int d = 0; d <= 2 * (H >= 0 ? H : 0); ++d) acc += v[kPad - (H >= 0 ? H : 0) + e + d];
+          const float y = acc * inv_full;
+          ymax = fmaxf(ymax, fabsf(y));
+          const float d = y - cmv;
+          sq = fmaf(d, d, sq);
+          dv[4 * qq + e] = d;
+        }
       }
     } else {
+      // x' over [n0 - h, n0 + kYCols + h): all loads issued before any store
+      constexpr int kSeg = (kYCols + 2 * kMaxMeanHalf) / 32;
+      float xv[kSeg];
+      float2 sv[kSeg];
 #pragma unroll
-      for (int q = 0; q < kQ; ++q) {
-        const int n = n0 + lane + 32 * q;
-        dv[q] = 0.f;
-        if (n < N) {
-          const float acc = window(q);
-          const int cnt = min(n + h, N - 1) - max(n - h, 0) + 1;
-          // a full window multiplies by 1 / (2h + 1); the truncated ones at the ends divide
-          const float y = cnt == 2 * h + 1 ? acc * inv_full : acc / (float)cnt;
+      for (int u = 0; u < kSeg; ++u) {
+        const int i = lane + 32 * u;
+        const int n = n0 - h + i;
+        const bool ok = i < kYCols + 2 * h && n >= 0 && n < N;
+        xv[u] = ok ? __ldg(xr + n) : 0.f;
+        sv[u] = ok ? __ldg(&F.stats[n]) : make_float2(0.f, 0.f);
+      }
+#pragma unroll
+      for (int u = 0; u < kSeg; ++u) {
+        const int i = lane + 32 * u;
+        if (i < kYCols + 2 * h) seg[warp][i] = xv[u] - sv[u].x - sv[u].y * dm;
+      }
+      __syncwarp();
+      const float* sg = &seg[warp][lane];
+      auto window = [&](int q) {
+        float acc = 0.f;
+        if constexpr (H >= 0) {
+#pragma unroll
+          for (int d = 0; d <= 2 * H; ++d) acc += sg[32 * q + d];
+        } else {
+          for (int d = 0; d <= 2 * h; ++d) acc += sg[32 * q + d];
+        }
+        return acc;
+      };
+      if (n0 - h >= 0 && n0 + kYCols + h <= N) {
+        // every window of this block lies inside the frame
+#pragma unroll
+        for (int q = 0; q < kQ; ++q) {
+          const float y = window(q) * inv_full;
           ymax = fmaxf(ymax, fabsf(y));
           const float d = y - cmv;
           sq = fmaf(d, d, sq);
           dv[q] = d;
+        }
+      } else {
+#pragma unroll
+        for (int q = 0; q < kQ; ++q) {
+          const int n = n0 + lane + 32 * q;
+          dv[q] = 0.f;
+          if (n < N) {
+            const float acc = window(q);
+            const int cnt = min(n + h, N - 1) - max(n - h, 0) + 1;
+            // a full window multiplies by 1 / (2h + 1); the truncated ones at the ends divide
+            const float y = cnt == 2 * h + 1 ? acc * inv_full : acc / (float)cnt;
+            ymax = fmaxf(ymax, fabsf(y));
+            const float d = y - cmv;
+            sq = fmaf(d, d, sq);
+            dv[q] = d;
+          }
         }
       }
     }
@@ -375,10 +450,28 @@ __global__ void __launch_bounds__(256, 4) k_ysplit(const __grid_constant__ PreBa
     }
     const int s0 = fp16_shift(mx0), s1 = fp16_shift(mx1);
     const float f0 = ldexpf(1.0f, s0), f1 = ldexpf(1.0f, s1);
+    if (fastv) {
+      // four consecutive samples per lane and group: one 8-byte store per plane
 #pragma unroll
-    for (int q = 0; q < kQ; ++q) {
-      const int n = n0 + lane + 32 * q;
-      if (n < F.npad) split_f16(dv[q] * (q < kQ / 2 ? f0 : f1), &yh[n], &yl[n]);
+      for (int qq = 0; qq < kQ / 4; ++qq) {
+        const int n = n0 + 4 * lane + 128 * qq;
+        const float f = qq < kQ / 8 ? f0 : f1;
+        __half hh[4], tt[4];
+#pragma unroll
+        for (int e = 0; e < 4; ++e) split_f16(dv[4 * qq + e] * f, &hh[e], &tt[e]);
+        *reinterpret_cast<uint2*>(yh + n) = make_uint2(
+            (unsigned)__half_as_ushort(hh[0]) | ((unsigned)__half_as_ushort(hh[1]) << 16),
+            (unsigned)__half_as_ushort(hh[2]) | ((unsigned)__half_as_ushort(hh[3]) << 16));
+        *reinterpret_cast<uint2*>(yl + n) = make_uint2(
+            (unsigned)__half_as_ushort(tt[0]) | ((unsigned)__half_as_ushort(tt[1]) << 16),
+            (unsigned)__half_as_ushort(tt[2]) | ((unsigned)__half_as_ushort(tt[3]) << 16));
+      }
+    } else {
+#pragma unroll
+      for (int q = 0; q < kQ; ++q) {
+        const int n = n0 + lane + 32 * q;
+        if (n < F.npad) split_f16(dv[q] * (q < kQ / 2 ? f0 : f1), &yh[n], &yl[n]);
+      }
     }
     if (lane == 0) {
       const int blk = 2 * cbk;
