@@ -340,7 +340,7 @@ rcfar_status rcfar_prepare(rcfar_handle h, const rcfar_frame_desc* frames, int32
 /* How rcfar_run_batch lays its work out on the GPU. Every tuning gives the
  * same results (bit for bit): only the schedule changes. */
 typedef struct rcfar_batch_tuning {
-  int32_t dft_kblocks_per_cta;  /* K blocks (128 samples) per band-DFT CTA; 0 = automatic (about two waves) */
+  int32_t dft_kblocks_per_cta;  /* K blocks (256 samples) per band-DFT CTA; 0 = automatic (about two waves) */
   int32_t sat_mode;             /* RCFAR_SAT_TILE_I64 (tile-local table, register-staged CFAR),
                                    RCFAR_SAT_I64 (table S itself, CFAR streaming it through a
                                    bulk-copy ring) or RCFAR_SAT_FUSED (no table: each CTA builds

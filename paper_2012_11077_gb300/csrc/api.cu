@@ -1298,7 +1298,7 @@ rcfar_status rcfar_run_batch(rcfar_handle h, const rcfar_frame_desc* frames, int
       pb.dft_smem = dft_smem_for(bn_max);
       kb_per_cta = h->tuning.dft_kblocks_per_cta > 0
                        ? h->tuning.dft_kblocks_per_cta
-                       : (int)std::max<long long>(1, units / (2 * 152));  // about two waves
+                       : (int)std::max<long long>(1, units / (2LL * std::max(1, h->sms)));  // about two waves
     }
     // table mode of this group: the streaming CFAR when tuned so and every
     // frame's window fits its ring
