@@ -410,6 +410,30 @@ def test_preprocess_strided_input(rc, h):
     assert map_err(P.cpu().numpy(), P_o).max() <= REL
 
 
+@pytest.mark.parametrize("det_mode", [0, 1])
+def test_preprocess_power_of_two_scale_invariance(rc, h, det_mode):
+    # Scaling the raw frame by 2^k scales every FP32 step of the chain exactly
+    # (for k small enough that no intermediate, down to the squared magnitude
+    # of the weakest bin, leaves the normal range), the per-(row, K block) FP16
+    # shift absorbs it, and the normalisation by max |y| removes it: the
+    # normalised band map must be bit-identical. A wrong block or row in the
+    # shift's bookkeeping breaks this at once.
+    case = synth.ChainCase(synth.FrameSpec(M=300, N=1100, n_targets=3, seed=12), synth.Window(8, 8, 2, 2, 1e-4))
+    X = synth.radar_frame(case.spec)
+    params = rc.make_pre_params(synth.FS_HZ, halo_c=10, detector=det_mode)
+    band = rc.rcfar_band_plan(case.spec.N, params)
+    maps = []
+    for k in (0, -20, 24):
+        P = torch.empty((case.spec.M, band.cols), dtype=torch.float32, device="cuda")
+        rc.rcfar_preprocess(h, dev_t(X * np.float32(2.0 ** k)), params, P)
+        assert rc.rcfar_get_error(h) == rc.RCFAR_OK
+        maps.append(P.cpu())
+    assert torch.equal(maps[0], maps[1]) and torch.equal(maps[0], maps[2])
+    P_o, _ = oracle.preprocess_frame(X, synth.FS_HZ, 5, halo=10, detector="square" if det_mode else "magnitude")
+    assert map_err(maps[0].numpy() if not det_mode else np.sqrt(np.maximum(maps[0].numpy(), 0)),
+                   P_o if not det_mode else np.sqrt(P_o)).max() <= REL
+
+
 # ------------------------------------------------------------------ batched chain
 def test_run_batch_parity_and_mix_invariance(rc, h):
     cases = synth.mixed_batch_cases(10, seed=3, m_range=(64, 300), n_range=(256, 1200))
