@@ -350,7 +350,9 @@ typedef struct rcfar_batch_tuning {
   int32_t cfar_tile_cols;
   double best_ms;               /* rcfar_tune_batch: time of one batch with this tuning */
   int32_t candidates;           /* rcfar_tune_batch: tunings timed */
-  int32_t pad;
+  int32_t dft_operands;         /* band-DFT operand staging: 0 = tensor memory accelerator (default),
+                                   1 = cp.async copies (the path taken when a tensor map cannot be
+                                   made); both give bit-identical results; the autotuner keeps 0 */
 } rcfar_batch_tuning;
 
 /* Autotuner: times rcfar_run_batch on these frames (outputs are written)

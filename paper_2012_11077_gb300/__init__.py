@@ -112,7 +112,7 @@ _lib = None
 class rcfar_batch_tuning(ctypes.Structure):
     _fields_ = [("dft_kblocks_per_cta", ctypes.c_int32), ("sat_mode", ctypes.c_int32),
                 ("cfar_tile_rows", ctypes.c_int32), ("cfar_tile_cols", ctypes.c_int32),
-                ("best_ms", ctypes.c_double), ("candidates", ctypes.c_int32), ("pad", ctypes.c_int32)]
+                ("best_ms", ctypes.c_double), ("candidates", ctypes.c_int32), ("dft_operands", ctypes.c_int32)]
 
 
 class rcfar_server_config(ctypes.Structure):
@@ -450,8 +450,11 @@ def rcfar_selftest_wait(device: int = 0, polls: int = 2000) -> int:
 
 # ---- batch tuning -------------------------------------------------------------
 
-def make_batch_tuning(dft_kblocks_per_cta: int = 0, sat_mode: int = RCFAR_SAT_TILE_I64, cfar_tile=(0, 0)):
-    return rcfar_batch_tuning(int(dft_kblocks_per_cta), int(sat_mode), int(cfar_tile[0]), int(cfar_tile[1]), 0.0, 0, 0)
+def make_batch_tuning(dft_kblocks_per_cta: int = 0, sat_mode: int = RCFAR_SAT_TILE_I64, cfar_tile=(0, 0),
+                      dft_operands: int = 0):
+    """dft_operands: 0 = band-DFT operands by the tensor memory accelerator, 1 = by cp.async."""
+    return rcfar_batch_tuning(int(dft_kblocks_per_cta), int(sat_mode), int(cfar_tile[0]), int(cfar_tile[1]), 0.0, 0,
+                              int(dft_operands))
 
 
 def rcfar_tune_batch(h: int, frames: Sequence[rcfar_frame_desc], params: rcfar_pre_params, reps: int = 3,

@@ -1347,7 +1347,7 @@ rcfar_status rcfar_run_batch(rcfar_handle h, const rcfar_frame_desc* frames, int
     db.n = cnt;
     db.dft_smem = pb.dft_smem;
     db.status = h->status;
-    bool dft_tma_ok = true;
+    bool dft_tma_ok = h->tuning.dft_operands == 0;
     // column statistics: several 64-row chunks per CTA when the batch has
     // chunks for more than two waves of CTAs at two chunks each (fewer
     // hand-offs between CTAs; the results do not depend on it)
@@ -1558,6 +1558,7 @@ rcfar_status rcfar_run_batch(rcfar_handle h, const rcfar_frame_desc* frames, int
 
 static bool valid_tuning(const rcfar_batch_tuning* t) {
   return t && t->dft_kblocks_per_cta >= 0 && t->dft_kblocks_per_cta <= 4096 &&
+         (t->dft_operands == 0 || t->dft_operands == 1) &&
          (t->sat_mode == RCFAR_SAT_TILE_I64 || t->sat_mode == RCFAR_SAT_I64 || t->sat_mode == RCFAR_SAT_FUSED) &&
          ((t->cfar_tile_rows == 0 && t->cfar_tile_cols == 0) ||
           (t->cfar_tile_rows > 0 && t->cfar_tile_rows <= 16 && t->cfar_tile_cols > 0 && 256 % t->cfar_tile_cols == 0 &&

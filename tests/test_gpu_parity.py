@@ -501,8 +501,9 @@ def test_run_batch_workspace_limit(rc):
 
 
 def test_batch_tunings_give_identical_results(rc):
-    # every batch tuning (band-DFT split, table mode, CFAR strip) changes only
-    # the schedule: outputs are bit-identical; the autotuner keeps the fastest
+    # every batch tuning (band-DFT split and operand staging, table mode, CFAR
+    # strip) changes only the schedule: outputs are bit-identical; the
+    # autotuner keeps the fastest
     cases = synth.mixed_batch_cases(12, seed=21, m_range=(64, 400), n_range=(256, 2048))
     params = rc.make_pre_params(synth.FS_HZ, mean_len=5, halo_c=-1)
     h2 = rc.rcfar_create(device=0, max_rows=512, max_cols=1100, max_n=2048, max_window=20, max_frames=16,
@@ -522,7 +523,9 @@ def test_batch_tunings_give_identical_results(rc):
         ref = None
         for t in [rc.make_batch_tuning(), rc.make_batch_tuning(1), rc.make_batch_tuning(8),
                   rc.make_batch_tuning(2, rc.RCFAR_SAT_I64), rc.make_batch_tuning(0, rc.RCFAR_SAT_TILE_I64, (8, 32)),
-                  rc.make_batch_tuning(0, rc.RCFAR_SAT_FUSED)]:
+                  rc.make_batch_tuning(0, rc.RCFAR_SAT_FUSED),
+                  # band-DFT operands by cp.async (the path without tensor maps), two K splits
+                  rc.make_batch_tuning(0, dft_operands=1), rc.make_batch_tuning(2, dft_operands=1)]:
             rc.rcfar_set_batch_tuning(h2, t)
             for d, th, mp in outs:
                 d.fill_(7)
