@@ -151,3 +151,37 @@ def test_os_factor_matches_oracle(rc):
         kk = k or ocfar.os_rank_default(n)
         o = ocfar.os_factor(n, kk, pfa)
         assert abs(f - o) <= 1e-12 * o, (tr, tc, gr, gc, pfa, k, f, o)
+
+
+def test_binding_structs_match_the_header(rc, tmp_path):
+    # every ctypes structure of the binding has the size and field offsets the
+    # C compiler gives the header's struct (a drift would corrupt arguments)
+    import ctypes
+    import shutil
+    import subprocess
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    structs = [n for n in dir(rc) if n.startswith("rcfar_") and isinstance(getattr(rc, n), type)
+               and issubclass(getattr(rc, n), ctypes.Structure)]
+    assert len(structs) >= 10
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "rcfar.h"', "int main(void) {"]
+    for n in structs:
+        lines.append(f'  printf("{n} size %zu\\n", sizeof({n}));')
+        for f, _ in getattr(rc, n)._fields_:
+            lines.append(f'  printf("{n} {f} %zu\\n", offsetof({n}, {f}));')
+    lines += ["  return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    inc = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include")
+    subprocess.run([cc, "-std=c11", "-I", inc, str(src), "-o", str(exe)], check=True, capture_output=True)
+    got = {}
+    for line in subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.splitlines():
+        name, field, value = line.split()
+        got[(name, field)] = int(value)
+    for n in structs:
+        cls = getattr(rc, n)
+        assert got[(n, "size")] == ctypes.sizeof(cls), n
+        for f, _ in cls._fields_:
+            assert got[(n, f)] == getattr(cls, f).offset, (n, f)
