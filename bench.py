@@ -208,6 +208,22 @@ def oracle_rate(budget_s: float = 10.0, max_frames: int = 50):
     return n / el, n, el
 
 
+def oracle_rate_single_core(budget_s: float = 8.0, max_frames: int = 10):
+    """The same on one core: a child process with every BLAS / OpenMP pool at one thread."""
+    env = dict(os.environ)
+    for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS", "BLIS_NUM_THREADS"):
+        env[k] = "1"
+    code = ("import json, sys; sys.path.insert(0, %r); import bench; "
+            "print(json.dumps(bench.oracle_rate(%r, %d)))" % (ROOT, budget_s, max_frames))
+    try:
+        r = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True, timeout=120)
+        v, n, el = json.loads(r.stdout.strip().splitlines()[-1])
+        return {"value": v, "unit": "frames/s", "cores": 1,
+                "sample": f"{n} frames of 1024x4096 in {el:.1f} s, numpy FP64, one thread"}
+    except Exception as e:  # the single-core figure is context only
+        return {"value": None, "unit": "frames/s", "cores": 1, "error": str(e)[:200]}
+
+
 def reference_arm(args, rank):
     if rank != 0:
         return
@@ -821,7 +837,8 @@ def ours(args, rank, world, local, dist):
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         v, n, el = oracle_rate()
         cpu = {"value": v, "unit": "frames/s", "cores": os.cpu_count(), "kind": "oracle",
-               "sample": f"{n} frames of 1024x4096 in {el:.1f} s, numpy FP64 (BLAS threads = all cores)"}
+               "sample": f"{n} frames of 1024x4096 in {el:.1f} s, numpy FP64 (BLAS threads = all cores)",
+               "single_core": oracle_rate_single_core()}
 
     rc.rcfar_destroy(h)
     if rank != 0:
