@@ -9,8 +9,17 @@
 //                 arithmetic, so the reference sum is exact up to the
 //                 quantisation of the map; T = (alpha / n_ref) * S_ref and
 //                 det = CUT > T.
+// k_cfar_ring   : the same on the I64 table S itself, whose rows stream
+//                 through a shared-memory ring fed by bulk copies.
+// k_sat_cfar_fused, k_sat_cfar_stream : SAT and CFAR in one pass, the table
+//                 never in device memory (per-block integral images; or a
+//                 strip's integral image walked down the rows in a ring).
 // k_cfar_direct : the sliding-window CFAR the SAT replaces: the same
 //                 decisions with S_ref summed over the n_ref training cells.
+// k_cfar_os     : ordered-statistic thresholds (a next-step variant, not a
+//                 region sum): the k-th smallest training cell per CUT.
+// Greatest-of / smallest-of thresholds take the two half sums of the
+// training ring from 16 lookups in every SAT kernel and k_cfar_direct.
 #include "rcfar_internal.cuh"
 #include "async_copy.cuh"
 #include "fixed_point.cuh"

@@ -6,14 +6,16 @@
 //   L      : table of the tile relative to its own origin (tile-local)
 //   CC_j(r): sum over the band's rows <= r and the columns left of the tile
 //   RC_b(c): S(last row of band b, c)
-// Three wait-free passes (reduce, then scan, then nothing else to wait for):
-//   k_sat_tile  : one CTA per tile; writes L and the tile's exact row and
-//                 column totals (warp-shuffle row scans, shared-memory column
-//                 scans across the 8 warps);
+// Wait-free passes (no CTA waits for another):
+//   k_sat_tile  : (TILE_I64, TILE_F32, NAIVE_F32) one CTA per tile; writes L
+//                 and the tile's exact row and column totals (warp-shuffle
+//                 row scans, shared-memory column scans across the 8 warps);
+//   k_sat_reduce: (I64) the tile totals only, without writing L;
 //   k_sat_hscan : one CTA per band; the band's row prefix of the column
 //                 totals across the whole width, and CC for every tile;
-//   k_sat_vscan : each column's prefix over bands -> RC.
-//   k_sat_finalize (I64 and NAIVE_F32 only) folds the carries into L.
+//   k_sat_vscan : each column's prefix over bands -> RC;
+//   k_sat_down  : (I64) the tile prefix plus the carries, written as S;
+//   k_sat_finalize (NAIVE_F32) folds the carries into L.
 // Carries are 64-bit fixed point q = round(x * 2^s) added modulo 2^64
 // (exact; every region sum below 2^63 comes out exact even if S wraps).
 #include "rcfar_internal.cuh"
