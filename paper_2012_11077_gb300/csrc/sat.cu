@@ -570,7 +570,7 @@ __global__ void __launch_bounds__(1024) k_sat_vscan(const __grid_constant__ SatB
   }
 }
 
-// I64 and NAIVE_F32: fold the carries into the tile-local table in place.
+// NAIVE_F32: fold the carries into the tile-local table in place.
 template <int MODE>
 __global__ void __launch_bounds__(256) k_sat_finalize(const __grid_constant__ SatBatch B) {
   pdl_trigger();
