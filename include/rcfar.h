@@ -249,7 +249,15 @@ const char* rcfar_status_string(rcfar_status s);
  *                                                      per-row z-score)
  *   P[m,j]  = | sum_n y[m,n] exp(-2 pi i (c0+j) n / N) |   (or its square)
  * band_out (host pointer, may be NULL) receives the bins used. The first call
- * for a new (N, band) builds its twiddle table (one allocation). */
+ * for a new (N, band) builds its twiddle table (one allocation).
+ * Arithmetic: FP32, the transform on the tensor cores with y and the twiddles
+ * each split into an FP16 head and tail (y scaled per row and 256-sample
+ * block by a power of two into the FP16 range) and FP32 accumulation drained
+ * every 256 samples; each map element is within 1e-4 of FP64 relative to
+ * max(|element|, 1e-2 x its row's peak). Errors: INVALID_ARG for sizes or
+ * parameters out of range (M, N <= 0, ldx or ld_map too small, even or too
+ * long a mean filter), UNSUPPORTED beyond the handle's maxima, CUDA_ERROR on
+ * a failed launch. */
 rcfar_status rcfar_preprocess(rcfar_handle h, const float* x, int32_t M, int32_t N, int64_t ldx,
                               const rcfar_pre_params* p, float* map, int64_t ld_map,
                               rcfar_band* band_out, rcfar_stream stream);
