@@ -195,6 +195,46 @@ def test_direct_equals_sat_random_maps():
         assert cmp.mismatches == 0
 
 
+@pytest.mark.parametrize("shape,win", [((40, 50), (3, 2, 1, 2, 1e-2)),    # non-square window
+                                       ((37, 61), (2, 6, 3, 0, 1e-3)),    # zero guard columns, guard rows > train
+                                       ((25, 25), (4, 4, 0, 0, 1e-1)),    # no guard at all
+                                       ((64, 31), (8, 8, 2, 2, 1e-4))])
+def test_direct_at_equals_sliding_window_every_cut(shape, win):
+    # cfar_direct_at (outer box sum minus guard box sum, per CUT) against
+    # cfar_direct (the n_ref offsets summed one at a time) at every interior
+    # CUT, and against a third form that masks the window cell by cell
+    rng = np.random.default_rng(21)
+    P = rng.exponential(size=shape)
+    P[rng.integers(0, shape[0], 6), rng.integers(0, shape[1], 6)] += 40.0
+    tr, tc, gr, gc, pfa = win
+    d = ocfar.cfar_direct(P, *win)
+    rs, cs = np.nonzero(d.cut)
+    assert rs.size > 0
+    det, thr = ocfar.cfar_direct_at(P, rs, cs, *win)
+    np.testing.assert_allclose(thr, d.thr[rs, cs], rtol=1e-13)
+    np.testing.assert_array_equal(det, d.det[rs, cs])
+    wr, wc = gr + tr, gc + tc
+    nr = ocfar.n_ref(tr, tc, gr, gc)
+    a = ocfar.alpha(nr, pfa)
+    dr, dc = np.meshgrid(np.arange(-wr, wr + 1), np.arange(-wc, wc + 1), indexing="ij")
+    train = ~((np.abs(dr) <= gr) & (np.abs(dc) <= gc))
+    assert int(train.sum()) == nr
+    for i in rng.choice(rs.size, size=min(rs.size, 40), replace=False):
+        r, c = rs[i], cs[i]
+        t = a * P[r - wr:r + wr + 1, c - wc:c + wc + 1][train].sum() / nr
+        assert abs(thr[i] - t) <= 1e-13 * t
+        assert det[i] == (1 if P[r, c] > t else 0)
+
+
+def test_direct_at_worked_example():
+    P, (tr, tc, gr, gc, pfa), sref, det = worked_example()
+    a = ocfar.alpha(ocfar.n_ref(tr, tc, gr, gc), pfa)
+    rs, cs = np.meshgrid(np.arange(2, 5), np.arange(2, 5), indexing="ij")
+    d, t = ocfar.cfar_direct_at(P, rs.ravel(), cs.ravel(), tr, tc, gr, gc, pfa)
+    np.testing.assert_array_equal(d, det[2:5, 2:5].ravel())
+    np.testing.assert_allclose(t, a * sref.ravel() / 16.0, rtol=1e-14)
+
+
 def test_scale_invariance_power_of_two():
     rng = np.random.default_rng(10)
     P = rng.exponential(size=(48, 48))
