@@ -41,6 +41,8 @@ RCFAR_CFAR_CA = 0
 RCFAR_CFAR_GO = 1
 RCFAR_CFAR_SO = 2
 RCFAR_CFAR_OS = 3
+RCFAR_MEM_HOST = 0
+RCFAR_MEM_DEVICE = 1
 
 SAT_TILE_H = 32
 SAT_TILE_W = 128
@@ -124,7 +126,8 @@ class rcfar_server_config(ctypes.Structure):
 class rcfar_request(ctypes.Structure):
     _fields_ = [("x", ctypes.c_void_p), ("M", ctypes.c_int32), ("N", ctypes.c_int32), ("ldx", ctypes.c_int64),
                 ("window", rcfar_window), ("det", ctypes.c_void_p), ("ld_det", ctypes.c_int64),
-                ("tag", ctypes.c_int64), ("arrival_ns", ctypes.c_int64)]
+                ("tag", ctypes.c_int64), ("arrival_ns", ctypes.c_int64), ("memory", ctypes.c_int32),
+                ("pad", ctypes.c_int32)]
 
 
 class rcfar_completion(ctypes.Structure):
@@ -227,6 +230,51 @@ def _ld(t) -> int:
     return int(t.stride(0))
 
 
+def _torch():
+    import torch
+    return torch
+
+
+def _require(t, name: str, dtypes, rows: int = 0, cols: int = 0, cuda: bool = True):
+    """Raise ValueError unless t is a 2D row-major tensor of one of dtypes with at
+    least rows x cols elements, on the current CUDA device (cuda=True) or in host
+    memory (cuda=False). Runs before any call into the library."""
+    torch = _torch()
+    if not isinstance(t, torch.Tensor):
+        raise ValueError(f"{name}: expected a torch tensor")
+    if t.dtype not in dtypes:
+        raise ValueError(f"{name}: dtype {t.dtype}, expected one of {tuple(str(d) for d in dtypes)}")
+    if t.dim() != 2 or t.stride(1) != 1:
+        raise ValueError(f"{name}: expected a row-major 2D tensor")
+    if t.shape[0] < rows or t.shape[1] < cols:
+        raise ValueError(f"{name}: shape {tuple(t.shape)} is smaller than {rows} x {cols}")
+    if cuda:
+        if not t.is_cuda or t.device.index != torch.cuda.current_device():
+            raise ValueError(f"{name}: must be on the current CUDA device")
+    elif t.device.type != "cpu":
+        raise ValueError(f"{name}: must be in host memory")
+
+
+def _f32():
+    return (_torch().float32,)
+
+
+def _f32_f16():
+    return (_torch().float32, _torch().float16)
+
+
+def _u8():
+    return (_torch().uint8,)
+
+
+def _require_status(t):
+    torch = _torch()
+    if not isinstance(t, torch.Tensor) or t.dtype != torch.int32 or t.numel() < 1 or not t.is_contiguous():
+        raise ValueError("status: expected a contiguous int32 tensor with at least one element")
+    if not t.is_cuda or t.device.index != torch.cuda.current_device():
+        raise ValueError("status: must be on the current CUDA device")
+
+
 def make_window(train_r, train_c, guard_r, guard_c, pfa, kind=RCFAR_CFAR_CA, os_rank=0) -> rcfar_window:
     """kind: RCFAR_CFAR_CA (cell averaging), RCFAR_CFAR_GO, RCFAR_CFAR_SO or RCFAR_CFAR_OS;
     os_rank: the OS rank k (0: ceil(3 n_ref / 4))."""
@@ -308,6 +356,8 @@ def rcfar_preprocess(h: int, x, params: rcfar_pre_params, map_out, stream=None) 
     """x: float32 CUDA tensor (row-major), [M][N] or, with params.x_layout = RCFAR_X_TRACE_MAJOR,
     [N][M]; map_out: float32 [M][>=cols]."""
     M, N = _frame_dims(x, params.x_layout == RCFAR_X_TRACE_MAJOR)
+    _require(x, "x", _f32())
+    _require(map_out, "map_out", _f32(), M, rcfar_band_plan(N, params).cols)
     band = rcfar_band()
     _check(lib().rcfar_preprocess(h, _ptr(x), M, N, _ld(x), ctypes.byref(params), _ptr(map_out), _ld(map_out),
                                   ctypes.byref(band), _stream(stream)), "rcfar_preprocess")
@@ -317,6 +367,7 @@ def rcfar_preprocess(h: int, x, params: rcfar_pre_params, map_out, stream=None) 
 def rcfar_sat(h: int, map_t, value_bound: float = 0.0, mode: int = RCFAR_SAT_TILE_I64, map_exp2: int = 0,
               stream=None) -> rcfar_sat_view:
     import torch
+    _require(map_t, "map", _f32_f16())
     dtype = RCFAR_MAP_F16 if map_t.dtype == torch.float16 else RCFAR_MAP_F32
     view = rcfar_sat_view()
     _check(lib().rcfar_sat(h, _ptr(map_t), dtype, int(map_exp2), int(map_t.shape[0]), int(map_t.shape[1]),
@@ -328,6 +379,11 @@ def rcfar_sat(h: int, map_t, value_bound: float = 0.0, mode: int = RCFAR_SAT_TIL
 def rcfar_cfar(h: int, view: rcfar_sat_view, map_t, window: rcfar_window, cut_c_lo: int, cut_c_hi: int, det,
                thr=None, map_exp2: int = 0, stream=None):
     import torch
+    if map_t is not None:
+        _require(map_t, "map", _f32_f16(), view.rows, view.cols)
+    _require(det, "det", _u8(), view.rows, view.cols)
+    if thr is not None:
+        _require(thr, "thr", _f32(), view.rows, view.cols)
     dtype = RCFAR_MAP_F16 if map_t is not None and map_t.dtype == torch.float16 else RCFAR_MAP_F32
     _check(lib().rcfar_cfar(h, ctypes.byref(view), _ptr(map_t), dtype, int(map_exp2),
                             _ld(map_t) if map_t is not None else 0,
@@ -337,6 +393,11 @@ def rcfar_cfar(h: int, view: rcfar_sat_view, map_t, window: rcfar_window, cut_c_
 
 def rcfar_cfar_direct(h: int, map_t, window: rcfar_window, cut_c_lo: int, cut_c_hi: int, det, thr=None,
                       stream=None):
+    _require(map_t, "map", _f32())
+    rows, cols = int(map_t.shape[0]), int(map_t.shape[1])
+    _require(det, "det", _u8(), rows, cols)
+    if thr is not None:
+        _require(thr, "thr", _f32(), rows, cols)
     _check(lib().rcfar_cfar_direct(h, _ptr(map_t), int(map_t.shape[0]), int(map_t.shape[1]), _ld(map_t),
                                    ctypes.byref(window), int(cut_c_lo), int(cut_c_hi), _ptr(det), _ld(det),
                                    _ptr(thr), _ld(thr) if thr is not None else 0, _stream(stream)),
@@ -344,6 +405,7 @@ def rcfar_cfar_direct(h: int, map_t, window: rcfar_window, cut_c_lo: int, cut_c_
 
 
 def rcfar_sat_materialize(h: int, view: rcfar_sat_view, out, stream=None):
+    _require(out, "out", (_torch().float64,), view.rows, view.cols)
     _check(lib().rcfar_sat_materialize(h, ctypes.byref(view), _ptr(out), _ld(out), _stream(stream)),
            "rcfar_sat_materialize")
 
@@ -355,12 +417,36 @@ def _frame_dims(x, trace_major: bool):
 
 def frame_desc(x, window: rcfar_window, det, thr=None, map_out=None, trace_major: bool = False) -> rcfar_frame_desc:
     M, N = _frame_dims(x, trace_major)
-    return rcfar_frame_desc(_ptr(x), M, N, _ld(x), window, _ptr(det), _ld(det),
+    _require(x, "x", _f32())
+    _require(det, "det", _u8(), M)
+    if thr is not None:
+        _require(thr, "thr", _f32(), M)
+    if map_out is not None:
+        _require(map_out, "map_out", _f32(), M)
+    d = rcfar_frame_desc(_ptr(x), M, N, _ld(x), window, _ptr(det), _ld(det),
                             _ptr(thr), _ld(thr) if thr is not None else 0, _ptr(map_out),
                             _ld(map_out) if map_out is not None else 0)
+    d._outputs = (det, thr, map_out)  # checked against the band's columns by rcfar_run_batch
+    return d
+
+
+def _check_batch_outputs(frames, params: rcfar_pre_params):
+    """Every frame's det / thr / map must hold the band's columns (known only with the params)."""
+    for i, f in enumerate(frames):
+        outs = getattr(f, "_outputs", None)
+        if outs is None:
+            continue
+        pf = rcfar_pre_params(params.fs_hz, params.f_lo_hz, params.f_hi_hz, params.mean_len,
+                              f.window.guard_c + f.window.train_c if params.halo_c < 0 else params.halo_c,
+                              params.detector, params.normalise, params.x_layout, 0)
+        cols = rcfar_band_plan(int(f.N), pf).cols
+        for name, t in zip(("det", "thr", "map"), outs):
+            if t is not None and t.shape[1] < cols:
+                raise ValueError(f"frame {i}: {name} has {t.shape[1]} columns, the band needs {cols}")
 
 
 def rcfar_run_batch(h: int, frames: Sequence[rcfar_frame_desc], params: rcfar_pre_params, stream=None):
+    _check_batch_outputs(frames, params)
     arr = (rcfar_frame_desc * len(frames))(*frames)
     _check(lib().rcfar_run_batch(h, arr, len(frames), ctypes.byref(params), _stream(stream)), "rcfar_run_batch")
 
@@ -385,6 +471,13 @@ def rcfar_trace_read(h: int) -> dict:
 def rcfar_sat_cfar_static(map_t, value_bound: float, window: rcfar_window, cut_c_lo: int, cut_c_hi: int, det,
                           thr=None, status=None, stream=None):
     """SAT + CA-CFAR of a float32 map without any device allocation (see rcfar.h)."""
+    _require(map_t, "map", _f32())
+    rows, cols = int(map_t.shape[0]), int(map_t.shape[1])
+    _require(det, "det", _u8(), rows, cols)
+    if thr is not None:
+        _require(thr, "thr", _f32(), rows, cols)
+    if status is not None:
+        _require_status(status)
     _check(lib().rcfar_sat_cfar_static(_ptr(map_t), int(map_t.shape[0]), int(map_t.shape[1]), _ld(map_t),
                                        float(value_bound), ctypes.byref(window), int(cut_c_lo), int(cut_c_hi),
                                        _ptr(det), _ld(det), _ptr(thr), _ld(thr) if thr is not None else 0,
@@ -405,13 +498,16 @@ def rcfar_server_create(device: int = 0, budget_bytes: int = 8 << 30, slots: int
 
 def rcfar_server_submit(srv: int, x, window: rcfar_window, det, tag: int, arrival_ns: int = 0,
                         trace_major: bool = False):
-    """x, det: host (CPU) tensors, row-major (pinned memory gives asynchronous copies); they must stay
-    alive until the frame's completion has been polled. trace_major: x is [N][M] (the server's
-    params must say so too)."""
-    if x.device.type != "cpu" or det.device.type != "cpu":
-        raise ValueError("serving takes host tensors")
+    """x, det: both host (CPU) tensors (pinned memory gives asynchronous copies) or both tensors on the
+    current CUDA device (the server's device: read and written in place; the work that wrote x must be
+    complete), row-major; they must stay alive until the frame's completion has been polled.
+    trace_major: x is [N][M] (the server's params must say so too)."""
     M, N = _frame_dims(x, trace_major)
-    req = rcfar_request(_ptr(x), M, N, _ld(x), window, _ptr(det), _ld(det), int(tag), int(arrival_ns))
+    device = bool(getattr(x, "is_cuda", False))
+    _require(x, "x", _f32(), cuda=device)
+    _require(det, "det", _u8(), M, cuda=device)
+    req = rcfar_request(_ptr(x), M, N, _ld(x), window, _ptr(det), _ld(det), int(tag), int(arrival_ns),
+                        RCFAR_MEM_DEVICE if device else RCFAR_MEM_HOST, 0)
     _check(lib().rcfar_server_submit(srv, ctypes.byref(req)), "rcfar_server_submit")
 
 
@@ -480,7 +576,11 @@ def rcfar_sat_cfar(h: int, map_t, value_bound: float, window: rcfar_window, cut_
                    thr=None, map_cut: bool = True, map_exp2: int = 0, stream=None):
     """Fused SAT + CFAR (no table in device memory); same decisions as rcfar_sat + rcfar_cfar."""
     import torch
+    _require(map_t, "map", _f32_f16())
     rows, cols = int(map_t.shape[0]), int(map_t.shape[1])
+    _require(det, "det", _u8(), rows, cols)
+    if thr is not None:
+        _require(thr, "thr", _f32(), rows, cols)
     dtype = RCFAR_MAP_F16 if map_t.dtype == torch.float16 else RCFAR_MAP_F32
     _check(lib().rcfar_sat_cfar(h, _ptr(map_t), dtype, int(map_exp2), rows, cols, _ld(map_t), float(value_bound),
                                 ctypes.byref(window), int(cut_c_lo), int(cut_c_hi), 1 if map_cut else 0, _ptr(det),

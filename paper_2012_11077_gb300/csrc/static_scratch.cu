@@ -1,12 +1,13 @@
 // rcfar_sat_cfar_static: the summed-area table and the SAT CA-CFAR of one map
 // with no device allocation at all.
 //
-// Some callers cannot call cudaMalloc (or any allocating routine): code that
-// records its work into a CUDA graph whose capture forbids allocation,
-// real-time loops whose memory was fixed at start-up and must not touch the
-// allocator (an allocation can synchronise the device and stall the loop),
-// and embedded hosts that run the library without a memory manager. They
-// cannot create a handle, because rcfar_create allocates its workspace.
+// Some callers cannot call cudaMalloc (or any allocating routine): real-time
+// radar loops whose device memory was fixed at start-up and must not touch
+// the allocator (an allocation can synchronise the device and stall the
+// loop), and hosts whose device memory is owned by another memory manager
+// (a framework's caching pool, an embedded runtime) that the library must
+// not bypass. They cannot create a handle, because rcfar_create allocates
+// its workspace.
 //
 // This entry point takes no handle. Its scratch -- the exact 64-bit
 // tile-local table, the tile row/column totals and the carries of the table
@@ -38,6 +39,8 @@ namespace {
 
 constexpr size_t kStaticScratchBytes = 16u << 20;  // 16 MiB
 constexpr int kMaxDevices = 64;
+constexpr long long kMaxStaticHalfRows = 1024;  // guard_r + train_r
+constexpr long long kMaxStaticHalfCols = 119;   // guard_c + train_c: 16 + 2 * 119 + 1 <= 256
 
 static __device__ __align__(256) unsigned char g_static_scratch[kStaticScratchBytes];
 
@@ -74,7 +77,12 @@ extern "C" rcfar_status rcfar_sat_cfar_static(const float* map, int32_t rows, in
   if (!(value_bound > 0.0f) || !std::isfinite(value_bound)) return RCFAR_ERR_INVALID_ARG;
   if (w->train_r < 0 || w->train_c < 0 || w->guard_r < 0 || w->guard_c < 0 || !(w->pfa > 0.0 && w->pfa < 1.0))
     return RCFAR_ERR_INVALID_ARG;
-  const int wr = w->guard_r + w->train_r, wc = w->guard_c + w->train_c;
+  // half-widths in 64 bits: guard + train of two large int32 counts overflows int;
+  // beyond these limits the CFAR's ring of table rows (kMaxStaticHalfRows) or its
+  // 256-column strip (kMaxStaticHalfCols) cannot hold the window
+  const long long wr64 = (long long)w->guard_r + w->train_r, wc64 = (long long)w->guard_c + w->train_c;
+  if (wr64 > kMaxStaticHalfRows || wc64 > kMaxStaticHalfCols) return RCFAR_ERR_UNSUPPORTED;
+  const int wr = (int)wr64, wc = (int)wc64;
   const long long n_ref = (2LL * wr + 1) * (2LL * wc + 1) - (2LL * w->guard_r + 1) * (2LL * w->guard_c + 1);
   double kfac = 0.0;
   if (n_ref <= 0 || !window_factor(*w, &kfac, nullptr)) return RCFAR_ERR_INVALID_ARG;

@@ -185,3 +185,18 @@ def test_binding_structs_match_the_header(rc, tmp_path):
         assert got[(n, "size")] == ctypes.sizeof(cls), n
         for f, _ in cls._fields_:
             assert got[(n, f)] == getattr(cls, f).offset, (n, f)
+
+
+def test_static_entry_rejects_huge_windows_before_any_device_work(rc):
+    # guard + train beyond what the CFAR's ring and strip can hold, including
+    # half-widths whose int32 sum overflows, is refused on the host before any
+    # CUDA call (the pointers below are never dereferenced)
+    import ctypes
+    L = rc.lib()
+    fake = ctypes.c_void_p(16)
+    for tr_r, tr_c, gd_r, gd_c in [(600_000_000, 0, 0, 0), (2**31 - 1, 1, 1, 1), (1, 2**31 - 1, 1, 1),
+                                   (1025, 0, 0, 0), (0, 120, 0, 0), (0, 100, 0, 20)]:
+        w = rc.make_window(tr_r, tr_c, gd_r, gd_c, 1e-3)
+        st = L.rcfar_sat_cfar_static(fake, 64, 64, 64, ctypes.c_float(1.0), ctypes.byref(w), 0, 63, fake, 64,
+                                     None, 0, None, None)
+        assert st == rc.RCFAR_ERR_UNSUPPORTED, (tr_r, tr_c, gd_r, gd_c, st)
