@@ -380,15 +380,17 @@ rcfar_status rcfar_get_batch_tuning(rcfar_handle h, rcfar_batch_tuning* out);
 
 /* SAT (exact TILE_I64 table) and SAT CA-CFAR of one float32 map, like
  * rcfar_sat + rcfar_cfar, for callers that cannot allocate device memory:
- * code that records into a CUDA graph whose capture forbids allocation,
  * real-time loops whose memory is fixed at start-up (an allocation may
- * synchronise the device), hosts without a memory manager. The paper has no
- * counterpart; this is a deployment variant of the same computation.
+ * synchronise the device and stall the loop), and hosts whose device memory
+ * belongs to another memory manager that the library must not bypass. The
+ * paper has no counterpart; this is a deployment variant of the same
+ * computation.
  * No handle and no allocation: the scratch (table and carries) is one
  * 16 MiB array in the library's device memory, held by every GPU that loads
  * the library until exit. Maps whose table does not fit (about 1.9 million
  * cells, e.g. 1024 x 1800) return RCFAR_ERR_UNSUPPORTED, as do windows whose
- * halo does not fit in shared memory. value_bound must be > 0 (an upper
+ * halo does not fit in shared memory (guard_r + train_r > 1024,
+ * guard_c + train_c > 119, or a ring too large for the device). value_bound must be > 0 (an upper
  * bound on |value|). status (optional device int32) is zeroed and then set to
  * a non-zero value if a map value exceeds value_bound or is NaN (results
  * invalid). The first call on a device looks up the array's device address
@@ -403,17 +405,21 @@ rcfar_status rcfar_sat_cfar_static(const float* map, int32_t rows, int32_t cols,
 /* ---- serving: continuous batching of frames from many sources ---------- */
 
 /* A request loop in the library: frames from many sources (drones) are
- * submitted from HOST memory at any time; a scheduler thread admits them, in
- * arrival order, into batches that fit the device-memory budget and runs up
- * to `slots` batches at once, each on its own stream (copies in, the
- * rcfar_run_batch chain, decisions out), so the work of requests that arrive
- * while others are on the GPU overlaps theirs; a completion thread returns the
- * decisions to the caller's host buffers with timestamps. Each frame's
- * decisions are identical to those of the frame run alone (rcfar_run_batch
- * results do not depend on the rest of the batch). The paper processes one
- * frame at a time (Sec. III); this is the deployment form for many radars.
- * Twiddle tables are kept on the device per (N, band) once built. The
- * server's threads call only the library; the server is thread-safe. */
+ * submitted at any time, each from HOST memory or already in DEVICE memory;
+ * a scheduler thread admits them, in arrival order, into batches that fit the
+ * device-memory budget and runs up to `slots` batches at once, each on its
+ * own stream (host frames: copies in, the rcfar_run_batch chain, decisions
+ * out; device frames: the chain reads the frame where it lies and writes the
+ * decisions to the caller's device buffer), so the work of requests that
+ * arrive while others are on the GPU overlaps theirs; a completion thread
+ * publishes each frame's completion with timestamps (and copies host
+ * frames' decisions to the caller's host buffers). Each frame's decisions are
+ * identical to those of the frame run alone (rcfar_run_batch results do not
+ * depend on the rest of the batch), whichever memory it came from. The paper
+ * processes one frame at a time (Sec. III); this is the deployment form for
+ * many radars. Twiddle tables are kept on the device per (N, band) once
+ * built. The server's threads call only the library; the server is
+ * thread-safe. */
 typedef struct rcfar_server_s* rcfar_server;
 
 typedef struct rcfar_server_config {
@@ -428,16 +434,26 @@ typedef struct rcfar_server_config {
   rcfar_pre_params params;   /* fs, band, mean filter; halo_c must be -1 (each frame its own window) */
 } rcfar_server_config;
 
+/* Where a request's frame and decisions live. */
+typedef enum rcfar_memory { RCFAR_MEM_HOST = 0, RCFAR_MEM_DEVICE = 1 } rcfar_memory;
+
 typedef struct rcfar_request {
-  const float* x;          /* HOST raw frame, M rows of ldx floats (pinned memory: asynchronous copy) */
+  const float* x;          /* raw frame, M rows of ldx floats (or N rows of M for trace-major frames).
+                              RCFAR_MEM_HOST: host memory (pinned memory: asynchronous copy);
+                              RCFAR_MEM_DEVICE: device memory of the server's device, read in place by
+                              the chain; the work that wrote it must be complete at submission */
   int32_t M, N;
   int64_t ldx;
   rcfar_window window;
-  uint8_t* det;            /* HOST output M x C, C = rcfar_band_plan(N, params with halo_c = the
-                              window's guard_c + train_c).cols; written before the completion appears */
+  uint8_t* det;            /* output M x C, C = rcfar_band_plan(N, params with halo_c = the window's
+                              guard_c + train_c).cols, in the same memory as x; written before the
+                              completion appears (device: by the server's stream, complete when the
+                              completion is polled) */
   int64_t ld_det;
   int64_t tag;             /* caller's identifier, returned with the completion */
   int64_t arrival_ns;      /* arrival time on rcfar_server_now_ns's clock; 0 = at submission */
+  int32_t memory;          /* rcfar_memory of x and det (0: host) */
+  int32_t pad;
 } rcfar_request;
 
 typedef struct rcfar_completion {
@@ -460,9 +476,12 @@ typedef struct rcfar_server_stats {
  * INVALID_ARG for a bad configuration, CUDA if allocation fails. */
 rcfar_status rcfar_server_create(const rcfar_server_config* cfg, rcfar_server* out);
 /* Queues one frame (the request is copied; x and det must stay valid until
- * its completion is polled). UNSUPPORTED if the frame exceeds the configured
- * maxima or could never fit one slot's share of the budget; INVALID_ARG for
- * bad sizes or window; BAD_STATE after destroy has begun. */
+ * its completion is polled). A device frame takes only its batch workspace
+ * from the slot's budget share (no staging copies). UNSUPPORTED if the frame
+ * exceeds the configured maxima or could never fit one slot's share of the
+ * budget; INVALID_ARG for bad sizes, window or memory kind, or a device
+ * pointer that is not memory of the server's device; BAD_STATE after destroy
+ * has begun. */
 rcfar_status rcfar_server_submit(rcfar_server srv, const rcfar_request* req);
 /* Builds, on every slot, the twiddle tables of frames with these slow-time
  * lengths N[i] and windows w[i] (host arrays of n), so that the first frames

@@ -1,6 +1,9 @@
 // Serving runtime: continuous batching of radar frames from many sources.
 //
-// Frames arrive from host memory at any time (rcfar_server_submit). A
+// Frames arrive at any time (rcfar_server_submit), from host memory or
+// already in device memory (a device frame is read in place and its
+// decisions written to the caller's device buffer: no staging copies, only
+// its batch workspace counts against the budget). A
 // scheduler thread takes them in arrival order into a batch for a free slot
 // while they fit that slot's share of the device-memory budget (workspace of
 // the rcfar_run_batch chain, the raw inputs, the decisions) and enqueues on
@@ -42,8 +45,9 @@ struct Pending {
   rcfar_request r;
   int C = 0;            // stored band columns of the frame's decisions
   size_t ws = 0;        // rcfar_run_batch workspace bytes
-  size_t in_b = 0;      // raw frame bytes on the device (packed rows)
-  size_t det_b = 0;     // decision bytes (packed rows)
+  size_t in_b = 0;      // raw frame bytes on the device (packed rows; 0 for a device frame)
+  size_t det_b = 0;     // decision bytes (packed rows; 0 for a device frame)
+  bool device = false;  // x and det are device memory: no copies
 };
 
 struct Slot {
@@ -88,8 +92,22 @@ void rcfar_server_s::launch(int si) {
   cudaSetDevice(cfg.device);
   rcfar_status st = RCFAR_OK;
   S.descs.resize(n);
+  bool any_host = false;
   for (int i = 0; i < n; ++i) {
     const rcfar_request& r = S.batch[i].r;
+    rcfar_frame_desc& d = S.descs[i];
+    std::memset(&d, 0, sizeof(d));
+    d.M = r.M;
+    d.N = r.N;
+    d.window = r.window;
+    if (S.batch[i].device) {  // read in place, decisions straight to the caller's buffer
+      d.x = r.x;
+      d.ldx = r.ldx;
+      d.det = r.det;
+      d.ld_det = r.ld_det;
+      continue;
+    }
+    any_host = true;
     float* xin = reinterpret_cast<float*>(S.dev_io + S.in_off[i]);
     // packed on the device in the frame's own layout (rows of N, or of M for trace-major frames)
     const bool tm = cfg.params.x_layout == RCFAR_X_TRACE_MAJOR;
@@ -103,20 +121,16 @@ void rcfar_server_s::launch(int si) {
             : cudaMemcpy2DAsync(xin, (size_t)width * sizeof(float), r.x, (size_t)r.ldx * sizeof(float),
                                 (size_t)width * sizeof(float), (size_t)height, cudaMemcpyHostToDevice, S.stream);
     if (ce != cudaSuccess) st = RCFAR_ERR_CUDA;
-    rcfar_frame_desc& d = S.descs[i];
-    std::memset(&d, 0, sizeof(d));
     d.x = xin;
-    d.M = r.M;
-    d.N = r.N;
     d.ldx = width;
-    d.window = r.window;
     d.det = reinterpret_cast<uint8_t*>(S.dev_io + S.in_cap + S.det_off[i]);
     d.ld_det = S.batch[i].C;
   }
   if (st == RCFAR_OK) st = rcfar_run_batch(S.h, S.descs.data(), n, &cfg.params, (rcfar_stream)S.stream);
-  if (st == RCFAR_OK) {
+  if (st == RCFAR_OK && any_host) {
     size_t total = 0;
-    for (int i = 0; i < n; ++i) total = std::max(total, S.det_off[i] + (size_t)S.batch[i].r.M * S.batch[i].C);
+    for (int i = 0; i < n; ++i)
+      if (!S.batch[i].device) total = std::max(total, S.det_off[i] + (size_t)S.batch[i].r.M * S.batch[i].C);
     // decisions are packed back to back: one copy for the batch
     if (cudaMemcpyAsync(S.host_det, S.dev_io + S.in_cap, total, cudaMemcpyDeviceToHost, S.stream) != cudaSuccess)
       st = RCFAR_ERR_CUDA;
@@ -194,7 +208,7 @@ void rcfar_server_s::completer() {
     std::vector<rcfar_completion> out(S.batch.size());
     for (size_t i = 0; i < S.batch.size(); ++i) {
       const Pending& q = S.batch[i];
-      if (st == RCFAR_OK) {
+      if (st == RCFAR_OK && !q.device) {
         const unsigned char* src = S.host_det + S.det_off[i];
         if (q.r.ld_det == q.C) {
           std::memcpy(q.r.det, src, (size_t)q.r.M * q.C);
@@ -300,8 +314,21 @@ rcfar_status rcfar_server_submit(rcfar_server srv, const rcfar_request* req) {
   if (!srv || !req) return RCFAR_ERR_INVALID_ARG;
   const rcfar_request& r = *req;
   const bool tm = srv->cfg.params.x_layout == RCFAR_X_TRACE_MAJOR;
-  if (!r.x || !r.det || r.M <= 0 || r.N <= 0 || r.ldx < (tm ? r.M : r.N) || srv->cfg.params.mean_len > r.N)
+  if (!r.x || !r.det || r.M <= 0 || r.N <= 0 || r.ldx < (tm ? r.M : r.N) || srv->cfg.params.mean_len > r.N ||
+      (r.memory != RCFAR_MEM_HOST && r.memory != RCFAR_MEM_DEVICE))
     return RCFAR_ERR_INVALID_ARG;
+  const bool device = r.memory == RCFAR_MEM_DEVICE;
+  if (device) {  // both buffers must be memory the server's device can address as its own
+    for (const void* p : {static_cast<const void*>(r.x), static_cast<const void*>(r.det)}) {
+      cudaPointerAttributes a;
+      if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return RCFAR_ERR_INVALID_ARG;
+      }
+      if ((a.type != cudaMemoryTypeDevice && a.type != cudaMemoryTypeManaged) || a.device != srv->cfg.device)
+        return RCFAR_ERR_INVALID_ARG;
+    }
+  }
   const rcfar_window& w = r.window;
   double factor = 0.0;
   if (rcfar_threshold_factor(&w, &factor, nullptr) != RCFAR_OK) return RCFAR_ERR_INVALID_ARG;
@@ -321,8 +348,9 @@ rcfar_status rcfar_server_submit(rcfar_server srv, const rcfar_request* req) {
   st = rcfar_batch_bytes(r.M, r.N, &srv->cfg.params, &w, &ws);
   if (st != RCFAR_OK) return st;
   q.ws = (size_t)ws;
-  q.in_b = a256((size_t)r.M * r.N * sizeof(float));
-  q.det_b = a256((size_t)r.M * q.C);
+  q.device = device;
+  q.in_b = device ? 0 : a256((size_t)r.M * r.N * sizeof(float));
+  q.det_b = device ? 0 : a256((size_t)r.M * q.C);
   const Slot& S0 = srv->slots[0];
   if (q.ws > S0.ws_cap || q.in_b > S0.in_cap || q.det_b > S0.det_cap) return RCFAR_ERR_UNSUPPORTED;
   if (q.r.arrival_ns == 0) q.r.arrival_ns = clock_ns();

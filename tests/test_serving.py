@@ -44,13 +44,24 @@ def win_of(rc, w):
     return rc.make_window(w.train_r, w.train_c, w.guard_r, w.guard_c, w.pfa)
 
 
-def run_stream(rc, srv, arrivals, drones, variants, pool, C_of, rate_scale=1.0):
-    """Submit the stream at its arrival times (scaled); returns completions and det buffers."""
+def run_stream(rc, srv, arrivals, drones, variants, pool, C_of, rate_scale=1.0, memory="host"):
+    """Submit the stream at its arrival times (scaled); returns completions and det buffers.
+    memory: "host" (pinned host frames and decisions), "device" (frames already in device
+    memory, decisions written there) or "mixed" (alternating)."""
     t0 = rc.rcfar_server_now_ns()
     dets, done = {}, {}
+    on_dev = {}
     for i, (ta, d, v) in enumerate(zip(arrivals, drones, variants)):
         x, w = pool[(int(d), int(v))]
-        det = torch.full((x.shape[0], C_of[int(d)]), 7, dtype=torch.uint8).pin_memory()
+        dev = memory == "device" or (memory == "mixed" and i % 2 == 1)
+        if dev:
+            if (int(d), int(v)) not in on_dev:
+                on_dev[(int(d), int(v))] = x.cuda()
+            x = on_dev[(int(d), int(v))]
+            det = torch.full((x.shape[0], C_of[int(d)]), 7, dtype=torch.uint8, device="cuda")
+            torch.cuda.synchronize()  # the frame and the filled buffer are complete before submission
+        else:
+            det = torch.full((x.shape[0], C_of[int(d)]), 7, dtype=torch.uint8).pin_memory()
         dets[i] = det
         t_arr = t0 + int(ta * rate_scale * 1e9)
         while rc.rcfar_server_now_ns() < t_arr:
@@ -62,10 +73,11 @@ def run_stream(rc, srv, arrivals, drones, variants, pool, C_of, rate_scale=1.0):
     while len(done) < len(arrivals) and time.time() < deadline:
         for c in rc.rcfar_server_poll(srv, 256, 100):
             done[c.tag] = c
-    return done, dets
+    return done, {i: d.cpu() for i, d in dets.items()}
 
 
-def test_serving_each_result_equals_alone(rc):
+@pytest.mark.parametrize("memory", ["host", "device", "mixed"])
+def test_serving_each_result_equals_alone(rc, memory):
     arrivals, drones, variants, cases = synth.serving_stream(
         n_requests=60, n_drones=5, rate_hz=50000.0, seed=11, m_range=(64, 256), n_range=(256, 1024), n_variants=2)
     srv = rc.rcfar_server_create(device=0, budget_bytes=256 << 20, slots=2, max_batch_frames=6, max_rows=256,
@@ -76,7 +88,7 @@ def test_serving_each_result_equals_alone(rc):
         for v, c in enumerate(vs):
             pool[(d, v)] = (torch.from_numpy(synth.radar_frame(c.spec)).pin_memory(), c.window)
     try:
-        done, dets = run_stream(rc, srv, arrivals, drones, variants, pool, C_of)
+        done, dets = run_stream(rc, srv, arrivals, drones, variants, pool, C_of, memory=memory)
         stats = rc.rcfar_server_get_stats(srv)
     finally:
         rc.rcfar_server_destroy(srv)
@@ -113,6 +125,26 @@ def test_serving_each_result_equals_alone(rc):
     res = oracle.cfar_chain(P_o, band_o, w.train_r, w.train_c, w.guard_r, w.guard_c, w.pfa)
     cmp = ocfar.compare_decisions(dets[0].numpy(), res.det, P_o, res.thr, res.cut, margin=MARGIN)
     assert cmp.mismatches == 0, cmp
+
+
+def test_serving_rejects_device_pointers_of_no_device_and_mixed_kinds(rc):
+    srv = rc.rcfar_server_create(device=0, budget_bytes=64 << 20, slots=1, max_batch_frames=4, max_rows=64,
+                                 max_n=512, max_window=8, params=params_of(rc))
+    try:
+        w = rc.make_window(4, 4, 1, 1, 1e-3)
+        x = torch.zeros((64, 512), dtype=torch.float32).pin_memory()
+        C = band_cols(rc, 512, w)
+        det = torch.zeros((64, C), dtype=torch.uint8).pin_memory()
+        # a host buffer declared as device memory is refused by the library itself
+        req = rc.rcfar_request(x.data_ptr(), 64, 512, 512, w, det.data_ptr(), C, 1, 0, rc.RCFAR_MEM_DEVICE, 0)
+        assert rc.lib().rcfar_server_submit(srv, rc.ctypes.byref(req)) == rc.RCFAR_ERR_INVALID_ARG
+        req.memory = 5
+        assert rc.lib().rcfar_server_submit(srv, rc.ctypes.byref(req)) == rc.RCFAR_ERR_INVALID_ARG
+        # a device frame with host decisions is refused by the binding
+        with pytest.raises(ValueError):
+            rc.rcfar_server_submit(srv, x.cuda(), w, det, tag=2)
+    finally:
+        rc.rcfar_server_destroy(srv)
 
 
 def test_serving_admission_limits(rc):
