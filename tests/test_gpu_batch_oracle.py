@@ -1,0 +1,111 @@
+"""The benchmark's 64-frame mixed batch at full size, every frame against the oracle.
+
+64 frames of uneven size (M ~ U{128..1024}, N ~ U{256..4096}) with mixed
+windows (training {4, 8, 16}, guard {1, 2, 4}, Pfa {1e-3, 1e-4, 1e-6}) and
+0-10 targets each -- the batch bench.py times -- go through one
+rcfar_run_batch call; every frame's band map, thresholds and decisions are
+compared with the oracle's whole chain (Sec. II.A preprocessing, eq. 3 table,
+eq. 4 lookups, eq. 2 threshold, eq. 1 decision) run on that frame alone. The
+batch is run again under the other table schedules, which must give the same
+bytes.
+
+Tolerances: decisions exact outside the 1e-5 tie margin (counted); thresholds
+within 1e-4 relative of FP64; band map per element within
+1e-4 max(|o|, 1e-6 max|o| of the frame's map).
+"""
+import numpy as np
+import pytest
+
+import oracle
+from oracle import cfar as ocfar
+import synth
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+REL = 1e-4
+MARGIN = 1e-5
+
+
+@pytest.fixture(scope="module")
+def rc():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2012_11077_gb300 import build as b
+    b.build()
+    import paper_2012_11077_gb300 as pkg
+    pkg.lib()
+    return pkg
+
+
+def map_rel_err(g, o):
+    """|g - o| / max(|o|, 1e-6 max|o|): relative error, floored for cells a
+    million times below the map's largest value."""
+    o = np.asarray(o, dtype=np.float64)
+    floor = 1e-6 * np.max(np.abs(o)) if o.size else 0.0
+    return np.abs(np.asarray(g, dtype=np.float64) - o) / np.maximum(np.abs(o), max(floor, 1e-300))
+
+
+def test_mixed_batch_64_full_size_against_oracle(rc):
+    cases = synth.mixed_batch_cases(64, seed=100)
+    params = rc.make_pre_params(synth.FS_HZ, mean_len=5, halo_c=-1)
+    h = rc.rcfar_create(device=0, max_rows=1024, max_cols=1024, max_n=4096, max_window=32, max_frames=64,
+                        batch_bytes=3 << 30)
+    try:
+        xs, descs, outs, bands = [], [], [], []
+        for c in cases:
+            w = c.window
+            band = rc.rcfar_band_plan(c.spec.N, rc.make_pre_params(synth.FS_HZ, mean_len=5,
+                                                                   halo_c=w.train_c + w.guard_c))
+            x = torch.from_numpy(synth.radar_frame(c.spec)).cuda()
+            det = torch.full((c.spec.M, band.cols), 7, dtype=torch.uint8, device="cuda")
+            thr = torch.full((c.spec.M, band.cols), -1.0, dtype=torch.float32, device="cuda")
+            P = torch.full((c.spec.M, band.cols), -1.0, dtype=torch.float32, device="cuda")
+            win = rc.make_window(w.train_r, w.train_c, w.guard_r, w.guard_c, w.pfa)
+            xs.append(x)
+            outs.append((det, thr, P))
+            bands.append(band)
+            descs.append(rc.frame_desc(x, win, det, thr, P))
+        rc.rcfar_prepare(h, descs, params)
+        rc.rcfar_run_batch(h, descs, params)
+        assert rc.rcfar_get_error(h) == rc.RCFAR_OK
+        worst_map, worst_thr, ties, dets, cuts, over = 0.0, 0.0, 0, 0, 0, 0
+        for i, (c, (det, thr, P), band) in enumerate(zip(cases, outs, bands)):
+            w = c.window
+            X = xs[i].cpu().numpy()
+            P_o, band_o, res_o = oracle.run_chain(X, synth.FS_HZ, 5, w.train_r, w.train_c, w.guard_r, w.guard_c,
+                                                  w.pfa)
+            assert (band.c0, band.cols) == (band_o.c0, band_o.cols)
+            cmp = ocfar.compare_decisions(det.cpu().numpy(), res_o.det, P_o, res_o.thr, res_o.cut, margin=MARGIN)
+            assert cmp.mismatches == 0, (i, c.spec, cmp)
+            ties += cmp.near_ties
+            dets += int(res_o.det.sum())
+            cuts += int(res_o.cut.sum())
+            t = thr.cpu().numpy().astype(np.float64)
+            if res_o.cut.any():
+                rel = np.abs(t[res_o.cut] - res_o.thr[res_o.cut]) / np.abs(res_o.thr[res_o.cut])
+                worst_thr = max(worst_thr, float(rel.max()))
+            assert np.all(t[~res_o.cut] == 0.0)
+            e = map_rel_err(P.cpu().numpy(), P_o)
+            worst_map = max(worst_map, float(e.max()))
+            over += int((e > REL).sum())
+        print(f"64-frame batch: {cuts} CUTs, {dets} oracle detections, {ties} near ties; "
+              f"threshold max rel err {worst_thr:.2e}; band map max rel err {worst_map:.2e} "
+              f"({over} cells above 1e-4)")
+        assert worst_thr <= REL
+        assert worst_map <= REL, (worst_map, over)
+        # the other table schedules give the same bytes
+        ref = [tuple(t.clone() for t in o) for o in outs]
+        for mode in (rc.RCFAR_SAT_FUSED, rc.RCFAR_SAT_I64, rc.RCFAR_SAT_TILE_I64):
+            rc.rcfar_set_batch_tuning(h, rc.make_batch_tuning(0, mode))
+            for o in outs:
+                for t in o:
+                    t.fill_(7)
+            rc.rcfar_run_batch(h, descs, params)
+            assert rc.rcfar_get_error(h) == rc.RCFAR_OK
+            for o, r in zip(outs, ref):
+                for t, tr in zip(o, r):
+                    assert torch.equal(t, tr), mode
+    finally:
+        rc.rcfar_destroy(h)

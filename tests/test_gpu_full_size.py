@@ -3,11 +3,12 @@
 * The 8192 x 8192 square-law map (200 targets over 80 dB, training 16 / guard 4,
   Pfa 1e-6) through the fused streaming SAT + CFAR call with the CUT value from
   the map, and through the split path (int64 table in device memory, then the
-  table CFAR). The two must agree on every decision; sampled CUTs -- every
-  target cell and its window's corners, the corners and edges of the interior,
-  and a seeded uniform sample -- are checked one by one against the oracle's
-  direct window sums (eq. 4's reference sum written out); every non-interior
-  cell must decide H0.
+  table CFAR). Every one of the 67 million decisions and every CUT's threshold
+  of both paths is compared with the FP64 oracle's SAT CFAR (eq. 3 table, eq. 4
+  lookups; near ties counted); as a second, independent oracle, sampled CUTs --
+  every target cell and its window's corners, the corners and edges of the
+  interior, and a seeded uniform sample -- are checked one by one against the
+  oracle's direct window sums; every non-interior cell must decide H0.
 * The 1024 x 4096 raw frame through the chain exactly as the benchmark runs it
   (rcfar_preprocess, then rcfar_sat_cfar with the CUT value from the table),
   against the oracle's whole chain; and the same frames eight at a time
@@ -81,13 +82,27 @@ def test_map_8192_fused_and_split_sampled_parity(rc):
         bound = float(P.max())
         win = rc.make_window(w.train_r, w.train_c, w.guard_r, w.guard_c, w.pfa)
         det_f = torch.full((R, R), 7, dtype=torch.uint8, device="cuda")
-        thr_f = torch.full((R, R), -1.0, dtype=torch.float32, device="cuda")
+        thr_f = torch.full((R, R), -1.0, dtype=torch.float32, device="cuda")  # written everywhere: 0 off the CUTs
         rc.rcfar_sat_cfar(h, Pt, bound, win, 0, R - 1, det_f, thr_f)
         det_s = torch.full((R, R), 7, dtype=torch.uint8, device="cuda")
+        thr_s = torch.full((R, R), -1.0, dtype=torch.float32, device="cuda")
         view = rc.rcfar_sat(h, Pt, value_bound=bound, mode=rc.RCFAR_SAT_I64)
-        rc.rcfar_cfar(h, view, Pt, win, 0, R - 1, det_s)
+        rc.rcfar_cfar(h, view, Pt, win, 0, R - 1, det_s, thr_s)
         assert rc.rcfar_get_error(h) == rc.RCFAR_OK
         assert torch.equal(det_f, det_s)
+        # every decision and threshold of both paths against the FP64 SAT CFAR
+        o = ocfar.cfar_sat(P, w.train_r, w.train_c, w.guard_r, w.guard_c, w.pfa)
+        for name, d_t, t_t in (("fused", det_f, thr_f), ("split", det_s, thr_s)):
+            cmp = ocfar.compare_decisions(d_t.cpu().numpy(), o.det, P, o.thr, o.cut, margin=MARGIN)
+            print(f"8192^2 {name}: {cmp.compared} cells compared, {cmp.mismatches} mismatches, "
+                  f"{cmp.near_ties} near ties, {int(o.det.sum())} oracle detections")
+            assert cmp.mismatches == 0, (name, cmp)
+            tt = t_t.cpu().numpy()
+            rel = np.abs(tt[o.cut].astype(np.float64) - o.thr[o.cut]) / np.abs(o.thr[o.cut])
+            print(f"8192^2 {name}: threshold max rel err {rel.max():.2e}")
+            assert rel.max() <= REL, (name, rel.max())
+            assert np.all(tt[~o.cut] == 0.0)
+            del tt, rel
         # non-interior cells decide H0 (and no byte is left unwritten)
         assert int(det_f[:wr].sum()) == 0 and int(det_f[R - wr:].sum()) == 0
         assert int(det_f[:, :wc].sum()) == 0 and int(det_f[:, R - wc:].sum()) == 0
