@@ -257,6 +257,10 @@ __device__ __forceinline__ void split_f16(float x, __half* h, __half* t) {
 // y pass: one warp per frame row, kYCols samples per CTA column block.
 //   x'[m,n] = x[m,n] - a_n - b_n (m - mbar)       (detrend)
 //   y[m,n]  = mean of x'[m, n-h..n+h] in [0, N)    (mean filter)
+// evaluated as ((x - rho_m) - a_n) - b_n (m - mbar) with one FMA, rho_m the
+// row's mean level, and the mean filter applied to that; y - c_m follows as
+// (y - rho_m) - (c_m - rho_m). In exact arithmetic nothing changes; in FP32
+// the large per-range offsets no longer pass through the roundings.
 // records max |y| and writes y - c_m, where c_m is the row's slow-time mean
 // (a constant only reaches bin 0; removing it keeps the FP32 rounding of the
 // large per-range offsets out of the other bins), scaled per K block of 256
@@ -312,7 +316,13 @@ __global__ void __launch_bounds__(256, 4) k_ysplit(const __grid_constant__ PreBa
       Bv += __shfl_xor_sync(0xffffffffu, Bv, o);
     }
     const float dm = (float)m - F.mbar;
-    const float cmv = (rs - A - dm * Bv) / (float)N;
+    // rho: a reference level of the row (its weighted mean of x, near the
+    // row's DC offset). x - rho is formed first, so that the detrend and the
+    // mean filter add numbers of the signal's size rather than of the offset's;
+    // a constant per row only reaches bin 0, where c_m = rho + cmr is added back.
+    const float rho = rs / (float)N;
+    const float cmr = -fmaf(dm, Bv, A) / (float)N;  // c_m - rho
+    const float cmv = rho + cmr;
     if (cbk == 0 && lane == 0) F.rowmean[m] = cmv;
     __half* yh = F.yhi + (long long)m * F.npad;
     __half* yl = F.ylo + (long long)m * F.npad;
@@ -341,11 +351,11 @@ __global__ void __launch_bounds__(256, 4) k_ysplit(const __grid_constant__ PreBa
       for (int u = 0; u < kGL; ++u) {
         const int g = lane + 32 * u;
         if (g < kG) {
-          float4 o;
-          o.x = xq[u].x - sa[u].x - sa[u].y * dm;
-          o.y = xq[u].y - sa[u].z - sa[u].w * dm;
-          o.z = xq[u].z - sb[u].x - sb[u].y * dm;
-          o.w = xq[u].w - sb[u].z - sb[u].w * dm;
+          float4 o;  // x - rho - a_n - b_n (m - mbar)
+          o.x = fmaf(-sa[u].y, dm, (xq[u].x - rho) - sa[u].x);
+          o.y = fmaf(-sa[u].w, dm, (xq[u].y - rho) - sa[u].z);
+          o.z = fmaf(-sb[u].y, dm, (xq[u].z - rho) - sb[u].x);
+          o.w = fmaf(-sb[u].w, dm, (xq[u].w - rho) - sb[u].z);
           *reinterpret_cast<float4*>(&seg[warp][4 * g]) = o;
         }
       }
@@ -370,9 +380,9 @@ __global__ void __launch_bounds__(256, 4) k_ysplit(const __grid_constant__ PreBa
           float acc = 0.f;
 #pragma unroll
           for (int d = 0; d <= 2 * (H >= 0 ? H : 0); ++d) acc += v[kPad - (H >= 0 ? H : 0) + e + d];
-          const float y = acc * inv_full;
-          ymax = fmaxf(ymax, fabsf(y));
-          const float d = y - cmv;
+          const float y = acc * inv_full;  // y - rho
+          ymax = fmaxf(ymax, fabsf(y + rho));
+          const float d = y - cmr;
           sq = fmaf(d, d, sq);
           dv[4 * qq + e] = d;
         }
@@ -393,7 +403,8 @@ __global__ void __launch_bounds__(256, 4) k_ysplit(const __grid_constant__ PreBa
 #pragma unroll
       for (int u = 0; u < kSeg; ++u) {
         const int i = lane + 32 * u;
-        if (i < kYCols + 2 * h) seg[warp][i] = xv[u] - sv[u].x - sv[u].y * dm;
+        const int n = n0 - h + i;  // samples outside the frame stay 0 (the truncated windows skip them)
+        if (i < kYCols + 2 * h) seg[warp][i] = (n >= 0 && n < N) ? fmaf(-sv[u].y, dm, (xv[u] - rho) - sv[u].x) : 0.f;
       }
       __syncwarp();
       const float* sg = &seg[warp][lane];
@@ -412,8 +423,8 @@ __global__ void __launch_bounds__(256, 4) k_ysplit(const __grid_constant__ PreBa
 #pragma unroll
         for (int q = 0; q < kQ; ++q) {
           const float y = window(q) * inv_full;
-          ymax = fmaxf(ymax, fabsf(y));
-          const float d = y - cmv;
+          ymax = fmaxf(ymax, fabsf(y + rho));
+          const float d = y - cmr;
           sq = fmaf(d, d, sq);
           dv[q] = d;
         }
@@ -427,8 +438,8 @@ __global__ void __launch_bounds__(256, 4) k_ysplit(const __grid_constant__ PreBa
             const int cnt = min(n + h, N - 1) - max(n - h, 0) + 1;
             // a full window multiplies by 1 / (2h + 1); the truncated ones at the ends divide
             const float y = cnt == 2 * h + 1 ? acc * inv_full : acc / (float)cnt;
-            ymax = fmaxf(ymax, fabsf(y));
-            const float d = y - cmv;
+            ymax = fmaxf(ymax, fabsf(y + rho));
+            const float d = y - cmr;
             sq = fmaf(d, d, sq);
             dv[q] = d;
           }
