@@ -49,14 +49,14 @@ EncodeTiledFn encode_tiled() {
   return fn;
 }
 
-// Tensor map of two planes [2][rows][npad] FP16 (plane stride rows * npad):
-// boxes of kDftBK samples (128 bytes) x box_rows rows x 1 plane, 128-byte
-// swizzle, rows past the end read as zeros.
-bool make_planes_map(CUtensorMap* out, const __half* base, long long rows, int npad, int box_rows) {
+// Tensor map of nplanes planes [nplanes][rows][npad] FP16 (plane stride rows
+// * npad): boxes of kDftBK samples (128 bytes) x box_rows rows x 1 plane,
+// 128-byte swizzle, rows past the end read as zeros.
+bool make_planes_map(CUtensorMap* out, const __half* base, long long rows, int npad, int box_rows, int nplanes) {
   EncodeTiledFn fn = encode_tiled();
   if (!fn || (reinterpret_cast<uintptr_t>(base) & 15) || (npad % kDftBK) || box_rows < 1 || box_rows > 256)
     return false;
-  const cuuint64_t dims[3] = {(cuuint64_t)npad, (cuuint64_t)rows, 2};
+  const cuuint64_t dims[3] = {(cuuint64_t)npad, (cuuint64_t)rows, (cuuint64_t)nplanes};
   const cuuint64_t strides[2] = {(cuuint64_t)npad * sizeof(__half), (cuuint64_t)rows * npad * sizeof(__half)};
   const cuuint32_t box[3] = {(cuuint32_t)kDftBK, (cuuint32_t)box_rows, 1};
   const cuuint32_t elem[3] = {1, 1, 1};
@@ -90,7 +90,7 @@ struct PreGeom {
   long long ldk, ldw;
 };
 
-// band DFT column tiling: ntiles tiles of bn real outputs (bn a multiple of 16, <= 256)
+// band DFT column tiling: ntiles tiles of bn real outputs (bn a multiple of 16, <= kDftMaxBN)
 inline void dft_cols(int C, int* ntiles, int* bn) {
   const long long twoC = 2LL * C;
   *ntiles = (int)ceil_div(twoC, kDftMaxBN);
@@ -235,7 +235,7 @@ struct rcfar_ctx {
   unsigned* ymax = nullptr;
   // per-step preprocessing
   float2* stats = nullptr;
-  float2* partial = nullptr;
+  float4* partial = nullptr;
   float* rowpart = nullptr;
   float2* strip_ab = nullptr;
   unsigned* strip_cnt = nullptr;
@@ -243,8 +243,7 @@ struct rcfar_ctx {
   float* kpart = nullptr;
   size_t kpart_floats = 0;
   void* kpart_own = nullptr;  // separately allocated K-block partials (grown on demand)
-  __half* yhi = nullptr;
-  __half* ylo = nullptr;
+  __half* yq = nullptr;  // the y planes (kDftYPlanes x the largest frame)
   float* yscale = nullptr;
   float* rowmean = nullptr;
   float* rowsq = nullptr;
@@ -517,7 +516,7 @@ static rcfar_status get_plan(rcfar_ctx* h, int N, int c0, int C, cudaStream_t s,
   dft_cols(C, &ntiles, &bn);
   t.ldw = (long long)ntiles * bn;
   const int npad = (int)round_up(N, kDftBK);
-  const size_t bytes = 2 * (size_t)t.ldw * npad * sizeof(__half);  // head and tail planes
+  const size_t bytes = (size_t)kDftWPlanes * t.ldw * npad * sizeof(__half);  // T0, T1, T2 planes
   if (cudaMalloc(&t.Wt, bytes) != cudaSuccess) return RCFAR_ERR_CUDA;
   cudaError_t e = cudaMemsetAsync(t.Wt, 0, bytes, s);  // padding rows and columns stay zero
   if (e == cudaSuccess) e = launch_twiddles(t.Wt, t.ldw, npad, N, c0, C, s);
@@ -527,7 +526,7 @@ static rcfar_status get_plan(rcfar_ctx* h, int N, int c0, int C, cudaStream_t s,
   }
   t.npad = npad;
   t.bn = bn;
-  t.has_map = make_planes_map(&t.mb, t.Wt, t.ldw, npad, bn);
+  t.has_map = make_planes_map(&t.mb, t.Wt, t.ldw, npad, bn, kDftWPlanes);
   h->plans[key] = t;
   *out = t;
   return RCFAR_OK;
@@ -537,8 +536,7 @@ static rcfar_status get_plan(rcfar_ctx* h, int N, int c0, int C, cudaStream_t s,
 // when a tensor map cannot be made; the cp.async kernel runs instead).
 static bool make_dft_frame(DftBatch& db, int k, const PreFrameDev& F, const Twiddle& tw, const PreGeom& g) {
   if (!tw.has_map || tw.bn != g.bn || tw.npad != g.npad) return false;
-  if (F.ylo != F.yhi + (long long)F.M * g.npad) return false;
-  if (!make_planes_map(&db.ma[k], F.yhi, F.M, g.npad, kDftBM)) return false;
+  if (!make_planes_map(&db.ma[k], F.yq, F.M, g.npad, kDftBM, kDftYPlanes)) return false;
   db.mb[k] = tw.mb;
   DftFrameDev& d = db.f[k];
   d.kpart = F.kpart;
@@ -573,6 +571,7 @@ static PreFrameDev make_pre_frame(const float* x, int M, int N, long long ldx, c
   F.inv_M = (float)(1.0 / (double)M);
   const double D = (double)M * ((double)M * M - 1.0) / 12.0;
   F.inv_D = D > 0 ? (float)(1.0 / D) : 0.0f;
+  F.inv_D64 = D > 0 ? 1.0 / D : 0.0;
   F.Wt = tw.Wt;
   F.ldw = tw.ldw;
   F.npad = g.npad;
@@ -597,11 +596,11 @@ static size_t frame_data_bytes(int M, int N, int C, int x_layout) {
   size_t t = 0;
   if (x_layout == RCFAR_X_TRACE_MAJOR) t += align256((size_t)M * round_up(N, 4) * sizeof(float));  // xt
   t += align256((size_t)N * sizeof(float2));                       // stats
-  t += align256((size_t)g.n_chunks * N * sizeof(float2));          // partial
+  t += align256((size_t)g.n_chunks * N * sizeof(float4));          // partial
   t += align256((size_t)g.n_strips * M * sizeof(float));           // rowpart
   t += align256((size_t)g.n_strips * sizeof(float2));              // strip_ab
   t += align256((size_t)g.nblocks * M * g.ldk * 4);              // K-block partials
-  t += 2 * align256((size_t)M * g.npad * sizeof(__half));          // yhi, ylo
+  t += align256((size_t)kDftYPlanes * M * g.npad * sizeof(__half));  // y planes
   t += align256((size_t)g.nblocks * M * sizeof(float));            // yscale
   t += align256((size_t)M * sizeof(float));                        // rowmean
   t += align256((size_t)g.ycols * M * sizeof(float));              // rowsq
@@ -694,13 +693,13 @@ rcfar_status rcfar_create(const rcfar_config* cfg, rcfar_handle* out) {
   size_t total = 0;
   total += 256;                                   // control words
   total += align256((size_t)Nm * sizeof(float2));  // stats
-  total += align256((size_t)max_chunks * Nm * sizeof(float2));
+  total += align256((size_t)max_chunks * Nm * sizeof(float4));  // column-statistics partials
   total += align256((size_t)max_strips * R * sizeof(float));
   total += align256((size_t)max_strips * sizeof(float2));
   total += align256((size_t)max_strips * 4);
   total += align256((size_t)max_tiles * 4);
   total += align256(kpart * 4);
-  total += 2 * align256((size_t)R * round_up(Nm, kDftBK) * sizeof(__half));  // yhi, ylo
+  total += align256((size_t)kDftYPlanes * R * round_up(Nm, kDftBK) * sizeof(__half));  // y planes
   const size_t nblocks_max = (size_t)ceil_div(round_up(Nm, kDftBK), kDftBlock);
   total += align256(nblocks_max * R * sizeof(float));                     // yscale
   total += align256((size_t)R * sizeof(float));                          // rowmean
@@ -721,15 +720,14 @@ rcfar_status rcfar_create(const rcfar_config* cfg, rcfar_handle* out) {
   h->map_bound = reinterpret_cast<float*>(ctl + 5);
   h->ymax = ctl + 6;
   h->stats = cv.take<float2>(Nm);
-  h->partial = cv.take<float2>((size_t)max_chunks * Nm);
+  h->partial = cv.take<float4>((size_t)max_chunks * Nm);
   h->rowpart = cv.take<float>((size_t)max_strips * R);
   h->strip_ab = cv.take<float2>(max_strips);
   h->strip_cnt = cv.take<unsigned>(max_strips);
   h->tile_cnt = cv.take<unsigned>(max_tiles);
   h->kpart = cv.take<float>(kpart);
   h->kpart_floats = kpart;
-  h->yhi = cv.take<__half>((size_t)R * round_up(Nm, kDftBK));
-  h->ylo = cv.take<__half>((size_t)R * round_up(Nm, kDftBK));
+  h->yq = cv.take<__half>((size_t)kDftYPlanes * R * round_up(Nm, kDftBK));
   h->yscale = cv.take<float>(nblocks_max * R);
   h->rowmean = cv.take<float>(R);
   h->rowsq = cv.take<float>(ycols_max * R);
@@ -873,8 +871,7 @@ rcfar_status rcfar_preprocess(rcfar_handle h, const float* x, int32_t M, int32_t
   F.ld_map = ld_map;
   F.kpart = h->kpart;
   F.tile_cnt = h->tile_cnt;
-  F.yhi = h->yhi;
-  F.ylo = h->yhi + (long long)M * g.npad;  // the two planes back to back (the tail runs into h->ylo's room)
+  F.yq = h->yq;  // the planes back to back, plane stride M * npad
   F.yscale = h->yscale;
   F.rowmean = h->rowmean;
   F.rowsq = h->rowsq;
@@ -1383,12 +1380,11 @@ rcfar_status rcfar_run_batch(rcfar_handle h, const rcfar_frame_desc* frames, int
         it_tr += F.n_tr;
       }
       F.stats = data.take<float2>(f.N);
-      F.partial = data.take<float2>((size_t)g.n_chunks * f.N);
+      F.partial = data.take<float4>((size_t)g.n_chunks * f.N);
       F.rowpart = data.take<float>((size_t)g.n_strips * f.M);
       F.strip_ab = data.take<float2>(g.n_strips);
       F.kpart = data.take<float>((size_t)g.nblocks * f.M * g.ldk);
-      F.yhi = data.take<__half>(2 * (size_t)f.M * g.npad);  // head and tail planes back to back
-      F.ylo = F.yhi ? F.yhi + (long long)f.M * g.npad : nullptr;
+      F.yq = data.take<__half>((size_t)kDftYPlanes * f.M * g.npad);  // the y planes back to back
       F.yscale = data.take<float>((size_t)g.nblocks * f.M);
       F.rowmean = data.take<float>(f.M);
       F.rowsq = data.take<float>((size_t)g.ycols * f.M);
@@ -1406,7 +1402,7 @@ rcfar_status rcfar_run_batch(rcfar_handle h, const rcfar_frame_desc* frames, int
       F.ymax = words;
       F.item_stats = it_stats;
       F.item_dft = it_dft;
-      dft_tma_ok = dft_tma_ok && F.yhi && F.kpart && make_dft_frame(db, k, F, tws[i], g);
+      dft_tma_ok = dft_tma_ok && F.yq && F.kpart && make_dft_frame(db, k, F, tws[i], g);
       F.item_norm = it_norm;
       F.item_y = it_y;
       it_y += g.n_y;
@@ -1414,7 +1410,7 @@ rcfar_status rcfar_run_batch(rcfar_handle h, const rcfar_frame_desc* frames, int
       it_stats += g.n_strips * (int)ceil_div(g.n_chunks, stats_cpc);
       it_dft += g.mtiles * g.ntiles * g.splitk;
       it_norm += g.n_norm;
-      if (!F.stats || !F.partial || !F.rowpart || !F.strip_ab || !F.yhi || !F.ylo || !F.yscale || !F.rowmean ||
+      if (!F.stats || !F.partial || !F.rowpart || !F.strip_ab || !F.yq || !F.yscale || !F.rowmean ||
           !F.rowsq || !F.kpart || !map || !F.strip_cnt || !F.tile_cnt || !words)
         return RCFAR_ERR_OUT_OF_WORKSPACE;
       if (f.window.kind == RCFAR_CFAR_OS) {
@@ -1464,7 +1460,7 @@ rcfar_status rcfar_run_batch(rcfar_handle h, const rcfar_frame_desc* frames, int
       it_tile += sg.n_bands * sg.n_chunks;
       it_band += sg.n_bands;
       it_vscan += (int)ceil_div(C, 32);
-      if (!F.stats || !F.partial || !F.rowpart || !F.strip_ab || !F.yhi || !F.ylo || !F.yscale || !F.rowmean || !F.rowsq ||
+      if (!F.stats || !F.partial || !F.rowpart || !F.strip_ab || !F.yq || !F.yscale || !F.rowmean || !F.rowsq ||
           !F.kpart || !map || !m.table ||
           !sat_ok || !F.strip_cnt || !F.tile_cnt || !words)
         return RCFAR_ERR_OUT_OF_WORKSPACE;

@@ -2,14 +2,17 @@
 //
 //   k_colstats : per trace n, the least-squares line over fast time m
 //                (a_n = mean, b_n = slope about mbar) -- "DC-shift removal and
-//                linear trend subtraction"; also the pieces of each row's
-//                slow-time mean of y (see k_ysplit).
+//                linear trend subtraction" -- from compensated column sums,
+//                so that a_n and b_n are correctly rounded; also the pieces
+//                of each row's slow-time mean of y (see k_ysplit).
 //   k_ysplit   : detrend + slow-time mean filter + max|y|; writes y minus
 //                its row mean, scaled per (row, K block) by a power of two
-//                into the FP16 range and split into FP16 head and tail.
+//                and split into an integer plane and the FP16 head and tail
+//                of the remainder.
 //   k_band_dft : band DFT as a GEMM of y [M x N] with the twiddle matrix
-//                [N x 2C] on the tcgen05 tensor cores (split FP16, three
-//                products, accumulator in tensor memory), then the magnitude;
+//                [N x 2C] on the tcgen05 tensor cores (six FP16 products
+//                per K step into two accumulators in tensor memory, the
+//                integer head x head one exact), then the magnitude;
 //                split-K for small frames. Each row's
 //                mean c_m was removed from y and N c_m is added back to bin
 //                0 only: a constant contributes to no other bin, and removing
@@ -20,7 +23,8 @@
 //   DFT is linear, so this equals transforming y / max|y|.
 //   k_twiddles : twiddle matrix W[n][2j] = cos(2 pi t/N), W[n][2j+1] = -sin,
 //                t = (c0 + j) n mod N, computed once per (N, band) in FP64 and
-//                stored split into FP16 head and tail.
+//                stored x 2^9 as an integer plane and the FP16 head and tail
+//                planes of the remainder.
 #include "rcfar_internal.cuh"
 #include "async_copy.cuh"
 
@@ -100,6 +104,24 @@ __global__ void __launch_bounds__(256) k_transpose(const __grid_constant__ PreBa
   }
 }
 
+// (value, error) pair += a + b, b the exact error of a: the sum's own FP32
+// rounding error is recovered (two_sum, Knuth) and kept in the pair's error.
+// The _rn intrinsics keep each operation a single IEEE add (never fused).
+__device__ __forceinline__ void acc_pair(float2& acc, float a, float b) {
+  const float s = __fadd_rn(acc.x, a);
+  const float bb = __fsub_rn(s, acc.x);
+  const float e = __fadd_rn(__fsub_rn(acc.x, __fsub_rn(s, bb)), __fsub_rn(a, bb));
+  acc.x = s;
+  acc.y = __fadd_rn(acc.y, __fadd_rn(e, b));
+}
+// Pairs (x, y) and (z, w) of t += those of u.
+__device__ __forceinline__ void add_pairs(float4& t, const float4& u) {
+  float2 p = make_float2(t.x, t.y), q = make_float2(t.z, t.w);
+  acc_pair(p, u.x, u.y);
+  acc_pair(q, u.z, u.w);
+  t = make_float4(p.x, p.y, q.x, q.y);
+}
+
 // grid: for every frame, n_strips x n_groups CTAs of 256 threads; a CTA takes
 // chunks_per_cta consecutive chunks of 64 rows (kStatsRowsPerChunk) of one
 // 128-column strip, n_groups = ceil(n_chunks / chunks_per_cta). Per chunk,
@@ -122,7 +144,7 @@ __global__ void __launch_bounds__(256, 4) k_colstats(const __grid_constant__ Pre
   float wj[4];
 #pragma unroll
   for (int k = 0; k < 4; ++k) wj[k] = mean_weight(col0 + k, F.N, F.h);
-  __shared__ float2 red[8][kStatsStrip];
+  __shared__ float4 red[8][kStatsStrip];  // (sum x, its error, sum (m - mbar) x, its error)
   __shared__ bool is_last;
 
   for (int chunk = ch0; chunk < ch1; ++chunk) {
@@ -138,7 +160,15 @@ __global__ void __launch_bounds__(256, 4) k_colstats(const __grid_constant__ Pre
         for (int k = 0; k < 4; ++k) v[i][k] = 0.f;
       }
     }
-    float sx[4] = {0.f, 0.f, 0.f, 0.f}, smx[4] = {0.f, 0.f, 0.f, 0.f};
+    // column sums carried as unevaluated pairs (value, rounding error), so
+    // that a_n and b_n come out correctly rounded: each FP32 add's error is
+    // recovered exactly (two_sum) and each product's by one FMA
+    float2 sx[4], smx[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      sx[k] = make_float2(0.f, 0.f);
+      smx[k] = make_float2(0.f, 0.f);
+    }
     float rs[8];
 #pragma unroll
     for (int i = 0; i < 8; ++i) {
@@ -146,8 +176,9 @@ __global__ void __launch_bounds__(256, 4) k_colstats(const __grid_constant__ Pre
       rs[i] = 0.f;
 #pragma unroll
       for (int k = 0; k < 4; ++k) {
-        sx[k] += v[i][k];
-        smx[k] = fmaf(dm, v[i][k], smx[k]);
+        acc_pair(sx[k], v[i][k], 0.f);
+        const float p = __fmul_rn(dm, v[i][k]);
+        acc_pair(smx[k], p, fmaf(dm, v[i][k], -p));  // the product's exact error
         rs[i] = fmaf(wj[k], v[i][k], rs[i]);
       }
     }
@@ -165,16 +196,13 @@ __global__ void __launch_bounds__(256, 4) k_colstats(const __grid_constant__ Pre
       if (m < F.M) F.rowpart[(long long)strip * F.M + m] = mine;
     }
 #pragma unroll
-    for (int k = 0; k < 4; ++k) red[g][lane * 4 + k] = make_float2(sx[k], smx[k]);
+    for (int k = 0; k < 4; ++k) red[g][lane * 4 + k] = make_float4(sx[k].x, sx[k].y, smx[k].x, smx[k].y);
     __syncthreads();
     if (threadIdx.x < kStatsStrip) {
       const int c = strip * kStatsStrip + threadIdx.x;
-      float2 t = red[0][threadIdx.x];
+      float4 t = red[0][threadIdx.x];
 #pragma unroll
-      for (int gg = 1; gg < 8; ++gg) {
-        t.x += red[gg][threadIdx.x].x;
-        t.y += red[gg][threadIdx.x].y;
-      }
+      for (int gg = 1; gg < 8; ++gg) add_pairs(t, red[gg][threadIdx.x]);
       if (c < F.N) F.partial[(long long)chunk * F.N + c] = t;
     }
     __syncthreads();  // red is rewritten by the next chunk
@@ -194,19 +222,20 @@ __global__ void __launch_bounds__(256, 4) k_colstats(const __grid_constant__ Pre
       const int c = strip * kStatsStrip + threadIdx.x;
       float2 st = make_float2(0.f, 0.f);
       if (c < F.N) {
-        float2 t = make_float2(0.f, 0.f);
+        float4 t = make_float4(0.f, 0.f, 0.f, 0.f);
         for (int cb = 0; cb < F.n_chunks; cb += 8) {  // fixed order: deterministic
-          float2 p[8];
+          float4 p[8];
 #pragma unroll
           for (int u = 0; u < 8; ++u)
-            p[u] = (cb + u < F.n_chunks) ? __ldcg(&F.partial[(long long)(cb + u) * F.N + c]) : make_float2(0.f, 0.f);
+            p[u] = (cb + u < F.n_chunks) ? __ldcg(&F.partial[(long long)(cb + u) * F.N + c])
+                                         : make_float4(0.f, 0.f, 0.f, 0.f);
 #pragma unroll
-          for (int u = 0; u < 8; ++u) {
-            t.x += p[u].x;
-            t.y += p[u].y;
-          }
+          for (int u = 0; u < 8; ++u) add_pairs(t, p[u]);
         }
-        st = make_float2(t.x * F.inv_M, t.y * F.inv_D);
+        // a_n = sum x / M, b_n = sum (m - mbar) x / D, each rounded once to FP32
+        // (one FP64 division per trace)
+        st = make_float2((float)(((double)t.x + (double)t.y) / (double)F.M),
+                         (float)(((double)t.z + (double)t.w) * F.inv_D64));
         F.stats[c] = st;
       }
       // (sum_j w_j a_j, sum_j w_j b_j) over the strip: a fixed shuffle tree per warp of 32
@@ -235,23 +264,27 @@ __global__ void __launch_bounds__(256, 4) k_colstats(const __grid_constant__ Pre
   if (local == 0 && threadIdx.x == 0) *F.ymax = 0u;
 }
 
-// Power-of-two shift s that brings a K block of y into the FP16 range:
-// mx 2^s < 2^14 for the block's largest magnitude mx (0 for an all-zero or
-// non-finite block; |s| <= 100 keeps 2^s and 2^-s normal FP32 numbers).
-__device__ __forceinline__ int fp16_shift(float mx) {
+// Power-of-two shift s of a K block of y: mx 2^s in [64, 128) for the
+// block's largest magnitude mx, so that rint(y 2^s) is an integer of at most
+// 8 bits (0 for an all-zero or non-finite block; |s| <= 100 keeps 2^s and
+// 2^-s normal FP32 numbers).
+__device__ __forceinline__ int y_shift(float mx) {
   if (!(mx > 0.f) || !(mx <= 3.0e38f)) return 0;
   int e;
   frexpf(mx, &e);  // mx = f 2^e, 1/2 <= f < 1
-  return max(-100, min(100, 14 - e));
+  return max(-100, min(100, 7 - e));
 }
 
-// x as an FP16 head plus an FP16 tail (about 22 significant bits together):
-// the head is x rounded to FP16, the tail the rounded remainder (x - head is
-// exact in FP32).
-__device__ __forceinline__ void split_f16(float x, __half* h, __half* t) {
-  const __half hh = __float2half_rn(x);
-  *h = hh;
-  *t = __float2half_rn(x - __half2float(hh));
+// v (|v| < 128) as three FP16 values: the integer q = rint(v) (exact in FP16)
+// and the FP16 head and tail of the remainder v - q (exact in FP32, |.| <= 1/2):
+// about 30 significant bits together.
+__device__ __forceinline__ void split_y3(float v, __half* q, __half* rh, __half* rt) {
+  const float qf = rintf(v);
+  const float r = v - qf;
+  const __half h = __float2half_rn(r);
+  *q = __float2half_rn(qf);
+  *rh = h;
+  *rt = __float2half_rn(r - __half2float(h));
 }
 
 // y pass: one warp per frame row, kYCols samples per CTA column block.
@@ -324,8 +357,8 @@ __global__ void __launch_bounds__(256, 4) k_ysplit(const __grid_constant__ PreBa
     const float cmr = -fmaf(dm, Bv, A) / (float)N;  // c_m - rho
     const float cmv = rho + cmr;
     if (cbk == 0 && lane == 0) F.rowmean[m] = cmv;
-    __half* yh = F.yhi + (long long)m * F.npad;
-    __half* yl = F.ylo + (long long)m * F.npad;
+    const long long yplane = (long long)F.M * F.npad;
+    __half* y0 = F.yq + (long long)m * F.npad;  // Y0; Rh and Rt one and two planes on
     const float inv_full = 1.0f / (float)(2 * h + 1);
     constexpr int kQ = kYCols / 32;
     // dv[k]: y - c_m of the lane's k-th sample (0 past the frame); k < kQ / 2
@@ -447,7 +480,8 @@ __global__ void __launch_bounds__(256, 4) k_ysplit(const __grid_constant__ PreBa
       }
     }
     // the block's two K blocks (q < kQ / 2 and q >= kQ / 2), each scaled by
-    // its own power of two into the FP16 range, split into head and tail
+    // its own power of two so that its largest magnitude lies in [64, 128),
+    // then split into the integer Y0 and the FP16 head and tail of the rest
     float mx0 = 0.f, mx1 = 0.f;
 #pragma unroll
     for (int q = 0; q < kQ; ++q) {
@@ -459,35 +493,36 @@ __global__ void __launch_bounds__(256, 4) k_ysplit(const __grid_constant__ PreBa
       mx0 = fmaxf(mx0, __shfl_xor_sync(0xffffffffu, mx0, o));
       mx1 = fmaxf(mx1, __shfl_xor_sync(0xffffffffu, mx1, o));
     }
-    const int s0 = fp16_shift(mx0), s1 = fp16_shift(mx1);
+    const int s0 = y_shift(mx0), s1 = y_shift(mx1);
     const float f0 = ldexpf(1.0f, s0), f1 = ldexpf(1.0f, s1);
+    auto pack = [](const __half* h) {
+      return make_uint2((unsigned)__half_as_ushort(h[0]) | ((unsigned)__half_as_ushort(h[1]) << 16),
+                        (unsigned)__half_as_ushort(h[2]) | ((unsigned)__half_as_ushort(h[3]) << 16));
+    };
     if (fastv) {
       // four consecutive samples per lane and group: one 8-byte store per plane
 #pragma unroll
       for (int qq = 0; qq < kQ / 4; ++qq) {
         const int n = n0 + 4 * lane + 128 * qq;
         const float f = qq < kQ / 8 ? f0 : f1;
-        __half hh[4], tt[4];
+        __half a[4], b[4], c[4];
 #pragma unroll
-        for (int e = 0; e < 4; ++e) split_f16(dv[4 * qq + e] * f, &hh[e], &tt[e]);
-        *reinterpret_cast<uint2*>(yh + n) = make_uint2(
-            (unsigned)__half_as_ushort(hh[0]) | ((unsigned)__half_as_ushort(hh[1]) << 16),
-            (unsigned)__half_as_ushort(hh[2]) | ((unsigned)__half_as_ushort(hh[3]) << 16));
-        *reinterpret_cast<uint2*>(yl + n) = make_uint2(
-            (unsigned)__half_as_ushort(tt[0]) | ((unsigned)__half_as_ushort(tt[1]) << 16),
-            (unsigned)__half_as_ushort(tt[2]) | ((unsigned)__half_as_ushort(tt[3]) << 16));
+        for (int e = 0; e < 4; ++e) split_y3(dv[4 * qq + e] * f, &a[e], &b[e], &c[e]);
+        *reinterpret_cast<uint2*>(y0 + n) = pack(a);
+        *reinterpret_cast<uint2*>(y0 + yplane + n) = pack(b);
+        *reinterpret_cast<uint2*>(y0 + 2 * yplane + n) = pack(c);
       }
     } else {
 #pragma unroll
       for (int q = 0; q < kQ; ++q) {
         const int n = n0 + lane + 32 * q;
-        if (n < F.npad) split_f16(dv[q] * (q < kQ / 2 ? f0 : f1), &yh[n], &yl[n]);
+        if (n < F.npad) split_y3(dv[q] * (q < kQ / 2 ? f0 : f1), &y0[n], &y0[yplane + n], &y0[2 * yplane + n]);
       }
     }
-    if (lane == 0) {
+    if (lane == 0) {  // the drain multiplies each partial by 2^-s 2^-kDftTBits (exact)
       const int blk = 2 * cbk;
-      if (blk < F.nblocks) F.yscale[(long long)blk * F.M + m] = ldexpf(1.0f, -s0);
-      if (blk + 1 < F.nblocks) F.yscale[(long long)(blk + 1) * F.M + m] = ldexpf(1.0f, -s1);
+      if (blk < F.nblocks) F.yscale[(long long)blk * F.M + m] = ldexpf(1.0f, -s0 - kDftTBits);
+      if (blk + 1 < F.nblocks) F.yscale[(long long)(blk + 1) * F.M + m] = ldexpf(1.0f, -s1 - kDftTBits);
     }
     if (F.normalise == RCFAR_NORM_ROW_ZSCORE) {
 #pragma unroll
@@ -526,20 +561,71 @@ __device__ __forceinline__ void umma_commit(unsigned bar) {
   asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
 }
 
-// Band DFT as a GEMM on the 5th-generation tensor cores: (yhi + ylo) [M x npad]
-// times (Whi + Wlo)^T [npad x ldw] in FP16, three products per K step
-// (tail*head + head*tail + head*head, about 22 bits per product). One CTA per
-// (128-row tile, bn-column tile, K split), 12 warps:
+// The six products of one K step (64 samples: four MMAs of 16 along K
+// each): ACC_A += Y0 T0 (integers: exact), ACC_B += Y0 T1 + Y0 T2 + Rh T0 +
+// Rh T1 + Rt T0. sa: the stage's Y0 plane (Rh, Rt follow kDftBM * 128 bytes
+// apart); sb: its T0 plane (T1, T2 follow bn * 128 bytes apart). first: the
+// block's first K step (the accumulators start from zero).
+__device__ __forceinline__ void dft_step_mmas(unsigned dA, unsigned dB, unsigned sa, unsigned sb, int bn,
+                                              unsigned idesc, bool first) {
+  const unsigned pa = kDftBM * 128, pb = (unsigned)bn * 128;
+#pragma unroll
+  for (int kk = 0; kk < kDftBK / 16; ++kk) {
+    const unsigned off = kk * 32;  // 16 FP16 values along K
+    const unsigned long long a0 = umma_desc(sa + off), a1 = umma_desc(sa + pa + off), a2 = umma_desc(sa + 2 * pa + off);
+    const unsigned long long b0 = umma_desc(sb + off), b1 = umma_desc(sb + pb + off), b2 = umma_desc(sb + 2 * pb + off);
+    const unsigned en = (!first || kk > 0) ? 1u : 0u;
+    umma_f16(dA, a0, b0, idesc, en);
+    umma_f16(dB, a0, b2, idesc, en);
+    umma_f16(dB, a0, b1, idesc, 1u);
+    umma_f16(dB, a1, b0, idesc, 1u);
+    umma_f16(dB, a1, b1, idesc, 1u);
+    umma_f16(dB, a2, b0, idesc, 1u);
+  }
+}
+
+// Drain one accumulator buffer (ACC_A at TMEM column ca, ACC_B at ca + bn)
+// for the warp's 32 TMEM lanes (quarter q of the tile) into a block's
+// partials: dst[c] = (ACC_A + ACC_B) * f, one rounding (f = 2^-s 2^-9, exact).
+__device__ __forceinline__ void dft_drain(unsigned tmem, int q, unsigned ca, int bn, float* dst, float f, bool ok) {
+  for (int c = 0; c < bn; c += 8) {
+    unsigned ra[8], rb[8];
+    const unsigned ta = tmem + ((unsigned)(32 * q) << 16) + ca + (unsigned)c;
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                 : "=r"(ra[0]), "=r"(ra[1]), "=r"(ra[2]), "=r"(ra[3]), "=r"(ra[4]), "=r"(ra[5]), "=r"(ra[6]),
+                   "=r"(ra[7])
+                 : "r"(ta));
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                 : "=r"(rb[0]), "=r"(rb[1]), "=r"(rb[2]), "=r"(rb[3]), "=r"(rb[4]), "=r"(rb[5]), "=r"(rb[6]),
+                   "=r"(rb[7])
+                 : "r"(ta + (unsigned)bn));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+    if (ok) {
+      float v[8];
+#pragma unroll
+      for (int k = 0; k < 8; ++k) v[k] = (__uint_as_float(ra[k]) + __uint_as_float(rb[k])) * f;
+      float4* d4 = reinterpret_cast<float4*>(dst + c);
+      d4[0] = make_float4(v[0], v[1], v[2], v[3]);
+      d4[1] = make_float4(v[4], v[5], v[6], v[7]);
+    }
+  }
+}
+
+// Band DFT as a GEMM on the 5th-generation tensor cores: y [M x npad] (three
+// FP16 planes Y0, Rh, Rt) times W^T [npad x ldw] (three planes T0, T1, T2),
+// six products per K step into two accumulators (dft_step_mmas; the integer
+// head x head product accumulates exactly). One CTA per (128-row tile,
+// bn-column tile, K split), 12 warps:
 //   warp 0     issues the MMAs (one thread) into tensor memory;
 //   warps 1-7  stage K steps of 64 samples with cp.async into a ring of
 //              stages in the 128-byte-swizzled K-major layout the MMA reads;
-//   warps 8-11 drain the accumulator every kDftKB K steps (a K block of 256
+//   warps 8-11 drain the accumulators every kDftKB K steps (a K block of 256
 //              samples) into that block's partial sums in global memory.
-// Two accumulators alternate, so the MMAs of block b+1 run while block b is
-// drained. k_dft_reduce adds the blocks' partials in a fixed order with
-// Kahan compensation. Every wait is bounded: a timeout records
-// kStatusTimeout and the CTA still drains its MMAs, frees its tensor memory
-// and returns.
+// When two accumulator buffers fit tensor memory they alternate, so the MMAs
+// of block b+1 run while block b is drained. k_dft_reduce adds the blocks'
+// partials in a fixed order with Kahan compensation. Every wait is bounded:
+// a timeout records kStatusTimeout and the CTA still drains its MMAs, frees
+// its tensor memory and returns.
 __global__ void __launch_bounds__(kDftThreads, 1) k_band_dft(const __grid_constant__ PreBatch b) {
   pdl_trigger();
   pdl_wait();
@@ -570,8 +656,9 @@ __global__ void __launch_bounds__(kDftThreads, 1) k_band_dft(const __grid_consta
   __shared__ int s_fail;
 
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int nbuf = dft_acc_buffers(bn);  // buffers of (ACC_A, ACC_B), 2 bn columns each
   unsigned tcols = 32;
-  while ((int)tcols < 2 * bn) tcols <<= 1;
+  while ((int)tcols < 2 * bn * nbuf) tcols <<= 1;
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_slot)),
                  "r"(tcols));
@@ -602,9 +689,10 @@ __global__ void __launch_bounds__(kDftThreads, 1) k_band_dft(const __grid_consta
     if (lane == 0) {
       for (int i = 0; i < nk; ++i) {
         const int slot = i % stages;
-        const int bi = i / kDftKB, acc = bi & 1;
+        const int bi = i / kDftKB, acc = bi % nbuf;
         const bool first = (i % kDftKB) == 0;
-        if (first && bi >= 2 && !mbar_wait(smem_u32(&bar_acce[acc]), (unsigned)(((bi - 2) >> 1) & 1))) {
+        if (first && bi >= nbuf &&
+            !mbar_wait(smem_u32(&bar_acce[acc]), (unsigned)(((bi - nbuf) / nbuf) & 1))) {
           s_fail = 1;
           break;
         }
@@ -613,54 +701,44 @@ __global__ void __launch_bounds__(kDftThreads, 1) k_band_dft(const __grid_consta
           break;
         }
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        unsigned char* st = base + slot * stage_bytes;
-        const unsigned sa_hi = smem_u32(st), sa_lo = sa_hi + kDftBM * 128;
-        const unsigned sb_hi = sa_lo + kDftBM * 128, sb_lo = sb_hi + bn * 128;
-        const unsigned dacc = tmem + (unsigned)(acc * bn);
-#pragma unroll
-        for (int kk = 0; kk < kDftBK / 16; ++kk) {
-          const unsigned off = kk * 32;  // 16 FP16 values along K
-          const unsigned long long ah = umma_desc(sa_hi + off), al = umma_desc(sa_lo + off);
-          const unsigned long long bh = umma_desc(sb_hi + off), bl = umma_desc(sb_lo + off);
-          umma_f16(dacc, al, bh, idesc, (!first || kk > 0) ? 1u : 0u);
-          umma_f16(dacc, ah, bl, idesc, 1u);
-          umma_f16(dacc, ah, bh, idesc, 1u);
-        }
+        const unsigned sa = smem_u32(base + slot * stage_bytes);
+        const unsigned dA = tmem + (unsigned)(acc * 2 * bn);
+        dft_step_mmas(dA, dA + (unsigned)bn, sa, sa + kDftYPlanes * kDftBM * 128, bn, idesc, first);
         umma_commit(smem_u32(&bar_empty[slot]));  // the slot is free once these MMAs finish
         if ((i % kDftKB) == kDftKB - 1 || i == nk - 1) umma_commit(smem_u32(&bar_accf[acc]));  // block done
       }
       umma_commit(smem_u32(&bar_done));  // tracks every MMA issued above
     }
   } else if (warp < 8) {
-    // producers: stage i -> ring slot i % stages: A head | A tail | B head | B tail
+    // producers: stage i -> ring slot i % stages: Y0 | Rh | Rt | T0 | T1 | T2
     const int ptid = tid - 32;
     const long long plane = F.ldw * F.npad;
+    const long long yplane = (long long)F.M * F.npad;
     for (int i = 0; i < nk; ++i) {
       const int slot = i % stages;
       if (i >= stages && !mbar_wait(smem_u32(&bar_empty[slot]), (unsigned)(((i - stages) / stages) & 1))) {
         s_fail = 1;
         break;
       }
-      unsigned char* st = base + slot * stage_bytes;
-      const unsigned sa_hi = smem_u32(st), sa_lo = sa_hi + kDftBM * 128;
-      const unsigned sb_hi = sa_lo + kDftBM * 128, sb_lo = sb_hi + bn * 128;
+      const unsigned sa = smem_u32(base + slot * stage_bytes);
+      const unsigned sb0 = sa + kDftYPlanes * kDftBM * 128;
       const int k0 = kbeg + i * kDftBK;
-      for (int id = ptid; id < kDftBM * 8; id += 224) {  // A: 128 rows x 8 chunks of 16 bytes
+      for (int id = ptid; id < kDftBM * 8; id += 224) {  // y: 128 rows x 8 chunks of 16 bytes, each plane
         const int rr = id >> 3, c = id & 7;
         const int m = m0 + rr;
         const bool ok = m < F.M;
         const long long off = (long long)(ok ? m : 0) * F.npad + k0 + 8 * c;
         const unsigned sw = rr * 128 + ((c ^ (rr & 7)) << 4);
-        cp_async16(sa_hi + sw, F.yhi + off, ok);
-        cp_async16(sa_lo + sw, F.ylo + off, ok);
+#pragma unroll
+        for (int pl = 0; pl < kDftYPlanes; ++pl) cp_async16(sa + pl * kDftBM * 128 + sw, F.yq + pl * yplane + off, ok);
       }
       const __half* wb = F.Wt + (long long)j0 * F.npad + k0;
-      for (int id = ptid; id < bn * 8; id += 224) {  // B: bn rows (output columns) x 8 chunks
+      for (int id = ptid; id < bn * 8; id += 224) {  // W: bn rows (output columns) x 8 chunks
         const int rr = id >> 3, c = id & 7;
         const __half* src = wb + (long long)rr * F.npad + 8 * c;
         const unsigned sw = rr * 128 + ((c ^ (rr & 7)) << 4);
-        cp_async16(sb_hi + sw, src, true);
-        cp_async16(sb_lo + sw, src + plane, true);
+#pragma unroll
+        for (int pl = 0; pl < kDftWPlanes; ++pl) cp_async16(sb0 + pl * bn * 128 + sw, src + pl * plane, true);
       }
       asm volatile("cp.async.commit_group;" ::: "memory");
       if (i >= 1) {  // two stages of copies in flight: publish the older one
@@ -679,30 +757,16 @@ __global__ void __launch_bounds__(kDftThreads, 1) k_band_dft(const __grid_consta
     const int q = warp & 3;
     const int m = m0 + 32 * q + lane;
     for (int bi = 0; bi < nblk; ++bi) {
-      const int acc = bi & 1;
-      if (!mbar_wait(smem_u32(&bar_accf[acc]), (unsigned)((bi >> 1) & 1))) {
+      const int acc = bi % nbuf;
+      if (!mbar_wait(smem_u32(&bar_accf[acc]), (unsigned)((bi / nbuf) & 1))) {
         s_fail = 1;
         break;
       }
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
       float* dst = F.kpart + ((long long)(blk0 + bi) * F.M + (m < F.M ? m : 0)) * F.ldk + j0;
-      // back to the units of y: the block's rows were scaled by 2^s(m, block) (exact)
+      // back to the units of y: the block's rows were scaled by 2^s(m, block), the twiddles by 2^9 (exact)
       const float f = m < F.M ? __ldg(F.yscale + (long long)(blk0 + bi) * F.M + m) : 0.f;
-      for (int c = 0; c < bn; c += 8) {
-        unsigned r[8];
-        const unsigned taddr = tmem + ((unsigned)(32 * q) << 16) + (unsigned)(acc * bn + c);
-        asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
-                     : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
-                     : "r"(taddr));
-        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-        if (m < F.M) {
-          float4* d4 = reinterpret_cast<float4*>(dst + c);
-          d4[0] = make_float4(__uint_as_float(r[0]) * f, __uint_as_float(r[1]) * f, __uint_as_float(r[2]) * f,
-                              __uint_as_float(r[3]) * f);
-          d4[1] = make_float4(__uint_as_float(r[4]) * f, __uint_as_float(r[5]) * f, __uint_as_float(r[6]) * f,
-                              __uint_as_float(r[7]) * f);
-        }
-      }
+      dft_drain(tmem, q, (unsigned)(acc * 2 * bn), bn, dst, f, m < F.M);
       asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
       mbar_arrive(smem_u32(&bar_acce[acc]));
     }
@@ -716,8 +780,8 @@ __global__ void __launch_bounds__(kDftThreads, 1) k_band_dft(const __grid_consta
 }
 
 // The same GEMM with the operands brought in by the tensor memory
-// accelerator: one thread of warp 1 issues, per K step, four box loads
-// (y head and tail: 64 samples x 128 rows; twiddle head and tail: 64
+// accelerator: one thread of warp 1 issues, per K step, six box loads
+// (the three y planes: 64 samples x 128 rows; the three twiddle planes: 64
 // samples x bn columns) that complete on the stage's mbarrier with their byte
 // count; rows past the frame arrive as zeros. Warp 0 issues the MMAs,
 // warps 2-5 drain the accumulators (warp w reads TMEM lanes 32 (w % 4) ..).
@@ -751,8 +815,9 @@ __global__ void __launch_bounds__(kDftTmaThreads, 1) k_band_dft_tma(const __grid
   __shared__ int s_issued, s_consumed;  // K steps whose loads were issued / waited for by the MMA thread
 
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int nbuf = dft_acc_buffers(bn);  // buffers of (ACC_A, ACC_B), 2 bn columns each
   unsigned tcols = 32;
-  while ((int)tcols < 2 * bn) tcols <<= 1;
+  while ((int)tcols < 2 * bn * nbuf) tcols <<= 1;
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_slot)),
                  "r"(tcols));
@@ -786,9 +851,10 @@ __global__ void __launch_bounds__(kDftTmaThreads, 1) k_band_dft_tma(const __grid
     if (lane == 0) {
       for (int i = 0; i < nk; ++i) {
         const int slot = i % stages;
-        const int bi = i / kDftKB, acc = bi & 1;
+        const int bi = i / kDftKB, acc = bi % nbuf;
         const bool first = (i % kDftKB) == 0;
-        if (first && bi >= 2 && !mbar_wait(smem_u32(&bar_acce[acc]), (unsigned)(((bi - 2) >> 1) & 1))) {
+        if (first && bi >= nbuf &&
+            !mbar_wait(smem_u32(&bar_acce[acc]), (unsigned)(((bi - nbuf) / nbuf) & 1))) {
           s_fail = 1;
           break;
         }
@@ -798,19 +864,9 @@ __global__ void __launch_bounds__(kDftTmaThreads, 1) k_band_dft_tma(const __grid
         }
         s_consumed = i + 1;
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        unsigned char* st = base + slot * stage_bytes;
-        const unsigned sa_hi = smem_u32(st), sa_lo = sa_hi + kDftBM * 128;
-        const unsigned sb_hi = sa_lo + kDftBM * 128, sb_lo = sb_hi + bn * 128;
-        const unsigned dacc = tmem + (unsigned)(acc * bn);
-#pragma unroll
-        for (int kk = 0; kk < kDftBK / 16; ++kk) {
-          const unsigned off = kk * 32;  // 16 FP16 values along K
-          const unsigned long long ah = umma_desc(sa_hi + off), al = umma_desc(sa_lo + off);
-          const unsigned long long bh = umma_desc(sb_hi + off), bl = umma_desc(sb_lo + off);
-          umma_f16(dacc, al, bh, idesc, (!first || kk > 0) ? 1u : 0u);
-          umma_f16(dacc, ah, bl, idesc, 1u);
-          umma_f16(dacc, ah, bh, idesc, 1u);
-        }
+        const unsigned sa = smem_u32(base + slot * stage_bytes);
+        const unsigned dA = tmem + (unsigned)(acc * 2 * bn);
+        dft_step_mmas(dA, dA + (unsigned)bn, sa, sa + kDftYPlanes * kDftBM * 128, bn, idesc, first);
         umma_commit(smem_u32(&bar_empty[slot]));
         if ((i % kDftKB) == kDftKB - 1 || i == nk - 1) umma_commit(smem_u32(&bar_accf[acc]));
       }
@@ -822,23 +878,22 @@ __global__ void __launch_bounds__(kDftTmaThreads, 1) k_band_dft_tma(const __grid
       const unsigned long long mb = reinterpret_cast<unsigned long long>(&b.mb[fi]);
       asm volatile("prefetch.tensormap [%0];" ::"l"(ma) : "memory");
       asm volatile("prefetch.tensormap [%0];" ::"l"(mb) : "memory");
-      const unsigned tx = (unsigned)(2 * kDftBM * 128 + 2 * bn * 128);
+      const unsigned tx = (unsigned)dft_stage_bytes(bn);
       for (int i = 0; i < nk; ++i) {
         const int slot = i % stages;
         if (i >= stages && !mbar_wait(smem_u32(&bar_empty[slot]), (unsigned)(((i - stages) / stages) & 1))) {
           s_fail = 1;
           break;
         }
-        unsigned char* st = base + slot * stage_bytes;
-        const unsigned sa_hi = smem_u32(st), sa_lo = sa_hi + kDftBM * 128;
-        const unsigned sb_hi = sa_lo + kDftBM * 128, sb_lo = sb_hi + bn * 128;
+        const unsigned sa = smem_u32(base + slot * stage_bytes);
+        const unsigned sb0 = sa + kDftYPlanes * kDftBM * 128;
         const unsigned bar = smem_u32(&bar_full[slot]);
         const int k0 = kbeg + i * kDftBK;
         mbar_arrive_expect_tx(bar, tx);
-        tma_load_3d(sa_hi, ma, k0, m0, 0, bar);
-        tma_load_3d(sa_lo, ma, k0, m0, 1, bar);
-        tma_load_3d(sb_hi, mb, k0, j0, 0, bar);
-        tma_load_3d(sb_lo, mb, k0, j0, 1, bar);
+#pragma unroll
+        for (int pl = 0; pl < kDftYPlanes; ++pl) tma_load_3d(sa + pl * kDftBM * 128, ma, k0, m0, pl, bar);
+#pragma unroll
+        for (int pl = 0; pl < kDftWPlanes; ++pl) tma_load_3d(sb0 + pl * bn * 128, mb, k0, j0, pl, bar);
         s_issued = i + 1;
       }
     }
@@ -846,30 +901,16 @@ __global__ void __launch_bounds__(kDftTmaThreads, 1) k_band_dft_tma(const __grid
     const int q = warp & 3;
     const int m = m0 + 32 * q + lane;
     for (int bi = 0; bi < nblk; ++bi) {
-      const int acc = bi & 1;
-      if (!mbar_wait(smem_u32(&bar_accf[acc]), (unsigned)((bi >> 1) & 1))) {
+      const int acc = bi % nbuf;
+      if (!mbar_wait(smem_u32(&bar_accf[acc]), (unsigned)((bi / nbuf) & 1))) {
         s_fail = 1;
         break;
       }
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
       float* dst = F.kpart + ((long long)(blk0 + bi) * F.M + (m < F.M ? m : 0)) * F.ldk + j0;
-      // back to the units of y: the block's rows were scaled by 2^s(m, block) (exact)
+      // back to the units of y: the block's rows were scaled by 2^s(m, block), the twiddles by 2^9 (exact)
       const float f = m < F.M ? __ldg(F.yscale + (long long)(blk0 + bi) * F.M + m) : 0.f;
-      for (int c = 0; c < bn; c += 8) {
-        unsigned r[8];
-        const unsigned taddr = tmem + ((unsigned)(32 * q) << 16) + (unsigned)(acc * bn + c);
-        asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
-                     : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
-                     : "r"(taddr));
-        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-        if (m < F.M) {
-          float4* d4 = reinterpret_cast<float4*>(dst + c);
-          d4[0] = make_float4(__uint_as_float(r[0]) * f, __uint_as_float(r[1]) * f, __uint_as_float(r[2]) * f,
-                              __uint_as_float(r[3]) * f);
-          d4[1] = make_float4(__uint_as_float(r[4]) * f, __uint_as_float(r[5]) * f, __uint_as_float(r[6]) * f,
-                              __uint_as_float(r[7]) * f);
-        }
-      }
+      dft_drain(tmem, q, (unsigned)(acc * 2 * bn), bn, dst, f, m < F.M);
       asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
       mbar_arrive(smem_u32(&bar_acce[acc]));
     }
@@ -949,12 +990,19 @@ __global__ void k_twiddles(__half* Wt, long long ldw, int npad, int N, int c0, i
     const long long t = ((long long)(c0 + j) * n) % N;
     double s, c;
     sincospi(2.0 * (double)t / (double)N, &s, &c);
-    // FP16 head and tail of the FP64 value (the tail is the rounded remainder)
-    const __half ch = __double2half(c), sh = __double2half(-s);
-    Wt[(long long)(2 * j) * npad + n] = ch;
-    Wt[plane + (long long)(2 * j) * npad + n] = __double2half(c - (double)__half2float(ch));
-    Wt[(long long)(2 * j + 1) * npad + n] = sh;
-    Wt[plane + (long long)(2 * j + 1) * npad + n] = __double2half(-s - (double)__half2float(sh));
+    // scaled by 2^kDftTBits: the integer T0 = rint(.) (exact in FP16, |T0| <= 512), the FP16
+    // head T1 of the remainder and the FP16 tail T2 of what is left
+    const double sc = (double)(1 << kDftTBits);
+    const double v[2] = {c * sc, -s * sc};
+#pragma unroll
+    for (int u = 0; u < 2; ++u) {
+      const double t0 = rint(v[u]);
+      const __half t1 = __double2half(v[u] - t0);
+      const long long row = (long long)(2 * j + u) * npad + n;
+      Wt[row] = __double2half(t0);
+      Wt[plane + row] = t1;
+      Wt[2 * plane + row] = __double2half(v[u] - t0 - (double)__half2float(t1));
+    }
   }
 }
 

@@ -34,24 +34,35 @@ constexpr int kSatTileW = 128;  // columns per chunk (32 lanes x 4)
 constexpr int kStatsStrip = 128;         // columns per column-statistics CTA
 constexpr int kStatsRowsPerChunk = 64;   // rows per column-statistics chunk (8 warps x 8)
 
-// Band DFT GEMM on tcgen05: 128 rows (TMEM lanes) x up to 256 real outputs
-// (TMEM columns) per CTA, K steps of 64 samples (one 128-byte swizzle row of
+// Band DFT GEMM on tcgen05: 128 rows (TMEM lanes) x up to kDftMaxBN real
+// outputs (TMEM columns) per CTA, K steps of 64 samples (one 128-byte swizzle row of
 // FP16 head or tail values).
 constexpr int kDftBM = 128;
-constexpr int kDftMaxBN = 256;
+constexpr int kDftMaxBN = 160;  // real outputs per CTA: two pipeline stages of operands fit shared memory
 constexpr int kDftBK = 64;
 constexpr int kDftMaxStages = 4;
 constexpr int kDftSmemCap = 220 * 1024;
-// K block: the tensor-memory accumulator is drained every kDftKB K steps
-// (256 samples) into a partial sum; partials are added with Kahan
-// compensation. The accumulator's own adds lose precision in proportion to
-// the run length (measured on 1024 x 4096 frames with TF32 operands: worst
-// map error 4e-5 of the element, floored at 1e-2 of the row peak, at 128
-// samples; 6e-5 at 256; 1.2e-4 without draining; 4.0e-5 at 256 with the FP16
-// operands). Each (row, K block) of y carries its own power-of-two scale
-// into the FP16 range (the y pass writes it, the drain divides it out).
+// Operand split of the band DFT. In each K block of 256 samples, y of row m
+// is scaled by 2^s(m, block) so that its largest magnitude lies in [64, 128)
+// and written as three FP16 planes: Y0 = rint(y 2^s) (an integer, |Y0| <= 128),
+// and the FP16 head Rh and tail Rt of the remainder y 2^s - Y0 (|.| <= 1/2).
+// The twiddles are scaled by 2^kDftTBits and written as three planes: the
+// integer T0 = rint(W 2^9) (|T0| <= 512), the FP16 head T1 of W 2^9 - T0 and
+// the FP16 tail T2 of what remains (about 31 bits together).
+// Six products per K step go into two accumulators in tensor memory:
+//   ACC_A = sum Y0 T0: integers, |.| <= 256 * 128 * 512 = 2^24 per block, so
+//           every partial sum is exactly representable in FP32 and the
+//           accumulation is exact however the tensor core rounds its adds;
+//   ACC_B = sum Y0 T1 + Y0 T2 + Rh T0 + Rh T1 + Rt T0: about 2^-8 of ACC_A's
+//           size, so the accumulator's own rounding (toward zero) costs 2^-8
+//           of what one FP32 accumulator of the whole product would.
+// The drain adds ACC_A + ACC_B once (round to nearest) and scales by
+// 2^-s 2^-9 (exact); blocks' partials are added with Kahan compensation.
 constexpr int kDftKB = 4;
 constexpr int kDftBlock = kDftBK * kDftKB;  // samples per K block
+constexpr int kDftYPlanes = 3;              // Y0, Rh, Rt
+constexpr int kDftWPlanes = 3;              // T0, T1, T2
+constexpr int kDftTBits = 9;                // twiddle scale 2^9: |T0| <= 512
 constexpr int kDftThreads = 384;  // warp 0 MMA, warps 1-7 producers, warps 8-11 drain
 // y pass: 8 rows (one per warp) x kYCols samples per CTA (two K blocks).
 constexpr int kYRows = 8;
@@ -65,12 +76,13 @@ struct PreFrameDev {
   int c0, C;  // stored bins c0 .. c0 + C - 1
   int h;      // mean filter half length
   float mbar, inv_M, inv_D;
-  const __half* Wt;  // twiddles, transposed and split: head [ldw][npad] then tail [ldw][npad];
-                     // row 2j = cos, 2j+1 = -sin of bin c0+j (FP16 head and tail); zero padded
+  double inv_D64;    // 1 / sum (m - mbar)^2 in FP64 (the slope's final division)
+  const __half* Wt;  // twiddles x 2^kDftTBits, transposed and split: planes T0, T1, T2, each [ldw][npad];
+                     // row 2j = cos, 2j+1 = -sin of bin c0+j; zero padded
   long long ldw;     // real output columns incl. padding = ntiles * bn
-  __half* yhi;       // [M][npad] (y minus its row mean) x 2^s(m, K block): FP16 head; zero for n >= N
-  __half* ylo;       // [M][npad] the FP16 tail
-  float* yscale;     // [nblocks][M] 2^-s(m, K block), by which the drain multiplies each partial
+  __half* yq;        // [kDftYPlanes][M][npad]: Y0, Rh, Rt of (y minus its row mean) x 2^s(m, K block)
+                     // (plane stride M * npad); zero for n >= N
+  float* yscale;     // [nblocks][M] 2^-s(m, K block) 2^-kDftTBits, by which the drain multiplies each partial
   float* rowmean;    // [M] the row means c_m removed from y
   float* rowsq;      // z-score normalisation: [ycols][M] per-block sums of (y - c_m)^2
   const float* xsrc; // trace-major input [N][ldsrc] transposed into x (nullptr: x is the input)
@@ -81,7 +93,7 @@ struct PreFrameDev {
   int npad;          // N rounded up to kDftBK
   int bn;            // real output columns per CTA (multiple of 16, <= kDftMaxBN)
   float2* stats;        // [N] (a_n, b_n) of the fast-time line fit
-  float2* partial;      // [n_chunks][N] partial sums (sum x, sum (m-mbar) x)
+  float4* partial;      // [n_chunks][N] partial sums (sum x, its error, sum (m-mbar) x, its error)
   float* rowpart;       // [n_strips][M] partial row sums sum_j w_j x[m, j]
   float2* strip_ab;     // [n_strips] (sum_j w_j a_j, sum_j w_j b_j) over the strip
   unsigned* strip_cnt;  // [n_strips] arrival counters (self-resetting)
@@ -107,8 +119,8 @@ struct PreBatch {
 };
 
 // Band DFT fed by the tensor memory accelerator: per frame, the tensor maps
-// of the y head/tail planes [2][M][npad] (box 32 x 128 x 1) and of the
-// twiddle head/tail planes [2][ldw][npad] (box 32 x bn x 1), both with the
+// of the y planes [3][M][npad] (box 64 x 128 x 1) and of the twiddle planes
+// [3][ldw][npad] (box 64 x bn x 1), both with the
 // 128-byte swizzle the MMA descriptors read. The maps are kernel parameters
 // (param space), so a launch needs no copy and is graph-capturable.
 struct DftFrameDev {
@@ -278,8 +290,11 @@ cudaError_t launch_band_dft(const PreBatch& b, int blocks, cudaStream_t s);
 cudaError_t launch_band_dft_tma(const DftBatch& b, int blocks, cudaStream_t s);
 cudaError_t launch_dft_reduce(const PreBatch& b, int blocks, cudaStream_t s);
 cudaError_t launch_twiddles(__half* Wt, long long ldw, int npad, int N, int c0, int C, cudaStream_t s);
-// bytes of one K step of the band DFT ring: A head and tail (128 rows), B head and tail (bn rows)
-__host__ __device__ inline int dft_stage_bytes(int bn) { return 2 * kDftBM * 128 + 2 * bn * 128; }
+// bytes of one K step of the band DFT ring: the y planes (128 rows), the twiddle planes (bn rows)
+__host__ __device__ inline int dft_stage_bytes(int bn) { return kDftYPlanes * kDftBM * 128 + kDftWPlanes * bn * 128; }
+// accumulator buffers of a band-DFT CTA (each holds ACC_A and ACC_B, bn columns apiece): two
+// when both fit the 512 tensor-memory columns, so a block's MMAs run while the previous drains
+__host__ __device__ inline int dft_acc_buffers(int bn) { return 4 * bn <= 512 ? 2 : 1; }
 
 cudaError_t launch_map_max(const void* map, int dtype, float in_scale, int rows, int cols, long long ld,
                            float* out_bits, cudaStream_t s);
@@ -354,4 +369,10 @@ size_t cfar_os_smem(int wr, int wc, int n_ref);
 cudaError_t launch_cfar_os(const CfarBatch& b, int max_n_ref, int blocks, size_t smem, cudaStream_t s);
 size_t cfar_direct_smem_bytes(int bh, int bw, int wr, int wc);
 
+}  // namespace rcfar
+
+namespace rcfar {
+static_assert(2 * (kDftYPlanes * kDftBM * 128 + kDftWPlanes * kDftMaxBN * 128) + 1024 <= kDftSmemCap,
+              "two operand stages of the widest band-DFT tile fit the shared memory cap");
+static_assert(2 * kDftMaxBN <= 512, "one accumulator buffer (ACC_A, ACC_B) fits tensor memory");
 }  // namespace rcfar

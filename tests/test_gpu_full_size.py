@@ -15,8 +15,9 @@
   through rcfar_run_batch under the fused and the tiled schedules, identical
   to the per-frame results.
 
-Tolerances as in test_gpu_parity: thresholds within 1e-4 relative of FP64,
-decisions exact outside the 1e-5 tie margin (counted).
+Tolerances as in test_gpu_parity: band map within 1e-4 relative of FP64
+(floored a million times below the map's largest value), thresholds within
+1e-4 relative, decisions exact outside the 1e-5 tie margin (counted).
 """
 import numpy as np
 import pytest
@@ -154,6 +155,9 @@ def test_chain_1024x4096_as_benchmarked(rc):
         rc.rcfar_sat_cfar(h, P, band.value_bound, win, band.k_lo - band.c0, band.k_hi - band.c0, det, thr,
                           map_cut=False)
         assert rc.rcfar_get_error(h) == rc.RCFAR_OK
+        e = np.abs(P.cpu().numpy().astype(np.float64) - P_o) / np.maximum(np.abs(P_o), 1e-6 * np.abs(P_o).max())
+        print(f"1024x4096 band map: max rel err {e.max():.2e}, cells above 1e-4: {int((e > REL).sum())}")
+        assert e.max() <= REL
         cmp = ocfar.compare_decisions(det.cpu().numpy(), res_o.det, P_o, res_o.thr, res_o.cut, margin=MARGIN)
         assert cmp.mismatches == 0, cmp
         t_g = thr.cpu().numpy().astype(np.float64)[res_o.cut]

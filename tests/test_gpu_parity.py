@@ -4,12 +4,9 @@ Tolerances (from the stated targets):
   * decisions: bit-exact, except CUTs with |CUT - T| / T < 1e-5 under the oracle,
     which are counted and reported (near ties);
   * thresholds: |gpu - oracle| <= 1e-4 |oracle| per CUT (observed ~1e-7);
-  * band map: |gpu - oracle| <= 1e-4 * max(|oracle|, 1e-2 * row peak) per element.
-    FP32 arithmetic on the raw frame (offsets and drifts of order 1 that the
-    detrend removes) leaves about u * max|x| absolute error per sample, which
-    a length-N transform spreads over every bin of the row: about 1e-6 of the
-    row's peak. Bins more than 40 dB below their row's peak are therefore held
-    to 1e-6 of that peak instead of 1e-4 of themselves;
+  * band map: |gpu - oracle| <= 1e-4 * max(|oracle|, 1e-6 * max|oracle| of the map)
+    per element: 1e-4 relative, floored for cells a million times below the
+    map's largest value;
   * table entries of integer-valued maps: exact.
 """
 import math
@@ -61,11 +58,8 @@ def rel_err(g, o):
 
 
 def map_err(g, o):
-    """Band-map error with the per-row floor (1e-2 x the row's peak)."""
-    o = np.asarray(o, dtype=np.float64)
-    g = np.asarray(g, dtype=np.float64)
-    floor = 1e-2 * np.max(np.abs(o), axis=1, keepdims=True)
-    return np.abs(g - o) / np.maximum(np.maximum(np.abs(o), floor), 1e-300)
+    """Band-map error: |g - o| / max(|o|, 1e-6 max|o|), per element."""
+    return rel_err(g, o)
 
 
 U32 = 2.0 ** -24
