@@ -613,96 +613,69 @@ __global__ void __launch_bounds__(256) k_sat_cfar_fused(const __grid_constant__ 
   if (tid == 0 && s_bad && B.status) atomicOr(B.status, kStatusRange);
 }
 
-// One CUT row of the streaming kernel: the lane's columns cl + 32 k
-// (k < ncg, c < cend). ra .. r0 are the shared-memory addresses of the ring
-// rows r - wr - 1, r + wr, r - gr - 1, r + gr, r, r - 1 at the region column
-// of map column cl. Cell averaging: S_ref from 8 lookups; greatest-of /
-// smallest-of: the two half sums from 16.
+// One CUT row of the streaming kernel: the lane's columns c = c0 + lane +
+// 32 k (k < ncg, c < cend). ra .. r0 point into the ring rows r - wr - 1,
+// r + wr, r - gr - 1, r + gr, r, r - 1 at the region column of map column
+// c0 + lane. Cell averaging: S_ref from 8 lookups (eq. 4 on the outer
+// rectangle minus eq. 4 on the guard rectangle); greatest-of / smallest-of:
+// the two half sums from 16. Box sums are taken modulo 2^64 (exact: every
+// region sum lies below 2^62).
 template <bool kMapCut, bool kHalves, int kCG>
-__device__ __forceinline__ void stream_cut_row(const CfarMapDev& P, int r, int cl, int ncg, int cend, unsigned ra,
-                                               unsigned rb, unsigned rc, unsigned rd, unsigned r1, unsigned r0,
-                                               bool greatest, float kthr, float inv_s, const float* map) {
-  const int wc = P.wc, gc = P.gc, clo = P.cut_lo, chi = P.cut_hi;
-  const bool row_cut = r >= P.row_lo && r <= P.row_hi;
-  unsigned char* drow = P.det + (long long)r * P.ld_det + cl;
-  float* trow = P.thr ? P.thr + (long long)r * P.ld_thr + cl : nullptr;
-  const unsigned owl = (unsigned)(-8 * (wc + 1)), owr = (unsigned)(8 * wc);
-  const unsigned ogl = (unsigned)(-8 * (gc + 1)), ogr = (unsigned)(8 * gc);
-  const unsigned a0 = ra + owl, a1 = ra + owr, b0 = rb + owl, b1 = rb + owr;
-  const unsigned e0 = rc + ogl, e1 = rc + ogr, f0 = rd + ogl, f1 = rd + ogr;
-  float cutv[kCG];
-  const float* mrow = map + (long long)r * P.ld_map + cl;
-  // every column of the lane is a CUT column (uniform over the warp): no per-column checks
-  const int cfirst = cl - (cl & 31);
-  if (row_cut && ncg == kCG && cend - cfirst == 32 * kCG && cfirst >= clo && cend - 1 <= chi) {
+__device__ __forceinline__ void stream_cut_row(const CfarMapDev& P, int ncg, bool all_cut, unsigned cut_mask,
+                                               unsigned col_mask, const u64* ra, const u64* rb, const u64* rc,
+                                               const u64* rd, const u64* r1, const u64* r0, bool greatest, float kthr,
+                                               float inv_s, unsigned char* drow, float* trow, const float* mrow) {
+  const int wc = P.wc, gc = P.gc;
+  // cut: the CUT's map value (kMapCut; only CUT columns are read, the others may lie past the map's edge)
+  auto one = [&](int k, float cut, unsigned char& d, float& th) {
+    const int o = 32 * k;
+    u64 st;
+    if constexpr (!kHalves) {
+      const u64 outer = (ra[o - wc - 1] + rb[o + wc]) - (ra[o + wc] + rb[o - wc - 1]);
+      const u64 guard = (rc[o - gc - 1] + rd[o + gc]) - (rc[o + gc] + rd[o - gc - 1]);
+      st = outer - guard;
+    } else {
+      // leading half: rows (r - wr - 1, r - 1] minus the guard rows (r - gr - 1, r - 1];
+      // lagging half: rows (r, r + wr] minus (r, r + gr]
+      const u64 lead = ((ra[o - wc - 1] + r0[o + wc]) - (ra[o + wc] + r0[o - wc - 1])) -
+                       ((rc[o - gc - 1] + r0[o + gc]) - (rc[o + gc] + r0[o - gc - 1]));
+      const u64 lag = ((r1[o - wc - 1] + rb[o + wc]) - (r1[o + wc] + rb[o - wc - 1])) -
+                      ((r1[o - gc - 1] + rd[o + gc]) - (r1[o + gc] + rd[o - gc - 1]));
+      st = ((long long)lead > (long long)lag) == greatest ? lead : lag;
+    }
+    const float ts = f32_from_q((long long)st) * kthr;  // T in fixed-point units
+    th = ts * inv_s;
+    if constexpr (kMapCut) {
+      d = cut > th ? 1 : 0;
+    } else {
+      const u64 qc = (r1[o] + r0[o - 1]) - (r0[o] + r1[o - 1]);
+      d = f32_from_q((long long)qc) > ts ? 1 : 0;
+    }
+  };
+  if (all_cut) {  // every column of the lane is a CUT (uniform over the warp)
+    float cutv[kCG];
     if constexpr (kMapCut) {
 #pragma unroll
       for (int k = 0; k < kCG; ++k) cutv[k] = __ldg(mrow + 32 * k);
     }
 #pragma unroll
     for (int k = 0; k < kCG; ++k) {
-      const unsigned o = 256u * k;
-      u64 st;
-      if constexpr (!kHalves) {
-        const u64 outer = (lds_u64(a0 + o) + lds_u64(b1 + o)) - (lds_u64(a1 + o) + lds_u64(b0 + o));
-        const u64 guard = (lds_u64(e0 + o) + lds_u64(f1 + o)) - (lds_u64(e1 + o) + lds_u64(f0 + o));
-        st = outer - guard;
-      } else {
-        const u64 lead = ((lds_u64(a0 + o) + lds_u64(r0 + owr + o)) - (lds_u64(a1 + o) + lds_u64(r0 + owl + o))) -
-                         ((lds_u64(e0 + o) + lds_u64(r0 + ogr + o)) - (lds_u64(e1 + o) + lds_u64(r0 + ogl + o)));
-        const u64 lag = ((lds_u64(r1 + owl + o) + lds_u64(b1 + o)) - (lds_u64(r1 + owr + o) + lds_u64(b0 + o))) -
-                        ((lds_u64(r1 + ogl + o) + lds_u64(f1 + o)) - (lds_u64(r1 + ogr + o) + lds_u64(f0 + o)));
-        st = ((long long)lead > (long long)lag) == greatest ? lead : lag;
-      }
-      const float ts = f32_from_q((long long)st) * kthr;
-      const float th = ts * inv_s;
       unsigned char d;
-      if constexpr (kMapCut) {
-        d = cutv[k] > th ? 1 : 0;
-      } else {
-        const u64 qc = (lds_u64(r1 + o) + lds_u64(r0 + o - 8u)) - (lds_u64(r0 + o) + lds_u64(r1 + o - 8u));
-        d = f32_from_q((long long)qc) > ts ? 1 : 0;
-      }
+      float th;
+      one(k, kMapCut ? cutv[k] : 0.f, d, th);
       drow[32 * k] = d;
       if (trow) trow[32 * k] = th;
     }
     return;
   }
-
 #pragma unroll 1
   for (int k = 0; k < ncg; ++k) {
-    const unsigned o = 256u * k;
-    const int c = cl + 32 * k;
-    if (c < cend) {
-      unsigned char d = 0;
-      float th = 0.f;
-      if (row_cut && c >= clo && c <= chi) {
-        u64 st;
-        if constexpr (!kHalves) {
-          const u64 outer = (lds_u64(a0 + o) + lds_u64(b1 + o)) - (lds_u64(a1 + o) + lds_u64(b0 + o));
-          const u64 guard = (lds_u64(e0 + o) + lds_u64(f1 + o)) - (lds_u64(e1 + o) + lds_u64(f0 + o));
-          st = outer - guard;
-        } else {
-          // leading half: rows (r - wr - 1, r - 1] minus the guard rows
-          // (r - gr - 1, r - 1]; lagging half: rows (r, r + wr] minus (r, r + gr]
-          const u64 lead = ((lds_u64(a0 + o) + lds_u64(r0 + owr + o)) - (lds_u64(a1 + o) + lds_u64(r0 + owl + o))) -
-                           ((lds_u64(e0 + o) + lds_u64(r0 + ogr + o)) - (lds_u64(e1 + o) + lds_u64(r0 + ogl + o)));
-          const u64 lag = ((lds_u64(r1 + owl + o) + lds_u64(b1 + o)) - (lds_u64(r1 + owr + o) + lds_u64(b0 + o))) -
-                          ((lds_u64(r1 + ogl + o) + lds_u64(f1 + o)) - (lds_u64(r1 + ogr + o) + lds_u64(f0 + o)));
-          st = ((long long)lead > (long long)lag) == greatest ? lead : lag;
-        }
-        const float ts = f32_from_q((long long)st) * kthr;
-        th = ts * inv_s;
-        if constexpr (kMapCut) {
-          d = __ldg(mrow + 32 * k) > th ? 1 : 0;
-        } else {
-          const u64 qc = (lds_u64(r1 + o) + lds_u64(r0 + o - 8u)) - (lds_u64(r0 + o) + lds_u64(r1 + o - 8u));
-          d = f32_from_q((long long)qc) > ts ? 1 : 0;
-        }
-      }
-      drow[32 * k] = d;
-      if (trow) trow[32 * k] = th;
-    }
+    if (!((col_mask >> k) & 1u)) continue;  // past the strip's last column
+    unsigned char d = 0;
+    float th = 0.f;
+    if ((cut_mask >> k) & 1u) one(k, kMapCut ? __ldg(mrow + 32 * k) : 0.f, d, th);
+    drow[32 * k] = d;
+    if (trow) trow[32 * k] = th;
   }
 }
 
@@ -715,7 +688,10 @@ __device__ __forceinline__ void stream_cut_row(const CfarMapDev& P, int r, int c
 // row g in slot g mod RB). Per stage, while cp.async brings the next
 // stage's map rows (16-byte copies when the map's rows are 16-byte aligned):
 //  (A) warp w quantises row w of the stage and prefixes it across the strip
-//      (kE contiguous columns per lane, one warp scan) into the ring;
+//      (kE contiguous columns per lane, one warp scan) into the ring; a row
+//      whose values all lie below 2^31 in fixed point is quantised with one
+//      32-bit conversion per value (the same round-to-nearest-even as the
+//      general path);
 //  (B) thread j adds each new row's prefix to column j + 1's running sum,
 //      which it keeps in a register for the whole run (eq. 3 as
 //      S(g, .) = S(g - 1, .) + H(g, .));
@@ -752,10 +728,9 @@ __global__ void __launch_bounds__(kStreamThreads, 2) k_sat_cfar_stream(const __g
   const bool vec = ((reinterpret_cast<uintptr_t>(map) & 15) == 0) && ((P.ld_map & 3) == 0);
   const int xoff = vec ? (cb & 3) : 0;
   const int x0 = cb - xoff;
-  const unsigned ring_a = smem_u32(smem_raw);
-  const unsigned span = (unsigned)(RB * pitch) * 8u;  // ring bytes
-  const unsigned raw_a = ring_a + span;               // 16-byte aligned (pitch even)
-  const unsigned pitch8 = (unsigned)pitch * 8u;
+  u64* ring = reinterpret_cast<u64*>(smem_raw);
+  float* raw = reinterpret_cast<float*>(smem_raw + (size_t)RB * pitch * 8);  // 16-byte aligned (pitch even)
+  const unsigned raw_a = smem_u32(raw);
   const int ro = R0 - wr - 1;       // table row of region row 0
   const int GT = R1 - R0 + 2 * wr;  // region rows 1 .. GT hold map rows
   const int nst = (GT + kStreamKS - 1) / kStreamKS;
@@ -763,12 +738,26 @@ __global__ void __launch_bounds__(kStreamThreads, 2) k_sat_cfar_stream(const __g
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const float scalef = ldexpf(1.0f, P.sat_scale);
   const float inv_s = ldexpf(1.0f, -P.sat_scale);
-  const float bound = P.bound;
+  // |x| below this (as bits) keeps |x 2^s| below 2^31: one 32-bit conversion suffices
+  const unsigned fast_bits = __float_as_uint(ldexpf(1.0f, 31 - P.sat_scale));
+  const unsigned bound_bits = __float_as_uint(P.bound);  // NaN bit patterns compare above it
   const float kthr = P.kthr;
   const int kind = P.kind;
   const int ncg = (cw + 31) >> 5;
   if (tid == 0) s_bad = 0;
-  for (int j = tid; j < pitch; j += kStreamThreads) sts_u64(ring_a + 8u * j, 0ull);  // region row 0 (slot 0)
+  for (int j = tid; j < pitch; j += kStreamThreads) ring[j] = 0ull;  // region row 0 (slot 0)
+
+  // the lane's CUT columns (fixed for the whole run): which are CUTs, and
+  // whether all of them are (then the row's loop has no per-column checks)
+  const int cl = c0 + lane;
+  unsigned cut_mask = 0, col_mask = 0;  // bit k: column cl + 32 k is a CUT / lies in the strip
+  for (int k = 0; k < ncg; ++k) {
+    const int c = cl + 32 * k;
+    if (c < c0 + cw) col_mask |= 1u << k;
+    if (c < c0 + cw && c >= P.cut_lo && c <= P.cut_hi) cut_mask |= 1u << k;
+  }
+  const bool cols_all = ncg == kCG && cw == 32 * kCG && c0 >= P.cut_lo && c0 + cw - 1 <= P.cut_hi;
+  const int jl = c0 - cb + 1 + lane;  // region column of the lane's first CUT column
 
   // stage t's map rows into raw buffer t & 1: warp w fetches row w
   auto fetch = [&](int t) {
@@ -798,13 +787,10 @@ __global__ void __launch_bounds__(kStreamThreads, 2) k_sat_cfar_stream(const __g
   };
 
   u64 colsum = 0;      // column tid + 1: sum of region rows 1 .. the last built
-  bool bad = false;
+  unsigned vmax = 0;   // largest |value| (bits) this thread quantised: range check at the end
   int next_cut = wr + 1;  // region row of the next CUT row (row R0)
   int slot0 = 1;          // ring slot of region row g0 (1 + t kStreamKS)
   int cut_slot = (wr + 1) % RB;
-  const unsigned ring_end = ring_a + span;
-  const int jl = c0 - cb + 1 + lane;  // region column of the lane's first CUT column
-  const unsigned lane_base = ring_a + (unsigned)jl * 8u;
   pdl_wait();  // the set-up above overlaps the previous kernel
   fetch(0);
   for (int t = 0; t < nst; ++t) {
@@ -819,15 +805,24 @@ __global__ void __launch_bounds__(kStreamThreads, 2) k_sat_cfar_stream(const __g
     if (warp < n) {
       int slot = slot0 + warp;
       if (slot >= RB) slot -= RB;
-      const unsigned ra = ring_a + (unsigned)(slot * pitch + 1 + kE * lane) * 8u;
-      const unsigned rr = raw_a + (unsigned)(((t & 1) * kStreamKS + warp) * ldr + xoff + kE * lane) * 4u;
+      u64* hrow = ring + slot * pitch + 1 + kE * lane;
+      const float* xr = raw + ((t & 1) * kStreamKS + warp) * ldr + xoff + kE * lane;
       const int lim = nin - kE * lane;  // this lane's columns inside the region
-      u64 v[kE];
+      float x[kE];
+      unsigned m = 0;
 #pragma unroll
       for (int e = 0; e < kE; ++e) {
-        const float x = e < lim ? lds_f32(rr + 4u * e) : 0.f;
-        bad |= !(fabsf(x) <= bound);
-        v[e] = (u64)q_from_f32(x, scalef);
+        x[e] = e < lim ? xr[e] : 0.f;
+        m = max(m, __float_as_uint(x[e]) & 0x7fffffffu);
+      }
+      vmax = max(vmax, m);
+      u64 v[kE];
+      if (__all_sync(0xffffffffu, m < fast_bits)) {
+#pragma unroll
+        for (int e = 0; e < kE; ++e) v[e] = (u64)(long long)__float2int_rn(x[e] * scalef);
+      } else {
+#pragma unroll
+        for (int e = 0; e < kE; ++e) v[e] = (u64)q_from_f32(x[e], scalef);
       }
 #pragma unroll
       for (int e = 1; e < kE; ++e) v[e] += v[e - 1];
@@ -839,19 +834,31 @@ __global__ void __launch_bounds__(kStreamThreads, 2) k_sat_cfar_stream(const __g
       }
       const u64 excl = incl - v[kE - 1];
 #pragma unroll
-      for (int e = 0; e < kE; ++e) sts_u64(ra + 8u * e, v[e] + excl);
-      if (lane == 0) sts_u64(ra - 8u, 0ull);  // region column 0
+      for (int e = 0; e < kE; ++e) hrow[e] = v[e] + excl;
+      if (lane == 0) hrow[-1] = 0ull;  // region column 0
     }
     __syncthreads();
     // (B) eq. 3 down the columns: S(g, .) = S(g - 1, .) + H(g, .); thread j
-    // keeps column j + 1's running sum in a register for the whole run
+    // keeps column j + 1's running sum in a register for the whole run. The
+    // stage's rows occupy slots slot0 .. slot0 + n - 1 (mod RB): every load
+    // is issued before the sums are formed.
     if (tid < nin) {
-      unsigned da = ring_a + (unsigned)(slot0 * pitch + 1 + tid) * 8u;
-      for (int i2 = 0; i2 < n; ++i2) {
-        colsum += lds_u64(da);
-        sts_u64(da, colsum);
-        da += pitch8;
-        if (da >= ring_end) da -= span;
+      u64* col = ring + 1 + tid;
+      u64 hv[kStreamKS];
+#pragma unroll
+      for (int i = 0; i < kStreamKS; ++i) {
+        int sl = slot0 + i;
+        if (sl >= RB) sl -= RB;
+        hv[i] = i < n ? col[sl * pitch] : 0ull;
+      }
+#pragma unroll
+      for (int i = 0; i < kStreamKS; ++i) {
+        if (i < n) {
+          int sl = slot0 + i;
+          if (sl >= RB) sl -= RB;
+          colsum += hv[i];
+          col[sl * pitch] = colsum;
+        }
       }
     }
     __syncthreads();
@@ -862,25 +869,27 @@ __global__ void __launch_bounds__(kStreamThreads, 2) k_sat_cfar_stream(const __g
       int sg = cut_slot + warp;
       if (sg >= RB) sg -= RB;
       // ring rows of region rows g + off at column jl (0 <= sg < RB, |off| <= wr + 1 < RB)
-      auto rp_below = [&](int off) {  // off < 0
+      auto row_at = [&](int off) {
         int x = sg + off;
         if (x < 0) x += RB;
-        return lane_base + (unsigned)x * pitch8;
-      };
-      auto rp_above = [&](int off) {  // off >= 0
-        int x = sg + off;
         if (x >= RB) x -= RB;
-        return lane_base + (unsigned)x * pitch8;
+        return ring + x * pitch + jl;
       };
-      const unsigned ra = rp_below(-wr - 1), rb = rp_above(wr), rc = rp_below(-gr - 1), rd = rp_above(gr);
-      const unsigned r1 = lane_base + (unsigned)sg * pitch8, r0 = rp_below(-1);
       const int r = ro + next_cut + warp;
+      const bool row_cut = r >= P.row_lo && r <= P.row_hi;
+      unsigned char* drow = P.det + (long long)r * P.ld_det + cl;
+      float* trow = P.thr ? P.thr + (long long)r * P.ld_thr + cl : nullptr;
+      const float* mrow = map + (long long)r * P.ld_map + cl;
+      const u64 *ra = row_at(-wr - 1), *rb = row_at(wr), *rc = row_at(-gr - 1), *rd = row_at(gr);
+      const u64 *r1 = row_at(0), *r0 = row_at(-1);
+      const unsigned mask = row_cut ? cut_mask : 0u;
+      const bool all = row_cut && cols_all;
       if (kind == RCFAR_CFAR_CA)
-        stream_cut_row<kMapCut, false, kCG>(P, r, c0 + lane, ncg, c0 + cw, ra, rb, rc, rd, r1, r0, false, kthr,
-                                            inv_s, map);
+        stream_cut_row<kMapCut, false, kCG>(P, ncg, all, mask, col_mask, ra, rb, rc, rd, r1, r0, false, kthr, inv_s,
+                                            drow, trow, mrow);
       else
-        stream_cut_row<kMapCut, true, kCG>(P, r, c0 + lane, ncg, c0 + cw, ra, rb, rc, rd, r1, r0,
-                                           kind == RCFAR_CFAR_GO, kthr, inv_s, map);
+        stream_cut_row<kMapCut, true, kCG>(P, ncg, all, mask, col_mask, ra, rb, rc, rd, r1, r0,
+                                           kind == RCFAR_CFAR_GO, kthr, inv_s, drow, trow, mrow);
     }
     if (cnt > 0) {
       next_cut += cnt;
@@ -890,7 +899,7 @@ __global__ void __launch_bounds__(kStreamThreads, 2) k_sat_cfar_stream(const __g
     slot0 += kStreamKS;
     if (slot0 >= RB) slot0 -= RB;
   }
-  if (bad) s_bad = 1;
+  if (vmax > bound_bits) s_bad = 1;
   __syncthreads();
   if (tid == 0 && s_bad && B.status) atomicOr(B.status, kStatusRange);
 }
