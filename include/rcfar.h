@@ -250,11 +250,14 @@ const char* rcfar_status_string(rcfar_status s);
  *   P[m,j]  = | sum_n y[m,n] exp(-2 pi i (c0+j) n / N) |   (or its square)
  * band_out (host pointer, may be NULL) receives the bins used. The first call
  * for a new (N, band) builds its twiddle table (one allocation).
- * Arithmetic: FP32, the transform on the tensor cores with y and the twiddles
- * each split into an FP16 head and tail (y scaled per row and 256-sample
- * block by a power of two into the FP16 range) and FP32 accumulation drained
- * every 256 samples; each map element is within 1e-4 of FP64 relative to
- * max(|element|, 1e-2 x its row's peak). Errors: INVALID_ARG for sizes or
+ * Arithmetic: FP32 (each row's mean level removed before the detrend and
+ * mean filter); the transform on the tensor cores with FP16 operands: per row
+ * and 256-sample block, y scaled by a power of two and split into an 8-bit
+ * integer and the FP16 head and tail of the remainder, the twiddles (x 2^9)
+ * into a 10-bit integer and the FP16 head and tail of the remainder; the
+ * integer x integer product accumulates exactly, the rest in a second FP32
+ * accumulator. Each map element is within 1e-4 of FP64 relative to
+ * max(|element|, 1e-6 x the map's largest element). Errors: INVALID_ARG for sizes or
  * parameters out of range (M, N <= 0, ldx or ld_map too small, even or too
  * long a mean filter), UNSUPPORTED beyond the handle's maxima, CUDA_ERROR on
  * a failed launch. */
@@ -483,6 +486,11 @@ rcfar_status rcfar_server_create(const rcfar_server_config* cfg, rcfar_server* o
  * pointer that is not memory of the server's device; BAD_STATE after destroy
  * has begun. */
 rcfar_status rcfar_server_submit(rcfar_server srv, const rcfar_request* req);
+/* Queues reqs[0..n) (a HOST array) in order, under one lock, as if submitted
+ * one by one at the same instant (a burst from a front-end). Stops at the
+ * first request that rcfar_server_submit would refuse and returns that
+ * status; *n_queued (may be NULL) receives how many were queued. */
+rcfar_status rcfar_server_submit_many(rcfar_server srv, const rcfar_request* reqs, int32_t n, int32_t* n_queued);
 /* Builds, on every slot, the twiddle tables of frames with these slow-time
  * lengths N[i] and windows w[i] (host arrays of n), so that the first frames
  * of each size do not wait for them. Optional. */

@@ -56,7 +56,7 @@ EXPORTS = (
     "rcfar_server_create", "rcfar_server_submit", "rcfar_server_prepare", "rcfar_server_poll", "rcfar_server_get_stats",
     "rcfar_server_now_ns", "rcfar_server_destroy", "rcfar_selftest_wait",
     "rcfar_tune_batch", "rcfar_set_batch_tuning", "rcfar_get_batch_tuning", "rcfar_sat_cfar",
-    "rcfar_threshold_factor",
+    "rcfar_threshold_factor", "rcfar_server_submit_many",
 )
 
 
@@ -177,6 +177,7 @@ def lib() -> ctypes.CDLL:
                                       I64, P, P],
             "rcfar_server_create": [ctypes.POINTER(rcfar_server_config), ctypes.POINTER(P)],
             "rcfar_server_submit": [P, ctypes.POINTER(rcfar_request)],
+            "rcfar_server_submit_many": [P, ctypes.POINTER(rcfar_request), I32, ctypes.POINTER(I32)],
             "rcfar_server_prepare": [P, ctypes.POINTER(I32), ctypes.POINTER(rcfar_window), I32],
             "rcfar_server_poll": [P, ctypes.POINTER(rcfar_completion), I32, ctypes.POINTER(I32), I32],
             "rcfar_server_get_stats": [P, ctypes.POINTER(rcfar_server_stats)],
@@ -502,13 +503,29 @@ def rcfar_server_submit(srv: int, x, window: rcfar_window, det, tag: int, arriva
     current CUDA device (the server's device: read and written in place; the work that wrote x must be
     complete), row-major; they must stay alive until the frame's completion has been polled.
     trace_major: x is [N][M] (the server's params must say so too)."""
+    req = server_request(x, window, det, tag, arrival_ns, trace_major)
+    _check(lib().rcfar_server_submit(srv, ctypes.byref(req)), "rcfar_server_submit")
+
+
+def server_request(x, window: rcfar_window, det, tag: int, arrival_ns: int = 0,
+                   trace_major: bool = False) -> rcfar_request:
+    """One request for rcfar_server_submit_many (same arguments and checks as rcfar_server_submit)."""
     M, N = _frame_dims(x, trace_major)
     device = bool(getattr(x, "is_cuda", False))
     _require(x, "x", _f32(), cuda=device)
     _require(det, "det", _u8(), M, cuda=device)
-    req = rcfar_request(_ptr(x), M, N, _ld(x), window, _ptr(det), _ld(det), int(tag), int(arrival_ns),
-                        RCFAR_MEM_DEVICE if device else RCFAR_MEM_HOST, 0)
-    _check(lib().rcfar_server_submit(srv, ctypes.byref(req)), "rcfar_server_submit")
+    return rcfar_request(_ptr(x), M, N, _ld(x), window, _ptr(det), _ld(det), int(tag), int(arrival_ns),
+                         RCFAR_MEM_DEVICE if device else RCFAR_MEM_HOST, 0)
+
+
+def rcfar_server_submit_many(srv: int, reqs: Sequence[rcfar_request]) -> int:
+    """Queues the requests in order under one lock; returns how many were queued (raises on a refusal,
+    after queueing the ones before it)."""
+    n = len(reqs)
+    arr = (rcfar_request * n)(*reqs)
+    done = ctypes.c_int32()
+    _check(lib().rcfar_server_submit_many(srv, arr, n, ctypes.byref(done)), "rcfar_server_submit_many")
+    return done.value
 
 
 def rcfar_server_prepare(srv: int, sizes: Sequence[int], windows: Sequence[rcfar_window]):

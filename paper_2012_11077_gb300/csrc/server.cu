@@ -310,7 +310,8 @@ rcfar_status rcfar_server_create(const rcfar_server_config* cfg, rcfar_server* o
   return RCFAR_OK;
 }
 
-rcfar_status rcfar_server_submit(rcfar_server srv, const rcfar_request* req) {
+// Checks one request and sizes what it takes from a slot (no lock held).
+static rcfar_status make_pending(rcfar_server srv, const rcfar_request* req, Pending* out) {
   if (!srv || !req) return RCFAR_ERR_INVALID_ARG;
   const rcfar_request& r = *req;
   const bool tm = srv->cfg.params.x_layout == RCFAR_X_TRACE_MAJOR;
@@ -353,15 +354,39 @@ rcfar_status rcfar_server_submit(rcfar_server srv, const rcfar_request* req) {
   q.det_b = device ? 0 : a256((size_t)r.M * q.C);
   const Slot& S0 = srv->slots[0];
   if (q.ws > S0.ws_cap || q.in_b > S0.in_cap || q.det_b > S0.det_cap) return RCFAR_ERR_UNSUPPORTED;
-  if (q.r.arrival_ns == 0) q.r.arrival_ns = clock_ns();
+  *out = q;
+  return RCFAR_OK;
+}
+
+rcfar_status rcfar_server_submit(rcfar_server srv, const rcfar_request* req) {
+  int32_t n = 0;
+  return rcfar_server_submit_many(srv, req, 1, &n);
+}
+
+rcfar_status rcfar_server_submit_many(rcfar_server srv, const rcfar_request* reqs, int32_t n, int32_t* n_queued) {
+  if (n_queued) *n_queued = 0;
+  if (!srv || n < 0 || (n > 0 && !reqs)) return RCFAR_ERR_INVALID_ARG;
+  std::vector<Pending> qs;
+  qs.reserve((size_t)n);
+  rcfar_status st = RCFAR_OK;
+  for (int32_t i = 0; i < n && st == RCFAR_OK; ++i) {
+    Pending q;
+    st = make_pending(srv, &reqs[i], &q);
+    if (st == RCFAR_OK) qs.push_back(q);
+  }
+  const int64_t now = clock_ns();
   {
     std::lock_guard<std::mutex> lk(srv->mu);
     if (srv->closing) return RCFAR_ERR_BAD_STATE;
-    srv->pending.push_back(q);
-    srv->stats.submitted += 1;
+    for (Pending& q : qs) {
+      if (q.r.arrival_ns == 0) q.r.arrival_ns = now;
+      srv->pending.push_back(q);
+    }
+    srv->stats.submitted += (int64_t)qs.size();
   }
-  srv->cv_sched.notify_one();
-  return RCFAR_OK;
+  if (n_queued) *n_queued = (int32_t)qs.size();
+  if (!qs.empty()) srv->cv_sched.notify_one();
+  return st;
 }
 
 rcfar_status rcfar_server_prepare(rcfar_server srv, const int32_t* N, const rcfar_window* w, int32_t n) {
