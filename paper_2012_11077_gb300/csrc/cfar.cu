@@ -843,22 +843,18 @@ __global__ void __launch_bounds__(kStreamThreads, 2) k_sat_cfar_stream(const __g
     // stage's rows occupy slots slot0 .. slot0 + n - 1 (mod RB): every load
     // is issued before the sums are formed.
     if (tid < nin) {
-      u64* col = ring + 1 + tid;
+      // the stage's rows are two straight runs of the ring: slots slot0 .. RB - 1,
+      // then (after the wrap) 0 ..; row i lies at (i < n1 ? p0 : p1) + i * pitch
+      u64* const p0 = ring + slot0 * pitch + 1 + tid;
+      u64* const p1 = p0 - RB * pitch;
+      const int n1 = RB - slot0;
       u64 hv[kStreamKS];
 #pragma unroll
-      for (int i = 0; i < kStreamKS; ++i) {
-        int sl = slot0 + i;
-        if (sl >= RB) sl -= RB;
-        hv[i] = i < n ? col[sl * pitch] : 0ull;
-      }
+      for (int i = 0; i < kStreamKS; ++i) hv[i] = i < n ? (i < n1 ? p0 : p1)[i * pitch] : 0ull;
 #pragma unroll
       for (int i = 0; i < kStreamKS; ++i) {
-        if (i < n) {
-          int sl = slot0 + i;
-          if (sl >= RB) sl -= RB;
-          colsum += hv[i];
-          col[sl * pitch] = colsum;
-        }
+        colsum += hv[i];
+        if (i < n) (i < n1 ? p0 : p1)[i * pitch] = colsum;
       }
     }
     __syncthreads();

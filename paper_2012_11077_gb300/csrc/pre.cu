@@ -587,26 +587,58 @@ __device__ __forceinline__ void dft_step_mmas(unsigned dA, unsigned dB, unsigned
 // Drain one accumulator buffer (ACC_A at TMEM column ca, ACC_B at ca + bn)
 // for the warp's 32 TMEM lanes (quarter q of the tile) into a block's
 // partials: dst[c] = (ACC_A + ACC_B) * f, one rounding (f = 2^-s 2^-9, exact).
+// Columns go 32 at a time (16 for a tail; bn is a multiple of 16): both
+// accumulators' loads are issued before one wait. Returns once every tensor-
+// memory load of the buffer has completed (the stores of the last chunk may
+// still be in flight), so the caller can release the buffer.
+__device__ __forceinline__ void tmem_ld32(unsigned ta, unsigned* r) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+      "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]),
+        "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
+        "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(ta));
+}
+__device__ __forceinline__ void tmem_ld16(unsigned ta, unsigned* r) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(ta));
+}
 __device__ __forceinline__ void dft_drain(unsigned tmem, int q, unsigned ca, int bn, float* dst, float f, bool ok) {
-  for (int c = 0; c < bn; c += 8) {
-    unsigned ra[8], rb[8];
-    const unsigned ta = tmem + ((unsigned)(32 * q) << 16) + ca + (unsigned)c;
-    asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
-                 : "=r"(ra[0]), "=r"(ra[1]), "=r"(ra[2]), "=r"(ra[3]), "=r"(ra[4]), "=r"(ra[5]), "=r"(ra[6]),
-                   "=r"(ra[7])
-                 : "r"(ta));
-    asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
-                 : "=r"(rb[0]), "=r"(rb[1]), "=r"(rb[2]), "=r"(rb[3]), "=r"(rb[4]), "=r"(rb[5]), "=r"(rb[6]),
-                   "=r"(rb[7])
-                 : "r"(ta + (unsigned)bn));
+  const unsigned ta = tmem + ((unsigned)(32 * q) << 16) + ca;
+  int c = 0;
+  for (; c + 32 <= bn; c += 32) {
+    unsigned ra[32], rb[32];
+    tmem_ld32(ta + (unsigned)c, ra);
+    tmem_ld32(ta + (unsigned)(bn + c), rb);
     asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
     if (ok) {
-      float v[8];
-#pragma unroll
-      for (int k = 0; k < 8; ++k) v[k] = (__uint_as_float(ra[k]) + __uint_as_float(rb[k])) * f;
       float4* d4 = reinterpret_cast<float4*>(dst + c);
-      d4[0] = make_float4(v[0], v[1], v[2], v[3]);
-      d4[1] = make_float4(v[4], v[5], v[6], v[7]);
+#pragma unroll
+      for (int k = 0; k < 8; ++k)
+        d4[k] = make_float4((__uint_as_float(ra[4 * k]) + __uint_as_float(rb[4 * k])) * f,
+                            (__uint_as_float(ra[4 * k + 1]) + __uint_as_float(rb[4 * k + 1])) * f,
+                            (__uint_as_float(ra[4 * k + 2]) + __uint_as_float(rb[4 * k + 2])) * f,
+                            (__uint_as_float(ra[4 * k + 3]) + __uint_as_float(rb[4 * k + 3])) * f);
+    }
+  }
+  if (c < bn) {  // a tail of 16 columns
+    unsigned ra[16], rb[16];
+    tmem_ld16(ta + (unsigned)c, ra);
+    tmem_ld16(ta + (unsigned)(bn + c), rb);
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+    if (ok) {
+      float4* d4 = reinterpret_cast<float4*>(dst + c);
+#pragma unroll
+      for (int k = 0; k < 4; ++k)
+        d4[k] = make_float4((__uint_as_float(ra[4 * k]) + __uint_as_float(rb[4 * k])) * f,
+                            (__uint_as_float(ra[4 * k + 1]) + __uint_as_float(rb[4 * k + 1])) * f,
+                            (__uint_as_float(ra[4 * k + 2]) + __uint_as_float(rb[4 * k + 2])) * f,
+                            (__uint_as_float(ra[4 * k + 3]) + __uint_as_float(rb[4 * k + 3])) * f);
     }
   }
 }
