@@ -65,6 +65,23 @@ bool make_planes_map(CUtensorMap* out, const __half* base, long long rows, int n
             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
+// Tensor map of a float32 matrix [rows][ld] (columns 0 .. cols - 1):
+// boxes of box_cols x box_rows, no swizzle, zeros outside the matrix.
+bool make_map2d(CUtensorMap* out, const void* base, long long rows, long long cols, long long ld, int box_cols,
+                int box_rows) {
+  EncodeTiledFn fn = encode_tiled();
+  if (!fn || (reinterpret_cast<uintptr_t>(base) & 15) || (ld % 4) || box_cols < 4 || box_cols > 256 || (box_cols % 4) ||
+      box_rows < 1 || box_rows > 256)
+    return false;
+  const cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
+  const cuuint64_t strides[1] = {(cuuint64_t)ld * sizeof(float)};
+  const cuuint32_t box[2] = {(cuuint32_t)box_cols, (cuuint32_t)box_rows};
+  const cuuint32_t elem[2] = {1, 1};
+  return fn(out, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<void*>(base), dims, strides, box, elem,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
 // Bump allocator over a device region.
 struct Carver {
   char* base;
@@ -1112,6 +1129,17 @@ rcfar_status rcfar_sat_cfar(rcfar_handle h, const void* map, int32_t dtype, int3
   // float32 maps: the streaming kernel; float16 maps (or windows whose ring
   // does not fit): one integral image per block
   StreamPlan sp;
+  // wide float32 maps with 16-byte aligned rows: the stages arrive by tensor-memory-accelerator boxes
+  if (dtype == RCFAR_MAP_F32 && cfar_stream_tma_plan(rows, cols, P.wr, P.wc, cap, h->sms, &sp)) {
+    static thread_local CfarTmaParams tp;
+    if (make_map2d(&tp.tm, map, rows, cols, ld_map, 32 * sp.e, kStreamKS)) {
+      tp.m = P;
+      tp.status = h->status;
+      const int blocks = cfar_stream_geometry(tp.m, rows, cols, sp);
+      TraceScope tr(h, "sat_cfar_fused_tma", s);
+      return cuda_fail(launch_cfar_stream_tma(tp, map_cut != 0, sp.e, blocks, sp.smem, s));
+    }
+  }
   if (dtype == RCFAR_MAP_F32 && cfar_stream_plan(rows, cols, P.wr, P.wc, cap, h->sms, 0, &sp)) {
     const int blocks = cfar_stream_geometry(P, rows, cols, sp);
     TraceScope tr(h, "sat_cfar_fused", s);

@@ -107,4 +107,16 @@ __device__ __forceinline__ void tma_load_3d(unsigned saddr, unsigned long long t
       : "memory");
 }
 
+// 2-D tiled tensor load global -> shared (box at coordinates {c0, c1},
+// innermost first), completing on the mbarrier with its byte count;
+// elements outside the tensor arrive as zeros. c0 times the element size
+// must be a multiple of 16 bytes.
+__device__ __forceinline__ void tma_load_2d(unsigned saddr, unsigned long long tmap, int c0, int c1, unsigned bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
+          saddr),
+      "l"(tmap), "r"(c0), "r"(c1), "r"(bar)
+      : "memory");
+}
+
 }  // namespace rcfar

@@ -900,6 +900,272 @@ __global__ void __launch_bounds__(kStreamThreads, 2) k_sat_cfar_stream(const __g
   if (tid == 0 && s_bad && B.status) atomicOr(B.status, kStatusRange);
 }
 
+// The streaming kernel fed by the tensor memory accelerator (float32 maps
+// whose rows start on 16-byte boundaries, strips of kStreamW CUT columns).
+// The decomposition is k_sat_cfar_stream's -- per stage of kStreamKS rows:
+// (A) warp w quantises and prefixes stage row w, kE contiguous columns per
+// lane and one warp scan; (B) thread j adds the new rows' prefixes to column
+// j + 1's running sum (eq. 3); (C) warp w takes one complete CUT row, 8 eq.
+// 4 lookups per CUT (16 for greatest-of / smallest-of) -- with these
+// differences:
+//  * one thread brings each stage's map rows as one 2-D box (kStreamKS rows
+//    x 32 kE columns from the strip's first halo column rounded down to a
+//    multiple of 4), one stage ahead, completing on an mbarrier; rows and
+//    columns outside the map arrive as zeros. Region column r >= 1 is map
+//    column x0 + r - 1;
+//  * ring rows are indexed so that region column r lives at index r + 1:
+//    index 1 is the zero column (written once), and every lane's kE
+//    columns start on a 16-byte boundary -- the prefix is stored with
+//    16-byte stores, which for kE = 6 (lane chunks 48 bytes apart) are free
+//    of bank conflicts;
+//  * every shared-memory access indexes a typed shared array, and each row
+//    offset is formed once per row.
+// Thresholds and decisions are bit-identical to k_sat_cfar_stream's and the
+// split path's (same quantisation, box sums exact modulo 2^64).
+template <bool kMapCut, int kE>
+__global__ void __launch_bounds__(kStreamThreads, 2) k_sat_cfar_stream_tma(const __grid_constant__ CfarTmaParams B) {
+  constexpr int KS = kStreamKS;
+  constexpr int RW = 32 * kE;  // floats per staged row (the box width)
+  constexpr int kCG = kStreamW / 32;
+  static_assert(kE % 2 == 0, "lanes read and write their columns in pairs");
+  pdl_trigger();
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  __shared__ __align__(8) unsigned long long bar_full[2];
+  __shared__ int s_bad, s_fail, s_issued, s_consumed;
+  const CfarMapDev& P = B.m;
+  const int local = (int)blockIdx.x;
+  const int ty = local / P.tiles_x, tx = local - ty * P.tiles_x;
+  const int rows = P.rows, cols = P.cols;
+  const int R0 = ty * P.run, R1 = min(rows, R0 + P.run);
+  const int wr = P.wr, wc = P.wc, gr = P.gr, gc = P.gc;
+  const int c0 = tx * P.bw;
+  const int cw = min(P.bw, cols - c0);
+  const int x0 = (c0 - wc) & ~3;      // map column of region column 1 (16-byte aligned)
+  const int xoff = c0 - wc - x0;      // 0 .. 3
+  const int nb = cw + 2 * wc + xoff;  // region columns the lookups read: 1 .. nb
+  const int pitch = P.hcp;            // u64 per ring row (32 kE + 2)
+  const int RB = P.ring_rows;         // >= KS + 2 wr + 1
+  u64* const ring = reinterpret_cast<u64*>(smem_raw);
+  // staged boxes: 2 x KS x RW floats after the ring, on a 128-byte boundary
+  float* const raw = reinterpret_cast<float*>(smem_raw + (((smem_u32(smem_raw) + (unsigned)RB * pitch * 8 + 127u) & ~127u) -
+                                                         smem_u32(smem_raw)));
+  const int ro = R0 - wr - 1;         // map row of region row 0
+  const int GT = R1 - R0 + 2 * wr;    // region rows 1 .. GT hold map rows
+  const int nst = (GT + KS - 1) / KS;
+  const int last_cut = R1 - 1 - ro;   // region row of CUT row R1 - 1
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const float scalef = ldexpf(1.0f, P.sat_scale);
+  const float inv_s = ldexpf(1.0f, -P.sat_scale);
+  const unsigned fast_bits = __float_as_uint(ldexpf(1.0f, 31 - P.sat_scale));
+  const unsigned bound_bits = __float_as_uint(P.bound);
+  const float kthr = P.kthr;
+  const int kind = P.kind;
+  const float* map = reinterpret_cast<const float*>(P.map);
+  const unsigned long long tmap = reinterpret_cast<unsigned long long>(&B.tm);
+  if (tid == 0) {
+    s_bad = 0;
+    s_fail = 0;
+    s_issued = 0;
+    s_consumed = 0;
+    mbar_init(smem_u32(&bar_full[0]), 1);
+    mbar_init(smem_u32(&bar_full[1]), 1);
+    mbar_init_fence();
+    asm volatile("prefetch.tensormap [%0];" ::"l"(tmap) : "memory");
+  }
+  for (int j = tid; j < pitch; j += kStreamThreads) ring[j] = 0ull;  // region row 0 (slot 0)
+  for (int r = 1 + tid; r < RB; r += kStreamThreads) ring[r * pitch + 1] = 0ull;  // region column 0
+  const int ncg = (cw + 31) >> 5;
+  const int cl = c0 + lane;
+  unsigned cut_mask = 0, col_mask = 0;  // bit k: column cl + 32 k is a CUT / lies in the strip
+  for (int k = 0; k < ncg; ++k) {
+    const int c = cl + 32 * k;
+    if (c < c0 + cw) col_mask |= 1u << k;
+    if (c < c0 + cw && c >= P.cut_lo && c <= P.cut_hi) cut_mask |= 1u << k;
+  }
+  const bool cols_all = cw == kStreamW && c0 >= P.cut_lo && c0 + cw - 1 <= P.cut_hi;
+  const int jl = c0 - x0 + 2 + lane;  // ring index of the lane's first CUT column
+  const unsigned tx_bytes = (unsigned)(KS * RW * 4);
+  __syncthreads();  // barriers initialised, ring zeroed
+
+  // stage t's box into raw buffer t & 1 (one thread)
+  auto issue = [&](int t) {
+    const unsigned bar = smem_u32(&bar_full[t & 1]);
+    mbar_arrive_expect_tx(bar, tx_bytes);
+    tma_load_2d(smem_u32(raw + (t & 1) * KS * RW), tmap, x0, ro + 1 + t * KS, bar);
+    s_issued = t + 1;
+  };
+
+  u64 colsum = 0;
+  unsigned vmax = 0;
+  int next_cut = wr + 1;
+  int slot0 = 1;
+  int cut_slot = (wr + 1) % RB;
+  pdl_wait();  // the map may be the previous kernel's output
+  if (tid == 0) issue(0);
+  for (int t = 0; t < nst; ++t) {
+    if (tid == 0 && t + 1 < nst && !s_fail) issue(t + 1);  // its buffer was last read by stage t - 1's (A)
+    const int g0 = 1 + t * KS;
+    const int n = min(KS, GT - g0 + 1);
+    // (A) stage row w: quantise, prefix across the strip, store the row's own prefix H(g, .)
+    if (warp < n) {
+      // after a failed wait no further boxes are issued, so later stages do not wait
+      if (*(volatile int*)&s_fail || !mbar_wait(smem_u32(&bar_full[t & 1]), (unsigned)((t >> 1) & 1)))
+        s_fail = 1;
+      else if (tid == 0)
+        s_consumed = t + 1;
+      int slot = slot0 + warp;
+      if (slot >= RB) slot -= RB;
+      const float2* xr = reinterpret_cast<const float2*>(raw + ((t & 1) * KS + warp) * RW + kE * lane);
+      float x[kE];
+      unsigned m = 0;
+#pragma unroll
+      for (int e = 0; e < kE / 2; ++e) {
+        const float2 v = xr[e];
+        x[2 * e] = v.x;
+        x[2 * e + 1] = v.y;
+        m = max(m, max(__float_as_uint(v.x) & 0x7fffffffu, __float_as_uint(v.y) & 0x7fffffffu));
+      }
+      vmax = max(vmax, m);
+      u64 v[kE];
+      if (__all_sync(0xffffffffu, m < fast_bits)) {
+#pragma unroll
+        for (int e = 0; e < kE; ++e) v[e] = (u64)(long long)__float2int_rn(x[e] * scalef);
+      } else {
+#pragma unroll
+        for (int e = 0; e < kE; ++e) v[e] = (u64)q_from_f32(x[e], scalef);
+      }
+#pragma unroll
+      for (int e = 1; e < kE; ++e) v[e] += v[e - 1];
+      u64 incl = v[kE - 1];
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const u64 y = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += y;
+      }
+      const u64 excl = incl - v[kE - 1];
+      ulonglong2* hrow = reinterpret_cast<ulonglong2*>(ring + slot * pitch + 2 + kE * lane);
+#pragma unroll
+      for (int e = 0; e < kE / 2; ++e) hrow[e] = make_ulonglong2(v[2 * e] + excl, v[2 * e + 1] + excl);
+    }
+    __syncthreads();
+    // (B) S(g, .) = S(g - 1, .) + H(g, .) for region column tid + 1 (ring index tid + 2);
+    // the stage's rows are slots slot0 .. RB - 1, then 0 .. after the wrap
+    if (tid < nb) {
+      const int a0 = slot0 * pitch + 2 + tid;
+      const int n1 = RB - slot0;
+      const int wrap = RB * pitch;
+      if (n == KS) {
+        u64 hv[KS];
+#pragma unroll
+        for (int i = 0; i < KS; ++i) hv[i] = ring[a0 + i * pitch - (i >= n1 ? wrap : 0)];
+#pragma unroll
+        for (int i = 0; i < KS; ++i) {
+          colsum += hv[i];
+          ring[a0 + i * pitch - (i >= n1 ? wrap : 0)] = colsum;
+        }
+      } else {
+        for (int i = 0; i < n; ++i) {
+          const int a = a0 + i * pitch - (i >= n1 ? wrap : 0);
+          colsum += ring[a];
+          ring[a] = colsum;
+        }
+      }
+    }
+    __syncthreads();
+    // (C) CUT rows whose windows are complete: region rows next_cut .. hi
+    const int hi = min(g0 + n - 1 - wr, last_cut);
+    const int cnt = hi - next_cut + 1;  // <= KS
+    if (warp < cnt) {
+      int sg = cut_slot + warp;
+      if (sg >= RB) sg -= RB;
+      auto rix = [&](int off) {  // ring index of region row (CUT row + off) at the lane's first CUT column
+        int x = sg + off;
+        if (x < 0) x += RB;
+        if (x >= RB) x -= RB;
+        return x * pitch + jl;
+      };
+      const int r = ro + next_cut + warp;
+      const bool row_cut = r >= P.row_lo && r <= P.row_hi;
+      unsigned char* drow = P.det + (long long)r * P.ld_det + cl;
+      float* trow = P.thr ? P.thr + (long long)r * P.ld_thr + cl : nullptr;
+      const float* mrow = map + (long long)r * P.ld_map + cl;
+      const int ra = rix(-wr - 1), rb = rix(wr), rc = rix(-gr - 1), rd = rix(gr);
+      const int r1 = rix(0), r0 = rix(-1);
+      const unsigned mask = row_cut ? cut_mask : 0u;
+      const bool all = row_cut && cols_all;
+      const bool halves = kind != RCFAR_CFAR_CA;
+      const bool greatest = kind == RCFAR_CFAR_GO;
+      // T and the decision of the lane's CUT k (o = 32 k columns along)
+      auto one = [&](int o, float cut, unsigned char& d, float& th) {
+        u64 st;
+        if (!halves) {
+          const u64 outer = (ring[ra - wc - 1 + o] + ring[rb + wc + o]) - (ring[ra + wc + o] + ring[rb - wc - 1 + o]);
+          const u64 guard = (ring[rc - gc - 1 + o] + ring[rd + gc + o]) - (ring[rc + gc + o] + ring[rd - gc - 1 + o]);
+          st = outer - guard;
+        } else {
+          // leading half: rows (r - wr - 1, r - 1] minus the guard rows (r - gr - 1, r - 1];
+          // lagging half: rows (r, r + wr] minus (r, r + gr]
+          const u64 lead = ((ring[ra - wc - 1 + o] + ring[r0 + wc + o]) - (ring[ra + wc + o] + ring[r0 - wc - 1 + o])) -
+                           ((ring[rc - gc - 1 + o] + ring[r0 + gc + o]) - (ring[rc + gc + o] + ring[r0 - gc - 1 + o]));
+          const u64 lag = ((ring[r1 - wc - 1 + o] + ring[rb + wc + o]) - (ring[r1 + wc + o] + ring[rb - wc - 1 + o])) -
+                          ((ring[r1 - gc - 1 + o] + ring[rd + gc + o]) - (ring[r1 + gc + o] + ring[rd - gc - 1 + o]));
+          st = ((long long)lead > (long long)lag) == greatest ? lead : lag;
+        }
+        const float ts = f32_from_q((long long)st) * kthr;  // T in fixed-point units
+        th = ts * inv_s;
+        if constexpr (kMapCut) {
+          d = cut > th ? 1 : 0;
+        } else {
+          const u64 qc = (ring[r1 + o] + ring[r0 - 1 + o]) - (ring[r0 + o] + ring[r1 - 1 + o]);
+          d = f32_from_q((long long)qc) > ts ? 1 : 0;
+        }
+      };
+      if (all) {
+        float cutv[kCG];
+        if constexpr (kMapCut) {
+#pragma unroll
+          for (int k = 0; k < kCG; ++k) cutv[k] = __ldg(mrow + 32 * k);
+        }
+#pragma unroll
+        for (int k = 0; k < kCG; ++k) {
+          unsigned char d;
+          float th;
+          one(32 * k, kMapCut ? cutv[k] : 0.f, d, th);
+          drow[32 * k] = d;
+          if (trow) trow[32 * k] = th;
+        }
+      } else {
+#pragma unroll 1
+        for (int k = 0; k < ncg; ++k) {
+          if (!((col_mask >> k) & 1u)) continue;  // past the strip's last column
+          unsigned char d = 0;
+          float th = 0.f;
+          if ((mask >> k) & 1u) one(32 * k, kMapCut ? __ldg(mrow + 32 * k) : 0.f, d, th);
+          drow[32 * k] = d;
+          if (trow) trow[32 * k] = th;
+        }
+      }
+    }
+    if (cnt > 0) {
+      next_cut += cnt;
+      cut_slot += cnt;
+      if (cut_slot >= RB) cut_slot -= RB;
+    }
+    slot0 += KS;
+    if (slot0 >= RB) slot0 -= RB;
+    __syncthreads();  // (C) has read the ring rows the next stage's (A) overwrites
+  }
+  if (vmax > bound_bits) s_bad = 1;
+  // after a failed wait, boxes issued but never waited for land before the shared memory is released
+  if (tid == 0)
+    for (int t = s_consumed; t < s_issued; ++t) mbar_wait(smem_u32(&bar_full[t & 1]), (unsigned)((t >> 1) & 1));
+  __syncthreads();
+  if (tid == 0 && B.status) {
+    if (s_bad) atomicOr(B.status, kStatusRange);
+    if (s_fail) atomicOr(B.status, kStatusTimeout);
+  }
+}
+
 // Ordered-statistic CFAR. A CTA holds the map tile of kOsRows x 32 CUTs plus
 // the window halo in shared memory, and the offsets of the n_ref training
 // cells (outer box minus guard box) relative to the CUT. Warp w takes CUT row
@@ -1318,6 +1584,57 @@ cudaError_t launch_cfar_stream(const CfarBatch& b, bool map_cut, int e, int bloc
   if (e == 5) return wide ? launch_stream_ce<8, 5>(b, map_cut, blocks, smem, s) : launch_stream_ce<4, 5>(b, map_cut, blocks, smem, s);
   if (e == 6) return wide ? launch_stream_ce<8, 6>(b, map_cut, blocks, smem, s) : launch_stream_ce<4, 6>(b, map_cut, blocks, smem, s);
   return wide ? launch_stream_ce<8, 8>(b, map_cut, blocks, smem, s) : launch_stream_ce<4, 8>(b, map_cut, blocks, smem, s);
+}
+
+bool cfar_stream_tma_plan(int rows, int cols, int wr, int wc, size_t smem_cap, int sm_share, StreamPlan* out) {
+  if (rows <= 0 || cols + 1 <= kFusedMaxCols) return false;
+  const int need = kStreamW + 2 * wc + 3;  // strip, halo and the alignment of its first column
+  const int e = need <= 32 * 6 ? 6 : need <= 32 * 8 ? 8 : 0;
+  if (e == 0) return false;
+  const int pitch = 32 * e + 2;
+  const int rb = kStreamKS + 2 * wr + 1;
+  const size_t smem = (size_t)rb * pitch * 8 + 128 + (size_t)2 * kStreamKS * 32 * e * 4;  // + alignment of the boxes
+  if (smem > smem_cap) return false;
+  const int per_sm = 2 * (smem + 1024 + 64) <= 228 * 1024 ? 2 : 1;
+  const long long slots = (long long)std::max(1, sm_share) * per_sm;
+  const long long strips = (cols + kStreamW - 1) / kStreamW;
+  int best_run = rows;
+  long long best = -1;
+  for (int run = 1; run <= rows + 7; run = run < 16 ? run + 1 : run + 8) {
+    const int rr = std::min(run, rows);
+    const long long ctas = strips * ((rows + rr - 1) / rr);
+    const long long waves = (ctas + slots - 1) / slots;
+    const long long stages = (rr + 2 * wr + kStreamKS - 1) / kStreamKS;
+    const long long cost = waves * stages;
+    if (best < 0 || cost < best || (cost == best && rr > best_run)) {
+      best = cost;
+      best_run = rr;
+    }
+    if (rr == rows) break;
+  }
+  out->run = best_run;
+  out->bw = kStreamW;
+  out->pitch = pitch;
+  out->ring_rows = rb;
+  out->e = e;
+  out->smem = smem;
+  out->ctas = (int)(strips * ((rows + best_run - 1) / best_run));
+  return true;
+}
+
+template <bool kMapCut, int kE>
+static cudaError_t launch_stream_tma_t(const CfarTmaParams& p, int blocks, size_t smem, cudaStream_t s) {
+  auto fn = k_sat_cfar_stream_tma<kMapCut, kE>;
+  cudaError_t e = ensure_smem(reinterpret_cast<const void*>(fn), smem);
+  if (e != cudaSuccess) return e;
+  return launch_pdl(fn, blocks, kStreamThreads, smem, s, p);
+}
+
+cudaError_t launch_cfar_stream_tma(const CfarTmaParams& p, bool map_cut, int e, int blocks, size_t smem,
+                                   cudaStream_t s) {
+  if (blocks <= 0) return cudaSuccess;
+  if (e == 6) return map_cut ? launch_stream_tma_t<true, 6>(p, blocks, smem, s) : launch_stream_tma_t<false, 6>(p, blocks, smem, s);
+  return map_cut ? launch_stream_tma_t<true, 8>(p, blocks, smem, s) : launch_stream_tma_t<false, 8>(p, blocks, smem, s);
 }
 
 int cfar_os_geometry(CfarMapDev& P, int rows, int cols) {

@@ -586,7 +586,9 @@ __device__ __forceinline__ void dft_step_mmas(unsigned dA, unsigned dB, unsigned
 
 // Drain one accumulator buffer (ACC_A at TMEM column ca, ACC_B at ca + bn)
 // for the warp's 32 TMEM lanes (quarter q of the tile) into a block's
-// partials: dst[c] = (ACC_A + ACC_B) * f, one rounding (f = 2^-s 2^-9, exact).
+// partials, which are column-major: dst[c * cs] = (ACC_A + ACC_B) * f for
+// output column c, one rounding (f = 2^-s 2^-9, exact). The lane is the row,
+// so each store of a column is 32 consecutive floats across the warp.
 // Columns go 32 at a time (16 for a tail; bn is a multiple of 16): both
 // accumulators' loads are issued before one wait. Returns once every tensor-
 // memory load of the buffer has completed (the stores of the last chunk may
@@ -608,7 +610,8 @@ __device__ __forceinline__ void tmem_ld16(unsigned ta, unsigned* r) {
         "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
       : "r"(ta));
 }
-__device__ __forceinline__ void dft_drain(unsigned tmem, int q, unsigned ca, int bn, float* dst, float f, bool ok) {
+__device__ __forceinline__ void dft_drain(unsigned tmem, int q, unsigned ca, int bn, float* dst, long long cs, float f,
+                                          bool ok) {
   const unsigned ta = tmem + ((unsigned)(32 * q) << 16) + ca;
   int c = 0;
   for (; c + 32 <= bn; c += 32) {
@@ -617,13 +620,9 @@ __device__ __forceinline__ void dft_drain(unsigned tmem, int q, unsigned ca, int
     tmem_ld32(ta + (unsigned)(bn + c), rb);
     asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
     if (ok) {
-      float4* d4 = reinterpret_cast<float4*>(dst + c);
+      float* d = dst + (long long)c * cs;
 #pragma unroll
-      for (int k = 0; k < 8; ++k)
-        d4[k] = make_float4((__uint_as_float(ra[4 * k]) + __uint_as_float(rb[4 * k])) * f,
-                            (__uint_as_float(ra[4 * k + 1]) + __uint_as_float(rb[4 * k + 1])) * f,
-                            (__uint_as_float(ra[4 * k + 2]) + __uint_as_float(rb[4 * k + 2])) * f,
-                            (__uint_as_float(ra[4 * k + 3]) + __uint_as_float(rb[4 * k + 3])) * f);
+      for (int k = 0; k < 32; ++k) d[k * cs] = (__uint_as_float(ra[k]) + __uint_as_float(rb[k])) * f;
     }
   }
   if (c < bn) {  // a tail of 16 columns
@@ -632,13 +631,9 @@ __device__ __forceinline__ void dft_drain(unsigned tmem, int q, unsigned ca, int
     tmem_ld16(ta + (unsigned)(bn + c), rb);
     asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
     if (ok) {
-      float4* d4 = reinterpret_cast<float4*>(dst + c);
+      float* d = dst + (long long)c * cs;
 #pragma unroll
-      for (int k = 0; k < 4; ++k)
-        d4[k] = make_float4((__uint_as_float(ra[4 * k]) + __uint_as_float(rb[4 * k])) * f,
-                            (__uint_as_float(ra[4 * k + 1]) + __uint_as_float(rb[4 * k + 1])) * f,
-                            (__uint_as_float(ra[4 * k + 2]) + __uint_as_float(rb[4 * k + 2])) * f,
-                            (__uint_as_float(ra[4 * k + 3]) + __uint_as_float(rb[4 * k + 3])) * f);
+      for (int k = 0; k < 16; ++k) d[k * cs] = (__uint_as_float(ra[k]) + __uint_as_float(rb[k])) * f;
     }
   }
 }
@@ -795,10 +790,10 @@ __global__ void __launch_bounds__(kDftThreads, 1) k_band_dft(const __grid_consta
         break;
       }
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-      float* dst = F.kpart + ((long long)(blk0 + bi) * F.M + (m < F.M ? m : 0)) * F.ldk + j0;
+      float* dst = F.kpart + ((long long)(blk0 + bi) * F.ldk + j0) * F.M + (m < F.M ? m : 0);
       // back to the units of y: the block's rows were scaled by 2^s(m, block), the twiddles by 2^9 (exact)
       const float f = m < F.M ? __ldg(F.yscale + (long long)(blk0 + bi) * F.M + m) : 0.f;
-      dft_drain(tmem, q, (unsigned)(acc * 2 * bn), bn, dst, f, m < F.M);
+      dft_drain(tmem, q, (unsigned)(acc * 2 * bn), bn, dst, F.M, f, m < F.M);
       asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
       mbar_arrive(smem_u32(&bar_acce[acc]));
     }
@@ -939,10 +934,10 @@ __global__ void __launch_bounds__(kDftTmaThreads, 1) k_band_dft_tma(const __grid
         break;
       }
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-      float* dst = F.kpart + ((long long)(blk0 + bi) * F.M + (m < F.M ? m : 0)) * F.ldk + j0;
+      float* dst = F.kpart + ((long long)(blk0 + bi) * F.ldk + j0) * F.M + (m < F.M ? m : 0);
       // back to the units of y: the block's rows were scaled by 2^s(m, block), the twiddles by 2^9 (exact)
       const float f = m < F.M ? __ldg(F.yscale + (long long)(blk0 + bi) * F.M + m) : 0.f;
-      dft_drain(tmem, q, (unsigned)(acc * 2 * bn), bn, dst, f, m < F.M);
+      dft_drain(tmem, q, (unsigned)(acc * 2 * bn), bn, dst, F.M, f, m < F.M);
       asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
       mbar_arrive(smem_u32(&bar_acce[acc]));
     }
@@ -964,18 +959,19 @@ __global__ void __launch_bounds__(kDftTmaThreads, 1) k_band_dft_tma(const __grid
 // (deterministic, and the same however the K range was split), magnitude,
 // bin 0's mean added back, and the normalisation by max |y| ("then
 // normalized": the DFT is linear, so this equals transforming y / max|y|).
-// Grid: per frame, ceil(M C / 256) CTAs; one thread per map cell.
+// Grid: per frame, ceil(M C / 256) CTAs; one thread per map cell, rows
+// fastest (the partials are column-major, so a warp's loads are contiguous).
 __global__ void __launch_bounds__(256) k_dft_reduce(const __grid_constant__ PreBatch b) {
   pdl_trigger();
   pdl_wait();
   const int fi = find_item(b.f, b.n, (int)blockIdx.x, &PreFrameDev::item_norm);
   const PreFrameDev& F = b.f[fi];
   const int local = (int)blockIdx.x - F.item_norm;
-  // cells in row-major order, 256 per CTA (a CTA may span several rows)
+  // cells in column-major order, 256 per CTA (a CTA may span several bins)
   const long long cell = (long long)local * 256 + threadIdx.x;
   if (cell >= (long long)F.M * F.C) return;
-  const int m = (int)(cell / F.C);
-  const int j = (int)(cell - (long long)m * F.C);
+  const int j = (int)(cell / F.M);
+  const int m = (int)(cell - (long long)j * F.M);
   float inv;
   if (F.normalise == RCFAR_NORM_ROW_ZSCORE) {
     // z-score: 1 / std of the row's y (population std; 0 for a constant row)
@@ -987,14 +983,15 @@ __global__ void __launch_bounds__(256) k_dft_reduce(const __grid_constant__ PreB
     const float mx = __uint_as_float(__ldcg(F.ymax));
     inv = mx > 0.f ? 1.f / mx : 1.f;
   }
+  // block b's partials: [ldk][M]; bin j's real part in column 2 j, its imaginary part in 2 j + 1
   const long long plane = (long long)F.M * F.ldk;
-  const float* src = F.kpart + (long long)m * F.ldk + 2 * j;
+  const float* src = F.kpart + (long long)(2 * j) * F.M + m;
   float re = 0.f, im = 0.f, cr = 0.f, ci = 0.f;
   for (int b0 = 0; b0 < F.nblocks; b0 += 8) {
     float2 v[8];  // the next 8 blocks' partials, loaded together
 #pragma unroll
     for (int u = 0; u < 8; ++u)
-      v[u] = (b0 + u < F.nblocks) ? __ldcg(reinterpret_cast<const float2*>(src + (b0 + u) * plane))
+      v[u] = (b0 + u < F.nblocks) ? make_float2(__ldcg(src + (b0 + u) * plane), __ldcg(src + (b0 + u) * plane + F.M))
                                   : make_float2(0.f, 0.f);
 #pragma unroll
     for (int u = 0; u < 8; ++u) {

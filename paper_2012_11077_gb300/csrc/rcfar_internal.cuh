@@ -100,7 +100,7 @@ struct PreFrameDev {
   unsigned* ymax;       // float bits of max |y| over the frame
   float* map;           // [M][ld_map] the normalised band map
   long long ld_map;
-  float* kpart;         // K-block partial sums [nblocks][M][ldk] (ldk = ldw)
+  float* kpart;         // K-block partial sums [nblocks][ldk][M], column-major (ldk = ldw)
   int nblocks;          // npad / kDftBlock, rounded up
   long long ldk;
   unsigned* tile_cnt;   // [mtiles * ntiles] arrival counters (self-resetting)
@@ -124,7 +124,7 @@ struct PreBatch {
 // 128-byte swizzle the MMA descriptors read. The maps are kernel parameters
 // (param space), so a launch needs no copy and is graph-capturable.
 struct DftFrameDev {
-  float* kpart;         // K-block partials [nblocks][M][ldk]
+  float* kpart;         // K-block partials [nblocks][ldk][M], column-major
   const float* yscale;  // [nblocks][M] 2^-s(m, block): the drain writes partials in the units of y
   long long ldk;
   int M, bn, mtiles, ntiles, kper, npad, item_dft, pad;
@@ -359,6 +359,20 @@ bool cfar_stream_plan(int rows, int cols, int wr, int wc, size_t smem_cap, int s
                       StreamPlan* out);
 int cfar_stream_geometry(CfarMapDev& P, int rows, int cols, const StreamPlan& sp);
 cudaError_t launch_cfar_stream(const CfarBatch& b, bool map_cut, int e, int blocks, size_t smem, cudaStream_t s);
+
+// The streaming kernel fed by the tensor memory accelerator, for one float32
+// map wider than one strip whose rows start on 16-byte boundaries: each
+// stage's map rows arrive as one 2-D box (kStreamKS rows x 32 e columns).
+// The plan fails (use the kernel above) when the strip plus halo exceeds
+// 32 e columns for e = 8 or the ring does not fit smem_cap.
+struct CfarTmaParams {
+  CUtensorMap tm;  // the map: float32 [rows][ld], box 32 e x kStreamKS, zero fill outside
+  CfarMapDev m;
+  int* status;
+};
+bool cfar_stream_tma_plan(int rows, int cols, int wr, int wc, size_t smem_cap, int sm_share, StreamPlan* out);
+cudaError_t launch_cfar_stream_tma(const CfarTmaParams& p, bool map_cut, int e, int blocks, size_t smem,
+                                   cudaStream_t s);
 
 // Ordered-statistic CFAR on float32 maps: CTAs of kOsRows x 32 CUTs, one warp
 // per CUT row; each CUT's k-th smallest training cell is selected exactly.
