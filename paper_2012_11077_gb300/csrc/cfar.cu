@@ -1000,6 +1000,14 @@ __global__ void __launch_bounds__(kStreamThreads, 2) k_sat_cfar_stream_tma(const
   int next_cut = wr + 1;
   int slot0 = 1;
   int cut_slot = (wr + 1) % RB;
+  // (C) state carried from stage to stage: the warp's last CUT row, the ring
+  // indices of its rows r - wr - 1, r + wr, r - gr - 1, r + gr, r, r - 1 at
+  // the lane's first CUT column, and its output / map row pointers
+  int pr = -(1 << 30);
+  int ba = 0, bb = 0, bc = 0, bd = 0, b1 = 0, b0 = 0;
+  unsigned char* drow = nullptr;
+  float* trow = nullptr;
+  const float* mrow = nullptr;
   pdl_wait();  // the map may be the previous kernel's output
   if (tid == 0) issue(0);
   for (int t = 0; t < nst; ++t) {
@@ -1023,7 +1031,7 @@ __global__ void __launch_bounds__(kStreamThreads, 2) k_sat_cfar_stream_tma(const
         const float2 v = xr[e];
         x[2 * e] = v.x;
         x[2 * e + 1] = v.y;
-        m = max(m, max(__float_as_uint(v.x) & 0x7fffffffu, __float_as_uint(v.y) & 0x7fffffffu));
+        m = __vimax3_u32(m, __float_as_uint(v.x) & 0x7fffffffu, __float_as_uint(v.y) & 0x7fffffffu);
       }
       vmax = max(vmax, m);
       u64 v[kE];
@@ -1055,13 +1063,17 @@ __global__ void __launch_bounds__(kStreamThreads, 2) k_sat_cfar_stream_tma(const
       const int n1 = RB - slot0;
       const int wrap = RB * pitch;
       if (n == KS) {
-        u64 hv[KS];
+        // two batches of KS / 2 rows: each batch's loads are issued before its sums
 #pragma unroll
-        for (int i = 0; i < KS; ++i) hv[i] = ring[a0 + i * pitch - (i >= n1 ? wrap : 0)];
+        for (int i0 = 0; i0 < KS; i0 += KS / 2) {
+          u64 hv[KS / 2];
 #pragma unroll
-        for (int i = 0; i < KS; ++i) {
-          colsum += hv[i];
-          ring[a0 + i * pitch - (i >= n1 ? wrap : 0)] = colsum;
+          for (int i = 0; i < KS / 2; ++i) hv[i] = ring[a0 + (i0 + i) * pitch - (i0 + i >= n1 ? wrap : 0)];
+#pragma unroll
+          for (int i = 0; i < KS / 2; ++i) {
+            colsum += hv[i];
+            ring[a0 + (i0 + i) * pitch - (i0 + i >= n1 ? wrap : 0)] = colsum;
+          }
         }
       } else {
         for (int i = 0; i < n; ++i) {
@@ -1076,39 +1088,60 @@ __global__ void __launch_bounds__(kStreamThreads, 2) k_sat_cfar_stream_tma(const
     const int hi = min(g0 + n - 1 - wr, last_cut);
     const int cnt = hi - next_cut + 1;  // <= KS
     if (warp < cnt) {
-      int sg = cut_slot + warp;
-      if (sg >= RB) sg -= RB;
-      auto rix = [&](int off) {  // ring index of region row (CUT row + off) at the lane's first CUT column
-        int x = sg + off;
-        if (x < 0) x += RB;
-        if (x >= RB) x -= RB;
-        return x * pitch + jl;
-      };
       const int r = ro + next_cut + warp;
+      if (r == pr + KS) {  // the row KS below the last one: every row offset moves KS ring rows on
+        const int step = KS * pitch, size = RB * pitch;
+        ba += step; ba -= ba >= size ? size : 0;
+        bb += step; bb -= bb >= size ? size : 0;
+        bc += step; bc -= bc >= size ? size : 0;
+        bd += step; bd -= bd >= size ? size : 0;
+        b1 += step; b1 -= b1 >= size ? size : 0;
+        b0 += step; b0 -= b0 >= size ? size : 0;
+        drow += (long long)KS * P.ld_det;
+        mrow += (long long)KS * P.ld_map;
+        if (trow) trow += (long long)KS * P.ld_thr;
+      } else {
+        int sg = cut_slot + warp;
+        if (sg >= RB) sg -= RB;
+        auto rix = [&](int off) {  // ring index of region row (CUT row + off) at the lane's first CUT column
+          int x = sg + off;
+          if (x < 0) x += RB;
+          if (x >= RB) x -= RB;
+          return x * pitch + jl;
+        };
+        ba = rix(-wr - 1);
+        bb = rix(wr);
+        bc = rix(-gr - 1);
+        bd = rix(gr);
+        b1 = rix(0);
+        b0 = rix(-1);
+        drow = P.det + (long long)r * P.ld_det + cl;
+        trow = P.thr ? P.thr + (long long)r * P.ld_thr + cl : nullptr;
+        mrow = map + (long long)r * P.ld_map + cl;
+      }
+      pr = r;
       const bool row_cut = r >= P.row_lo && r <= P.row_hi;
-      unsigned char* drow = P.det + (long long)r * P.ld_det + cl;
-      float* trow = P.thr ? P.thr + (long long)r * P.ld_thr + cl : nullptr;
-      const float* mrow = map + (long long)r * P.ld_map + cl;
-      const int ra = rix(-wr - 1), rb = rix(wr), rc = rix(-gr - 1), rd = rix(gr);
-      const int r1 = rix(0), r0 = rix(-1);
       const unsigned mask = row_cut ? cut_mask : 0u;
       const bool all = row_cut && cols_all;
       const bool halves = kind != RCFAR_CFAR_CA;
       const bool greatest = kind == RCFAR_CFAR_GO;
+      // the eight corners of eq. 4 (outer and guard rectangles) relative to the lane's CUT column
+      const int al = ba - wc - 1, ar = ba + wc, bl = bb - wc - 1, br = bb + wc;
+      const int cL = bc - gc - 1, cR = bc + gc, dL = bd - gc - 1, dR = bd + gc;
       // T and the decision of the lane's CUT k (o = 32 k columns along)
       auto one = [&](int o, float cut, unsigned char& d, float& th) {
         u64 st;
         if (!halves) {
-          const u64 outer = (ring[ra - wc - 1 + o] + ring[rb + wc + o]) - (ring[ra + wc + o] + ring[rb - wc - 1 + o]);
-          const u64 guard = (ring[rc - gc - 1 + o] + ring[rd + gc + o]) - (ring[rc + gc + o] + ring[rd - gc - 1 + o]);
+          const u64 outer = (ring[al + o] + ring[br + o]) - (ring[ar + o] + ring[bl + o]);
+          const u64 guard = (ring[cL + o] + ring[dR + o]) - (ring[cR + o] + ring[dL + o]);
           st = outer - guard;
         } else {
           // leading half: rows (r - wr - 1, r - 1] minus the guard rows (r - gr - 1, r - 1];
           // lagging half: rows (r, r + wr] minus (r, r + gr]
-          const u64 lead = ((ring[ra - wc - 1 + o] + ring[r0 + wc + o]) - (ring[ra + wc + o] + ring[r0 - wc - 1 + o])) -
-                           ((ring[rc - gc - 1 + o] + ring[r0 + gc + o]) - (ring[rc + gc + o] + ring[r0 - gc - 1 + o]));
-          const u64 lag = ((ring[r1 - wc - 1 + o] + ring[rb + wc + o]) - (ring[r1 + wc + o] + ring[rb - wc - 1 + o])) -
-                          ((ring[r1 - gc - 1 + o] + ring[rd + gc + o]) - (ring[r1 + gc + o] + ring[rd - gc - 1 + o]));
+          const u64 lead = ((ring[al + o] + ring[b0 + wc + o]) - (ring[ar + o] + ring[b0 - wc - 1 + o])) -
+                           ((ring[cL + o] + ring[b0 + gc + o]) - (ring[cR + o] + ring[b0 - gc - 1 + o]));
+          const u64 lag = ((ring[b1 - wc - 1 + o] + ring[br + o]) - (ring[b1 + wc + o] + ring[bl + o])) -
+                          ((ring[b1 - gc - 1 + o] + ring[dR + o]) - (ring[b1 + gc + o] + ring[dL + o]));
           st = ((long long)lead > (long long)lag) == greatest ? lead : lag;
         }
         const float ts = f32_from_q((long long)st) * kthr;  // T in fixed-point units
@@ -1116,7 +1149,7 @@ __global__ void __launch_bounds__(kStreamThreads, 2) k_sat_cfar_stream_tma(const
         if constexpr (kMapCut) {
           d = cut > th ? 1 : 0;
         } else {
-          const u64 qc = (ring[r1 + o] + ring[r0 - 1 + o]) - (ring[r0 + o] + ring[r1 - 1 + o]);
+          const u64 qc = (ring[b1 + o] + ring[b0 - 1 + o]) - (ring[b0 + o] + ring[b1 - 1 + o]);
           d = f32_from_q((long long)qc) > ts ? 1 : 0;
         }
       };

@@ -929,14 +929,15 @@ __global__ void __launch_bounds__(kDftTmaThreads, 1) k_band_dft_tma(const __grid
     const int m = m0 + 32 * q + lane;
     for (int bi = 0; bi < nblk; ++bi) {
       const int acc = bi % nbuf;
+      // back to the units of y: the block's rows were scaled by 2^s(m, block), the twiddles by 2^9
+      // (exact); loaded before the wait so that its latency overlaps the block's MMAs
+      const float f = m < F.M ? __ldg(F.yscale + (long long)(blk0 + bi) * F.M + m) : 0.f;
       if (!mbar_wait(smem_u32(&bar_accf[acc]), (unsigned)((bi / nbuf) & 1))) {
         s_fail = 1;
         break;
       }
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
       float* dst = F.kpart + ((long long)(blk0 + bi) * F.ldk + j0) * F.M + (m < F.M ? m : 0);
-      // back to the units of y: the block's rows were scaled by 2^s(m, block), the twiddles by 2^9 (exact)
-      const float f = m < F.M ? __ldg(F.yscale + (long long)(blk0 + bi) * F.M + m) : 0.f;
       dft_drain(tmem, q, (unsigned)(acc * 2 * bn), bn, dst, F.M, f, m < F.M);
       asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
       mbar_arrive(smem_u32(&bar_acce[acc]));
