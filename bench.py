@@ -41,7 +41,7 @@ METRIC = "SAT+CA-CFAR Gcells/s and full-chain frames/s at 1 GB300; % HBM rooflin
 # (bench.py --profile chain); the I64 table kernels and k_cfar_ring on a 4096x4096 map (bench.py
 # --profile map), times 4 for the 8192x8192 map; k_sat_cfar_stream_tma on a 6144x6144 map (bench.py
 # --profile fused --map-size 6144), times (8192/6144)^2 (their traffic grows with the cells).
-TRAFFIC = {"band_dft": 32.43e6, "sat_i64_8192": 4 * 222.6e6, "cfar_ring_8192": 4 * 221.4e6,
+TRAFFIC = {"band_dft": 32.43e6, "sat_i64_8192": 4 * 222.3e6, "cfar_ring_8192": 4 * 220.2e6,
            "sat_cfar_stream_8192": 319.1e6}
 RING = 16
 MIN_TIMED_MS = 250.0  # device time the headline is timed over, whatever K is
