@@ -303,8 +303,12 @@ rcfar_status rcfar_cfar(rcfar_handle h, const rcfar_sat_view* view, const void* 
  * bit-identical to rcfar_sat(TILE_I64 or I64) followed by rcfar_cfar with the
  * same CUT source: the map's values when map_cut != 0, else the table's 1 x 1
  * region sums. map: [rows][ld_map] of dtype (F16 values times 2^map_exp2).
- * UNSUPPORTED when the window's halo does not fit shared memory. A value
- * above value_bound (or NaN) is reported by rcfar_get_error as RANGE. */
+ * Float32 maps wider than one strip whose rows start on 16-byte boundaries
+ * (map 16-byte aligned, ld_map a multiple of 4) have each stage's rows
+ * brought by the tensor memory accelerator, which is faster; the results are
+ * the same either way. UNSUPPORTED when the window's halo does not fit shared
+ * memory. A value above value_bound (or NaN) is reported by rcfar_get_error
+ * as RANGE. */
 rcfar_status rcfar_sat_cfar(rcfar_handle h, const void* map, int32_t dtype, int32_t map_exp2, int32_t rows,
                             int32_t cols, int64_t ld_map, float value_bound, const rcfar_window* w, int32_t cut_c_lo,
                             int32_t cut_c_hi, int32_t map_cut, uint8_t* det, int64_t ld_det, float* thr,
