@@ -994,7 +994,7 @@ def ours(args, rank, world, local, dist):
                  "roofline": {"kernel": "sat_cfar_stream", "bound": "hbm", "achieved": fach,
                               "peak": peaks["hbm_gbs"], "unit": "GB/s", "frac": fach / peaks["hbm_gbs"],
                               "traffic": TRAFFIC.get("sat_cfar_stream_8192"),
-                              "note": "issue-bound on 64-bit integer arithmetic, not on DRAM"}}
+                              "note": "bound on the SM side (shared-memory wavefronts and 64-bit integer issue), not on DRAM"}}
         best = fused if fms <= mms else split
         sat_cfar = {"value": best["value"], "unit": "Gcells/s", "ms": best["ms"],
                     "path": "fused" if best is fused else "split",
