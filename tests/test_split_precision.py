@@ -57,7 +57,7 @@ def magnitude(out, c, k, N):
     return np.hypot(out[:, :C] + N * c * (k == 0), out[:, C:])
 
 
-def survey_err(g, o, omax):
+def floored_rel_err(g, o, omax):
     return np.abs(g - o) / np.maximum(np.abs(o), 1e-6 * omax)
 
 
@@ -114,7 +114,7 @@ def head_tail_dft(yd, W):
 def test_exact_head_split_holds_the_band_bins_and_the_old_split_does_not():
     yd, c, W, k, N, P_o, omax = frame_rows()
     # FP64 transform of the same y: the split's error alone
-    new = survey_err(magnitude(exact_split_dft(yd, W), c, k, N), P_o, omax)
-    old = survey_err(magnitude(head_tail_dft(yd, W), c, k, N), P_o, omax)
+    new = floored_rel_err(magnitude(exact_split_dft(yd, W), c, k, N), P_o, omax)
+    old = floored_rel_err(magnitude(head_tail_dft(yd, W), c, k, N), P_o, omax)
     assert new.max() < 1e-5, new.max()
     assert old.max() > 1e-4, old.max()
