@@ -1351,7 +1351,9 @@ rcfar_status rcfar_run_batch(rcfar_handle h, const rcfar_frame_desc* frames, int
       for (int k = 0; k < cnt && sat_mode == RCFAR_SAT_FUSED; ++k) {
         const rcfar_frame_desc& f = frames[base + k];
         if (f.window.kind == RCFAR_CFAR_OS) continue;
-        const int share = (int)std::max<long long>(1, (long long)h->sms * f.M / std::max<long long>(1, rows_all));
+        // the frame's share of the SMs by rows, rounded to nearest (the shares add up to about all SMs)
+        const long long ra = std::max<long long>(1, rows_all);
+        const int share = (int)std::max<long long>(1, ((long long)h->sms * f.M + ra / 2) / ra);
         if (!cfar_stream_plan(f.M, bands[base + k].cols, f.window.guard_r + f.window.train_r,
                               f.window.guard_c + f.window.train_c, cap, share, stream_e, &splans[k]))
           sat_mode = RCFAR_SAT_TILE_I64;
